@@ -1,0 +1,278 @@
+"""Smoothed-aggregation AMG with MIS-2 aggregation and an l1-Jacobi V-cycle (oracle; test infrastructure).
+
+The paper's preconditioner (Sec. 5.2) is a symmetric V-cycle (eq. (Vcycle))
+over Galerkin coarse matrices M_{l+1} = P_l^T M_l P_l built by decoupled
+smoothed aggregation (DSVMB, Vanek-Mandel-Brezina) from the diffusion-only
+matrix, with an l1-Jacobi smoother.  The paper names these pieces without
+formulas; the oracle fixes them as follows (each reading is listed in the
+design notes):
+
+  strength     j != i is strong for i iff a_ij^2 >= theta^2 |a_ii a_jj|,
+               symmetrised (strong if either direction is), theta = 0.08.
+  priority     key(i) = (top 30 bits of splitmix64(seed ^ i)) << 32 | i;
+               splitmix64 is the published SplitMix64 finaliser (Steele, Lea
+               and Flood 2014).  Larger key wins; keys are distinct.
+  MIS-2        synchronous rounds over tuples (state, key) with state
+               OUT=0 < UNDECIDED=1 < IN=2: m = max over the closed 2-hop
+               neighbourhood (two 1-hop max passes of the previous round's
+               tuples); an undecided node whose m is its own tuple turns IN,
+               an undecided node whose m belongs to an IN node turns OUT.
+  aggregates   roots = IN nodes numbered by increasing index; pass 1: a
+               non-root with a strong root neighbour joins the one with the
+               largest key; pass 2: a remaining node joins the aggregate of
+               the pass-1 neighbour whose root has the largest key.
+  prolongator  P = (I - omega D^-1 A) P_tent, P_tent[i, agg(i)] = 1,
+               omega = 4 / (3 rho), rho = max_i sum_j |a_ij| / |a_ii|;
+               structural pattern, no dropping.
+  coarse       A_c = R (A P) with R = P^T, structural pattern.  Coarsening
+               stops when a level has fewer than coarse_max unknowns, the
+               size ratio exceeds 0.8, or max_levels is reached; the last
+               level is solved by dense Cholesky.
+  smoother     l1-Jacobi x <- x + D_l1^-1 (b - A x), D_l1,ii = sum_j |a_ij|.
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+STATE_OUT, STATE_UNDECIDED, STATE_IN = 0, 1, 2
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_LOW32 = np.uint64(0xFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 output function applied to counter values x (uint64, wraps mod 2^64)."""
+    z = np.asarray(x, dtype=np.uint64) + _GOLDEN
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def priority_keys(n, seed):
+    """Distinct 62-bit keys: (top 30 bits of splitmix64(seed ^ i)) << 32 | i."""
+    idx = np.arange(n, dtype=np.uint64)
+    pi = splitmix64(np.uint64(seed) ^ idx)
+    return ((pi >> np.uint64(34)) << np.uint64(32)) | idx
+
+
+def _pattern(rows, cols, n):
+    m = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    m.sum_duplicates()
+    m.sort_indices()
+    m.data[:] = 1.0
+    return m
+
+
+def strength(A, theta):
+    """Symmetrised strength pattern (no diagonal) of a square CSR matrix."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    cols = A.indices
+    d = A.diagonal()
+    strong = (cols != rows) & (A.data * A.data >= theta * theta * np.abs(d[rows] * d[cols]))
+    r, c = rows[strong], cols[strong]
+    return _pattern(np.concatenate([r, c]), np.concatenate([c, r]), n)
+
+
+def _closed(S):
+    n = S.shape[0]
+    return _pattern(np.concatenate([np.repeat(np.arange(n), np.diff(S.indptr)), np.arange(n)]),
+                    np.concatenate([S.indices, np.arange(n)]), n)
+
+
+def _max_closed(Sc, v):
+    """m[i] = max of v over the closed neighbourhood of i (every row holds i itself)."""
+    return np.maximum.reduceat(v[Sc.indices], Sc.indptr[:-1])
+
+
+def mis2(S, keys):
+    """Distance-2 maximal independent set by synchronous rounds; returns (state, rounds)."""
+    Sc = _closed(S)
+    n = S.shape[0]
+    state = np.full(n, STATE_UNDECIDED, dtype=np.uint64)
+    rounds = 0
+    while np.any(state == STATE_UNDECIDED):
+        t = (state << np.uint64(62)) | keys
+        m = _max_closed(Sc, _max_closed(Sc, t))
+        und = state == STATE_UNDECIDED
+        new_in = und & (m == t)
+        new_out = und & ((m >> np.uint64(62)) == STATE_IN)
+        state[new_in] = STATE_IN
+        state[new_out] = STATE_OUT
+        rounds += 1
+    return state, rounds
+
+
+def aggregate(S, state, keys):
+    """Aggregate index per node (int64) and number of aggregates."""
+    Sc = _closed(S)
+    n = S.shape[0]
+    roots = state == STATE_IN
+    agg_id = np.cumsum(roots) - 1
+    agg = np.full(n, -1, dtype=np.int64)
+    agg[roots] = agg_id[roots]
+    # pass 1: strong root neighbour with the largest key
+    rootval = np.where(roots, keys + np.uint64(1), np.uint64(0))
+    best = _max_closed(Sc, rootval)
+    pass1 = (~roots) & (best > 0)
+    agg[pass1] = agg_id[((best[pass1] - np.uint64(1)) & _LOW32).astype(np.int64)]
+    # pass 2: neighbour assigned in pass 1 whose root has the largest key
+    root_of_agg = np.flatnonzero(roots)
+    val2 = np.zeros(n, dtype=np.uint64)
+    val2[pass1] = keys[root_of_agg[agg[pass1]]] + np.uint64(1)
+    rest = agg < 0
+    best2 = _max_closed(Sc, val2)
+    take = rest & (best2 > 0)
+    agg[take] = agg_id[((best2[take] - np.uint64(1)) & _LOW32).astype(np.int64)]
+    if np.any(agg < 0):
+        raise RuntimeError("aggregation left nodes unassigned")
+    return agg, int(roots.sum())
+
+
+def spgemm(A, B):
+    """C = A B with the structural pattern of the product (entries that cancel to 0 are kept).
+
+    scipy's product drops entries whose sum is exactly zero, so the pattern is
+    taken from the product of the all-ones pattern matrices and the values
+    from the numeric product.
+    """
+    A = sp.csr_matrix(A)
+    B = sp.csr_matrix(B)
+    onesA = sp.csr_matrix((np.ones_like(A.data), A.indices, A.indptr), shape=A.shape)
+    onesB = sp.csr_matrix((np.ones_like(B.data), B.indices, B.indptr), shape=B.shape)
+    pat = (onesA @ onesB).tocsr()
+    pat.sort_indices()
+    num = (A @ B).tocsr()
+    num.sort_indices()
+    ncol = np.int64(pat.shape[1])
+    kp = np.repeat(np.arange(pat.shape[0], dtype=np.int64), np.diff(pat.indptr)) * ncol + pat.indices
+    kn = np.repeat(np.arange(num.shape[0], dtype=np.int64), np.diff(num.indptr)) * ncol + num.indices
+    vals = np.zeros(len(kp))
+    vals[np.searchsorted(kp, kn)] = num.data
+    return sp.csr_matrix((vals, pat.indices.copy(), pat.indptr.copy()), shape=pat.shape)
+
+
+def transpose(P):
+    R = sp.csr_matrix(P.T)
+    R.sort_indices()
+    return R
+
+
+def tentative_prolongator(agg, nc):
+    n = len(agg)
+    return sp.csr_matrix((np.ones(n), agg.astype(np.int64), np.arange(n + 1)), shape=(n, nc))
+
+
+def smoothed_prolongator(A, Pt):
+    """P = (I - omega D^-1 A) P_tent with omega = 4/(3 ||D^-1 A||_inf)."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    d = A.diagonal()
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    rho = np.max(np.bincount(rows, weights=np.abs(A.data), minlength=n) / np.abs(d))
+    omega = 4.0 / (3.0 * rho)
+    vals = -omega * A.data / d[rows]
+    vals = vals + (A.indices == rows)
+    Smat = sp.csr_matrix((vals, A.indices.copy(), A.indptr.copy()), shape=A.shape)
+    return spgemm(Smat, Pt), omega
+
+
+def l1_diagonal(A):
+    A = sp.csr_matrix(A)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    return np.bincount(rows, weights=np.abs(A.data), minlength=A.shape[0])
+
+
+class Level:
+    def __init__(self, A):
+        self.A = sp.csr_matrix(A)
+        self.dl1 = l1_diagonal(self.A)
+        self.P = None
+        self.R = None
+        self.agg = None
+        self.S = None
+        self.mis_rounds = 0
+
+
+class Hierarchy:
+    def __init__(self, levels, chol):
+        self.levels = levels
+        self.chol = chol  # lower Cholesky factor of the coarsest matrix
+
+    @property
+    def sizes(self):
+        return [lv.A.shape[0] for lv in self.levels]
+
+    def operator_complexity(self):
+        return sum(lv.A.nnz for lv in self.levels) / self.levels[0].A.nnz
+
+
+def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8):
+    """Build the hierarchy from a symmetric positive definite CSR matrix."""
+    levels = [Level(A)]
+    while True:
+        lv = levels[-1]
+        n = lv.A.shape[0]
+        if n < coarse_max or len(levels) >= max_levels:
+            break
+        S = strength(lv.A, theta)
+        keys = priority_keys(n, seed)
+        state, rounds = mis2(S, keys)
+        agg, nc = aggregate(S, state, keys)
+        if nc > max_ratio * n:
+            break
+        P, _ = smoothed_prolongator(lv.A, tentative_prolongator(agg, nc))
+        R = transpose(P)
+        Ac = spgemm(R, spgemm(lv.A, P))
+        lv.S, lv.agg, lv.P, lv.R, lv.mis_rounds = S, agg, P, R, rounds
+        levels.append(Level(Ac))
+    Ac = levels[-1].A.toarray()
+    chol = np.linalg.cholesky(Ac)
+    return Hierarchy(levels, chol)
+
+
+def update_fine(h, A):
+    """Replace the finest matrix (and its l1 diagonal); P, R and coarse levels stay frozen.
+
+    This is the paper's reuse scheme (Sec. 6, experimental setup): the
+    hierarchy is built once and later Jacobians only update the smoother.
+    """
+    lv = h.levels[0]
+    lv.A = sp.csr_matrix(A)
+    lv.dl1 = l1_diagonal(lv.A)
+    if len(h.levels) == 1:
+        h.chol = np.linalg.cholesky(lv.A.toarray())
+
+
+def refresh(h, A):
+    """Keep aggregates, P and R; recompute every coarse matrix A_{l+1} = R_l A_l P_l from the new A.
+
+    The integer part of the setup (strength, MIS-2, aggregates) and all
+    sparsity patterns are reused; only values change.
+    """
+    h.levels[0].A = sp.csr_matrix(A)
+    h.levels[0].dl1 = l1_diagonal(h.levels[0].A)
+    for l in range(len(h.levels) - 1):
+        lv = h.levels[l]
+        Ac = spgemm(lv.R, spgemm(lv.A, lv.P))
+        h.levels[l + 1].A = Ac
+        h.levels[l + 1].dl1 = l1_diagonal(Ac)
+    h.chol = np.linalg.cholesky(h.levels[-1].A.toarray())
+
+
+def vcycle(h, b, nu1=1, nu2=1, level=0):
+    """One symmetric V-cycle x = B b, zero initial guess (eq. (Vcycle))."""
+    lv = h.levels[level]
+    if level == len(h.levels) - 1:
+        return sla.cho_solve((h.chol, True), b)
+    x = np.zeros_like(b)
+    for _ in range(nu1):
+        x = x + (b - lv.A @ x) / lv.dl1
+    r = b - lv.A @ x
+    xc = vcycle(h, lv.R @ r, nu1, nu2, level + 1)
+    x = x + lv.P @ xc
+    for _ in range(nu2):
+        x = x + (b - lv.A @ x) / lv.dl1
+    return x

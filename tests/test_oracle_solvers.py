@@ -1,0 +1,292 @@
+"""Pins of the oracle's AMG, Krylov and Newton pieces against brute force, textbook identities and invariants."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import amg, krylov, newton
+from oracle import constitutive as cst
+from oracle import discretization as disc
+from paper_2112_05051_gb300 import synth
+
+SOIL = synth.Soil()
+
+
+# ---------------------------------------------------------------- priority generator
+
+def test_splitmix64_published_vectors():
+    # SplitMix64 started from state 0 (Steele, Lea, Flood 2014; Vigna's reference
+    # generator): the first outputs are the finaliser at 1x and 2x the golden gamma.
+    g = 0x9E3779B97F4A7C15
+    assert int(amg.splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+    assert int(amg.splitmix64(np.uint64(g))) == 0x6E789E6AA1B965F4
+    k = amg.priority_keys(1000, 5)
+    assert len(np.unique(k)) == 1000
+    assert np.all((k & np.uint64(0xFFFFFFFF)) == np.arange(1000, dtype=np.uint64))
+
+
+# ---------------------------------------------------------------- MIS-2 and aggregation
+
+def _random_graph(n, p, seed):
+    rng = np.random.default_rng(seed)
+    m = np.triu(rng.random((n, n)) < p, 1)
+    m = m | m.T
+    return sp.csr_matrix(m.astype(float))
+
+
+def _greedy_mis2(S, keys):
+    """Sequential greedy distance-2 independent set in decreasing key order (brute force)."""
+    n = S.shape[0]
+    A = (S.toarray() != 0)
+    A2 = A | (A.astype(int) @ A.astype(int) > 0)
+    np.fill_diagonal(A2, False)
+    chosen = np.zeros(n, bool)
+    blocked = np.zeros(n, bool)
+    for i in sorted(range(n), key=lambda v: int(keys[v]), reverse=True):
+        if not blocked[i]:
+            chosen[i] = True
+            blocked |= A2[i]
+            blocked[i] = True
+    return chosen
+
+
+def _grid_graph(nx, ny, nz):
+    grid = synth.Grid(nx, ny, nz)
+    st = np.zeros((grid.n, 7))
+    st[:, 0] = 6.0
+    st[:, 1:] = -1.0
+    A = disc._stencil_to_csr(grid, st)
+    return amg.strength(A, 0.08)
+
+
+@pytest.mark.parametrize("case", ["rand40", "rand120", "rand200", "grid"])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_mis2_equals_sequential_greedy(case, seed):
+    if case == "grid":
+        S = _grid_graph(6, 5, 4)
+    else:
+        n = int(case[4:])
+        S = _random_graph(n, 4.0 / n, seed)
+    keys = amg.priority_keys(S.shape[0], seed)
+    state, rounds = amg.mis2(S, keys)
+    np.testing.assert_array_equal(state == amg.STATE_IN, _greedy_mis2(S, keys))
+    assert np.all(state != amg.STATE_UNDECIDED)
+
+
+def _bfs_dist(A, src):
+    n = A.shape[0]
+    dist = np.full(n, -1)
+    dist[src] = 0
+    frontier = [src]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for v in A.indices[A.indptr[u]:A.indptr[u + 1]]:
+                if dist[v] < 0:
+                    dist[v] = dist[u] + 1
+                    nxt.append(v)
+        frontier = nxt
+    return dist
+
+
+@pytest.mark.parametrize("case", ["rand150", "grid"])
+def test_aggregates_are_partition_with_radius_two(case):
+    S = _grid_graph(7, 6, 5) if case == "grid" else _random_graph(150, 0.03, 9)
+    keys = amg.priority_keys(S.shape[0], 4)
+    state, _ = amg.mis2(S, keys)
+    agg, nc = amg.aggregate(S, state, keys)
+    roots = np.flatnonzero(state == amg.STATE_IN)
+    assert nc == len(roots)
+    assert set(agg.tolist()) == set(range(nc))
+    np.testing.assert_array_equal(agg[roots], np.arange(nc))  # numbered by root index
+    for a, r in enumerate(roots):
+        members = np.flatnonzero(agg == a)
+        sub = S[members][:, members]
+        d = _bfs_dist(sp.csr_matrix(sub), int(np.flatnonzero(members == r)[0]))
+        assert np.all(d >= 0) and d.max() <= 2          # connected, radius <= 2 from its root
+        dfull = _bfs_dist(S, r)
+        others = np.setdiff1d(roots, [r])
+        assert np.all((dfull[others] < 0) | (dfull[others] >= 3))  # roots pairwise >= 3 apart
+
+
+# ---------------------------------------------------------------- sparse products and the hierarchy
+
+def test_structural_spgemm_keeps_cancelled_entries():
+    A = sp.csr_matrix(np.array([[1.0, 1.0], [0.0, 2.0]]))
+    B = sp.csr_matrix(np.array([[1.0, 3.0], [-1.0, 1.0]]))
+    C = amg.spgemm(A, B)
+    np.testing.assert_array_equal(C.toarray(), A.toarray() @ B.toarray())
+    assert C.nnz == 4  # C[0,0] = 1 - 1 = 0 is kept in the pattern
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        A = sp.random(30, 20, 0.2, random_state=rng, format="csr")
+        B = sp.random(20, 25, 0.2, random_state=rng, format="csr")
+        C = amg.spgemm(A, B)
+        np.testing.assert_allclose(C.toarray(), A.toarray() @ B.toarray(), rtol=1e-14, atol=1e-15)
+        pat = (np.abs(A.toarray()) > 0).astype(int) @ (np.abs(B.toarray()) > 0).astype(int) > 0
+        assert C.nnz == pat.sum()
+
+
+def _aux(grid, seed=1, dt=1.0, kmean=synth.KMEAN_ARITH, het=True):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(-60, -20, grid.n)
+    ks = synth.ks_field(grid, seed, 1.0, (3.0, 3.0, 2.0)) if het else None
+    return disc.aux_matrix(grid, SOIL, synth.infiltration_bc(), kmean, p, dt, ks)
+
+
+def test_prolongator_and_galerkin_product_against_dense_algebra():
+    grid = synth.Grid(8, 7, 6)
+    A = _aux(grid)
+    S = amg.strength(A, 0.08)
+    keys = amg.priority_keys(grid.n, 3)
+    state, _ = amg.mis2(S, keys)
+    agg, nc = amg.aggregate(S, state, keys)
+    Pt = amg.tentative_prolongator(agg, nc)
+    P, omega = amg.smoothed_prolongator(A, Pt)
+    Ad = A.toarray()
+    D = np.diag(Ad)
+    rho = np.max(np.abs(Ad).sum(1) / np.abs(D))
+    assert omega == pytest.approx(4.0 / (3.0 * rho), rel=1e-15)
+    Pd = (np.eye(grid.n) - omega * Ad / D[:, None]) @ Pt.toarray()
+    np.testing.assert_allclose(P.toarray(), Pd, rtol=1e-13, atol=1e-15)
+    Ac = amg.spgemm(amg.transpose(P), amg.spgemm(A, P))
+    # Galerkin identity x_c^T A_c y_c = (P x_c)^T A (P y_c)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        x, y = rng.standard_normal(nc), rng.standard_normal(nc)
+        assert x @ (Ac @ y) == pytest.approx((P @ x) @ (A @ (P @ y)), rel=1e-12)
+    Acd = Ac.toarray()
+    assert np.abs(Acd - Acd.T).max() <= 1e-13 * np.abs(Acd).max()
+    np.linalg.cholesky(Acd)
+
+
+def test_hierarchy_coarsens_and_vcycle_is_symmetric_positive_contraction():
+    grid = synth.Grid(8, 8, 8)
+    A = _aux(grid, 2, dt=0.5)
+    h = amg.setup(A, theta=0.08, seed=1, coarse_max=100)
+    assert len(h.levels) >= 2 and h.sizes[-1] < 100
+    assert all(b < a for a, b in zip(h.sizes, h.sizes[1:]))
+    n = grid.n
+    for nu in (1, 2):
+        B = np.column_stack([amg.vcycle(h, e, nu, nu) for e in np.eye(n)])
+        assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()      # symmetric V-cycle
+        assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0          # SPD
+        rho = np.abs(np.linalg.eigvals(np.eye(n) - B @ A.toarray())).max()
+        assert rho < 1.0                                             # convergent
+    # single-level hierarchy = exact dense solve
+    h1 = amg.setup(A, coarse_max=10 ** 6)
+    b = np.arange(n, dtype=float)
+    np.testing.assert_allclose(A @ amg.vcycle(h1, b), b, rtol=0, atol=1e-10 * np.abs(b).max())
+
+
+def test_refresh_equals_galerkin_products_of_new_matrix():
+    grid = synth.Grid(8, 8, 6)
+    A1 = _aux(grid, 3)
+    A2 = _aux(grid, 4)
+    h = amg.setup(A1, coarse_max=50)
+    amg.refresh(h, A2)
+    for l in range(len(h.levels) - 1):
+        lv = h.levels[l]
+        Pd = lv.P.toarray()
+        np.testing.assert_allclose(h.levels[l + 1].A.toarray(), Pd.T @ lv.A.toarray() @ Pd, rtol=1e-12,
+                                   atol=1e-12 * np.abs(lv.A.data).max())
+
+
+# ---------------------------------------------------------------- Krylov
+
+def test_fgmres_full_space_is_exact_solve_and_monotone():
+    rng = np.random.default_rng(3)
+    n = 27
+    M = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.5
+    b = rng.standard_normal(n)
+    x, its, ok, hist = krylov.fgmres(lambda v: M @ v, lambda v: v, b, 1e-13, 200, n)
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-11, atol=1e-12)
+    assert ok and its <= n
+    assert all(b2 <= b1 * (1 + 1e-12) for b1, b2 in zip(hist, hist[1:]))
+    # restarted with a varying (flexible) preconditioner still converges
+    D = np.diag(M)
+    k = itertools.count()
+    prec = lambda v: v / D * (1.0 + 0.1 * (next(k) % 3))
+    x, its, ok, _ = krylov.fgmres(lambda v: M @ v, prec, b, 1e-10, 500, 5)
+    assert ok and np.linalg.norm(M @ x - b) <= 1e-10 * np.linalg.norm(b) * 1.01
+
+
+def test_fcg_unpreconditioned_iterates_minimise_energy_error_on_krylov_space():
+    # With B = I on an SPD matrix, FCG is CG: x_k minimises the A-norm error over K_k(A, b).
+    rng = np.random.default_rng(4)
+    n = 40
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(np.linspace(1, 20, n)) @ Q.T
+    b = rng.standard_normal(n)
+    for k in range(1, 6):
+        xk, its, _, _ = krylov.fcg(lambda v: A @ v, lambda v: v, b, 1e-300, k)
+        Kb = np.column_stack([np.linalg.matrix_power(A, j) @ b for j in range(k)])
+        V = np.linalg.qr(Kb)[0]
+        xopt = V @ np.linalg.solve(V.T @ A @ V, V.T @ b)
+        np.testing.assert_allclose(xk, xopt, rtol=1e-9, atol=1e-12)
+    x, its, ok, _ = krylov.fcg(lambda v: A @ v, lambda v: v, b, 1e-12, 200)
+    assert ok
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- Newton-Armijo
+
+def test_hydrostatic_state_needs_no_newton_iteration():
+    grid = synth.Grid(4, 4, 6)
+    hz = grid.h[2]
+    z = (np.arange(grid.nz) + 1) * hz
+    p = np.broadcast_to((-12.0 - z)[:, None, None], grid.shape).ravel().copy()
+    bc = synth.BC(kind=(0, 0, 0, 0, 0, 1), value=(0, 0, 0, 0, 0, -12.0 - (grid.nz + 1) * hz))
+    prob = newton.Problem(grid, SOIL, bc, synth.KMEAN_ARITH)
+    # a converged state: the initial residual is round-off, so use an absolute tolerance
+    p1, st = newton.step(prob, p, 1.0, newton.NewtonOptions(rtol=0.0, atol=1e-12))
+    assert st.newton_its == 0 and st.converged
+    np.testing.assert_array_equal(p1, p)
+
+
+@pytest.mark.parametrize("kmean", [synth.KMEAN_ARITH, synth.KMEAN_UPSTREAM, synth.KMEAN_HARMONIC])
+def test_newton_step_converges_quadratically_and_conserves_mass(kmean):
+    grid = synth.Grid(6, 6, 8)
+    ks = synth.ks_field(grid, 1, 1.0, (3.0, 3.0, 2.0))
+    bc = synth.infiltration_bc()
+    prob = newton.Problem(grid, SOIL, bc, kmean, ks)
+    # a milder initial jump than the workloads' (-61.5 under a -20.7 top): with the
+    # harmonic mean a 40 cm jump across one cell makes the boundary rows of J
+    # indefinite and the diffusion-only preconditioner needs hundreds of iterations
+    p0 = np.full(grid.n, -25.0)
+    opt = newton.NewtonOptions(krylov="fgmres", eta=1e-12, rtol=1e-12, coarse_max=50)
+    p1, st = newton.step(prob, p0, 5.0, opt)
+    assert st.converged
+    F = prob.residual(p1, cst.saturation(p0, SOIL), 5.0)
+    assert np.linalg.norm(F) <= 1e-12 * st.res0 * 1.0001
+    r = st.res_hist
+    # local quadratic convergence once the full step is taken
+    full = [i for i, lam in enumerate(st.lambdas) if lam == 1.0]
+    ratios = [r[i + 1] / r[i] ** 2 for i in full if r[i] < 1e-2 * r[0] and r[i + 1] > 1e-14 * r[0]]
+    assert all(q < 1e3 for q in ratios)
+    # mass balance: storage change = inflow through the Dirichlet top face, up to ||Phi||_1.
+    # The top-face flux is isolated as Phi(p1) minus Phi(p1) with that face closed.
+    s0 = cst.saturation(p0, SOIL)
+    closed = disc.residual(grid, SOIL, synth.all_noflux_bc(), kmean, p1, s0, 5.0, ks)
+    top_flux = (F - closed).sum()
+    storage = SOIL.rho_phi * (cst.saturation(p1, SOIL) - s0).sum() / 5.0
+    assert storage > 0 and top_flux < 0   # wetting from the top
+    assert abs(storage + top_flux) <= np.abs(F).sum() + 1e-12 * storage
+
+
+def test_converged_pressure_is_independent_of_solver_choices():
+    grid = synth.Grid(6, 5, 7)
+    bc = synth.infiltration_bc()
+    p0 = np.full(grid.n, synth.P_INITIAL)
+    res = []
+    for kry, pol, nu in (("fcg", "refresh", 1), ("fgmres", "setup_once", 2), ("fgmres", "rebuild_step", 1)):
+        prob = newton.Problem(grid, SOIL, bc, synth.KMEAN_UPSTREAM)
+        opt = newton.NewtonOptions(krylov=kry, amg_policy=pol, nu1=nu, nu2=nu, coarse_max=40, rtol=1e-10)
+        p = p0
+        for dt in (1.0, 2.0):
+            p, st = newton.step(prob, p, dt, opt)
+            assert st.converged
+        res.append(p)
+    for q in res[1:]:
+        np.testing.assert_allclose(q, res[0], rtol=1e-8)
