@@ -1,0 +1,245 @@
+/*
+ * richards.h - C ABI of the GB300 backward-Euler Richards solver.
+ *
+ * The library advances the mixed-form Richards equation
+ *     rho*phi ds(p)/dt - div(K(p) grad p) - dK(p)/dz = 0
+ * (Sec. 2 of Bertaccini, D'Ambra, Durastante, Filippone, "Why
+ * diffusion-based preconditioning of Richards equation works", arXiv
+ * 2112.05051) by fully implicit backward-Euler steps on a cell-centred
+ * 7-point grid (eq. (dynamic_of_the_problem), Sec. 2.1).  Each step runs an
+ * inexact Newton iteration with an Armijo line search (Sec. 3) whose
+ * corrections J d = -Phi are solved by flexible CG or flexible GMRES,
+ * right-preconditioned (eq. (precsystem)) by a smoothed-aggregation AMG
+ * V-cycle (eq. (Vcycle), Sec. 5.2) built on the diffusion-only matrix of
+ * Sec. 4 (the Jacobian with the gravity and dK/dp terms dropped).
+ *
+ * Conventions shared by every call
+ *   - Cell (i,j,k), 0-based, is unknown c = i + nx*(j + ny*k); z (k) points up.
+ *     The grid has nx*ny*nz unknown cells; spacing h_d = l_d/(n_d + 1): the
+ *     paper's N = n + 2 nodes per direction with the outermost on the boundary.
+ *   - Faces are numbered -x, +x, -y, +y, -z (bottom), +z (top).
+ *   - Every pointer named *_dev is a device pointer on the context's device;
+ *     it is borrowed for the duration of the call and never freed by the
+ *     library.  Pointers named *_host are host memory.
+ *   - Work is enqueued on the CUDA stream given to rich_create.  Calls that
+ *     return scalars or statistics synchronise that stream before returning.
+ *   - Every call returns RICH_OK (0) or a negative error code; rich_strerror
+ *     gives its text.  On error no output is guaranteed except as stated.
+ *   - Stencil arrays ("7n") hold 7 blocks of n doubles: the diagonal, then the
+ *     coefficients of the -x, +x, -y, +y, -z, +z neighbours (0 where the
+ *     neighbour lies outside the grid).
+ */
+#ifndef RICHARDS_GB300_H
+#define RICHARDS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RICH_OK                0
+#define RICH_EINVAL           -1  /* bad size, null pointer, non-positive dt, bad option */
+#define RICH_ENOMEM           -2  /* device allocation failed */
+#define RICH_ECUDA            -3  /* a CUDA call failed (see rich_last_cuda_error) */
+#define RICH_ENOTCONV_LIN     -4  /* Krylov solve reached maxit without meeting eta */
+#define RICH_ENOTCONV_NEWTON  -5  /* Newton reached max_newton without meeting rtol */
+#define RICH_ELINESEARCH      -6  /* line search step fell below lambda_min or no descent */
+#define RICH_ENONFINITE       -7  /* NaN or Inf in a residual or Krylov scalar */
+#define RICH_ESTATE           -8  /* call made before its prerequisite (e.g. no Jacobian yet) */
+#define RICH_ELIMIT           -9  /* a size limit of the implementation was exceeded */
+
+/* ---- enumerations ------------------------------------------------------- */
+/* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
+ * (eq. (upstream_mean)) K_U if p_U - p_L >= 0 else K_L with U the +d cell;
+ * harmonic 2 K_L K_U / (K_L + K_U). */
+#define RICH_KMEAN_ARITH     0
+#define RICH_KMEAN_UPSTREAM  1
+#define RICH_KMEAN_HARMONIC  2
+
+#define RICH_BC_NOFLUX     0  /* the whole face flux (diffusion + gravity) is zero */
+#define RICH_BC_DIRICHLET  1  /* ghost node at p = value, K from the adjacent cell's K_s */
+
+/* Precision of the AMG preconditioner.  The Newton residual, the Jacobian,
+ * line-search norms and the outer Krylov vectors and dot products are FP64
+ * in both modes; MIXED stores and applies the hierarchy (matrices,
+ * transfer operators, l1 diagonals, coarsest inverse, V-cycle vectors) in
+ * FP32 with FP32 accumulation. */
+#define RICH_PREC_FP64   0
+#define RICH_PREC_MIXED  1
+
+#define RICH_KRYLOV_FCG     0  /* Notay's flexible CG, truncation 1 */
+#define RICH_KRYLOV_FGMRES  1  /* Saad's flexible GMRES(m), CGS2, Givens */
+
+/* AMG reuse across Newton iterations.
+ *  REFRESH      aggregates, P and R from the first setup of the run are kept;
+ *               each new diffusion matrix refreshes every coarse matrix
+ *               A_{l+1} = R A_l P numerically (same sparsity patterns).
+ *  SETUP_ONCE   the paper's scheme (Sec. 6): the hierarchy of the first
+ *               Jacobian is kept and only the finest matrix and its smoother
+ *               are replaced.
+ *  REBUILD_STEP a full setup at the first Newton iteration of each step,
+ *               REFRESH at the following ones. */
+#define RICH_AMG_REFRESH       0
+#define RICH_AMG_SETUP_ONCE    1
+#define RICH_AMG_REBUILD_STEP  2
+
+/* ---- parameter structs -------------------------------------------------- */
+typedef struct {
+  int nx, ny, nz;          /* unknown cells per direction, each >= 1 */
+  double lx, ly, lz;       /* box size (cm) */
+} rich_grid;
+
+/* Celia/Haverkamp laws, eqs. (s(p)) and (K(p)) of Sec. 2:
+ *   s(p) = alpha (theta_s - theta_r)/(alpha + |p|^beta) + theta_r,
+ *   K(p) = K_s a / (a + |p|^gamma)            for p < 0;
+ *   s = theta_s, K = K_s, s' = K' = 0        for p >= 0 (saturated). */
+typedef struct {
+  double alpha, beta, theta_s, theta_r, a, gamma;
+  double ks_const;         /* K_s when ks_field_dev is NULL */
+  double rho_phi;          /* factor of the storage term (1 in the paper's 1D forms) */
+  const double* ks_field_dev; /* per-cell K_s (n doubles, device) or NULL; copied at create */
+} rich_soil;
+
+typedef struct {
+  int kind[6];             /* RICH_BC_* per face */
+  double value[6];         /* Dirichlet pressure head (cm) per face */
+} rich_bc;
+
+typedef struct {
+  double theta;            /* strength threshold (0.08): a_ij^2 >= theta^2 |a_ii a_jj| */
+  uint64_t seed;           /* MIS-2 priority seed: key(i) = top30(splitmix64(seed^i))<<32 | i */
+  int coarse_max;          /* stop coarsening below this many unknowns (2000) */
+  int max_levels;          /* at most this many levels (10) */
+  int nu1, nu2;            /* l1-Jacobi pre/post sweeps (1, 1) */
+} rich_amg_opts;
+
+typedef struct {
+  int kind;                /* RICH_KRYLOV_* */
+  int restart;             /* m of FGMRES(m), <= 64 */
+  double eta;              /* stop when ||b - J x||_2 <= eta ||b||_2 */
+  int maxit;               /* iteration limit */
+} rich_krylov_opts;
+
+typedef struct {
+  int iterations;          /* Krylov iterations done */
+  int converged;           /* 1 if eta was met */
+  double res0, res;        /* ||b||_2 and the final ||b - J x||_2 */
+} rich_krylov_stats;
+
+typedef struct {
+  rich_krylov_opts krylov;
+  rich_amg_opts amg;
+  int amg_policy;          /* RICH_AMG_* */
+  double rtol, atol;       /* converged when ||Phi||_2 <= max(rtol ||Phi_0||_2, atol) */
+  int max_newton;          /* Newton iteration limit (50) */
+  double armijo_c;         /* sufficient-decrease constant (1e-4) */
+  double lambda_min;       /* smallest line-search step (1e-10) */
+  int fcg_fallback_restart;/* FGMRES(m) retry after an FCG failure (30) */
+} rich_newton_opts;
+
+typedef struct {
+  int newton_its;          /* Newton corrections applied */
+  int linear_its;          /* Krylov iterations over all corrections (incl. fallbacks) */
+  int line_search_evals;   /* residual evaluations inside line searches */
+  int fallbacks;           /* FCG solves retried with FGMRES */
+  int amg_setups;          /* full hierarchy builds during the step */
+  int amg_refreshes;       /* numeric refreshes / fine-level updates during the step */
+  int converged;           /* 1 if rtol/atol was met */
+  double res0, res;        /* ||Phi||_2 at the start and at the end of the step */
+  double min_lambda;       /* smallest accepted step length */
+} rich_step_stats;
+
+typedef struct {
+  int levels;              /* number of levels incl. the finest */
+  int n[16];               /* unknowns per level */
+  long long nnz[16];       /* nonzeros of A per level */
+  int mis_rounds[16];      /* MIS-2 rounds used to coarsen level l */
+  double omega[16];        /* prolongator damping 4/(3 rho) of level l */
+  double operator_complexity; /* sum nnz(A_l) / nnz(A_0) */
+} rich_amg_info;
+
+typedef struct rich_ctx rich_ctx;
+
+/* ---- lifetime ---------------------------------------------------------- */
+/* Create a context on the current device.  stream is a cudaStream_t (NULL =
+ * legacy default stream).  Copies the K_s field.  Allocates the per-grid
+ * buffers (constitutive values, Jacobian and diffusion stencils, CSR pattern
+ * of the finest AMG level, Krylov work vectors are allocated lazily). */
+int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const rich_bc* bc,
+                int precision, void* stream, rich_ctx** out);
+int rich_destroy(rich_ctx* ctx);
+const char* rich_strerror(int status);
+const char* rich_last_cuda_error(void);
+int rich_num_cells(const rich_ctx* ctx, long long* n_out);
+
+/* ---- Sec. 2: constitutive law and residual ----------------------------- */
+/* s_dev[c] = s(p_dev[c]) (eq. (s(p))).  Used for s(p^{l-1}) of a step. */
+int rich_saturation(rich_ctx* ctx, const double* p_dev, double* s_dev);
+
+/* Phi(p) of eq. (dynamic_of_the_problem) with s(p^{l-1}) = s_old_dev and time
+ * step dt > 0, written to F_dev (n doubles).  If norms_host is not NULL it
+ * receives {||Phi||_2, ||Phi||_inf} (and the call synchronises); a
+ * non-finite Phi returns RICH_ENONFINITE after writing F_dev. */
+int rich_residual(rich_ctx* ctx, const double* p_dev, const double* s_old_dev, double dt,
+                  double* F_dev, double* norms_host);
+
+/* ---- Sec. 3-4: Jacobian and diffusion-only preconditioner matrix ------- */
+/* Assemble J(p) = dPhi/dp (exact derivative of the residual; in the interior
+ * the printed entries of Supplementary A (arithmetic) and C (upstream)) and
+ * the diffusion-only SPD matrix A_aux = diag(rho_phi s'/dt) + sum over faces
+ * of (K_av/h^2)(e_c - e_nb)(e_c - e_nb)^T (Dirichlet faces on the diagonal),
+ * the frozen-coefficient matrix of q_prec = -K(p) grad p (Sec. 4).  Both are
+ * kept in the context for amg_setup / krylov_solve.  J7_dev and A7_dev, if
+ * not NULL, receive copies in the 7n stencil layout. */
+int rich_jacobian(rich_ctx* ctx, const double* p_dev, double dt, double* J7_dev, double* A7_dev);
+
+/* y_dev = J x_dev with the context's current Jacobian (stencil SpMV). */
+int rich_jacobian_apply(rich_ctx* ctx, const double* x_dev, double* y_dev);
+
+/* ---- Sec. 5.2: AMG ----------------------------------------------------- */
+/* Build the smoothed-aggregation hierarchy from the context's current A_aux
+ * (strength, MIS-2 aggregation, P = (I - omega D^-1 A) P_tent, R = P^T,
+ * A_{l+1} = R A_l P, dense inverse of the coarsest matrix).  opts NULL =
+ * defaults.  info_host, if not NULL, receives the level sizes. */
+int amg_setup(rich_ctx* ctx, const rich_amg_opts* opts, rich_amg_info* info_host);
+/* Refresh the hierarchy from the context's current A_aux (policy
+ * RICH_AMG_REFRESH or RICH_AMG_SETUP_ONCE semantics). */
+int amg_update(rich_ctx* ctx, int policy);
+/* z_dev = B r_dev: one V-cycle with zero initial guess (FP64 in and out; in
+ * MIXED mode the cycle itself runs in FP32). */
+int amg_vcycle(rich_ctx* ctx, const double* r_dev, double* z_dev);
+/* Export level l for inspection (host buffers sized from rich_amg_info):
+ * aggregate index per node of level l (n[l] ints, level < levels-1), and the
+ * CSR of A_l (rowptr n[l]+1, col nnz, val nnz).  Any pointer may be NULL. */
+int amg_export_level(rich_ctx* ctx, int level, int* agg_host, int* rowptr_host, int* col_host,
+                     double* val_host);
+/* Export P_l (n[l] x n[l+1]) as CSR to host buffers; nnz via nnz_out. */
+int amg_export_prolongator(rich_ctx* ctx, int level, long long* nnz_out, int* rowptr_host, int* col_host,
+                           double* val_host);
+
+/* ---- Sec. 3: Newton correction solve ------------------------------------ */
+/* Solve J x = b (current Jacobian, current hierarchy) with x0 = 0. */
+int krylov_solve(rich_ctx* ctx, const double* b_dev, double* x_dev, const rich_krylov_opts* opts,
+                 rich_krylov_stats* stats_host);
+
+/* ---- Sec. 3: one backward-Euler step ------------------------------------ */
+/* p_dev holds p^{l-1} on entry and p^l on return (or the last accepted
+ * Newton iterate on error).  opts NULL = defaults.  The first call of a
+ * context builds the AMG hierarchy. */
+int rich_step(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_opts* opts,
+              rich_step_stats* stats_host);
+/* The same step on a host array: copies p_host to the device, steps, and
+ * copies the result back (both copies on the context's stream). */
+int rich_step_host(rich_ctx* ctx, double* p_host, double dt, const rich_newton_opts* opts,
+                   rich_step_stats* stats_host);
+
+/* Default option structs (as listed in the comments above). */
+void rich_default_newton_opts(rich_newton_opts* o);
+void rich_default_amg_opts(rich_amg_opts* o);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RICHARDS_GB300_H */

@@ -1,0 +1,177 @@
+// Deterministic reductions, scans and dot products.  Every reduction writes one
+// partial per block of a fixed grid and a second single-block kernel sums the
+// partials in block order, so FP64 results reproduce bit for bit run to run.
+#include "common.cuh"
+
+namespace rich {
+
+__global__ void k_finish_sums(const double* __restrict__ partials, int nb, int nq, double* __restrict__ dst) {
+  for (int q = 0; q < nq; ++q) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v[0] += partials[(long long)q * nb + b];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) dst[q] = v[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_finish_max(const double* __restrict__ partials, int nb, double* __restrict__ dst) {
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double a = partials[b];
+    m = (a > m || a != a) ? a : m;
+  }
+  m = block_max(m);
+  if (threadIdx.x == 0) dst[0] = m;
+}
+
+int finish_sums(rich_ctx* c, const double* partials, int nb, int nq, double* dst) {
+  k_finish_sums<<<1, kBlock, 0, c->st>>>(partials, nb, nq, dst);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+int finish_max(rich_ctx* c, const double* partials, int nb, double* dst) {
+  k_finish_max<<<1, kBlock, 0, c->st>>>(partials, nb, dst);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+int fetch_scalars(rich_ctx* c, const double* dsrc, int count, double* host) {
+  RICH_CUDA(cudaMemcpyAsync(c->hsc, dsrc, count * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < count; ++i) host[i] = c->hsc[i];
+  return RICH_OK;
+}
+
+// ---------------------------------------------------------------- dot products
+
+__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                      double* __restrict__ partials) {
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[0] += x[i] * y[i];
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+int dot(rich_ctx* c, const double* x, const double* y, long long n, double* dst) {
+  int nb = red_grid(n);
+  k_dot<<<nb, kBlock, 0, c->st>>>(x, y, n, c->partials);
+  RICH_LAUNCH_CHECK();
+  return finish_sums(c, c->partials, nb, 1, dst);
+}
+
+int nrm2sq(rich_ctx* c, const double* x, long long n, double* dst) { return dot(c, x, x, n, dst); }
+
+// ---------------------------------------------------------------- exclusive scan (3 phases)
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total) {
+  __shared__ T sh[kBlock / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  __syncthreads();
+  if (lane == 31) sh[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < kBlock / 32 ? sh[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kBlock / 32) sh[lane] = wi - w;
+    if (lane == kBlock / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  return sh[wid] + inc - v;
+}
+
+template <class TI, class TO>
+__global__ void k_scan_tiles(const TI* __restrict__ in, long long n, TO* __restrict__ tile_sums) {
+  long long base = (long long)blockIdx.x * kScanTile;
+  TO s = 0;
+  for (int t = 0; t < kScanItems; ++t) {
+    long long i = base + (long long)t * kBlock + threadIdx.x;
+    if (i < n) s += (TO)in[i];
+  }
+  __shared__ TO tot;
+  block_exclusive_scan<TO>(s, &tot);
+  __syncthreads();
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+template <class TO>
+__global__ void k_scan_sums(TO* __restrict__ sums, long long nt, TO* __restrict__ total_out) {
+  __shared__ TO carry;
+  __shared__ TO tot;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long base = 0; base < nt; base += blockDim.x) {
+    long long i = base + threadIdx.x;
+    TO v = i < nt ? sums[i] : TO(0);
+    TO ex = block_exclusive_scan<TO>(v, &tot);
+    if (i < nt) sums[i] = ex + carry;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+template <class TI, class TO>
+__global__ void k_scan_apply(const TI* __restrict__ in, long long n, const TO* __restrict__ tile_off,
+                             TO* __restrict__ out) {
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  TO loc[kScanItems];
+  TO s = 0;
+  for (int t = 0; t < kScanItems; ++t) {
+    long long i = base + t;
+    loc[t] = i < n ? (TO)in[i] : TO(0);
+    s += loc[t];
+  }
+  __shared__ TO tot;
+  TO ex = block_exclusive_scan<TO>(s, &tot) + tile_off[blockIdx.x];
+  for (int t = 0; t < kScanItems; ++t) {
+    long long i = base + t;
+    if (i < n) out[i] = ex;
+    ex += loc[t];
+  }
+}
+
+// The tile sums of k_scan_tiles are taken over strided items while k_scan_apply
+// scans contiguous items; both cover the same tile [base, base + kScanTile), so the
+// tile total is the same.
+template <class TI, class TO>
+static int scan_impl(rich_ctx* c, const TI* in, TO* out, long long n) {
+  long long nt = (n + kScanTile - 1) / kScanTile;
+  if (nt < 1) nt = 1;
+  TO* sums = nullptr;
+  RICH_CHECK(dalloc(&sums, nt));
+  k_scan_tiles<TI, TO><<<(int)nt, kBlock, 0, c->st>>>(in, n, sums);
+  RICH_LAUNCH_CHECK();
+  k_scan_sums<TO><<<1, kBlock, 0, c->st>>>(sums, nt, out + n);
+  RICH_LAUNCH_CHECK();
+  k_scan_apply<TI, TO><<<(int)nt, kBlock, 0, c->st>>>(in, n, sums, out);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  dfree(sums);
+  return RICH_OK;
+}
+
+int scan_exclusive_int(rich_ctx* c, const int* in, int* out, long long n) { return scan_impl<int, int>(c, in, out, n); }
+int scan_exclusive_ll(rich_ctx* c, const long long* in, long long* out, long long n) {
+  return scan_impl<long long, long long>(c, in, out, n);
+}
+
+}  // namespace rich

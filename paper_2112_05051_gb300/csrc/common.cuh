@@ -1,0 +1,313 @@
+// Shared definitions of the GB300 Richards solver: context, sparse/level structs,
+// launch helpers, deterministic block reductions and the constitutive law.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/richards.h"
+
+namespace rich {
+
+constexpr int kBlock = 256;          // threads per block of every elementwise kernel
+constexpr int kNumSM = 152;          // GB300 SM count (2 dies x 76)
+constexpr int kRedBlocks = 8 * kNumSM;  // fixed grid of the reduction kernels (deterministic order)
+
+void set_cuda_error(cudaError_t e, const char* where);
+
+#define RICH_CUDA(call)                                              \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) {                                         \
+      ::rich::set_cuda_error(e_, #call);                             \
+      return RICH_ECUDA;                                             \
+    }                                                                \
+  } while (0)
+
+#define RICH_CHECK(expr)                 \
+  do {                                   \
+    int s_ = (expr);                     \
+    if (s_ != RICH_OK) return s_;        \
+  } while (0)
+
+#define RICH_LAUNCH_CHECK() RICH_CUDA(cudaGetLastError())
+
+inline int grid_for(long long n, int block = kBlock) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 2147483647LL) g = 2147483647LL;
+  return (int)g;
+}
+inline int red_grid(long long n) {
+  long long g = (n + kBlock - 1) / kBlock;
+  if (g > kRedBlocks) g = kRedBlocks;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+struct SoilP {
+  double alpha, beta, ts, tr, a, gamma, ks, rho_phi;
+};
+
+struct GridP {
+  int nx, ny, nz;
+  long long n;
+  double inv_h[3];   // 1/h_d
+  double inv_h2[3];  // 1/h_d^2
+};
+
+struct BCP {
+  int kind[6];
+  double value[6];
+};
+
+template <class T>
+struct Csr {
+  int nrows = 0, ncols = 0;
+  long long nnz = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  T* val = nullptr;
+};
+
+// One level of the AMG hierarchy.  Level 0 holds the diffusion matrix of the
+// finest grid; levels 1.. hold Galerkin products.  FP32 copies exist in MIXED mode.
+struct Level {
+  int n = 0;
+  Csr<double> A;
+  float* A32 = nullptr;            // values of A in FP32 (pattern of A)
+  double* dinv = nullptr;          // 1 / sum_j |a_ij|
+  float* dinv32 = nullptr;
+  int* agg = nullptr;              // aggregate of each node (levels with a coarser level)
+  Csr<double> P, R, AP;            // to the next level; AP = A P (pattern kept for refresh)
+  float* P32 = nullptr;            // values of P/R in FP32
+  float* R32 = nullptr;
+  int mis_rounds = 0;
+  double omega = 0.0;
+  // V-cycle work vectors, typed by the hierarchy precision (double or float)
+  void* x = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+  void* t = nullptr;
+};
+
+struct Hierarchy {
+  std::vector<Level> lv;
+  int nlev = 0;
+  int cn = 0;                     // coarsest size
+  double* cdense = nullptr;       // coarsest matrix, dense, then its inverse (cn x cn)
+  float* cinv32 = nullptr;
+  double* cwork = nullptr;        // Gauss-Jordan pivot row/column buffers (2 cn)
+  rich_amg_opts opts{};
+  bool built = false;
+};
+
+struct KrylovWork {
+  long long n = 0;
+  int m = 0;
+  double* V = nullptr;  // (m+1) x n
+  double* Z = nullptr;  // m x n
+  double* x = nullptr;
+  double* r = nullptr;
+  double* p = nullptr;
+  double* q = nullptr;
+  double* qprev = nullptr;
+  double* z = nullptr;
+  double* w = nullptr;
+  double* hcoef = nullptr;  // device coefficients (m+1)
+};
+
+}  // namespace rich
+
+struct rich_ctx {
+  rich::GridP g{};
+  rich::SoilP soil{};
+  rich::BCP bc{};
+  int kmean = 0;
+  int prec = 0;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  double* ks = nullptr;        // per-cell K_s or nullptr
+  // constitutive values at the last p given to constit()
+  double* K = nullptr;
+  double* dK = nullptr;
+  double* S = nullptr;
+  double* dS = nullptr;
+  // stencils (7n)
+  double* J7 = nullptr;
+  double* A7 = nullptr;
+  bool have_jac = false;
+  bool a0_fresh = false;       // finest CSR values match A7
+  // finest-level CSR pattern (built at create)
+  rich::Csr<double> A0;
+  rich::Hierarchy H;
+  rich::KrylovWork kw;
+  // reductions: partial sums per block and device scalars
+  double* partials = nullptr;  // kRedBlocks * 64
+  double* dsc = nullptr;       // device scalars (128)
+  double* hsc = nullptr;       // pinned host mirror (128)
+  int* iflag = nullptr;        // device int flags (16)
+  int* hflag = nullptr;        // pinned host (16)
+  // Newton work
+  double* s_old = nullptr;
+  double* F = nullptr;
+  double* Ft = nullptr;
+  double* d = nullptr;
+  double* ptrial = nullptr;
+  double* rhs = nullptr;
+  double* pbuf = nullptr;      // device p for rich_step_host
+  bool amg_ever = false;
+};
+
+namespace rich {
+
+// ---------------------------------------------------------------- device helpers
+
+// Constitutive law, eqs. (s(p)), (K(p)) and (derivativeofcoefficients) of Sec. 2-3.
+// |p|^beta and |p|^gamma share one log|p|; |p|^(x-1) = |p|^x / |p|.
+__device__ __forceinline__ void constit(double p, double ks, const SoilP& so, double& S, double& dS,
+                                        double& K, double& dK) {
+  if (p < 0.0) {
+    double ap = -p;
+    double lp = log(ap);
+    double pb = exp(so.beta * lp);
+    double pg = exp(so.gamma * lp);
+    double ds_ = so.alpha + pb;
+    double dk_ = so.a + pg;
+    S = so.alpha * (so.ts - so.tr) / ds_ + so.tr;
+    dS = so.alpha * so.beta * (pb / ap) * (so.ts - so.tr) / (ds_ * ds_);
+    K = ks * so.a / dk_;
+    dK = so.a * so.gamma * ks * (pg / ap) / (dk_ * dk_);
+  } else {
+    S = so.ts;
+    dS = 0.0;
+    K = ks;
+    dK = 0.0;
+  }
+}
+
+__device__ __forceinline__ double conductivity_only(double p, double ks, const SoilP& so) {
+  if (p < 0.0) return ks * so.a / (so.a + exp(so.gamma * log(-p)));
+  return ks;
+}
+
+// Face mean between the lower (L) and upper (+d side, U) cell and its partials.
+__device__ __forceinline__ double face_mean(int kmean, double kL, double kU, double pL, double pU,
+                                            double& dL, double& dU) {
+  if (kmean == RICH_KMEAN_ARITH) {
+    dL = 0.5;
+    dU = 0.5;
+    return 0.5 * (kL + kU);
+  }
+  if (kmean == RICH_KMEAN_UPSTREAM) {
+    bool up = (pU - pL) >= 0.0;
+    dL = up ? 0.0 : 1.0;
+    dU = up ? 1.0 : 0.0;
+    return up ? kU : kL;
+  }
+  double s = kL + kU;
+  if (s > 0.0) {
+    double is = 1.0 / s;
+    dL = 2.0 * kU * kU * is * is;
+    dU = 2.0 * kL * kL * is * is;
+    return 2.0 * kL * kU * is;
+  }
+  dL = dU = 0.0;
+  return 0.0;
+}
+
+// Warp/block sum of NQ doubles in a fixed order; result valid in thread 0.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ]) {
+  __shared__ double sh[NQ][kBlock / 32];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[q][wid] = v[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double t = lane < kBlock / 32 ? sh[q][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[q] = t;
+    }
+  }
+}
+
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double shm[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) shm[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double t = lane < kBlock / 32 ? shm[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    v = t;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- host helpers (blas.cu)
+
+// Sum nq quantities of per-block partials (partials[q*nb + b]) into dst[q] (device), fixed order.
+int finish_sums(rich_ctx* c, const double* partials, int nb, int nq, double* dst);
+int finish_max(rich_ctx* c, const double* partials, int nb, double* dst);
+int fetch_scalars(rich_ctx* c, const double* dsrc, int count, double* host);
+int scan_exclusive_int(rich_ctx* c, const int* in, int* out, long long n);         // out[n] = total
+int scan_exclusive_ll(rich_ctx* c, const long long* in, long long* out, long long n);
+int dot(rich_ctx* c, const double* x, const double* y, long long n, double* dst_dev);
+int nrm2sq(rich_ctx* c, const double* x, long long n, double* dst_dev);
+
+template <class T>
+int dalloc(T** p, long long count) {
+  if (count <= 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "cudaMalloc");
+    *p = nullptr;
+    return RICH_ENOMEM;
+  }
+  return RICH_OK;
+}
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// physics.cu
+int constit_eval(rich_ctx* c, const double* p);
+int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms);
+int jacobian_eval(rich_ctx* c, const double* p, double dt);
+int stencil_apply(rich_ctx* c, const double* A7, const double* x, double* y);
+int refresh_a0_values(rich_ctx* c);
+
+// amg_setup.cu
+int amg_build(rich_ctx* c, const rich_amg_opts* o);
+int amg_refresh(rich_ctx* c);
+int amg_update_fine(rich_ctx* c);
+void amg_free(rich_ctx* c);
+
+// solve.cu
+int vcycle_apply(rich_ctx* c, const double* r, double* z);
+int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st);
+
+}  // namespace rich

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of the C ABI in include/richards.h (argument marshalling only).
+
+Device buffers are torch CUDA tensors (float64, contiguous); the binding passes
+their data pointers and the current torch CUDA stream.  Every numerical step
+runs in the CUDA library; when the library is missing the binding raises.
+"""
+import ctypes
+import os
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librichards_gb300.so")
+
+RICH_OK = 0
+KRYLOV_FCG, KRYLOV_FGMRES = 0, 1
+AMG_REFRESH, AMG_SETUP_ONCE, AMG_REBUILD_STEP = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+
+ERRORS = {-1: "RICH_EINVAL", -2: "RICH_ENOMEM", -3: "RICH_ECUDA", -4: "RICH_ENOTCONV_LIN",
+          -5: "RICH_ENOTCONV_NEWTON", -6: "RICH_ELINESEARCH", -7: "RICH_ENONFINITE", -8: "RICH_ESTATE",
+          -9: "RICH_ELIMIT"}
+
+
+class RichError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (%d)%s" % (what, ERRORS.get(status, "?"), status,
+                                                   (" [" + _last_cuda() + "]") if status == -3 else ""))
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class Soil(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("theta_s", ctypes.c_double),
+                ("theta_r", ctypes.c_double), ("a", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("ks_const", ctypes.c_double), ("rho_phi", ctypes.c_double), ("ks_field_dev", ctypes.c_void_p)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 6), ("value", ctypes.c_double * 6)]
+
+
+class AmgOpts(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("coarse_max", ctypes.c_int),
+                ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int)]
+
+
+class KrylovOpts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("restart", ctypes.c_int), ("eta", ctypes.c_double),
+                ("maxit", ctypes.c_int)]
+
+
+class KrylovStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double)]
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("krylov", KrylovOpts), ("amg", AmgOpts), ("amg_policy", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("armijo_c", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("fcg_fallback_restart", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int), ("linear_its", ctypes.c_int), ("line_search_evals", ctypes.c_int),
+                ("fallbacks", ctypes.c_int), ("amg_setups", ctypes.c_int), ("amg_refreshes", ctypes.c_int),
+                ("converged", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
+                ("min_lambda", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AmgInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("n", ctypes.c_int * 16), ("nnz", ctypes.c_longlong * 16),
+                ("mis_rounds", ctypes.c_int * 16), ("omega", ctypes.c_double * 16),
+                ("operator_complexity", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+EXPORTS = {
+    "rich_create": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Soil), ctypes.c_int, ctypes.POINTER(BC),
+                                   ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "rich_destroy": (ctypes.c_int, [_P]),
+    "rich_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "rich_last_cuda_error": (ctypes.c_char_p, []),
+    "rich_num_cells": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "rich_saturation": (ctypes.c_int, [_P, _P, _P]),
+    "rich_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rich_jacobian": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P]),
+    "rich_jacobian_apply": (ctypes.c_int, [_P, _P, _P]),
+    "amg_setup": (ctypes.c_int, [_P, ctypes.POINTER(AmgOpts), ctypes.POINTER(AmgInfo)]),
+    "amg_update": (ctypes.c_int, [_P, ctypes.c_int]),
+    "amg_vcycle": (ctypes.c_int, [_P, _P, _P]),
+    "amg_export_level": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
+    "amg_export_prolongator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _P, _P, _P]),
+    "krylov_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(KrylovOpts), ctypes.POINTER(KrylovStats)]),
+    "rich_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(NewtonOpts), ctypes.POINTER(StepStats)]),
+    "rich_step_host": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(NewtonOpts),
+                                      ctypes.POINTER(StepStats)]),
+    "rich_default_newton_opts": (None, [ctypes.POINTER(NewtonOpts)]),
+    "rich_default_amg_opts": (None, [ctypes.POINTER(AmgOpts)]),
+}
+
+
+def load():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librichards_gb300.so is missing: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _last_cuda():
+    try:
+        return load().rich_last_cuda_error().decode()
+    except Exception:  # pragma: no cover
+        return ""
+
+
+def check(status, what):
+    if status != RICH_OK:
+        raise RichError(status, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_contiguous(), "tensor must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_newton_opts(**kw):
+    o = NewtonOpts()
+    load().rich_default_newton_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k in ("kind", "restart", "eta", "maxit"):
+            setattr(o.krylov, k, v)
+        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2"):
+            setattr(o.amg, k, v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def default_amg_opts(**kw):
+    o = AmgOpts()
+    load().rich_default_amg_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """A solver context on the current CUDA device (wraps rich_create/rich_destroy)."""
+
+    def __init__(self, grid: synth.Grid, soil: synth.Soil, bc: synth.BC, kmean: int, ks=None,
+                 precision=PREC_FP64):
+        import torch
+        lib = load()
+        g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        self._ks = None
+        if ks is not None:
+            self._ks = torch.as_tensor(ks, dtype=torch.float64).reshape(-1).cuda().contiguous()
+        s = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
+                 _ptr(self._ks) if self._ks is not None else None)
+        b = BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value))
+        h = ctypes.c_void_p()
+        check(lib.rich_create(ctypes.byref(g), ctypes.byref(s), kmean, ctypes.byref(b), precision, _stream(),
+                              ctypes.byref(h)), "rich_create")
+        self.h = h
+        self.n = grid.n
+        self.grid = grid
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rich_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def saturation(self, p, s):
+        check(load().rich_saturation(self.h, _ptr(p), _ptr(s)), "rich_saturation")
+
+    def residual(self, p, s_old, dt, F, norms=True):
+        arr = (ctypes.c_double * 2)() if norms else None
+        check(load().rich_residual(self.h, _ptr(p), _ptr(s_old), dt, _ptr(F), arr), "rich_residual")
+        return (arr[0], arr[1]) if norms else None
+
+    def jacobian(self, p, dt, J7=None, A7=None):
+        check(load().rich_jacobian(self.h, _ptr(p), dt, _ptr(J7), _ptr(A7)), "rich_jacobian")
+
+    def jacobian_apply(self, x, y):
+        check(load().rich_jacobian_apply(self.h, _ptr(x), _ptr(y)), "rich_jacobian_apply")
+
+    def amg_setup(self, opts=None):
+        info = AmgInfo()
+        check(load().amg_setup(self.h, ctypes.byref(opts) if opts is not None else None, ctypes.byref(info)),
+              "amg_setup")
+        return info
+
+    def amg_update(self, policy=AMG_REFRESH):
+        check(load().amg_update(self.h, policy), "amg_update")
+
+    def vcycle(self, r, z):
+        check(load().amg_vcycle(self.h, _ptr(r), _ptr(z)), "amg_vcycle")
+
+    def export_level(self, level, info):
+        import numpy as np
+        n = info.n[level]
+        nnz = info.nnz[level]
+        agg = np.zeros(n, dtype=np.int32) if level < info.levels - 1 else None
+        rp = np.zeros(n + 1, dtype=np.int32)
+        col = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz, dtype=np.float64)
+        cp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+        check(load().amg_export_level(self.h, level, cp(agg), cp(rp), cp(col), cp(val)), "amg_export_level")
+        return agg, rp, col, val
+
+    def export_prolongator(self, level, info):
+        import numpy as np
+        nnz = ctypes.c_longlong()
+        check(load().amg_export_prolongator(self.h, level, ctypes.byref(nnz), None, None, None),
+              "amg_export_prolongator")
+        rp = np.zeros(info.n[level] + 1, dtype=np.int32)
+        col = np.zeros(nnz.value, dtype=np.int32)
+        val = np.zeros(nnz.value, dtype=np.float64)
+        cp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        check(load().amg_export_prolongator(self.h, level, ctypes.byref(nnz), cp(rp), cp(col), cp(val)),
+              "amg_export_prolongator")
+        return rp, col, val
+
+    def krylov_solve(self, b, x, kind=KRYLOV_FCG, restart=30, eta=1e-7, maxit=200, check_status=True):
+        o = KrylovOpts(kind, restart, eta, maxit)
+        st = KrylovStats()
+        s = load().krylov_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        if check_status:
+            check(s, "krylov_solve")
+        return s, st
+
+    def step(self, p, dt, opts=None):
+        st = StepStats()
+        check(load().rich_step(self.h, _ptr(p), dt, ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(st)), "rich_step")
+        return st
+
+    def step_host(self, p_host, dt, opts=None):
+        """p_host: numpy float64 array or pinned CPU tensor (updated in place)."""
+        st = StepStats()
+        if hasattr(p_host, "data_ptr"):
+            ptr = ctypes.c_void_p(p_host.data_ptr())
+        else:
+            ptr = p_host.ctypes.data_as(ctypes.c_void_p)
+        check(load().rich_step_host(self.h, ptr, dt, ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(st)), "rich_step_host")
+        return st
