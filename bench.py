@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput of the backward-Euler Richards step on GB300: DOF * Newton-steps / s.
+
+A bench "step" is one backward-Euler time step of the workload (constitutive
+evaluation, residual, Jacobian and diffusion-matrix assembly, AMG refresh,
+right-preconditioned Krylov solves with the AMG V-cycle, Newton-Armijo line
+search) -- every stage of the path.  Default workload: 128^3 cells (2.1M DOF),
+homogeneous Haverkamp soil, upstream-mean K, Dirichlet top at -20.7 cm, no-flux
+elsewhere, p0 = -61.5 cm, dt ramped linearly 1 -> 30 s over 20 steps, FGMRES(30)
+with an AMG V(2,2) l1-Jacobi cycle, coarsest level (< 2000 unknowns) by dense
+inverse, Newton-Armijo to 1e-8 relative, FP64 throughout.  The default
+--warmup 3 --steps 17 runs exactly the 20-step schedule; other counts cycle it.
+
+value   = sum over ranks of (DOF * Newton iterations in the timed steps) / max
+          over ranks of the CUDA-event time of the timed steps (inputs resident).
+e2e     = the same metric through rich_step_host: each step copies p from pinned
+          host memory to the device and the result back.
+The AMG hierarchy (aggregates, P, R) is built in the first warm-up step and
+refreshed numerically on every Newton iteration afterwards.
+
+--impl reference times the CPU oracle (the plain FP64 numpy/scipy restatement)
+on the same workload: each step is one Newton iteration of the first time step
+(a bounded sample; the AMG setup happens in the first warm-up step).
+With torchrun (N > 1) every rank runs an independent replica of the workload
+(the path has no cross-rank exchange on one GPU each); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the roofline kernel
+# (profiles/ summary of the same kernel and workload); None until captured.
+NCU_TRAFFIC_BYTES = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=17)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="richards128_fp64")
+    ap.add_argument("--roofline-kernel", default="multidot")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def workload_setup(name):
+    from paper_2112_05051_gb300 import synth
+    w = synth.WORKLOADS[name]
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w)
+    return w, grid, soil, bc, ks, p0, dts
+
+
+def newton_opts(rb, w):
+    return rb.default_newton_opts(kind=rb.KRYLOV_FGMRES if w.krylov == "fgmres" else rb.KRYLOV_FCG,
+                                  restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu, seed=w.amg_seed,
+                                  coarse_max=w.coarse_max, amg_policy=rb.AMG_REFRESH)
+
+
+def cpu_baseline(workload, budget, warm_only=False):
+    """Oracle Newton iterations on the workload's first time step, in a 1-thread subprocess."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, str(budget)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=budget * 20 + 600)
+    if r.returncode != 0:
+        return {"value": None, "unit": "DOF*Newton-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_main(workload, budget, steps=None, warmup=None):
+    """Time oracle Newton iterations (each from the state the previous one left)."""
+    from oracle import newton
+    w, grid, soil, bc, ks, p0, dts = workload_setup(workload)
+    prob = newton.Problem(grid, soil, bc, w.kmean, ks)
+    opt = newton.NewtonOptions(krylov=w.krylov, restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu,
+                               amg_seed=w.amg_seed, coarse_max=w.coarse_max, max_newton=1)
+    p = p0.copy()
+    t0 = time.perf_counter()
+    p, st = newton.step(prob, p, dts[0], opt)  # builds the hierarchy (not timed)
+    setup_s = time.perf_counter() - t0
+    its = 0
+    times = []
+    nw = warmup or 0
+    for _ in range(nw):
+        p, st = newton.step(prob, p, dts[0], opt)
+    t0 = time.perf_counter()
+    while True:
+        t1 = time.perf_counter()
+        p, st = newton.step(prob, p, dts[0], opt)
+        times.append(time.perf_counter() - t1)
+        its += st.newton_its
+        if steps is not None:
+            if len(times) >= steps:
+                break
+        elif time.perf_counter() - t0 >= budget:
+            break
+    el = time.perf_counter() - t0
+    return {"value": grid.n * its / el, "unit": "DOF*Newton-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d Newton iterations of the first time step (dt=%g) of %s, %.1f s, one thread; "
+                      "AMG setup (%.1f s) excluded" % (its, dts[0], workload, el, setup_s),
+            "step_times": times}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload)
+    env_threads = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1"}
+    for k, v in env_threads.items():
+        os.environ.setdefault(k, v)
+    res = oracle_sample_main(args.workload, 0.0, steps=args.steps, warmup=args.warmup)
+    total = sum(res["step_times"])
+    value = res["value"]
+    line = {"metric": "DOF*Newton-steps/s", "value": value, "unit": "DOF*Newton-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": workload_config(w, grid),
+            "cpu_baseline": {"value": value, "unit": "DOF*Newton-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "DOF*Newton-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(w, grid):
+    from paper_2112_05051_gb300 import synth
+    return {"workload": w.name, "grid": [grid.nx, grid.ny, grid.nz], "dof": grid.n,
+            "kmean": synth.KMEAN_NAMES[w.kmean], "krylov": "%s(%d)" % (w.krylov, w.restart) if w.restart else w.krylov,
+            "vcycle": "V(%d,%d) l1-Jacobi" % (w.nu, w.nu), "amg_precision": "fp32" if w.mixed else "fp64",
+            "newton_rtol": 1e-8, "eta": 1e-7, "dt": w.dt, "schedule_steps": w.steps,
+            "l2": "working set > 129 MB L2 (7-diagonal Jacobian alone 118 MB, FGMRES basis 1 GB)"}
+
+
+def run_ours(args):
+    import torch
+    from paper_2112_05051_gb300 import richards as rb
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    lib = rb.load()
+    w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload)
+    opts = newton_opts(rb, w)
+    prec = rb.PREC_MIXED if w.mixed else rb.PREC_FP64
+    stream = torch.cuda.current_stream()
+
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
+    pd = torch.tensor(p0, device="cuda")
+    sched = lambda m: dts[m % len(dts)]
+    for m in range(args.warmup):
+        ctx.step(pd, sched(m), opts)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    import ctypes
+    lib.rich_profile_kernel.argtypes = [ctypes.c_char_p]
+    lib.rich_profile_kernel(args.roofline_kernel.encode())
+    l0 = ctypes.c_longlong()
+    lib.rich_kernel_launches(ctypes.byref(l0))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    newton_its = 0
+    lin_its = 0
+    stats = []
+    for m in range(args.warmup, args.warmup + args.steps):
+        st = ctx.step(pd, sched(m), opts)
+        newton_its += st.newton_its
+        lin_its += st.linear_its
+        stats.append(st.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    l1 = ctypes.c_longlong()
+    lib.rich_kernel_launches(ctypes.byref(l1))
+    ms_k = ctypes.c_double()
+    n_k = ctypes.c_longlong()
+    by_k = ctypes.c_double()
+    lib.rich_profile_result(ctypes.byref(ms_k), ctypes.byref(n_k), ctypes.byref(by_k))
+    lib.rich_profile_kernel(None)
+    clocks = clk.stop()
+    work = float(grid.n) * newton_its
+    if dist:
+        t = torch.tensor([elapsed, work], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        elapsed, work = float(tmax[0]), float(t[1])
+    value = work / elapsed
+
+    # end to end through the host-buffer entry point (fresh replica of the same run)
+    e2e = None
+    if not args.no_e2e:
+        ctx2 = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
+        ph = torch.tensor(p0, dtype=torch.float64).pin_memory()
+        for m in range(args.warmup):
+            ctx2.step_host(ph, sched(m), opts)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its2 = 0
+        for m in range(args.warmup, args.warmup + args.steps):
+            its2 += ctx2.step_host(ph, sched(m), opts).newton_its
+        torch.cuda.synchronize()
+        el2 = time.perf_counter() - t0
+        work2 = float(grid.n) * its2
+        if dist:
+            t = torch.tensor([el2, work2], dtype=torch.float64, device="cuda")
+            tmax = t.clone()
+            dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+            el2, work2 = float(tmax[0]), float(t[1])
+        e2e = {"value": work2 / el2, "unit": "DOF*Newton-steps/s", "h2d_bytes_per_step": 8 * grid.n,
+               "d2h_bytes_per_step": 8 * grid.n}
+        ctx2.close()
+
+    peak, peak_kind = measured_peaks()
+    achieved = (by_k.value / (ms_k.value / 1000.0) / 1e9) if ms_k.value > 0 else None
+    per_launch_bytes = by_k.value / n_k.value if n_k.value else None
+    traffic = NCU_TRAFFIC_BYTES.get((args.workload, args.roofline_kernel))
+    roof = {"kernel": args.roofline_kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes, "launches_timed": n_k.value,
+            "avg_launch_us": 1000.0 * ms_k.value / n_k.value if n_k.value else None,
+            "kernel_share_of_step": (ms_k.value / 1000.0) / elapsed if elapsed > 0 else None}
+    line = {"metric": "DOF*Newton-steps/s", "value": value, "unit": "DOF*Newton-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, grid), "e2e": e2e,
+            "gpu_launches": int(l1.value - l0.value), "clocks": clocks, "roofline": roof,
+            "newton_its": newton_its, "linear_its": lin_its,
+            "parallelism": "replicas" if ws > 1 else "single"}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    if len(sys.argv) >= 2 and sys.argv[1] == "--oracle-sample":
+        res = oracle_sample_main(sys.argv[2], float(sys.argv[3]))
+        res.pop("step_times", None)
+        print(json.dumps(res))
+        return 0
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

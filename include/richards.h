@@ -108,7 +108,7 @@ typedef struct {
 } rich_bc;
 
 typedef struct {
-  double theta;            /* strength threshold (0.08): a_ij^2 >= theta^2 |a_ii a_jj| */
+  double theta;            /* strength threshold (0.08): a_ij^2 >= theta_l^2 |a_ii a_jj|, theta_l = theta 2^-l */
   uint64_t seed;           /* MIS-2 priority seed: key(i) = top30(splitmix64(seed^i))<<32 | i */
   int coarse_max;          /* stop coarsening below this many unknowns (2000) */
   int max_levels;          /* at most this many levels (10) */
@@ -234,6 +234,19 @@ int rich_step(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_opts* o
  * copies the result back (both copies on the context's stream). */
 int rich_step_host(rich_ctx* ctx, double* p_host, double dt, const rich_newton_opts* opts,
                    rich_step_stats* stats_host);
+
+/* ---- instrumentation ----------------------------------------------------- */
+/* Number of kernels this library has launched since it was loaded. */
+int rich_kernel_launches(long long* out);
+/* Time every launch of the kernel called name (NULL disables) with CUDA events
+ * on its launching stream, from now until the next call.  Names: "residual",
+ * "assemble", "stencil_spmv", "l1jacobi_l0", "l1jacobi", "csr_resid",
+ * "restrict", "prolong", "coarse_gemv", "multidot", "multiaxpy", "fcg_update",
+ * "spgemm_numeric". */
+int rich_profile_kernel(const char* name);
+/* Sum of the recorded launch durations (ms), number of recorded launches and
+ * the algorithmic bytes those launches must move (synchronises the events). */
+int rich_profile_result(double* ms_total, long long* launches, double* bytes_total);
 
 /* Default option structs (as listed in the comments above). */
 void rich_default_newton_opts(rich_newton_opts* o);

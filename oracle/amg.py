@@ -7,8 +7,13 @@ matrix, with an l1-Jacobi smoother.  The paper names these pieces without
 formulas; the oracle fixes them as follows (each reading is listed in the
 design notes):
 
-  strength     j != i is strong for i iff a_ij^2 >= theta^2 |a_ii a_jj|,
-               symmetrised (strong if either direction is), theta = 0.08.
+  strength     j != i is strong for i iff a_ij^2 >= theta_l^2 |a_ii a_jj|,
+               symmetrised (strong if either direction is); theta_l =
+               theta 2^-l on level l (theta = 0.08).  A constant threshold
+               leaves most couplings of the smoothed-aggregation coarse
+               operators weak, the aggregates there shrink to 1-3 nodes and
+               the operator complexity explodes (about 27 at 40^3); halving
+               it per level keeps it near 3.
   priority     key(i) = (top 30 bits of splitmix64(seed ^ i)) << 32 | i;
                splitmix64 is the published SplitMix64 finaliser (Steele, Lea
                and Flood 2014).  Larger key wins; keys are distinct.
@@ -217,7 +222,7 @@ def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8):
         n = lv.A.shape[0]
         if n < coarse_max or len(levels) >= max_levels:
             break
-        S = strength(lv.A, theta)
+        S = strength(lv.A, theta * 0.5 ** (len(levels) - 1))
         keys = priority_keys(n, seed)
         state, rounds = mis2(S, keys)
         agg, nc = aggregate(S, state, keys)

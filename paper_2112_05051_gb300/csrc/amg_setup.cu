@@ -1,7 +1,938 @@
+// Smoothed-aggregation AMG setup on the GPU (Sec. 5.2: DSVMB-style decoupled
+// smoothed aggregation; on one GPU the whole domain is one block).
+//
+//   strength   j != i strong iff max(a_ij^2, a_ji^2) >= theta_l^2 |a_ii a_jj|
+//              (symmetrised; a_ji found by binary search, the pattern is symmetric),
+//              theta_l = theta 2^-l on level l
+//              (a constant threshold lets the coarse-operator density explode)
+//   MIS-2      synchronous rounds over 64-bit tuples (state << 62 | key),
+//              key(i) = top30(splitmix64(seed ^ i)) << 32 | i; two 1-hop max passes
+//   aggregates roots numbered by an exclusive scan; pass 1 joins the strong
+//              root neighbour of largest key, pass 2 the pass-1 neighbour whose
+//              root has the largest key
+//   P          (I - omega D^-1 A) P_tent, omega = 4/(3 max_i sum_j|a_ij|/|a_ii|)
+//   Galerkin   A_c = R (A P), R = P^T
+// Sparse products are row-wise expand-sort-compress: one warp per output row
+// sorts 64-bit keys (column << 32 | product index) with a bitonic network and
+// sums each column's products in product order, so patterns are structural
+// and values deterministic.  The numeric refresh recomputes values on the kept
+// patterns with one thread per row in the same product order.
 #include "common.cuh"
+
 namespace rich {
-int amg_build(rich_ctx* c, const rich_amg_opts* o) { return RICH_ESTATE; }
-int amg_refresh(rich_ctx* c) { return RICH_ESTATE; }
-int amg_update_fine(rich_ctx* c) { return RICH_ESTATE; }
-void amg_free(rich_ctx* c) {}
+
+// ---------------------------------------------------------------- priorities
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
 }
+
+__device__ __forceinline__ uint64_t prio_key(uint64_t seed, long long i) {
+  uint64_t pi = splitmix64(seed ^ (uint64_t)i);
+  return ((pi >> 34) << 32) | (uint64_t)i;
+}
+
+constexpr uint64_t kStateShift = 62;
+constexpr uint64_t kUndecided = 1;
+constexpr uint64_t kIn = 2;
+constexpr uint64_t kLow32 = 0xFFFFFFFFull;
+constexpr uint64_t kKeyMask = (1ull << 62) - 1;
+
+// ---------------------------------------------------------------- small kernels
+
+__global__ void k_diag(int n, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                       double* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+      if (col[e] == i) v = val[e];
+    d[i] = v;
+  }
+}
+
+__device__ __forceinline__ int find_col(const int* __restrict__ col, int lo, int hi, int key) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (col[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool strong_sym(int i, int e, const int* __restrict__ rp, const int* __restrict__ col,
+                                           const double* __restrict__ val, const double* __restrict__ d,
+                                           double theta2) {
+  int j = col[e];
+  if (j == i) return false;
+  double rhs = theta2 * fabs(d[i] * d[j]);
+  double a = val[e];
+  if (a * a >= rhs) return true;
+  int q = find_col(col, rp[j], rp[j + 1], i);
+  if (q < rp[j + 1] && col[q] == i) {
+    double b = val[q];
+    if (b * b >= theta2 * fabs(d[j] * d[i])) return true;
+  }
+  return false;
+}
+
+__global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ d, double theta2,
+                           const int* __restrict__ srp, int* __restrict__ cnt, int* __restrict__ scol) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int o = srp ? srp[i] : 0;
+    int c = 0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      if (strong_sym(i, e, rp, col, val, d, theta2)) {
+        if (scol) scol[o + c] = col[e];
+        ++c;
+      }
+    }
+    if (cnt) cnt[i] = c;
+  }
+}
+
+__global__ void k_mis_init(int n, uint64_t seed, uint64_t* __restrict__ t) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    t[i] = (kUndecided << kStateShift) | prio_key(seed, i);
+}
+
+// m[i] = max of v over the closed strength neighbourhood of i
+__global__ void k_max_closed(int n, const int* __restrict__ srp, const int* __restrict__ scol,
+                             const uint64_t* __restrict__ v, uint64_t* __restrict__ m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint64_t best = v[i];
+    for (int e = srp[i]; e < srp[i + 1]; ++e) {
+      uint64_t w = v[scol[e]];
+      best = w > best ? w : best;
+    }
+    m[i] = best;
+  }
+}
+
+// second 1-hop pass and the state update of one MIS-2 round
+__global__ void k_mis_update(int n, const int* __restrict__ srp, const int* __restrict__ scol,
+                             const uint64_t* __restrict__ m1, uint64_t* __restrict__ t, int* __restrict__ undecided) {
+  int any = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint64_t ti = t[i];
+    if ((ti >> kStateShift) != kUndecided) continue;
+    uint64_t best = m1[i];
+    for (int e = srp[i]; e < srp[i + 1]; ++e) {
+      uint64_t w = m1[scol[e]];
+      best = w > best ? w : best;
+    }
+    if (best == ti) {
+      t[i] = (kIn << kStateShift) | (ti & kKeyMask);
+    } else if ((best >> kStateShift) == kIn) {
+      t[i] = ti & kKeyMask;  // OUT = 0
+    } else {
+      any = 1;
+    }
+  }
+  if (any) atomicOr(undecided, 1);
+}
+
+__global__ void k_is_root(int n, const uint64_t* __restrict__ t, int* __restrict__ isroot) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    isroot[i] = (t[i] >> kStateShift) == kIn ? 1 : 0;
+}
+
+__global__ void k_rootval(int n, const uint64_t* __restrict__ t, uint64_t* __restrict__ rv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint64_t ti = t[i];
+    rv[i] = (ti >> kStateShift) == kIn ? (ti & kKeyMask) + 1 : 0;
+  }
+}
+
+// pass 1 result: agg (or -1) and the root index of pass-1 nodes (-1 otherwise)
+__global__ void k_agg_pass1(int n, const uint64_t* __restrict__ t, const uint64_t* __restrict__ best,
+                            const int* __restrict__ aggid, int* __restrict__ agg, int* __restrict__ p1root) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bool root = (t[i] >> kStateShift) == kIn;
+    p1root[i] = -1;
+    if (root) {
+      agg[i] = aggid[i];
+    } else if (best[i] > 0) {
+      int r = (int)((best[i] - 1) & kLow32);
+      agg[i] = aggid[r];
+      p1root[i] = r;
+    } else {
+      agg[i] = -1;
+    }
+  }
+}
+
+__global__ void k_val2(int n, const uint64_t* __restrict__ t, const int* __restrict__ p1root, uint64_t* __restrict__ v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int r = p1root[i];
+    v[i] = r >= 0 ? (t[r] & kKeyMask) + 1 : 0;
+  }
+}
+
+__global__ void k_agg_pass2(int n, const uint64_t* __restrict__ best2, const int* __restrict__ aggid,
+                            int* __restrict__ agg, int* __restrict__ unassigned) {
+  int miss = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (agg[i] >= 0) continue;
+    if (best2[i] > 0) agg[i] = aggid[(int)((best2[i] - 1) & kLow32)];
+    else miss = 1;
+  }
+  if (miss) atomicOr(unassigned, 1);
+}
+
+__global__ void k_rowratio(int n, const int* __restrict__ rp, const double* __restrict__ val,
+                           const double* __restrict__ d, double* __restrict__ partials) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s += fabs(val[e]);
+    double r = s / fabs(d[i]);
+    m = (r > m || r != r) ? r : m;
+  }
+  m = block_max(m);
+  if (threadIdx.x == 0) partials[blockIdx.x] = m;
+}
+
+// S = I - omega D^-1 A on the pattern of A (same operation order as the oracle)
+__global__ void k_smoother_vals(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ d, double omega,
+                                double* __restrict__ sval) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) sval[e] = -omega * val[e] / d[i] + (col[e] == i ? 1.0 : 0.0);
+}
+
+__global__ void k_seq(int n, int* __restrict__ a) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+__global__ void k_fill(long long n, double v, double* __restrict__ a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+__global__ void k_l1dinv(int n, const int* __restrict__ rp, const double* __restrict__ val, double* __restrict__ dinv,
+                         float* __restrict__ dinv32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s += fabs(val[e]);
+    double r = 1.0 / s;
+    dinv[i] = r;
+    if (dinv32) dinv32[i] = (float)r;
+  }
+}
+
+__global__ void k_cast(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------- transpose
+
+__global__ void k_tr_count(int n, const int* __restrict__ rp, const int* __restrict__ col, int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) atomicAdd(&cnt[col[e]], 1);
+}
+
+__global__ void k_tr_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                          const double* __restrict__ val, const int* __restrict__ trp, int* __restrict__ fillc,
+                          int* __restrict__ tcol, double* __restrict__ tval) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      int J = col[e];
+      int pos = trp[J] + atomicAdd(&fillc[J], 1);
+      tcol[pos] = i;
+      tval[pos] = val[e];
+    }
+}
+
+// ---------------------------------------------------------------- expand-sort-compress SpGEMM
+
+__global__ void k_spgemm_upper(int n, const int* __restrict__ arp, const int* __restrict__ acol,
+                               const int* __restrict__ brp, int* __restrict__ u) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    long long s = 0;
+    for (int e = arp[i]; e < arp[i + 1]; ++e) s += brp[acol[e] + 1] - brp[acol[e]];
+    u[i] = s > 2147483647LL ? 2147483647 : (int)s;
+  }
+}
+
+__global__ void k_max_int(int n, const int* __restrict__ a, int* __restrict__ out) {
+  int m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, a[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t* keys, int M, int lane) {
+  for (int k = 2; k <= M; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < M; t += 32) {
+        int ixj = t ^ j;
+        if (ixj > t) {
+          uint64_t a = keys[t], b = keys[ixj];
+          bool asc = (t & k) == 0;
+          if ((a > b) == asc) {
+            keys[t] = b;
+            keys[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+constexpr int kEscWarps = 2;     // warps per block of the shared-memory ESC kernel
+constexpr int kEscCap = 1024;    // products per warp held in shared memory
+
+// mode 0: cnt[row] = number of distinct columns; mode 1: write the compressed row at crp[row].
+// Rows whose product count exceeds cap are skipped unless gkeys is given (global-scratch pass,
+// where goff[row] is the row's scratch offset and big rows only are processed).
+__global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* __restrict__ acol,
+                             const double* __restrict__ aval, const int* __restrict__ brp,
+                             const int* __restrict__ bcol, const double* __restrict__ bval,
+                             const int* __restrict__ u, int mode, const int* __restrict__ crp,
+                             int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt,
+                             uint64_t* __restrict__ gkeys, double* __restrict__ gvals,
+                             const long long* __restrict__ goff) {
+  extern __shared__ unsigned char smem[];
+  int wpb = blockDim.x >> 5;
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* skeys = reinterpret_cast<uint64_t*>(smem) + (size_t)w * kEscCap;
+  double* svals = reinterpret_cast<double*>(smem + (size_t)wpb * kEscCap * sizeof(uint64_t)) + (size_t)w * kEscCap;
+  for (int row = blockIdx.x * wpb + w; row < nrows; row += gridDim.x * wpb) {
+    int ur = u[row];
+    bool big = ur > kEscCap;
+    if (gkeys ? !big : big) continue;
+    uint64_t* keys = gkeys ? gkeys + goff[row] : skeys;
+    double* vals = gkeys ? gvals + goff[row] : svals;
+    int M = 1;
+    while (M < ur) M <<= 1;
+    // expand in product order: A entries in column order, then B entries in column order
+    int t0 = 0;
+    for (int e = arp[row]; e < arp[row + 1]; ++e) {
+      int j = acol[e];
+      double a = aval ? aval[e] : 1.0;
+      int b0 = brp[j], len = brp[j + 1] - b0;
+      for (int q = lane; q < len; q += 32) {
+        int t = t0 + q;
+        keys[t] = ((uint64_t)(uint32_t)bcol[b0 + q] << 32) | (uint32_t)t;
+        vals[t] = a * (bval ? bval[b0 + q] : 1.0);
+      }
+      t0 += len;
+    }
+    for (int t = ur + lane; t < M; t += 32) keys[t] = ~0ull;
+    __syncwarp();
+    warp_bitonic_sort(keys, M, lane);
+    // segment heads
+    int base = (mode == 1) ? crp[row] : 0;
+    int running = 0;
+    for (int t0s = 0; t0s < ur; t0s += 32) {
+      int t = t0s + lane;
+      bool head = false;
+      uint32_t c = 0;
+      if (t < ur) {
+        c = (uint32_t)(keys[t] >> 32);
+        head = (t == 0) || ((uint32_t)(keys[t - 1] >> 32) != c);
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, head);
+      if (mode == 1 && head) {
+        int pos = base + running + __popc(mask & ((1u << lane) - 1));
+        double s = 0.0;
+        for (int q = t; q < ur && (uint32_t)(keys[q] >> 32) == c; ++q) s += vals[(uint32_t)(keys[q] & kLow32)];
+        ccol[pos] = (int)c;
+        cval[pos] = s;
+      }
+      running += __popc(mask);
+    }
+    if (mode == 0 && lane == 0) cnt[row] = running;
+    __syncwarp();
+  }
+}
+
+// Values of C = A B on C's known pattern; one thread per row, products in the ESC order.
+__global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const int* __restrict__ acol,
+                                 const double* __restrict__ aval, const int* __restrict__ brp,
+                                 const int* __restrict__ bcol, const double* __restrict__ bval,
+                                 const int* __restrict__ crp, const int* __restrict__ ccol,
+                                 double* __restrict__ cval) {
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += gridDim.x * blockDim.x) {
+    int c0 = crp[row], c1 = crp[row + 1];
+    for (int q = c0; q < c1; ++q) cval[q] = 0.0;
+    for (int e = arp[row]; e < arp[row + 1]; ++e) {
+      int j = acol[e];
+      double a = aval[e];
+      for (int f = brp[j]; f < brp[j + 1]; ++f) {
+        int pos = find_col(ccol, c0, c1, bcol[f]);
+        cval[pos] += a * bval[f];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- coarsest level: dense inverse
+
+__global__ void k_csr_to_dense(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ dense) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int j = 0; j < n; ++j) dense[(long long)i * n + j] = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) dense[(long long)i * n + col[e]] = val[e];
+  }
+}
+
+__global__ void k_gj_prepare(int n, const double* __restrict__ a, double* __restrict__ buf) {
+  // buf[0..n): row 0, buf[n..2n): column 0 (parity 0 buffers)
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    buf[t] = a[t];
+    buf[n + t] = a[(long long)t * n];
+  }
+}
+
+// One Gauss-Jordan pivot step (no pivoting: the matrix is SPD).  Row k and column k
+// before the step come from the parity buffer; the updated row/column k+1 are
+// written to the other parity buffer for the next step.
+__global__ void k_gj_step(int n, int k, double* __restrict__ a, double* __restrict__ buf) {
+  const double* rowk = buf + (k & 1) * 2 * n;
+  const double* colk = rowk + n;
+  double* rown = buf + ((k + 1) & 1) * 2 * n;
+  double* coln = rown + n;
+  double piv = rowk[k];
+  long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t / n), j = (int)(t % n);
+    double v;
+    if (i == k && j == k) v = 1.0 / piv;
+    else if (i == k) v = rowk[j] / piv;
+    else if (j == k) v = -colk[i] / piv;
+    else v = a[t] - colk[i] * rowk[j] / piv;
+    a[t] = v;
+    if (j == k + 1) coln[i] = v;
+    if (i == k + 1) rown[j] = v;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C) {
+  int n = A.nrows;
+  C.nrows = n;
+  C.ncols = B.ncols;
+  int* u = nullptr;
+  int* cnt = nullptr;
+  RICH_CHECK(dalloc(&u, n));
+  RICH_CHECK(dalloc(&cnt, n));
+  RICH_CHECK(dalloc(&C.rowptr, (long long)n + 1));
+  k_spgemm_upper<<<grid_for(n), kBlock, 0, c->st>>>(n, A.rowptr, A.col, B.rowptr, u);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
+  k_max_int<<<grid_for(n), kBlock, 0, c->st>>>(n, u, c->iflag);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  int umax = c->hflag[0];
+  if (umax >= (1 << 30)) return RICH_ELIMIT;
+  size_t smem = (size_t)kEscWarps * kEscCap * (sizeof(uint64_t) + sizeof(double));
+  int nblk = (n + kEscWarps - 1) / kEscWarps;
+  if (nblk > 65535 * 4) nblk = 65535 * 4;
+  // global scratch for rows beyond the shared-memory capacity
+  uint64_t* gk = nullptr;
+  double* gv = nullptr;
+  long long* goff = nullptr;
+  long long* gsz = nullptr;
+  bool need_global = umax > kEscCap;
+  if (need_global) {
+    std::vector<int> hu(n);
+    RICH_CUDA(cudaMemcpy(hu.data(), u, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    std::vector<long long> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      long long M = 0;
+      if (hu[i] > kEscCap) {
+        M = 1;
+        while (M < hu[i]) M <<= 1;
+      }
+      off[i + 1] = off[i] + M;
+    }
+    RICH_CHECK(dalloc(&goff, n + 1));
+    RICH_CUDA(cudaMemcpy(goff, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    RICH_CHECK(dalloc(&gk, off[n]));
+    RICH_CHECK(dalloc(&gv, off[n]));
+  }
+  for (int mode = 0; mode < 2; ++mode) {
+    if (mode == 1) {
+      RICH_CHECK(scan_exclusive_int(c, cnt, C.rowptr, n));
+      int nnz = 0;
+      RICH_CUDA(cudaMemcpy(&nnz, C.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+      C.nnz = nnz;
+      RICH_CHECK(dalloc(&C.col, nnz));
+      RICH_CHECK(dalloc(&C.val, nnz));
+    }
+    k_spgemm_esc<<<nblk, 32 * kEscWarps, smem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
+                                                       C.rowptr, C.col, C.val, cnt, nullptr, nullptr, nullptr);
+    RICH_LAUNCH_CHECK();
+    if (need_global) {
+      k_spgemm_esc<<<grid_for(n, 32), 32, 0, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
+                                                     C.rowptr, C.col, C.val, cnt, gk, gv, goff);
+      RICH_LAUNCH_CHECK();
+    }
+  }
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  dfree(u);
+  dfree(cnt);
+  dfree(gk);
+  dfree(gv);
+  dfree(goff);
+  dfree(gsz);
+  return RICH_OK;
+}
+
+static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C) {
+  ProfScope ps("spgemm_numeric", c->st, (double)A.nrows * 4 + A.nnz * 12.0 + (double)C.nrows * 4 + C.nnz * 12.0);
+  k_spgemm_numeric<<<grid_for(A.nrows, 128), 128, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                              B.val, C.rowptr, C.col, C.val);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+static void csr_free(Csr<double>& m, bool pattern = true) {
+  if (pattern) {
+    dfree(m.rowptr);
+    dfree(m.col);
+  }
+  dfree(m.val);
+  m.nnz = 0;
+}
+
+static int identity_csr(rich_ctx* c, int m, Csr<double>& I) {
+  I.nrows = I.ncols = m;
+  I.nnz = m;
+  RICH_CHECK(dalloc(&I.rowptr, (long long)m + 1));
+  RICH_CHECK(dalloc(&I.col, m));
+  I.val = nullptr;  // treated as all-ones by the ESC kernel
+  k_seq<<<grid_for(m + 1), kBlock, 0, c->st>>>(m, I.rowptr);
+  RICH_LAUNCH_CHECK();
+  k_seq<<<grid_for(m), kBlock, 0, c->st>>>(m - 1, I.col);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+// R = P^T with sorted columns (atomic placement, then a sort through R_unsorted * I)
+static int transpose(rich_ctx* c, const Csr<double>& P, Csr<double>& R) {
+  int n = P.nrows, m = P.ncols;
+  Csr<double> T;
+  T.nrows = m;
+  T.ncols = n;
+  T.nnz = P.nnz;
+  int* cnt = nullptr;
+  int* fillc = nullptr;
+  RICH_CHECK(dalloc(&cnt, m));
+  RICH_CHECK(dalloc(&fillc, m));
+  RICH_CHECK(dalloc(&T.rowptr, (long long)m + 1));
+  RICH_CHECK(dalloc(&T.col, P.nnz));
+  RICH_CHECK(dalloc(&T.val, P.nnz));
+  RICH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * m, c->st));
+  RICH_CUDA(cudaMemsetAsync(fillc, 0, sizeof(int) * m, c->st));
+  k_tr_count<<<grid_for(n), kBlock, 0, c->st>>>(n, P.rowptr, P.col, cnt);
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(scan_exclusive_int(c, cnt, T.rowptr, m));
+  k_tr_fill<<<grid_for(n), kBlock, 0, c->st>>>(n, P.rowptr, P.col, P.val, T.rowptr, fillc, T.col, T.val);
+  RICH_LAUNCH_CHECK();
+  Csr<double> I;
+  RICH_CHECK(identity_csr(c, n, I));
+  RICH_CHECK(spgemm_symbolic(c, T, I, R));
+  csr_free(T);
+  csr_free(I);
+  dfree(cnt);
+  dfree(fillc);
+  return RICH_OK;
+}
+
+static int coarse_inverse(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  Level& L = H.lv[H.nlev - 1];
+  int n = L.n;
+  k_csr_to_dense<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, H.cdense);
+  RICH_LAUNCH_CHECK();
+  k_gj_prepare<<<grid_for(n), kBlock, 0, c->st>>>(n, H.cdense, H.cwork);
+  RICH_LAUNCH_CHECK();
+  long long nn = (long long)n * n;
+  int g = grid_for(nn);
+  if (g > 4 * kNumSM) g = 4 * kNumSM;
+  for (int k = 0; k < n; ++k) {
+    k_gj_step<<<g, kBlock, 0, c->st>>>(n, k, H.cdense, H.cwork);
+    RICH_LAUNCH_CHECK();
+  }
+  if (H.cinv32) {
+    k_cast<<<grid_for(nn), kBlock, 0, c->st>>>(nn, H.cdense, H.cinv32);
+    RICH_LAUNCH_CHECK();
+  }
+  return RICH_OK;
+}
+
+__global__ void k_stencil4(long long n, const double* __restrict__ A7, double* __restrict__ d, double* __restrict__ wx,
+                           double* __restrict__ wy, double* __restrict__ wz, float* __restrict__ d32,
+                           float* __restrict__ wx32, float* __restrict__ wy32, float* __restrict__ wz32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double a = A7[i], x = -A7[2 * n + i], y = -A7[4 * n + i], z = -A7[6 * n + i];
+    if (d) { d[i] = a; wx[i] = x; wy[i] = y; wz[i] = z; }
+    if (d32) { d32[i] = (float)a; wx32[i] = (float)x; wy32[i] = (float)y; wz32[i] = (float)z; }
+  }
+}
+
+// Finest-level stencil copy of the diffusion matrix for the V-cycle (FP64 or FP32).
+static int fine_stencil(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  long long n = c->g.n;
+  bool mp = c->prec == RICH_PREC_MIXED;
+  if (mp && !H.st32.diag) {
+    RICH_CHECK(dalloc(&H.st32.diag, n));
+    RICH_CHECK(dalloc(&H.st32.wx, n));
+    RICH_CHECK(dalloc(&H.st32.wy, n));
+    RICH_CHECK(dalloc(&H.st32.wz, n));
+  }
+  if (!mp && !H.st64.diag) {
+    RICH_CHECK(dalloc(&H.st64.diag, n));
+    RICH_CHECK(dalloc(&H.st64.wx, n));
+    RICH_CHECK(dalloc(&H.st64.wy, n));
+    RICH_CHECK(dalloc(&H.st64.wz, n));
+  }
+  k_stencil4<<<grid_for(n), kBlock, 0, c->st>>>(n, c->A7, H.st64.diag, H.st64.wx, H.st64.wy, H.st64.wz, H.st32.diag,
+                                                H.st32.wx, H.st32.wy, H.st32.wz);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+static int level_diag_data(rich_ctx* c, Level& L) {
+  bool mp = c->prec == RICH_PREC_MIXED;
+  k_l1dinv<<<grid_for(L.n), kBlock, 0, c->st>>>(L.n, L.A.rowptr, L.A.val, L.dinv, mp ? L.dinv32 : nullptr);
+  RICH_LAUNCH_CHECK();
+  if (mp) {
+    k_cast<<<grid_for(L.A.nnz), kBlock, 0, c->st>>>(L.A.nnz, L.A.val, L.A32);
+    RICH_LAUNCH_CHECK();
+  }
+  return RICH_OK;
+}
+
+static int level_alloc_vectors(rich_ctx* c, Level& L) {
+  size_t es = c->prec == RICH_PREC_MIXED ? sizeof(float) : sizeof(double);
+  long long n = L.n > 0 ? L.n : 1;
+  RICH_CUDA(cudaMalloc(&L.x, es * n));
+  RICH_CUDA(cudaMalloc(&L.b, es * n));
+  RICH_CUDA(cudaMalloc(&L.r, es * n));
+  RICH_CUDA(cudaMalloc(&L.t, es * n));
+  RICH_CHECK(dalloc(&L.dinv, n));
+  if (c->prec == RICH_PREC_MIXED) {
+    RICH_CHECK(dalloc(&L.dinv32, n));
+    RICH_CHECK(dalloc(&L.A32, L.A.nnz));
+  }
+  return RICH_OK;
+}
+
+void amg_free(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  for (int l = 0; l < (int)H.lv.size(); ++l) {
+    Level& L = H.lv[l];
+    if (l > 0) csr_free(L.A);
+    csr_free(L.P);
+    csr_free(L.R);
+    csr_free(L.AP);
+    dfree(L.A32);
+    dfree(L.dinv);
+    dfree(L.dinv32);
+    dfree(L.agg);
+    dfree(L.P32);
+    dfree(L.R32);
+    if (L.x) cudaFree(L.x);
+    if (L.b) cudaFree(L.b);
+    if (L.r) cudaFree(L.r);
+    if (L.t) cudaFree(L.t);
+  }
+  H.lv.clear();
+  H.nlev = 0;
+  dfree(H.st64.diag); dfree(H.st64.wx); dfree(H.st64.wy); dfree(H.st64.wz);
+  dfree(H.st32.diag); dfree(H.st32.wx); dfree(H.st32.wy); dfree(H.st32.wz);
+  dfree(H.cdense);
+  dfree(H.cinv32);
+  dfree(H.cwork);
+  H.built = false;
+}
+
+constexpr int kMaxCoarseDense = 8192;
+
+// Coarsen level L into a new level; returns RICH_OK with *stop = true when coarsening stops.
+static int coarsen(rich_ctx* c, int l, bool* stop) {
+  Hierarchy& H = c->H;
+  const rich_amg_opts& o = H.opts;
+  Level& L = H.lv[l];
+  int n = L.n;
+  *stop = false;
+  double* d = nullptr;
+  int* cnt = nullptr;
+  Csr<double> S;
+  RICH_CHECK(dalloc(&d, n));
+  RICH_CHECK(dalloc(&cnt, n));
+  k_diag<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d);
+  RICH_LAUNCH_CHECK();
+  double theta_l = o.theta * std::ldexp(1.0, -l);
+  double theta2 = theta_l * theta_l;
+  k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, nullptr, cnt, nullptr);
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(dalloc(&S.rowptr, (long long)n + 1));
+  RICH_CHECK(scan_exclusive_int(c, cnt, S.rowptr, n));
+  int snnz = 0;
+  RICH_CUDA(cudaMemcpy(&snnz, S.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+  RICH_CHECK(dalloc(&S.col, snnz));
+  k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, S.rowptr, nullptr, S.col);
+  RICH_LAUNCH_CHECK();
+  // MIS-2
+  uint64_t *t = nullptr, *m1 = nullptr;
+  RICH_CHECK(dalloc(&t, n));
+  RICH_CHECK(dalloc(&m1, n));
+  k_mis_init<<<grid_for(n), kBlock, 0, c->st>>>(n, o.seed, t);
+  RICH_LAUNCH_CHECK();
+  int rounds = 0;
+  for (;;) {
+    RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
+    k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, t, m1);
+    RICH_LAUNCH_CHECK();
+    k_mis_update<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, m1, t, c->iflag);
+    RICH_LAUNCH_CHECK();
+    ++rounds;
+    RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    RICH_CUDA(cudaStreamSynchronize(c->st));
+    if (!c->hflag[0]) break;
+    if (rounds > 100000) return RICH_ELIMIT;  // a round always decides the largest undecided key
+  }
+  // aggregates
+  int* isroot = cnt;
+  int* aggid = nullptr;
+  int* p1root = nullptr;
+  uint64_t* rv = m1;
+  uint64_t* best = nullptr;
+  RICH_CHECK(dalloc(&aggid, (long long)n + 1));
+  RICH_CHECK(dalloc(&p1root, n));
+  RICH_CHECK(dalloc(&best, n));
+  RICH_CHECK(dalloc(&L.agg, n));
+  k_is_root<<<grid_for(n), kBlock, 0, c->st>>>(n, t, isroot);
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(scan_exclusive_int(c, isroot, aggid, n));
+  int nc = 0;
+  RICH_CUDA(cudaMemcpy(&nc, aggid + n, sizeof(int), cudaMemcpyDeviceToHost));
+  k_rootval<<<grid_for(n), kBlock, 0, c->st>>>(n, t, rv);
+  RICH_LAUNCH_CHECK();
+  k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
+  RICH_LAUNCH_CHECK();
+  k_agg_pass1<<<grid_for(n), kBlock, 0, c->st>>>(n, t, best, aggid, L.agg, p1root);
+  RICH_LAUNCH_CHECK();
+  k_val2<<<grid_for(n), kBlock, 0, c->st>>>(n, t, p1root, rv);
+  RICH_LAUNCH_CHECK();
+  k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
+  k_agg_pass2<<<grid_for(n), kBlock, 0, c->st>>>(n, best, aggid, L.agg, c->iflag);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  bool unassigned = c->hflag[0] != 0;
+  dfree(t);
+  dfree(m1);
+  dfree(p1root);
+  dfree(best);
+  csr_free(S);
+  if (unassigned) {
+    dfree(d);
+    dfree(cnt);
+    dfree(aggid);
+    return RICH_ELIMIT;
+  }
+  L.mis_rounds = rounds;
+  if (nc > 0.8 * n || nc < 1) {  // coarsening stalled: this level becomes the coarsest
+    dfree(L.agg);
+    dfree(d);
+    dfree(cnt);
+    dfree(aggid);
+    *stop = true;
+    return RICH_OK;
+  }
+  // prolongator
+  int nb = red_grid(n);
+  k_rowratio<<<nb, kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.val, d, c->partials);
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(finish_max(c, c->partials, nb, c->dsc));
+  double rho = 0.0;
+  RICH_CHECK(fetch_scalars(c, c->dsc, 1, &rho));
+  double omega = 4.0 / (3.0 * rho);
+  L.omega = omega;
+  Csr<double> Sm;
+  Sm.nrows = Sm.ncols = n;
+  Sm.nnz = L.A.nnz;
+  Sm.rowptr = L.A.rowptr;
+  Sm.col = L.A.col;
+  RICH_CHECK(dalloc(&Sm.val, L.A.nnz));
+  k_smoother_vals<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, omega, Sm.val);
+  RICH_LAUNCH_CHECK();
+  Csr<double> Pt;
+  Pt.nrows = n;
+  Pt.ncols = nc;
+  Pt.nnz = n;
+  RICH_CHECK(dalloc(&Pt.rowptr, (long long)n + 1));
+  k_seq<<<grid_for(n + 1), kBlock, 0, c->st>>>(n, Pt.rowptr);
+  RICH_LAUNCH_CHECK();
+  Pt.col = L.agg;
+  Pt.val = nullptr;
+  RICH_CHECK(spgemm_symbolic(c, Sm, Pt, L.P));
+  dfree(Sm.val);
+  dfree(Pt.rowptr);
+  RICH_CHECK(transpose(c, L.P, L.R));
+  RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP));
+  Level nxt;
+  nxt.n = nc;
+  RICH_CHECK(spgemm_symbolic(c, L.R, L.AP, nxt.A));
+  if (c->prec == RICH_PREC_MIXED) {
+    RICH_CHECK(dalloc(&L.P32, L.P.nnz));
+    RICH_CHECK(dalloc(&L.R32, L.R.nnz));
+    k_cast<<<grid_for(L.P.nnz), kBlock, 0, c->st>>>(L.P.nnz, L.P.val, L.P32);
+    RICH_LAUNCH_CHECK();
+    k_cast<<<grid_for(L.R.nnz), kBlock, 0, c->st>>>(L.R.nnz, L.R.val, L.R32);
+    RICH_LAUNCH_CHECK();
+  }
+  dfree(d);
+  dfree(cnt);
+  dfree(aggid);
+  H.lv.push_back(nxt);
+  return RICH_OK;
+}
+
+int amg_build(rich_ctx* c, const rich_amg_opts* o) {
+  if (!c->have_jac) return RICH_ESTATE;
+  amg_free(c);
+  Hierarchy& H = c->H;
+  if (o) H.opts = *o; else rich_default_amg_opts(&H.opts);
+  if (H.opts.max_levels < 1 || H.opts.max_levels > 16 || H.opts.nu1 < 0 || H.opts.nu2 < 0 || H.opts.coarse_max < 1)
+    return RICH_EINVAL;
+  RICH_CHECK(refresh_a0_values(c));
+  Level L0;
+  L0.n = (int)c->g.n;
+  L0.A = c->A0;  // aliases the context's finest CSR
+  H.lv.push_back(L0);
+  for (;;) {
+    int l = (int)H.lv.size() - 1;
+    if (H.lv[l].n < H.opts.coarse_max || (int)H.lv.size() >= H.opts.max_levels) break;
+    bool stop = false;
+    RICH_CHECK(coarsen(c, l, &stop));
+    if (stop) break;
+  }
+  H.nlev = (int)H.lv.size();
+  H.cn = H.lv[H.nlev - 1].n;
+  if (H.cn > kMaxCoarseDense) {
+    amg_free(c);
+    return RICH_ELIMIT;
+  }
+  for (int l = 0; l < H.nlev; ++l) {
+    RICH_CHECK(level_alloc_vectors(c, H.lv[l]));
+    RICH_CHECK(level_diag_data(c, H.lv[l]));
+  }
+  RICH_CHECK(fine_stencil(c));
+  RICH_CHECK(dalloc(&H.cdense, (long long)H.cn * H.cn));
+  RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn));
+  if (c->prec == RICH_PREC_MIXED) RICH_CHECK(dalloc(&H.cinv32, (long long)H.cn * H.cn));
+  RICH_CHECK(coarse_inverse(c));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  H.built = true;
+  return RICH_OK;
+}
+
+// New finest matrix: recompute every Galerkin product on the kept patterns.
+int amg_refresh(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  if (!H.built) return RICH_ESTATE;
+  RICH_CHECK(refresh_a0_values(c));
+  H.lv[0].A = c->A0;
+  for (int l = 0; l + 1 < H.nlev; ++l) {
+    Level& L = H.lv[l];
+    RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP));
+    RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A));
+  }
+  for (int l = 0; l < H.nlev; ++l) RICH_CHECK(level_diag_data(c, H.lv[l]));
+  RICH_CHECK(fine_stencil(c));
+  return coarse_inverse(c);
+}
+
+// The paper's reuse: only the finest matrix and its smoother change.
+int amg_update_fine(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  if (!H.built) return RICH_ESTATE;
+  RICH_CHECK(refresh_a0_values(c));
+  H.lv[0].A = c->A0;
+  RICH_CHECK(level_diag_data(c, H.lv[0]));
+  RICH_CHECK(fine_stencil(c));
+  if (H.nlev == 1) return coarse_inverse(c);
+  return RICH_OK;
+}
+
+}  // namespace rich
+
+using namespace rich;
+
+extern "C" {
+
+int amg_setup(rich_ctx* c, const rich_amg_opts* o, rich_amg_info* info) {
+  if (!c) return RICH_EINVAL;
+  RICH_CHECK(amg_build(c, o));
+  if (info) {
+    Hierarchy& H = c->H;
+    memset(info, 0, sizeof(*info));
+    info->levels = H.nlev;
+    long long tot = 0;
+    for (int l = 0; l < H.nlev && l < 16; ++l) {
+      info->n[l] = H.lv[l].n;
+      info->nnz[l] = H.lv[l].A.nnz;
+      info->mis_rounds[l] = H.lv[l].mis_rounds;
+      info->omega[l] = H.lv[l].omega;
+      tot += H.lv[l].A.nnz;
+    }
+    info->operator_complexity = (double)tot / (double)H.lv[0].A.nnz;
+  }
+  return RICH_OK;
+}
+
+int amg_update(rich_ctx* c, int policy) {
+  if (!c) return RICH_EINVAL;
+  if (policy == RICH_AMG_SETUP_ONCE) return amg_update_fine(c);
+  if (policy == RICH_AMG_REFRESH) return amg_refresh(c);
+  return RICH_EINVAL;
+}
+
+int amg_export_level(rich_ctx* c, int level, int* agg, int* rp, int* col, double* val) {
+  if (!c) return RICH_EINVAL;
+  Hierarchy& H = c->H;
+  if (!H.built) return RICH_ESTATE;
+  if (level < 0 || level >= H.nlev) return RICH_EINVAL;
+  Level& L = H.lv[level];
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  if (agg) {
+    if (!L.agg) return RICH_EINVAL;
+    RICH_CUDA(cudaMemcpy(agg, L.agg, sizeof(int) * L.n, cudaMemcpyDeviceToHost));
+  }
+  if (rp) RICH_CUDA(cudaMemcpy(rp, L.A.rowptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
+  if (col) RICH_CUDA(cudaMemcpy(col, L.A.col, sizeof(int) * L.A.nnz, cudaMemcpyDeviceToHost));
+  if (val) RICH_CUDA(cudaMemcpy(val, L.A.val, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost));
+  return RICH_OK;
+}
+
+int amg_export_prolongator(rich_ctx* c, int level, long long* nnz, int* rp, int* col, double* val) {
+  if (!c) return RICH_EINVAL;
+  Hierarchy& H = c->H;
+  if (!H.built) return RICH_ESTATE;
+  if (level < 0 || level + 1 >= H.nlev) return RICH_EINVAL;
+  Level& L = H.lv[level];
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  if (nnz) *nnz = L.P.nnz;
+  if (rp) RICH_CUDA(cudaMemcpy(rp, L.P.rowptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
+  if (col) RICH_CUDA(cudaMemcpy(col, L.P.col, sizeof(int) * L.P.nnz, cudaMemcpyDeviceToHost));
+  if (val) RICH_CUDA(cudaMemcpy(val, L.P.val, sizeof(double) * L.P.nnz, cudaMemcpyDeviceToHost));
+  return RICH_OK;
+}
+
+}  // extern "C"

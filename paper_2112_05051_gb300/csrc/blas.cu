@@ -3,7 +3,41 @@
 // partials in block order, so FP64 results reproduce bit for bit run to run.
 #include "common.cuh"
 
+#include <atomic>
+#include <string>
+
 namespace rich {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- live kernel timing
+
+constexpr int kProfEvents = 16384;
+static std::string g_prof_target;
+static std::vector<cudaEvent_t> g_prof_ev;
+static int g_prof_n = 0;          // recorded launch pairs
+static long long g_prof_seen = 0; // launches of the target (recorded or not)
+static double g_prof_bytes = 0.0;
+
+ProfScope::ProfScope(const char* name, cudaStream_t s, double b) : on(false), st(s), bytes(b) {
+  if (g_prof_target.empty() || g_prof_target != name) return;
+  ++g_prof_seen;
+  if (g_prof_n >= kProfEvents / 2) return;
+  if (g_prof_ev.empty()) {
+    g_prof_ev.resize(kProfEvents);
+    for (auto& e : g_prof_ev) cudaEventCreate(&e);
+  }
+  on = true;
+  cudaEventRecord(g_prof_ev[2 * g_prof_n], st);
+}
+
+ProfScope::~ProfScope() {
+  if (!on) return;
+  cudaEventRecord(g_prof_ev[2 * g_prof_n + 1], st);
+  g_prof_bytes += bytes;
+  ++g_prof_n;
+}
 
 __global__ void k_finish_sums(const double* __restrict__ partials, int nb, int nq, double* __restrict__ dst) {
   for (int q = 0; q < nq; ++q) {
@@ -175,3 +209,36 @@ int scan_exclusive_ll(rich_ctx* c, const long long* in, long long* out, long lon
 }
 
 }  // namespace rich
+
+extern "C" {
+
+int rich_kernel_launches(long long* out) {
+  if (!out) return RICH_EINVAL;
+  *out = rich::g_launches.load();
+  return RICH_OK;
+}
+
+int rich_profile_kernel(const char* name) {
+  rich::g_prof_target = name ? name : "";
+  rich::g_prof_n = 0;
+  rich::g_prof_seen = 0;
+  rich::g_prof_bytes = 0.0;
+  return RICH_OK;
+}
+
+int rich_profile_result(double* ms_total, long long* launches, double* bytes_total) {
+  if (!ms_total || !launches || !bytes_total) return RICH_EINVAL;
+  double ms = 0.0;
+  for (int i = 0; i < rich::g_prof_n; ++i) {
+    cudaEventSynchronize(rich::g_prof_ev[2 * i + 1]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, rich::g_prof_ev[2 * i], rich::g_prof_ev[2 * i + 1]);
+    ms += t;
+  }
+  *ms_total = ms;
+  *launches = rich::g_prof_n;
+  *bytes_total = rich::g_prof_bytes;
+  return RICH_OK;
+}
+
+}  // extern "C"

@@ -35,7 +35,23 @@ void set_cuda_error(cudaError_t e, const char* where);
     if (s_ != RICH_OK) return s_;        \
   } while (0)
 
-#define RICH_LAUNCH_CHECK() RICH_CUDA(cudaGetLastError())
+// Every kernel launch is followed by RICH_LAUNCH_CHECK, which also counts it.
+void count_launch();
+#define RICH_LAUNCH_CHECK()        \
+  do {                             \
+    ::rich::count_launch();        \
+    RICH_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// Optional live timing of one named kernel: when its name matches the profiling
+// target, CUDA events are recorded around its launches on the launching stream.
+struct ProfScope {
+  bool on;
+  cudaStream_t st;
+  double bytes;
+  ProfScope(const char* name, cudaStream_t s, double algorithmic_bytes);
+  ~ProfScope();
+};
 
 inline int grid_for(long long n, int block = kBlock) {
   long long g = (n + block - 1) / block;
@@ -96,7 +112,20 @@ struct Level {
   void* t = nullptr;
 };
 
+// Finest level of the V-cycle in stencil form: the diffusion matrix is symmetric
+// with non-negative face weights w (coupling -w), so four arrays hold it:
+// diagonal, and the +x, +y, +z face weights of each cell (0 on the boundary).
+template <class T>
+struct Stencil4 {
+  T* diag = nullptr;
+  T* wx = nullptr;
+  T* wy = nullptr;
+  T* wz = nullptr;
+};
+
 struct Hierarchy {
+  Stencil4<double> st64;
+  Stencil4<float> st32;
   std::vector<Level> lv;
   int nlev = 0;
   int cn = 0;                     // coarsest size

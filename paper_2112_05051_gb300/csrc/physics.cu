@@ -236,8 +236,11 @@ int constit_eval(rich_ctx* c, const double* p) {
 int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms) {
   RICH_CHECK(constit_eval(c, p));
   int nb = red_grid(c->g.n);
-  k_residual<<<nb, kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->S, s_old, c->ks, dt, F,
-                                       c->partials);
+  {
+    ProfScope ps("residual", c->st, (double)c->g.n * (32.0 + (c->ks ? 8.0 : 0.0)));
+    k_residual<<<nb, kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->S, s_old, c->ks, dt, F,
+                                         c->partials);
+  }
   RICH_LAUNCH_CHECK();
   if (want_norms) {
     RICH_CHECK(finish_sums(c, c->partials, nb, 1, c->dsc + 0));
@@ -248,8 +251,11 @@ int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, 
 
 int jacobian_eval(rich_ctx* c, const double* p, double dt) {
   RICH_CHECK(constit_eval(c, p));
-  k_assemble<<<grid_for(c->g.n), kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->dK, c->dS, c->ks,
-                                                    dt, c->J7, c->A7);
+  {
+    ProfScope ps("assemble", c->st, (double)c->g.n * (8.0 + (c->ks ? 8.0 : 0.0) + 14 * 8.0));
+    k_assemble<<<grid_for(c->g.n), kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->dK, c->dS,
+                                                      c->ks, dt, c->J7, c->A7);
+  }
   RICH_LAUNCH_CHECK();
   c->have_jac = true;
   c->a0_fresh = false;
@@ -257,6 +263,7 @@ int jacobian_eval(rich_ctx* c, const double* p, double dt) {
 }
 
 int stencil_apply(rich_ctx* c, const double* A7, const double* x, double* y) {
+  ProfScope ps("stencil_spmv", c->st, (double)c->g.n * 72.0);
   k_stencil_spmv<<<grid_for(c->g.n), kBlock, 0, c->st>>>(c->g, A7, x, y);
   RICH_LAUNCH_CHECK();
   return RICH_OK;

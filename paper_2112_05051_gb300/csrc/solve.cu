@@ -1,15 +1,697 @@
+// V-cycle (eq. (Vcycle), Sec. 5.2), flexible Krylov solvers for the right-
+// preconditioned Newton system (eq. (precsystem), Sec. 3) and the inexact
+// Newton-Armijo backward-Euler step (Sec. 3).
+//
+// V-cycle on level l with zero initial guess: nu1 l1-Jacobi sweeps
+// x <- x + D_l1^-1 (b - A x), residual r = b - A x, b_{l+1} = R r, recursion
+// (the coarsest level multiplies by its dense inverse), x <- x + P x_{l+1},
+// nu2 sweeps.  In MIXED precision every level works in FP32 with FP32
+// accumulation; the Krylov vectors and dot products stay FP64.
+//
+// Krylov scalars live in device memory; each iteration reads one small block
+// of them back for the convergence test.
+#include <algorithm>
+
 #include "common.cuh"
+
 namespace rich {
-int vcycle_apply(rich_ctx* c, const double* r, double* z) { return RICH_ESTATE; }
-int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) { return RICH_ESTATE; }
+
+// ---------------------------------------------------------------- V-cycle kernels (T = double | float)
+
+template <class T>
+__global__ void k_jacobi0(int n, const T* __restrict__ dinv, const T* __restrict__ b, T* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = dinv[i] * b[i];
 }
+
+template <class T>
+__global__ void k_jacobi(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+                         const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+                         T* __restrict__ xo) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T s = b[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s -= val[e] * x[col[e]];
+    xo[i] = x[i] + dinv[i] * s;
+  }
+}
+
+template <class T>
+__global__ void k_resid(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+                        const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T s = b[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s -= val[e] * x[col[e]];
+    r[i] = s;
+  }
+}
+
+template <class T>
+__global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+                       const T* __restrict__ x, T* __restrict__ y, int add) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T s = add ? y[i] : T(0);
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s += val[e] * x[col[e]];
+    y[i] = s;
+  }
+}
+
+// x = M b for a dense row-major n x n matrix; one warp per row.
+template <class T>
+__global__ void k_gemv(int n, const T* __restrict__ M, const T* __restrict__ b, T* __restrict__ x) {
+  int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    T s = 0;
+    for (int j = lane; j < n; j += 32) s += M[(long long)row * n + j] * b[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = s;
+  }
+}
+
+__global__ void k_d2f(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// Finest-level l1-Jacobi sweep and residual on the stencil form.  The l1 row norm
+// is diag + sum of the six face weights (all couplings are -w with w >= 0).
+// mode 0: xo = D_l1^-1 b (first sweep from x = 0); 1: xo = x + D_l1^-1 (b - A x);
+// 2: xo = b - A x (residual).
+template <class T, int MODE>
+__global__ void k_st_smooth(GridP g, Stencil4<T> A, const T* __restrict__ b, const T* __restrict__ x,
+                            T* __restrict__ xo) {
+  long long n = g.n;
+  long long sxy = (long long)g.nx * g.ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(c % g.nx);
+    long long r = c / g.nx;
+    int j = (int)(r % g.ny);
+    int k = (int)(r / g.ny);
+    T wxp = A.wx[c], wyp = A.wy[c], wzp = A.wz[c];
+    T wxm = i > 0 ? A.wx[c - 1] : T(0);
+    T wym = j > 0 ? A.wy[c - g.nx] : T(0);
+    T wzm = k > 0 ? A.wz[c - sxy] : T(0);
+    T d = A.diag[c];
+    if (MODE == 0) {
+      T l1 = d + ((wxm + wxp) + (wym + wyp) + (wzm + wzp));
+      xo[c] = b[c] / l1;
+      continue;
+    }
+    T xc = x[c];
+    T ax = d * xc;
+    if (i > 0) ax -= wxm * x[c - 1];
+    if (i < g.nx - 1) ax -= wxp * x[c + 1];
+    if (j > 0) ax -= wym * x[c - g.nx];
+    if (j < g.ny - 1) ax -= wyp * x[c + g.nx];
+    if (k > 0) ax -= wzm * x[c - sxy];
+    if (k < g.nz - 1) ax -= wzp * x[c + sxy];
+    if (MODE == 2) {
+      xo[c] = b[c] - ax;
+    } else {
+      T l1 = d + ((wxm + wxp) + (wym + wyp) + (wzm + wzp));
+      xo[c] = xc + (b[c] - ax) / l1;
+    }
+  }
+}
+
+template <class T>
+static const Stencil4<T>& fine(rich_ctx* c);
+template <>
+const Stencil4<double>& fine<double>(rich_ctx* c) { return c->H.st64; }
+template <>
+const Stencil4<float>& fine<float>(rich_ctx* c) { return c->H.st32; }
+
+template <class T>
+struct LevelView {
+  int n;
+  const int *rp, *col;
+  const T* val;
+  const T* dinv;
+  const int *prp, *pcol, *rrp, *rcol;
+  const T *pval, *rval;
+};
+
+template <class T>
+static LevelView<T> view(rich_ctx* c, int l);
+
+template <>
+LevelView<double> view<double>(rich_ctx* c, int l) {
+  Level& L = c->H.lv[l];
+  return LevelView<double>{L.n, L.A.rowptr, L.A.col, L.A.val, L.dinv, L.P.rowptr, L.P.col, L.R.rowptr, L.R.col,
+                           L.P.val, L.R.val};
+}
+template <>
+LevelView<float> view<float>(rich_ctx* c, int l) {
+  Level& L = c->H.lv[l];
+  return LevelView<float>{L.n, L.A.rowptr, L.A.col, L.A32, L.dinv32, L.P.rowptr, L.P.col, L.R.rowptr, L.R.col,
+                          L.P32, L.R32};
+}
+
+template <class T>
+static const T* coarse_inv(rich_ctx* c);
+template <>
+const double* coarse_inv<double>(rich_ctx* c) { return c->H.cdense; }
+template <>
+const float* coarse_inv<float>(rich_ctx* c) { return c->H.cinv32; }
+
+// b is the level's right-hand side, the result is left in *xres (one of the level's buffers).
+template <class T>
+static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
+  Hierarchy& H = c->H;
+  Level& L = H.lv[l];
+  LevelView<T> v = view<T>(c, l);
+  int n = v.n;
+  int g = grid_for(n);
+  T* x = (T*)L.x;
+  T* t = (T*)L.t;
+  const double es = sizeof(T);
+  // algorithmic bytes of one sweep over this level's CSR matrix (pattern + values + 4 vectors)
+  const double sweep_bytes = (double)n * (4.0 + 4.0 * es) + (double)L.A.nnz * (4.0 + es);
+  if (l == H.nlev - 1) {
+    ProfScope ps("coarse_gemv", c->st, (double)n * n * es + 2.0 * n * es);
+    k_gemv<T><<<grid_for((long long)n * 32), kBlock, 0, c->st>>>(n, coarse_inv<T>(c), b, x);
+    RICH_LAUNCH_CHECK();
+    *xres = x;
+    return RICH_OK;
+  }
+  int nu1 = H.opts.nu1, nu2 = H.opts.nu2;
+  // finest level: stencil form (4 coefficient arrays + b + x in, x out)
+  const bool st0 = (l == 0);
+  const double st_bytes = (double)n * 7.0 * es;
+  if (nu1 > 0) {
+    if (st0) {
+      k_st_smooth<T, 0><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, nullptr, x);
+    } else {
+      k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
+    }
+    RICH_LAUNCH_CHECK();
+    for (int s = 1; s < nu1; ++s) {
+      {
+        ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
+        if (st0) k_st_smooth<T, 1><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
+        else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+      }
+      RICH_LAUNCH_CHECK();
+      std::swap(x, t);
+    }
+    {
+      ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st, st0 ? st_bytes : sweep_bytes - (double)n * es);
+      if (st0) k_st_smooth<T, 2><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
+      else k_resid<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, b, x, (T*)L.r);
+    }
+    RICH_LAUNCH_CHECK();
+  } else {
+    RICH_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, c->st));
+    RICH_CUDA(cudaMemcpyAsync(L.r, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->st));
+  }
+  Level& C = H.lv[l + 1];
+  {
+    ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
+    k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
+  }
+  RICH_LAUNCH_CHECK();
+  T* xc = nullptr;
+  RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
+  {
+    ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
+    k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
+  }
+  RICH_LAUNCH_CHECK();
+  for (int s = 0; s < nu2; ++s) {
+    {
+      ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
+      if (st0) k_st_smooth<T, 1><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
+      else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+    }
+    RICH_LAUNCH_CHECK();
+    std::swap(x, t);
+  }
+  // keep the level's buffer pointers consistent with where the result lives
+  if (x != (T*)L.x) {
+    L.t = L.x;
+    L.x = x;
+  }
+  *xres = x;
+  return RICH_OK;
+}
+
+int vcycle_apply(rich_ctx* c, const double* r, double* z) {
+  Hierarchy& H = c->H;
+  if (!H.built) return RICH_ESTATE;
+  long long n = c->g.n;
+  if (c->prec == RICH_PREC_MIXED) {
+    Level& L0 = H.lv[0];
+    k_d2f<<<grid_for(n), kBlock, 0, c->st>>>(n, r, (float*)L0.b);
+    RICH_LAUNCH_CHECK();
+    float* x = nullptr;
+    RICH_CHECK(vcycle_level<float>(c, 0, (const float*)L0.b, &x));
+    k_f2d<<<grid_for(n), kBlock, 0, c->st>>>(n, x, z);
+    RICH_LAUNCH_CHECK();
+  } else {
+    double* x = nullptr;
+    RICH_CHECK(vcycle_level<double>(c, 0, r, &x));
+    RICH_CUDA(cudaMemcpyAsync(z, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  }
+  return RICH_OK;
+}
+
+// ---------------------------------------------------------------- Krylov kernels (FP64)
+
+__global__ void k_dot2(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                       const double* __restrict__ cc, const double* __restrict__ d, double* __restrict__ partials) {
+  double v[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    v[0] += a[i] * b[i];
+    v[1] += cc[i] * d[i];
+  }
+  block_sum<2>(v);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = v[0];
+    partials[gridDim.x + blockIdx.x] = v[1];
+  }
+}
+
+// p = z - (s[num] / s[den]) p
+__global__ void k_fcg_dir(long long n, const double* __restrict__ z, double* __restrict__ p,
+                          const double* __restrict__ s, int num, int den) {
+  double beta = s[num] / s[den];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] - beta * p[i];
+}
+
+// alpha = s[num]/s[den]; x += alpha p; r -= alpha q; partial sums of r.r
+__global__ void k_fcg_update(long long n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                             const double* __restrict__ q, const double* __restrict__ s, int num, int den,
+                             double* __restrict__ partials) {
+  double alpha = s[num] / s[den];
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+// partials[q*nb + b] = sum over block b of V[q] . w  for q < nv
+__global__ void k_multidot(long long n, int nv, const double* __restrict__ V, const double* __restrict__ w,
+                           double* __restrict__ partials) {
+  for (int q0 = 0; q0 < nv; q0 += 4) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < nv) v[u] += V[(long long)(q0 + u) * n + i] * wi;
+    }
+    block_sum<4>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
+    }
+    __syncthreads();
+  }
+}
+
+// y += sign * sum_q coef[q] V[q]
+__global__ void k_multiaxpy(long long n, int nv, const double* __restrict__ V, const double* __restrict__ coef,
+                            double sign, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nv; ++q) s += coef[q] * V[(long long)q * n + i];
+    y[i] += sign * s;
+  }
+}
+
+__global__ void k_scale(long long n, const double* __restrict__ a, double f, double* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = f * a[i];
+}
+
+// y = a - b
+__global__ void k_sub(long long n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a[i] - b[i];
+}
+
+// y = a + lam * d
+__global__ void k_axpby(long long n, const double* __restrict__ a, double lam, const double* __restrict__ d,
+                        double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a[i] + lam * d[i];
+}
+
+__global__ void k_copy_scalar(double* s, int from, int to) { s[to] = s[from]; }
+
+static int ensure_krylov(rich_ctx* c, int m) {
+  KrylovWork& k = c->kw;
+  long long n = c->g.n;
+  if (k.n != n) {
+    dfree(k.x); dfree(k.r); dfree(k.p); dfree(k.q); dfree(k.qprev); dfree(k.z); dfree(k.w);
+    RICH_CHECK(dalloc(&k.x, n));
+    RICH_CHECK(dalloc(&k.r, n));
+    RICH_CHECK(dalloc(&k.p, n));
+    RICH_CHECK(dalloc(&k.q, n));
+    RICH_CHECK(dalloc(&k.qprev, n));
+    RICH_CHECK(dalloc(&k.z, n));
+    RICH_CHECK(dalloc(&k.w, n));
+    RICH_CHECK(dalloc(&k.hcoef, 128));
+    k.n = n;
+  }
+  if (m > 0 && k.m < m) {
+    dfree(k.V);
+    dfree(k.Z);
+    RICH_CHECK(dalloc(&k.V, (long long)(m + 1) * n));
+    RICH_CHECK(dalloc(&k.Z, (long long)m * n));
+    k.m = m;
+  }
+  return RICH_OK;
+}
+
+// Flexible CG (Notay, truncation 1).  Returns RICH_ENOTCONV_LIN on maxit, on
+// (p, q) <= 0, or when ||r|| exceeds 10x the smallest seen.
+static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
+  KrylovWork& k = c->kw;
+  long long n = c->g.n;
+  int g = grid_for(n);
+  int nb = red_grid(n);
+  double* s = c->dsc;  // 0 rr, 1 zq, 2 pq, 3 pr, 4 pq_prev
+  RICH_CHECK(nrm2sq(c, b, n, s + 0));
+  double h[4];
+  RICH_CHECK(fetch_scalars(c, s, 1, h));
+  double bn = sqrt(h[0]);
+  st->res0 = bn;
+  st->res = bn;
+  st->iterations = 0;
+  st->converged = 0;
+  RICH_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, c->st));
+  if (!(bn > 0)) {
+    st->converged = std::isfinite(bn) ? 1 : 0;
+    return std::isfinite(bn) ? RICH_OK : RICH_ENONFINITE;
+  }
+  if (!std::isfinite(bn)) return RICH_ENONFINITE;
+  RICH_CUDA(cudaMemcpyAsync(k.r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  double target = o->eta * bn, best = bn;
+  double* q = k.q;
+  double* qprev = k.qprev;
+  for (int it = 1; it <= o->maxit; ++it) {
+    RICH_CHECK(vcycle_apply(c, k.r, k.z));
+    if (it == 1) {
+      RICH_CUDA(cudaMemcpyAsync(k.p, k.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    } else {
+      RICH_CHECK(dot(c, k.z, qprev, n, s + 1));
+      k_fcg_dir<<<g, kBlock, 0, c->st>>>(n, k.z, k.p, s, 1, 4);
+      RICH_LAUNCH_CHECK();
+    }
+    RICH_CHECK(stencil_apply(c, c->J7, k.p, q));
+    k_dot2<<<nb, kBlock, 0, c->st>>>(n, k.p, q, k.p, k.r, c->partials);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(finish_sums(c, c->partials, nb, 2, s + 2));
+    {
+      ProfScope ps("fcg_update", c->st, (double)n * 48.0);
+      k_fcg_update<<<nb, kBlock, 0, c->st>>>(n, x, k.r, k.p, q, s, 3, 2, c->partials);
+    }
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(finish_sums(c, c->partials, nb, 1, s + 0));
+    k_copy_scalar<<<1, 1, 0, c->st>>>(s, 2, 4);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(fetch_scalars(c, s, 3, h));
+    double rn = sqrt(h[0]);
+    st->iterations = it;
+    st->res = rn;
+    if (!std::isfinite(rn) || !std::isfinite(h[2])) return RICH_ENONFINITE;
+    if (!(h[2] > 0)) return RICH_ENOTCONV_LIN;
+    if (rn <= target) {
+      st->converged = 1;
+      return RICH_OK;
+    }
+    if (rn > 10.0 * best) return RICH_ENOTCONV_LIN;
+    best = std::min(best, rn);
+    std::swap(q, qprev);
+  }
+  return RICH_ENOTCONV_LIN;
+}
+
+// Flexible GMRES(m) (Saad) with classical Gram-Schmidt and one re-orthogonalisation.
+static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
+  KrylovWork& k = c->kw;
+  long long n = c->g.n;
+  int m = o->restart;
+  int g = grid_for(n);
+  int nb = red_grid(n);
+  double* s = c->dsc;
+  RICH_CHECK(nrm2sq(c, b, n, s));
+  double h0[1];
+  RICH_CHECK(fetch_scalars(c, s, 1, h0));
+  double bn = sqrt(h0[0]);
+  st->res0 = bn;
+  st->res = bn;
+  st->iterations = 0;
+  st->converged = 0;
+  RICH_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, c->st));
+  if (!std::isfinite(bn)) return RICH_ENONFINITE;
+  if (!(bn > 0)) {
+    st->converged = 1;
+    return RICH_OK;
+  }
+  double target = o->eta * bn;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  double beta = bn;
+  const double* r0 = b;
+  int its = 0;
+  for (;;) {
+    k_scale<<<g, kBlock, 0, c->st>>>(n, r0, 1.0 / beta, k.V);
+    RICH_LAUNCH_CHECK();
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    bool conv = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = k.V + (long long)j * n;
+      double* Zj = k.Z + (long long)j * n;
+      RICH_CHECK(vcycle_apply(c, Vj, Zj));
+      RICH_CHECK(stencil_apply(c, c->J7, Zj, k.w));
+      for (int pass = 0; pass < 2; ++pass) {
+        {
+          ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2));
+          k_multidot<<<nb, kBlock, 0, c->st>>>(n, j + 1, k.V, k.w, c->partials);
+        }
+        RICH_LAUNCH_CHECK();
+        RICH_CHECK(finish_sums(c, c->partials, nb, j + 1, s + 64 * pass));
+        {
+          ProfScope ps("multiaxpy", c->st, (double)n * 8.0 * (j + 3));
+          k_multiaxpy<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s + 64 * pass, -1.0, k.w);
+        }
+        RICH_LAUNCH_CHECK();
+      }
+      RICH_CHECK(nrm2sq(c, k.w, n, s + 127));
+      RICH_CUDA(cudaMemcpyAsync(c->hsc, s, 128 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      RICH_CUDA(cudaStreamSynchronize(c->st));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = c->hsc[i] + c->hsc[64 + i];
+      double hn = sqrt(c->hsc[127]);
+      if (!std::isfinite(hn)) return RICH_ENONFINITE;
+      Hij(j + 1, j) = hn;
+      if (hn > 0) {
+        k_scale<<<g, kBlock, 0, c->st>>>(n, k.w, 1.0 / hn, k.V + (long long)(j + 1) * n);
+        RICH_LAUNCH_CHECK();
+      }
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cs[j] = Hij(j, j) / den;
+      sn[j] = Hij(j + 1, j) / den;
+      Hij(j, j) = den;
+      Hij(j + 1, j) = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++its;
+      jdone = j + 1;
+      st->res = fabs(gv[j + 1]);
+      if (fabs(gv[j + 1]) <= target || hn == 0.0) {
+        conv = true;
+        break;
+      }
+      if (its >= o->maxit) break;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int q = i + 1; q < jdone; ++q) acc -= Hij(i, q) * y[q];
+      y[i] = acc / Hij(i, i);
+    }
+    for (int i = 0; i < jdone; ++i) c->hsc[i] = y[i];
+    RICH_CUDA(cudaMemcpyAsync(k.hcoef, c->hsc, sizeof(double) * jdone, cudaMemcpyHostToDevice, c->st));
+    k_multiaxpy<<<g, kBlock, 0, c->st>>>(n, jdone, k.Z, k.hcoef, 1.0, x);
+    RICH_LAUNCH_CHECK();
+    st->iterations = its;
+    if (conv) {
+      st->converged = 1;
+      return RICH_OK;
+    }
+    if (its >= o->maxit) return RICH_ENOTCONV_LIN;
+    // restart: r = b - J x
+    RICH_CHECK(stencil_apply(c, c->J7, x, k.w));
+    k_sub<<<g, kBlock, 0, c->st>>>(n, b, k.w, k.r);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(nrm2sq(c, k.r, n, s));
+    RICH_CHECK(fetch_scalars(c, s, 1, h0));
+    beta = sqrt(h0[0]);
+    st->res = beta;
+    if (beta <= target) {
+      st->converged = 1;
+      return RICH_OK;
+    }
+    r0 = k.r;
+  }
+}
+
+int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
+  if (o->maxit < 1 || !(o->eta > 0)) return RICH_EINVAL;
+  if (o->kind == RICH_KRYLOV_FGMRES) {
+    if (o->restart < 1 || o->restart > 63) return RICH_EINVAL;
+    RICH_CHECK(ensure_krylov(c, o->restart));
+    return fgmres(c, b, x, o, st);
+  }
+  if (o->kind != RICH_KRYLOV_FCG) return RICH_EINVAL;
+  RICH_CHECK(ensure_krylov(c, 0));
+  return fcg(c, b, x, o, st);
+}
+
+// ---------------------------------------------------------------- Newton-Armijo step
+
+static int ensure_newton(rich_ctx* c) {
+  if (c->F) return RICH_OK;
+  long long n = c->g.n;
+  RICH_CHECK(dalloc(&c->s_old, n));
+  RICH_CHECK(dalloc(&c->F, n));
+  RICH_CHECK(dalloc(&c->Ft, n));
+  RICH_CHECK(dalloc(&c->d, n));
+  RICH_CHECK(dalloc(&c->ptrial, n));
+  RICH_CHECK(dalloc(&c->rhs, n));
+  return RICH_OK;
+}
+
+static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) {
+  RICH_CHECK(ensure_newton(c));
+  long long n = c->g.n;
+  int g = grid_for(n);
+  memset(st, 0, sizeof(*st));
+  st->min_lambda = 1.0;
+  double h[2];
+  RICH_CHECK(rich_saturation(c, p, c->s_old));
+  RICH_CHECK(residual_eval(c, p, c->s_old, dt, c->F, true));
+  RICH_CHECK(fetch_scalars(c, c->dsc, 1, h));
+  double fn = sqrt(h[0]);
+  if (!std::isfinite(fn)) return RICH_ENONFINITE;
+  st->res0 = st->res = fn;
+  double tol = std::max(o->rtol * fn, o->atol);
+  for (int r = 0;; ++r) {
+    if (fn <= tol) {
+      st->converged = 1;
+      break;
+    }
+    if (r == o->max_newton) return RICH_ENOTCONV_NEWTON;
+    RICH_CHECK(jacobian_eval(c, p, dt));
+    bool rebuild = !c->H.built || (o->amg_policy == RICH_AMG_REBUILD_STEP && r == 0);
+    if (rebuild) {
+      RICH_CHECK(amg_build(c, &o->amg));
+      st->amg_setups++;
+    } else {
+      RICH_CHECK(o->amg_policy == RICH_AMG_SETUP_ONCE ? amg_update_fine(c) : amg_refresh(c));
+      st->amg_refreshes++;
+    }
+    k_scale<<<g, kBlock, 0, c->st>>>(n, c->F, -1.0, c->rhs);
+    RICH_LAUNCH_CHECK();
+    rich_krylov_stats ks;
+    int s = krylov_run(c, c->rhs, c->d, &o->krylov, &ks);
+    st->linear_its += ks.iterations;
+    if (s == RICH_ENOTCONV_LIN && o->krylov.kind == RICH_KRYLOV_FCG) {
+      rich_krylov_opts fb = o->krylov;
+      fb.kind = RICH_KRYLOV_FGMRES;
+      fb.restart = o->fcg_fallback_restart;
+      st->fallbacks++;
+      s = krylov_run(c, c->rhs, c->d, &fb, &ks);
+      st->linear_its += ks.iterations;
+    }
+    if (s != RICH_OK) return s;
+    // slope of f = 1/2 ||Phi||^2 along d: g = Phi . (J d)
+    RICH_CHECK(stencil_apply(c, c->J7, c->d, c->Ft));
+    RICH_CHECK(dot(c, c->F, c->Ft, n, c->dsc + 2));
+    RICH_CHECK(fetch_scalars(c, c->dsc + 2, 1, h));
+    double slope = h[0];
+    if (!(slope < 0.0)) return RICH_ELINESEARCH;
+    double f0 = 0.5 * fn * fn;
+    double lam = 1.0, ft = 0.0;
+    for (;;) {
+      k_axpby<<<g, kBlock, 0, c->st>>>(n, p, lam, c->d, c->ptrial);
+      RICH_LAUNCH_CHECK();
+      RICH_CHECK(residual_eval(c, c->ptrial, c->s_old, dt, c->Ft, true));
+      RICH_CHECK(fetch_scalars(c, c->dsc, 1, h));
+      st->line_search_evals++;
+      ft = 0.5 * h[0];
+      if (!std::isfinite(ft)) return RICH_ENONFINITE;
+      if (ft <= f0 + o->armijo_c * lam * slope) break;
+      double lq = -slope * lam * lam / (2.0 * (ft - f0 - slope * lam));
+      lam = std::min(std::max(lq, 0.1 * lam), 0.5 * lam);
+      if (lam < o->lambda_min) return RICH_ELINESEARCH;
+    }
+    RICH_CUDA(cudaMemcpyAsync(p, c->ptrial, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    std::swap(c->F, c->Ft);
+    fn = sqrt(2.0 * ft);
+    st->res = fn;
+    st->newton_its++;
+    st->min_lambda = std::min(st->min_lambda, lam);
+  }
+  return RICH_OK;
+}
+
+}  // namespace rich
+
+using namespace rich;
+
 extern "C" {
-int amg_setup(rich_ctx* c, const rich_amg_opts* o, rich_amg_info* info) { return RICH_ESTATE; }
-int amg_update(rich_ctx* c, int policy) { return RICH_ESTATE; }
-int amg_vcycle(rich_ctx* c, const double* r, double* z) { return RICH_ESTATE; }
-int amg_export_level(rich_ctx* c, int level, int* agg, int* rp, int* col, double* val) { return RICH_ESTATE; }
-int amg_export_prolongator(rich_ctx* c, int level, long long* nnz, int* rp, int* col, double* val) { return RICH_ESTATE; }
-int krylov_solve(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) { return RICH_ESTATE; }
-int rich_step(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) { return RICH_ESTATE; }
-int rich_step_host(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) { return RICH_ESTATE; }
+
+int amg_vcycle(rich_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z) return RICH_EINVAL;
+  return vcycle_apply(c, r, z);
 }
+
+int krylov_solve(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
+  if (!c || !b || !x || !o) return RICH_EINVAL;
+  if (!c->have_jac || !c->H.built) return RICH_ESTATE;
+  rich_krylov_stats tmp;
+  return krylov_run(c, b, x, o, st ? st : &tmp);
+}
+
+int rich_step(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) {
+  if (!c || !p || !(dt > 0)) return RICH_EINVAL;
+  rich_newton_opts def;
+  if (!o) {
+    rich_default_newton_opts(&def);
+    o = &def;
+  }
+  rich_step_stats tmp;
+  return step_impl(c, p, dt, o, st ? st : &tmp);
+}
+
+int rich_step_host(rich_ctx* c, double* p_host, double dt, const rich_newton_opts* o, rich_step_stats* st) {
+  if (!c || !p_host || !(dt > 0)) return RICH_EINVAL;
+  long long n = c->g.n;
+  if (!c->pbuf) RICH_CHECK(dalloc(&c->pbuf, n));
+  RICH_CUDA(cudaMemcpyAsync(c->pbuf, p_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  int s = rich_step(c, c->pbuf, dt, o, st);
+  RICH_CUDA(cudaMemcpyAsync(p_host, c->pbuf, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+"""GPU parity of the AMG hierarchy, V-cycle, Krylov solves and the Newton step against the FP64 oracle.
+
+Bars: aggregates, level sizes and sparsity patterns bit-exact; FP64 matrix
+values normwise 1e-10; FP64 V-cycle output normwise 1e-10; pressure after a
+converged step 1e-8 relative.  MIXED precision: the V-cycle is compared at
+FP32 level (normwise 1e-4) and the converged pressure still to 1e-8 (the
+Newton residual and outer Krylov are FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import amg, newton
+from oracle import constitutive as cst
+from oracle import discretization as disc
+from paper_2112_05051_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SOIL = synth.Soil()
+
+
+def _rb():
+    from paper_2112_05051_gb300 import richards as rb
+    rb.load()
+    return rb
+
+
+def _nrel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _problem(dims, seed, kmean=0, het=True, dt=1.0, bc=None):
+    grid = synth.Grid(*dims)
+    rng = np.random.default_rng(seed)
+    # a smooth wetting front below the top face plus small noise (a state the
+    # Newton iteration meets); independent random heads per cell make J far
+    # from symmetric and FCG inapplicable
+    z = (np.arange(grid.nz) + 1.0) / (grid.nz + 1)
+    front = -61.5 + 40.8 * np.exp(-(1.0 - z) / 0.2)
+    p = np.broadcast_to(front[:, None, None], grid.shape).ravel() + rng.uniform(-0.5, 0.5, grid.n)
+    ks = synth.ks_field(grid, seed, 1.0, (3.0, 3.0, 2.0)) if het else None
+    bc = bc or synth.infiltration_bc()
+    return grid, p, ks, bc, dt, kmean
+
+
+def _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, seed=7, prec=0):
+    rb = _rb()
+    ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+    pd = torch.tensor(p, device="cuda")
+    ctx.jacobian(pd, dt)
+    info = ctx.amg_setup(rb.default_amg_opts(seed=seed, coarse_max=coarse_max))
+    A = disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks)
+    h = amg.setup(A, 0.08, seed, coarse_max)
+    return ctx, info, h
+
+
+def _compare_hierarchy(ctx, info, h):
+    assert info.levels == len(h.levels)
+    for l, lv in enumerate(h.levels):
+        assert info.n[l] == lv.A.shape[0]
+        agg, rp, col, val = ctx.export_level(l, info)
+        np.testing.assert_array_equal(rp, lv.A.indptr)
+        np.testing.assert_array_equal(col, lv.A.indices)
+        assert _nrel(val, lv.A.data) <= 1e-10
+        if l < info.levels - 1:
+            np.testing.assert_array_equal(agg, lv.agg)
+            prp, pcol, pval = ctx.export_prolongator(l, info)
+            np.testing.assert_array_equal(prp, lv.P.indptr)
+            np.testing.assert_array_equal(pcol, lv.P.indices)
+            assert _nrel(pval, lv.P.data) <= 1e-10
+            assert info.mis_rounds[l] == lv.mis_rounds
+
+
+@pytest.mark.parametrize("dims,coarse_max,kmean", [((10, 9, 8), 60, 0), ((24, 24, 24), 300, 1),
+                                                    ((33, 17, 9), 150, 2), ((1, 1, 50), 5, 0),
+                                                    ((40, 40, 40), 2000, 1)])
+def test_hierarchy_bit_exact(dims, coarse_max, kmean):
+    grid, p, ks, bc, dt, _ = _problem(dims, 3, kmean)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, coarse_max)
+    _compare_hierarchy(ctx, info, h)
+    assert info.operator_complexity == pytest.approx(h.operator_complexity(), rel=1e-12)
+    ctx.close()
+
+
+@pytest.mark.parametrize("nu", [1, 2])
+def test_vcycle_parity_fp64_and_mixed(nu):
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((20, 18, 16), 5, 1)
+    r = np.random.default_rng(2).standard_normal(grid.n)
+    A = disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks)
+    h = amg.setup(A, 0.08, 7, 200)
+    zref = amg.vcycle(h, r, nu, nu)
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+        ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+        ctx.amg_setup(rb.default_amg_opts(seed=7, coarse_max=200, nu1=nu, nu2=nu))
+        z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+        ctx.vcycle(torch.tensor(r, device="cuda"), z)
+        assert _nrel(z.cpu().numpy(), zref) <= tol
+        ctx.close()
+
+
+def test_refresh_matches_oracle_galerkin_refresh():
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((18, 16, 14), 8, 0)
+    p2 = p + np.random.default_rng(4).uniform(0, 15, grid.n)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, 150)
+    ctx.jacobian(torch.tensor(p2, device="cuda"), 2.0 * dt)
+    ctx.amg_update(rb.AMG_REFRESH)
+    amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, p2, 2.0 * dt, ks))
+    _compare_hierarchy(ctx, info, h)
+    r = np.random.default_rng(1).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", ["fcg", "fgmres"])
+def test_krylov_solution_parity(kind):
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((16, 14, 12), 11, 1)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, 100)
+    b = np.random.default_rng(3).standard_normal(grid.n)
+    x = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    k = rb.KRYLOV_FCG if kind == "fcg" else rb.KRYLOV_FGMRES
+    # J of the same p, on the GPU context (rich_jacobian was called in _setup_both)
+    s, st = ctx.krylov_solve(torch.tensor(b, device="cuda"), x, kind=k, restart=10, eta=1e-11, maxit=400)
+    J = disc.jacobian(grid, SOIL, bc, kmean, p, dt, ks)
+    from oracle import krylov
+    prec = lambda v: amg.vcycle(h, v)
+    if kind == "fcg":
+        xr, its, ok, _ = krylov.fcg(lambda v: J @ v, prec, b, 1e-11, 400)
+    else:
+        xr, its, ok, _ = krylov.fgmres(lambda v: J @ v, prec, b, 1e-11, 400, 10)
+    assert ok and st.converged
+    assert abs(st.iterations - its) <= 1
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(J @ xg - b) <= 1e-11 * np.linalg.norm(b) * 1.0001
+    assert _nrel(xg, xr) <= 1e-8
+    ctx.close()
+
+
+def _run_steps(workload, n, steps, prec=0, policy=0, opts_kw=None):
+    rb = _rb()
+    w = synth.WORKLOADS[workload]
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w, n)
+    kw = dict(kind=rb.KRYLOV_FGMRES if w.krylov == "fgmres" else rb.KRYLOV_FCG, restart=max(w.restart, 1),
+              nu1=w.nu, nu2=w.nu, seed=w.amg_seed, coarse_max=w.coarse_max, amg_policy=policy)
+    kw.update(opts_kw or {})
+    opts = rb.default_newton_opts(**kw)
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
+    pd = torch.tensor(p0, device="cuda")
+    gstats = []
+    for dt in dts[:steps]:
+        gstats.append(ctx.step(pd, dt, opts))
+    pol = {0: "refresh", 1: "setup_once", 2: "rebuild_step"}[policy]
+    prob = newton.Problem(grid, soil, bc, w.kmean, ks)
+    oopt = newton.NewtonOptions(krylov=w.krylov, restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu,
+                                amg_seed=w.amg_seed, coarse_max=w.coarse_max, amg_policy=pol)
+    for k, v in (opts_kw or {}).items():
+        if k == "coarse_max":
+            oopt.coarse_max = v
+    p = p0
+    ostats = []
+    for dt in dts[:steps]:
+        p, st = newton.step(prob, p, dt, oopt)
+        ostats.append(st)
+    ctx_p = pd.cpu().numpy()
+    ctx.close()
+    return ctx_p, p, gstats, ostats
+
+
+@pytest.mark.parametrize("policy", [0, 1, 2])
+def test_step_parity_richards16(policy):
+    pg, po, gs, os_ = _run_steps("richards16_fp64", None, 5, policy=policy)
+    np.testing.assert_allclose(pg, po, rtol=1e-8)
+    for g, o in zip(gs, os_):
+        assert g.converged and o.converged
+        assert g.newton_its == o.newton_its
+
+
+def test_step_parity_richards128_shape_at_32():
+    # the 128^3 workload's settings (upstream mean, FGMRES(30), V(2,2), dt ramp) on a 32^3 grid
+    pg, po, gs, os_ = _run_steps("richards128_fp64", 32, 4)
+    np.testing.assert_allclose(pg, po, rtol=1e-8)
+    for g, o in zip(gs, os_):
+        assert g.newton_its == o.newton_its
+
+
+@pytest.mark.parametrize("workload,n,steps", [("richards512_mixed", 24, 1), ("richards16_fp64", None, 5)])
+def test_step_mixed_precision_matches_fp64_oracle(workload, n, steps):
+    # FP32 hierarchy and V-cycle, FP64 residual/Jacobian/outer Krylov: the converged
+    # pressure is the FP64 oracle's to the Newton tolerance.
+    pg, po, gs, os_ = _run_steps(workload, n, steps, prec=1)
+    np.testing.assert_allclose(pg, po, rtol=1e-8)
