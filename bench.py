@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default="richards128_fp64")
     ap.add_argument("--roofline-kernel", default="multidot")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-AMG comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     return ap.parse_args()
@@ -251,17 +252,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     e0.record(stream)
+    marks[0].record(stream)
     newton_its = 0
     lin_its = 0
     stats = []
-    for m in range(args.warmup, args.warmup + args.steps):
+    for q, m in enumerate(range(args.warmup, args.warmup + args.steps)):
         st = ctx.step(pd, sched(m), opts)
+        marks[q + 1].record(stream)
         newton_its += st.newton_its
         lin_its += st.linear_its
         stats.append(st.as_dict())
     e1.record(stream)
     torch.cuda.synchronize()
+    step_ms = sorted(marks[q].elapsed_time(marks[q + 1]) for q in range(args.steps))
     if dist:
         dist.barrier()
     elapsed = e0.elapsed_time(e1) / 1000.0
@@ -309,6 +314,34 @@ def run_ours(args):
                "d2h_bytes_per_step": 8 * grid.n}
         ctx2.close()
 
+    # the same schedule with the FP32 AMG hierarchy and V-cycle (FP64 residual,
+    # Jacobian, line search and outer Krylov): speed and deviation from FP64
+    mixed = None
+    if not args.no_mixed and not w.mixed:
+        ctx3 = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_MIXED)
+        p3 = torch.tensor(p0, device="cuda")
+        for m in range(args.warmup):
+            ctx3.step(p3, sched(m), opts)
+        ref_p = pd  # FP64 state after the same steps
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        its3 = lin3 = 0
+        for m in range(args.warmup, args.warmup + args.steps):
+            st3 = ctx3.step(p3, sched(m), opts)
+            its3 += st3.newton_its
+            lin3 += st3.linear_its
+        f1.record(stream)
+        torch.cuda.synchronize()
+        el3 = f0.elapsed_time(f1) / 1000.0
+        v3 = float(grid.n) * its3 / el3
+        dev = float((p3 - ref_p).abs().max() / ref_p.abs().max())
+        mixed = {"value": v3, "unit": "DOF*Newton-steps/s", "speedup_vs_fp64": v3 / (float(grid.n) * newton_its / elapsed),
+                 "newton_its": its3, "linear_its": lin3, "fp64_newton_its": newton_its, "fp64_linear_its": lin_its,
+                 "max_rel_dev_p_vs_fp64": dev, "ms_per_step": 1000.0 * el3 / max(args.steps, 1)}
+        ctx3.close()
+
     peak, peak_kind = measured_peaks()
     achieved = (by_k.value / (ms_k.value / 1000.0) / 1e9) if ms_k.value > 0 else None
     per_launch_bytes = by_k.value / n_k.value if n_k.value else None
@@ -324,6 +357,10 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(w, grid), "e2e": e2e,
             "gpu_launches": int(l1.value - l0.value), "clocks": clocks, "roofline": roof,
             "newton_its": newton_its, "linear_its": lin_its,
+            "latency_ms_per_time_step": {"p50": step_ms[len(step_ms) // 2],
+                                         "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
+                                         "max": step_ms[-1]},
+            "fp32_amg": mixed,
             "parallelism": "replicas" if ws > 1 else "single"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)

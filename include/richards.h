@@ -53,10 +53,11 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
  * (eq. (upstream_mean)) K_U if p_U - p_L >= 0 else K_L with U the +d cell;
- * harmonic 2 K_L K_U / (K_L + K_U). */
-#define RICH_KMEAN_ARITH     0
-#define RICH_KMEAN_UPSTREAM  1
-#define RICH_KMEAN_HARMONIC  2
+ * harmonic 2 K_L K_U / (K_L + K_U); geometric sqrt(K_L K_U). */
+#define RICH_KMEAN_ARITH      0
+#define RICH_KMEAN_UPSTREAM   1
+#define RICH_KMEAN_HARMONIC   2
+#define RICH_KMEAN_GEOMETRIC  3
 
 #define RICH_BC_NOFLUX     0  /* the whole face flux (diffusion + gravity) is zero */
 #define RICH_BC_DIRICHLET  1  /* ghost node at p = value, K from the adjacent cell's K_s */
@@ -132,7 +133,9 @@ typedef struct {
   rich_krylov_opts krylov;
   rich_amg_opts amg;
   int amg_policy;          /* RICH_AMG_* */
-  double rtol, atol;       /* converged when ||Phi||_2 <= max(rtol ||Phi_0||_2, atol) */
+  double rtol, atol;       /* converged when ||Phi||_2 <= max(rtol ||Phi_0||_2, atol, eps ||m||_2),
+                              m_c = sum of the magnitudes of the products summed into Phi_c
+                              (the accuracy to which Phi can be evaluated) */
   int max_newton;          /* Newton iteration limit (50) */
   double armijo_c;         /* sufficient-decrease constant (1e-4) */
   double lambda_min;       /* smallest line-search step (1e-10) */

@@ -16,7 +16,8 @@ Readings where the paper is silent (all listed in the design notes):
   * face means (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream (eq.
     (upstream_mean)) K_U if p_U - p_L >= 0 else K_L, where U is the cell on
     the +d side of the face, ties taking K_U; harmonic 2 K_L K_U/(K_L+K_U)
-    (the abstract names it, no formula is printed).
+    (the abstract names it, no formula is printed); geometric sqrt(K_L K_U)
+    (Sec. 2.1).
   * Dirichlet face: the ghost node holds p = p_bc and K = K(p_bc) with the
     Ks of the adjacent interior cell; T and G use it as a neighbour.
   * No-flux face: the whole face flux T + G is zero.
@@ -44,7 +45,7 @@ from . import constitutive as cst
 
 # (axis, side) per face, axis 0 = x, 1 = y, 2 = z; order -x,+x,-y,+y,-z,+z.
 FACES = ((0, -1), (0, 1), (1, -1), (1, 1), (2, -1), (2, 1))
-KMEAN_ARITH, KMEAN_UPSTREAM, KMEAN_HARMONIC = 0, 1, 2
+KMEAN_ARITH, KMEAN_UPSTREAM, KMEAN_HARMONIC, KMEAN_GEOMETRIC = 0, 1, 2, 3
 BC_NOFLUX, BC_DIRICHLET = 0, 1
 
 
@@ -85,6 +86,8 @@ def face_mean(kmean, k_lo, k_up, p_lo, p_up):
         s = k_lo + k_up
         with np.errstate(divide="ignore", invalid="ignore"):
             return np.where(s > 0.0, 2.0 * k_lo * k_up / s, 0.0)
+    if kmean == KMEAN_GEOMETRIC:
+        return np.sqrt(k_lo * k_up)
     raise ValueError("unknown K mean")
 
 
@@ -101,6 +104,12 @@ def face_mean_partials(kmean, k_lo, k_up, p_lo, p_up):
         with np.errstate(divide="ignore", invalid="ignore"):
             d_lo = np.where(s > 0.0, 2.0 * k_up * k_up / (s * s), 0.0)
             d_up = np.where(s > 0.0, 2.0 * k_lo * k_lo / (s * s), 0.0)
+        return d_lo, d_up
+    if kmean == KMEAN_GEOMETRIC:
+        g = np.sqrt(k_lo * k_up)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            d_lo = np.where(k_lo > 0.0, 0.5 * g / k_lo, 0.0)
+            d_up = np.where(k_up > 0.0, 0.5 * g / k_up, 0.0)
         return d_lo, d_up
     raise ValueError("unknown K mean")
 
@@ -141,19 +150,33 @@ class _Faces:
         return nb_K, self.K3, nb_p, self.p3
 
 
-def residual(grid, soil, bc, kmean, p, s_old, dt, ks=None):
-    """Phi(p) of eq. (dynamic_of_the_problem), flat array of n cells."""
+def residual(grid, soil, bc, kmean, p, s_old, dt, ks=None, with_scale=False):
+    """Phi(p) of eq. (dynamic_of_the_problem), flat array of n cells.
+
+    with_scale=True also returns ||m||_2 with m_c = rho_phi (|s_c| + |s_old,c|)/dt
+    + sum_f [K_av,f (|p_c| + |p_nb|)/h_d^2 + (K_c + K_nb)/(2 h_z) on z faces],
+    the magnitudes of the products summed into Phi_c before they cancel:
+    machine epsilon times it is the accuracy to which Phi can be evaluated.
+    """
     ks = soil.ks if ks is None else ks
     fd = _Faces(grid, soil, bc, p, ks)
-    phi = soil.rho_phi * (cst.saturation(fd.p3, soil) - np.asarray(s_old).reshape(fd.shape)) / dt
+    s_new = cst.saturation(fd.p3, soil)
+    s_o = np.asarray(s_old).reshape(fd.shape)
+    phi = soil.rho_phi * (s_new - s_o) / dt
+    mag = soil.rho_phi * (np.abs(s_new) + np.abs(s_o)) / dt
     for axis, side, nb_p, nb_K, nb_dK, interior, active in fd.faces:
         h = fd.h[axis]
         k_lo, k_up, p_lo, p_up = fd.lower_upper(side, nb_p, nb_K)
         kav = face_mean(kmean, k_lo, k_up, p_lo, p_up)
         t = kav * (fd.p3 - nb_p) / (h * h)
+        m = kav * (np.abs(fd.p3) + np.abs(nb_p)) / (h * h)
         if axis == 2:
             t = t - side * (fd.K3 + nb_K) / (2.0 * h)
+            m = m + (fd.K3 + nb_K) / (2.0 * h)
         phi = phi + np.where(active, t, 0.0)
+        mag = mag + np.where(active, m, 0.0)
+    if with_scale:
+        return phi.reshape(-1), float(np.sqrt(np.sum(mag * mag)))
     return phi.reshape(-1)
 
 

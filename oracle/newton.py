@@ -7,7 +7,12 @@ preconditioned by the AMG V-cycle built on the diffusion-only matrix; the
 step length lambda comes from an Armijo-type line search.  The paper gives
 no constants; the readings used here (shared with the CUDA path) are:
 
-  * convergence: ||Phi(p_r)||_2 <= max(rtol ||Phi(p_0)||_2, atol).
+  * convergence: ||Phi(p_r)||_2 <= max(rtol ||Phi(p_0)||_2, atol, eps ||m||_2)
+    where m_c sums the magnitudes of the products that make up Phi_c before
+    they cancel (discretization.residual, with_scale): late in a run, when a
+    step starts close to steady state, rtol ||Phi_0|| falls below the accuracy
+    to which Phi can be evaluated and the line search cannot make progress;
+    the last term declares convergence at that attainable accuracy instead.
   * a fresh J and A_aux every Newton iteration.  The AMG hierarchy is built
     on the first A_aux of the run; afterwards
       'refresh'      (default) keeps aggregates, P and R and recomputes the
@@ -31,6 +36,9 @@ from . import amg
 from . import constitutive as cst
 from . import discretization as disc
 from . import krylov
+
+
+FLOOR_EPS = np.finfo(np.float64).eps
 
 
 @dataclasses.dataclass
@@ -73,8 +81,8 @@ class Problem:
         self.ks = soil.ks if ks is None else ks
         self.hierarchy = None
 
-    def residual(self, p, s_old, dt):
-        return disc.residual(self.grid, self.soil, self.bc, self.kmean, p, s_old, dt, self.ks)
+    def residual(self, p, s_old, dt, with_scale=False):
+        return disc.residual(self.grid, self.soil, self.bc, self.kmean, p, s_old, dt, self.ks, with_scale)
 
     def jacobian(self, p, dt):
         return disc.jacobian(self.grid, self.soil, self.bc, self.kmean, p, dt, self.ks)
@@ -102,13 +110,13 @@ def step(prob, p, dt, opt):
     p = np.array(p, dtype=np.float64)
     s_old = cst.saturation(p, prob.soil)
     st = StepStats()
-    F = prob.residual(p, s_old, dt)
+    F, scale = prob.residual(p, s_old, dt, with_scale=True)
     fn = np.linalg.norm(F)
     st.res0 = fn
     tol = max(opt.rtol * fn, opt.atol)
     st.res_hist.append(fn)
     for r in range(opt.max_newton + 1):
-        if fn <= tol:
+        if fn <= max(tol, FLOOR_EPS * scale):
             st.converged = True
             break
         if r == opt.max_newton:
@@ -131,7 +139,7 @@ def step(prob, p, dt, opt):
         f0 = 0.5 * fn * fn
         lam = 1.0
         while True:
-            Ft = prob.residual(p + lam * d, s_old, dt)
+            Ft, scale_t = prob.residual(p + lam * d, s_old, dt, with_scale=True)
             st.line_search_evals += 1
             ft = 0.5 * float(Ft @ Ft)
             if ft <= f0 + opt.armijo_c * lam * g:
@@ -141,7 +149,7 @@ def step(prob, p, dt, opt):
             if lam < opt.lambda_min:
                 raise RuntimeError("line search failed")
         p = p + lam * d
-        F = Ft
+        F, scale = Ft, scale_t
         fn = np.linalg.norm(F)
         st.res_hist.append(fn)
         st.lambdas.append(lam)

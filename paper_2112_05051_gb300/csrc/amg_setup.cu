@@ -288,15 +288,12 @@ constexpr int kEscWarps = 2;     // warps per block of the shared-memory ESC ker
 constexpr int kEscCap = 1024;    // products per warp held in shared memory
 
 // mode 0: cnt[row] = number of distinct columns; mode 1: write the compressed row at crp[row].
-// Rows whose product count exceeds cap are skipped unless gkeys is given (global-scratch pass,
-// where goff[row] is the row's scratch offset and big rows only are processed).
+// Rows whose product count exceeds kEscCap are left to k_spgemm_hash.
 __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* __restrict__ acol,
                              const double* __restrict__ aval, const int* __restrict__ brp,
                              const int* __restrict__ bcol, const double* __restrict__ bval,
                              const int* __restrict__ u, int mode, const int* __restrict__ crp,
-                             int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt,
-                             uint64_t* __restrict__ gkeys, double* __restrict__ gvals,
-                             const long long* __restrict__ goff) {
+                             int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
   extern __shared__ unsigned char smem[];
   int wpb = blockDim.x >> 5;
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -304,10 +301,9 @@ __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* 
   double* svals = reinterpret_cast<double*>(smem + (size_t)wpb * kEscCap * sizeof(uint64_t)) + (size_t)w * kEscCap;
   for (int row = blockIdx.x * wpb + w; row < nrows; row += gridDim.x * wpb) {
     int ur = u[row];
-    bool big = ur > kEscCap;
-    if (gkeys ? !big : big) continue;
-    uint64_t* keys = gkeys ? gkeys + goff[row] : skeys;
-    double* vals = gkeys ? gvals + goff[row] : svals;
+    if (ur > kEscCap) continue;
+    uint64_t* keys = skeys;
+    double* vals = svals;
     int M = 1;
     while (M < ur) M <<= 1;
     // expand in product order: A entries in column order, then B entries in column order
@@ -352,13 +348,123 @@ __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* 
   }
 }
 
-// Values of C = A B on C's known pattern; one thread per row, products in the ESC order.
+// Rows with more than kEscCap products: one block per row accumulates the products
+// into a shared-memory hash table keyed by column (linear probing, atomicCAS), then
+// sorts the occupied keys.  The column set is exact; the FP64 sums depend on the
+// order of the shared-memory atomics (rounding-level differences only).
+constexpr int kHashSlots = 8192;
+constexpr int kHashThreads = 256;
+
+__global__ void __launch_bounds__(kHashThreads) k_spgemm_hash(
+    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
+    const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
+    const int* __restrict__ u, int mode, const int* __restrict__ crp, int* __restrict__ ccol,
+    double* __restrict__ cval, int* __restrict__ cnt, int* __restrict__ overflow) {
+  extern __shared__ unsigned char smem[];
+  int* hkey = reinterpret_cast<int*>(smem);
+  double* hval = reinterpret_cast<double*>(smem + kHashSlots * sizeof(int));
+  __shared__ int nfill;
+  __shared__ int fail;
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+    if (u[row] <= kEscCap) continue;
+    for (int t = threadIdx.x; t < kHashSlots; t += blockDim.x) {
+      hkey[t] = -1;
+      hval[t] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+      nfill = 0;
+      fail = 0;
+    }
+    __syncthreads();
+    // products: A entries of the row in turn, B entries strided over the block
+    for (int e = arp[row]; e < arp[row + 1]; ++e) {
+      int j = acol[e];
+      double a = aval ? aval[e] : 1.0;
+      for (int f = brp[j] + threadIdx.x; f < brp[j + 1]; f += blockDim.x) {
+        int col = bcol[f];
+        double v = a * (bval ? bval[f] : 1.0);
+        unsigned h = ((unsigned)col * 2654435761u) & (kHashSlots - 1);
+        int probes = 0;
+        for (;;) {
+          int k = ((volatile int*)hkey)[h];
+          if (k == col) break;
+          if (k == -1) {
+            int prev = atomicCAS(&hkey[h], -1, col);
+            if (prev == -1 || prev == col) break;
+          }
+          h = (h + 1) & (kHashSlots - 1);
+          if (++probes >= kHashSlots) {
+            fail = 1;
+            break;
+          }
+        }
+        if (probes < kHashSlots) atomicAdd(&hval[h], v);
+      }
+    }
+    __syncthreads();
+    if (fail) {
+      if (threadIdx.x == 0) atomicOr(overflow, 1);
+      __syncthreads();
+      continue;
+    }
+    // compact occupied slots to the front: (col << 32 | slot) keys reuse hkey/hval storage order
+    // via a second pass; collect into a sorted list with a block bitonic sort of 64-bit keys
+    // stored in the (now free) upper part of smem.
+    uint64_t* keys = reinterpret_cast<uint64_t*>(smem + kHashSlots * (sizeof(int) + sizeof(double)));
+    for (int t = threadIdx.x; t < kHashSlots; t += blockDim.x) {
+      int k = hkey[t];
+      if (k >= 0) {
+        int pos = atomicAdd(&nfill, 1);
+        keys[pos] = ((uint64_t)(uint32_t)k << 32) | (uint32_t)t;
+      }
+    }
+    __syncthreads();
+    int L = nfill;
+    int M = 1;
+    while (M < L) M <<= 1;
+    for (int t = L + threadIdx.x; t < M; t += blockDim.x) keys[t] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= M; k <<= 1) {
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int t = threadIdx.x; t < M; t += blockDim.x) {
+          int ixj = t ^ jj;
+          if (ixj > t) {
+            uint64_t x = keys[t], y = keys[ixj];
+            bool asc = (t & k) == 0;
+            if ((x > y) == asc) {
+              keys[t] = y;
+              keys[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (mode == 0) {
+      if (threadIdx.x == 0) cnt[row] = L;
+    } else {
+      int base = crp[row];
+      for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        ccol[base + t] = (int)(keys[t] >> 32);
+        cval[base + t] = hval[(uint32_t)(keys[t] & kLow32)];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Values of C = A B on C's known pattern.  Rows with at most kNumSmall products:
+// one thread per row, products in the ESC order (sums identical to the symbolic
+// pass).  Larger rows: k_spgemm_numeric_block.
+constexpr int kNumSmall = 64;
+
 __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const int* __restrict__ acol,
                                  const double* __restrict__ aval, const int* __restrict__ brp,
                                  const int* __restrict__ bcol, const double* __restrict__ bval,
                                  const int* __restrict__ crp, const int* __restrict__ ccol,
-                                 double* __restrict__ cval) {
+                                 double* __restrict__ cval, const int* __restrict__ u) {
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += gridDim.x * blockDim.x) {
+    if (u[row] > kNumSmall) continue;
     int c0 = crp[row], c1 = crp[row + 1];
     for (int q = c0; q < c1; ++q) cval[q] = 0.0;
     for (int e = arp[row]; e < arp[row + 1]; ++e) {
@@ -369,6 +475,54 @@ __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const i
         cval[pos] += a * bval[f];
       }
     }
+  }
+}
+
+// One block per row with more than kNumSmall products: the row's column list and
+// accumulators sit in shared memory (rows up to kNumLmax entries; longer rows
+// accumulate in global memory); products are spread over the block and added with
+// atomics (rounding-level order dependence).
+constexpr int kNumLmax = 4096;
+
+__global__ void __launch_bounds__(256) k_spgemm_numeric_block(
+    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
+    const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
+    const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval,
+    const int* __restrict__ u) {
+  __shared__ int scol[kNumLmax];
+  __shared__ double sacc[kNumLmax];
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+    if (u[row] <= kNumSmall) continue;
+    int c0 = crp[row], c1 = crp[row + 1], L = c1 - c0;
+    bool sh = L <= kNumLmax;
+    if (sh) {
+      for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        scol[t] = ccol[c0 + t];
+        sacc[t] = 0.0;
+      }
+    } else {
+      for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = 0.0;
+    }
+    __syncthreads();
+    for (int e = arp[row]; e < arp[row + 1]; ++e) {
+      int j = acol[e];
+      double a = aval[e];
+      for (int f = brp[j] + threadIdx.x; f < brp[j + 1]; f += blockDim.x) {
+        int key = bcol[f];
+        double v = a * bval[f];
+        if (sh) {
+          int pos = find_col(scol, 0, L, key);
+          atomicAdd(&sacc[pos], v);
+        } else {
+          int pos = find_col(ccol, c0, c1, key);
+          atomicAdd(&cval[pos], v);
+        }
+      }
+    }
+    __syncthreads();
+    if (sh)
+      for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = sacc[t];
+    __syncthreads();
   }
 }
 
@@ -415,7 +569,25 @@ __global__ void k_gj_step(int n, int k, double* __restrict__ a, double* __restri
 
 // ---------------------------------------------------------------- host side
 
-static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C) {
+static int spgemm_upper(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, int* u, int* umax) {
+  int n = A.nrows;
+  k_spgemm_upper<<<grid_for(n), kBlock, 0, c->st>>>(n, A.rowptr, A.col, B.rowptr, u);
+  RICH_LAUNCH_CHECK();
+  if (umax) {
+    RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
+    k_max_int<<<grid_for(n), kBlock, 0, c->st>>>(n, u, c->iflag);
+    RICH_LAUNCH_CHECK();
+    RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    RICH_CUDA(cudaStreamSynchronize(c->st));
+    *umax = c->hflag[0];
+  }
+  return RICH_OK;
+}
+
+// C = A B: structural pattern (sorted columns) and values.  *u_keep, if given,
+// receives the per-row product counts (kept for the numeric refresh).
+static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C,
+                           int** u_keep = nullptr) {
   int n = A.nrows;
   C.nrows = n;
   C.ncols = B.ncols;
@@ -424,73 +596,54 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
   RICH_CHECK(dalloc(&u, n));
   RICH_CHECK(dalloc(&cnt, n));
   RICH_CHECK(dalloc(&C.rowptr, (long long)n + 1));
-  k_spgemm_upper<<<grid_for(n), kBlock, 0, c->st>>>(n, A.rowptr, A.col, B.rowptr, u);
-  RICH_LAUNCH_CHECK();
-  RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
-  k_max_int<<<grid_for(n), kBlock, 0, c->st>>>(n, u, c->iflag);
-  RICH_LAUNCH_CHECK();
-  RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  RICH_CUDA(cudaStreamSynchronize(c->st));
-  int umax = c->hflag[0];
+  int umax = 0;
+  RICH_CHECK(spgemm_upper(c, A, B, u, &umax));
   if (umax >= (1 << 30)) return RICH_ELIMIT;
   size_t smem = (size_t)kEscWarps * kEscCap * (sizeof(uint64_t) + sizeof(double));
   int nblk = (n + kEscWarps - 1) / kEscWarps;
   if (nblk > 65535 * 4) nblk = 65535 * 4;
-  // global scratch for rows beyond the shared-memory capacity
-  uint64_t* gk = nullptr;
-  double* gv = nullptr;
-  long long* goff = nullptr;
-  long long* gsz = nullptr;
-  bool need_global = umax > kEscCap;
-  if (need_global) {
-    std::vector<int> hu(n);
-    RICH_CUDA(cudaMemcpy(hu.data(), u, sizeof(int) * n, cudaMemcpyDeviceToHost));
-    std::vector<long long> off(n + 1, 0);
-    for (int i = 0; i < n; ++i) {
-      long long M = 0;
-      if (hu[i] > kEscCap) {
-        M = 1;
-        while (M < hu[i]) M <<= 1;
-      }
-      off[i + 1] = off[i] + M;
-    }
-    RICH_CHECK(dalloc(&goff, n + 1));
-    RICH_CUDA(cudaMemcpy(goff, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
-    RICH_CHECK(dalloc(&gk, off[n]));
-    RICH_CHECK(dalloc(&gv, off[n]));
-  }
+  bool big = umax > kEscCap;
+  size_t hsmem = (size_t)kHashSlots * (sizeof(int) + sizeof(double) + sizeof(uint64_t));
+  if (big) RICH_CUDA(cudaFuncSetAttribute(k_spgemm_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+  int* ovf = c->iflag + 1;
+  RICH_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c->st));
   for (int mode = 0; mode < 2; ++mode) {
     if (mode == 1) {
       RICH_CHECK(scan_exclusive_int(c, cnt, C.rowptr, n));
       int nnz = 0;
       RICH_CUDA(cudaMemcpy(&nnz, C.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+      if (nnz < 0) return RICH_ELIMIT;
       C.nnz = nnz;
       RICH_CHECK(dalloc(&C.col, nnz));
       RICH_CHECK(dalloc(&C.val, nnz));
     }
     k_spgemm_esc<<<nblk, 32 * kEscWarps, smem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
-                                                       C.rowptr, C.col, C.val, cnt, nullptr, nullptr, nullptr);
+                                                       C.rowptr, C.col, C.val, cnt);
     RICH_LAUNCH_CHECK();
-    if (need_global) {
-      k_spgemm_esc<<<grid_for(n, 32), 32, 0, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
-                                                     C.rowptr, C.col, C.val, cnt, gk, gv, goff);
+    if (big) {
+      int hb = n < 8 * kNumSM ? n : 8 * kNumSM;
+      k_spgemm_hash<<<hb, kHashThreads, hsmem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
+                                                        C.rowptr, C.col, C.val, cnt, ovf);
       RICH_LAUNCH_CHECK();
+      RICH_CUDA(cudaMemcpyAsync(c->hflag + 1, ovf, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      RICH_CUDA(cudaStreamSynchronize(c->st));
+      if (c->hflag[1]) return RICH_ELIMIT;  // a row has more distinct columns than the hash table holds
     }
   }
   RICH_CUDA(cudaStreamSynchronize(c->st));
-  dfree(u);
+  if (u_keep) *u_keep = u; else dfree(u);
   dfree(cnt);
-  dfree(gk);
-  dfree(gv);
-  dfree(goff);
-  dfree(gsz);
   return RICH_OK;
 }
 
-static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C) {
+static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C, const int* u) {
   ProfScope ps("spgemm_numeric", c->st, (double)A.nrows * 4 + A.nnz * 12.0 + (double)C.nrows * 4 + C.nnz * 12.0);
   k_spgemm_numeric<<<grid_for(A.nrows, 128), 128, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                              B.val, C.rowptr, C.col, C.val);
+                                                              B.val, C.rowptr, C.col, C.val, u);
+  RICH_LAUNCH_CHECK();
+  int nb = A.nrows < 16 * kNumSM ? A.nrows : 16 * kNumSM;
+  k_spgemm_numeric_block<<<nb, 256, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
+                                               C.col, C.val, u);
   RICH_LAUNCH_CHECK();
   return RICH_OK;
 }
@@ -643,6 +796,8 @@ void amg_free(rich_ctx* c) {
     dfree(L.agg);
     dfree(L.P32);
     dfree(L.R32);
+    dfree(L.u_ap);
+    dfree(L.u_rap);
     if (L.x) cudaFree(L.x);
     if (L.b) cudaFree(L.b);
     if (L.r) cudaFree(L.r);
@@ -785,10 +940,10 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   dfree(Sm.val);
   dfree(Pt.rowptr);
   RICH_CHECK(transpose(c, L.P, L.R));
-  RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP));
+  RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP, &L.u_ap));
   Level nxt;
   nxt.n = nc;
-  RICH_CHECK(spgemm_symbolic(c, L.R, L.AP, nxt.A));
+  RICH_CHECK(spgemm_symbolic(c, L.R, L.AP, nxt.A, &L.u_rap));
   if (c->prec == RICH_PREC_MIXED) {
     RICH_CHECK(dalloc(&L.P32, L.P.nnz));
     RICH_CHECK(dalloc(&L.R32, L.R.nnz));
@@ -851,8 +1006,8 @@ int amg_refresh(rich_ctx* c) {
   H.lv[0].A = c->A0;
   for (int l = 0; l + 1 < H.nlev; ++l) {
     Level& L = H.lv[l];
-    RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP));
-    RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A));
+    RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP, L.u_ap));
+    RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A, L.u_rap));
   }
   for (int l = 0; l < H.nlev; ++l) RICH_CHECK(level_diag_data(c, H.lv[l]));
   RICH_CHECK(fine_stencil(c));

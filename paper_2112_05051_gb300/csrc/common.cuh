@@ -101,6 +101,8 @@ struct Level {
   float* dinv32 = nullptr;
   int* agg = nullptr;              // aggregate of each node (levels with a coarser level)
   Csr<double> P, R, AP;            // to the next level; AP = A P (pattern kept for refresh)
+  int* u_ap = nullptr;             // products per row of A P and of R (A P) (refresh kernels' split)
+  int* u_rap = nullptr;
   float* P32 = nullptr;            // values of P/R in FP32
   float* R32 = nullptr;
   int mis_rounds = 0;
@@ -238,6 +240,12 @@ __device__ __forceinline__ double face_mean(int kmean, double kL, double kU, dou
     dL = up ? 0.0 : 1.0;
     dU = up ? 1.0 : 0.0;
     return up ? kU : kL;
+  }
+  if (kmean == RICH_KMEAN_GEOMETRIC) {
+    double g = sqrt(kL * kU);
+    dL = kL > 0.0 ? 0.5 * g / kL : 0.0;
+    dU = kU > 0.0 ? 0.5 * g / kU : 0.0;
+    return g;
   }
   double s = kL + kU;
   if (s > 0.0) {

@@ -80,7 +80,7 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
                            const double* __restrict__ K, const double* __restrict__ S,
                            const double* __restrict__ s_old, const double* __restrict__ ks, double dt,
                            double* __restrict__ F, double* __restrict__ partials) {
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   double amax = 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.n;
        c += (long long)gridDim.x * blockDim.x) {
@@ -90,7 +90,9 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
     int k = (int)(r / g.ny);
     double pc = p[c], Kc = K[c];
     double ksc = ks ? ks[c] : so.ks;
-    double phi = so.rho_phi * (S[c] - s_old[c]) / dt;
+    double sc = S[c], so_c = s_old[c];
+    double phi = so.rho_phi * (sc - so_c) / dt;
+    double mag = so.rho_phi * (fabs(sc) + fabs(so_c)) / dt;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       FaceNb nb;
@@ -101,19 +103,26 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
       double ka = (f & 1) ? face_mean(kmean, Kc, nb.K, pc, nb.p, dL, dU)
                           : face_mean(kmean, nb.K, Kc, nb.p, pc, dL, dU);
       double t = ka * (pc - nb.p) * g.inv_h2[axis];
-      if (axis == 2) t -= side * (Kc + nb.K) * 0.5 * g.inv_h[2];
+      double m = ka * (fabs(pc) + fabs(nb.p)) * g.inv_h2[axis];
+      if (axis == 2) {
+        t -= side * (Kc + nb.K) * 0.5 * g.inv_h[2];
+        m += (Kc + nb.K) * 0.5 * g.inv_h[2];
+      }
       phi += t;
+      mag += m;
     }
     F[c] = phi;
     acc[0] += phi * phi;
+    acc[1] += mag * mag;
     double a = fabs(phi);
     amax = (a > amax || a != a) ? a : amax;  // NaN propagates into the max
   }
-  block_sum<1>(acc);
+  block_sum<2>(acc);
   double m = block_max(amax);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = acc[0];
     partials[gridDim.x + blockIdx.x] = m;
+    partials[2 * gridDim.x + blockIdx.x] = acc[1];
   }
 }
 
@@ -242,9 +251,10 @@ int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, 
                                          c->partials);
   }
   RICH_LAUNCH_CHECK();
-  if (want_norms) {
+  if (want_norms) {  // dsc[0] = ||F||^2, dsc[1] = ||F||_inf, dsc[2] = ||term magnitudes||^2
     RICH_CHECK(finish_sums(c, c->partials, nb, 1, c->dsc + 0));
     RICH_CHECK(finish_max(c, c->partials + nb, nb, c->dsc + 1));
+    RICH_CHECK(finish_sums(c, c->partials + 2 * nb, nb, 1, c->dsc + 2));
   }
   return RICH_OK;
 }
@@ -359,7 +369,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   *out = nullptr;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return RICH_EINVAL;
   if (!(grid->lx > 0 && grid->ly > 0 && grid->lz > 0)) return RICH_EINVAL;
-  if (kmean < 0 || kmean > 2 || (precision != RICH_PREC_FP64 && precision != RICH_PREC_MIXED)) return RICH_EINVAL;
+  if (kmean < 0 || kmean > 3 || (precision != RICH_PREC_FP64 && precision != RICH_PREC_MIXED)) return RICH_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   if (n > 2147483647LL / 8) return RICH_ELIMIT;  // 32-bit CSR indices of the 7-point pattern
   for (int f = 0; f < 6; ++f)

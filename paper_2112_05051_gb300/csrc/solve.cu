@@ -54,6 +54,28 @@ __global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict_
   }
 }
 
+// CSR row operation with one warp per row, for levels whose rows are long
+// (coarse Galerkin operators carry tens to hundreds of entries per row).
+// MODE 0: y = A x; 1: y += A x; 2: y = x + dinv (b - A x); 3: y = b - A x.
+template <class T, int MODE>
+__global__ void k_csr_warp(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+                           const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+                           T* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    T s = 0;
+    for (int e = rp[row] + lane; e < rp[row + 1]; e += 32) s += val[e] * x[col[e]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (MODE == 0) y[row] = s;
+      else if (MODE == 1) y[row] += s;
+      else if (MODE == 2) y[row] = x[row] + dinv[row] * (b[row] - s);
+      else y[row] = b[row] - s;
+    }
+  }
+}
+
 // x = M b for a dense row-major n x n matrix; one warp per row.
 template <class T>
 __global__ void k_gemv(int n, const T* __restrict__ M, const T* __restrict__ b, T* __restrict__ x) {
@@ -180,6 +202,9 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   int nu1 = H.opts.nu1, nu2 = H.opts.nu2;
   // finest level: stencil form (4 coefficient arrays + b + x in, x out)
   const bool st0 = (l == 0);
+  // warp-per-row CSR kernels where rows are long
+  const bool wA = L.A.nnz > 12LL * n;
+  const int gw = grid_for((long long)n * 32);
   const double st_bytes = (double)n * 7.0 * es;
   if (nu1 > 0) {
     if (st0) {
@@ -192,6 +217,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       {
         ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
         if (st0) k_st_smooth<T, 1><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
+        else if (wA) k_csr_warp<T, 2><<<gw, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
         else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
       }
       RICH_LAUNCH_CHECK();
@@ -200,6 +226,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     {
       ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st, st0 ? st_bytes : sweep_bytes - (double)n * es);
       if (st0) k_st_smooth<T, 2><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
+      else if (wA) k_csr_warp<T, 3><<<gw, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, nullptr, b, x, (T*)L.r);
       else k_resid<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, b, x, (T*)L.r);
     }
     RICH_LAUNCH_CHECK();
@@ -210,20 +237,28 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   Level& C = H.lv[l + 1];
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
-    k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
+    if (L.R.nnz > 8LL * C.n)
+      k_csr_warp<T, 0><<<grid_for((long long)C.n * 32), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, nullptr,
+                                                                            nullptr, (const T*)L.r, (T*)C.b);
+    else
+      k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
+    if (L.P.nnz > 8LL * n)
+      k_csr_warp<T, 1><<<gw, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, nullptr, nullptr, xc, x);
+    else
+      k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < nu2; ++s) {
     {
       ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
       if (st0) k_st_smooth<T, 1><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
+      else if (wA) k_csr_warp<T, 2><<<gw, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
       else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
     }
     RICH_LAUNCH_CHECK();
@@ -298,6 +333,41 @@ __global__ void k_fcg_update(long long n, double* __restrict__ x, double* __rest
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
 }
 
+// partials[q*nb + b] = sum over block b of V[q] . w  for q < nv: a single pass in
+// which each element's V values are consumed as they arrive (NVMAX >= nv).
+template <int NVMAX>
+__global__ void k_multidot_rb(long long n, int nv, const double* __restrict__ V, const double* __restrict__ w,
+                              double* __restrict__ partials) {
+  double acc[NVMAX];
+#pragma unroll
+  for (int q = 0; q < NVMAX; ++q) acc[q] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < NVMAX; ++q)
+      if (q < nv) acc[q] += V[(long long)q * n + i] * wi;
+  }
+#pragma unroll
+  for (int q0 = 0; q0 < NVMAX; q0 += 4) {
+    if (q0 >= nv) break;
+    double v[4] = {acc[q0], acc[q0 + 1], acc[q0 + 2], acc[q0 + 3]};
+    block_sum<4>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
+    }
+  }
+}
+
+static void launch_multidot(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* w,
+                            double* partials) {
+  if (nv <= 8) k_multidot_rb<8><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
+  else if (nv <= 16) k_multidot_rb<16><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
+  else if (nv <= 32) k_multidot_rb<32><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
+  else k_multidot_rb<64><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
+}
+
 // partials[q*nb + b] = sum over block b of V[q] . w  for q < nv
 __global__ void k_multidot(long long n, int nv, const double* __restrict__ V, const double* __restrict__ w,
                            double* __restrict__ partials) {
@@ -316,6 +386,69 @@ __global__ void k_multidot(long long n, int nv, const double* __restrict__ V, co
         if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
     }
     __syncthreads();
+  }
+}
+
+// w' = w - sum_q h1[q] V[q] (written back to w), with the partial sums of V^T w'
+// (nv of them) and of ||w'||^2 from the same single pass over V: each element's
+// V values stay in registers (NVMAX >= nv, a compile-time bound).
+template <int NVMAX>
+__global__ void k_orth_pass2(long long n, int nv, const double* __restrict__ V, const double* __restrict__ h1,
+                             double* __restrict__ w, double* __restrict__ partials) {
+  __shared__ double hs[NVMAX];
+  for (int q = threadIdx.x; q < NVMAX; q += blockDim.x) hs[q] = q < nv ? h1[q] : 0.0;
+  __syncthreads();
+  double acc[NVMAX];
+  double nrm = 0.0;
+#pragma unroll
+  for (int q = 0; q < NVMAX; ++q) acc[q] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double vq[NVMAX];
+    double t = w[i];
+#pragma unroll
+    for (int q = 0; q < NVMAX; ++q) {
+      vq[q] = q < nv ? V[(long long)q * n + i] : 0.0;
+      t -= hs[q] * vq[q];
+    }
+    w[i] = t;
+    nrm += t * t;
+#pragma unroll
+    for (int q = 0; q < NVMAX; ++q) acc[q] += vq[q] * t;
+  }
+  double nr[1] = {nrm};
+  block_sum<1>(nr);
+  if (threadIdx.x == 0) partials[(long long)nv * gridDim.x + blockIdx.x] = nr[0];
+#pragma unroll
+  for (int q0 = 0; q0 < NVMAX; q0 += 4) {
+    if (q0 >= nv) break;
+    double v[4] = {acc[q0], acc[q0 + 1], acc[q0 + 2], acc[q0 + 3]};
+    block_sum<4>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
+    }
+  }
+}
+
+static void launch_orth_pass2(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* h1,
+                              double* w, double* partials) {
+  if (nv <= 8) k_orth_pass2<8><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
+  else if (nv <= 16) k_orth_pass2<16><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
+  else if (nv <= 32) k_orth_pass2<32><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
+  else k_orth_pass2<64><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
+}
+
+// out = f * (w - sum_q h2[q] V[q])
+__global__ void k_orth_final(long long n, int nv, const double* __restrict__ V, const double* __restrict__ h2,
+                             const double* __restrict__ w, double f, double* __restrict__ out) {
+  __shared__ double hs[64];
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) hs[q] = h2[q];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double t = w[i];
+    for (int q = 0; q < nv; ++q) t -= hs[q] * V[(long long)q * n + i];
+    out[i] = f * t;
   }
 }
 
@@ -478,30 +611,38 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       double* Zj = k.Z + (long long)j * n;
       RICH_CHECK(vcycle_apply(c, Vj, Zj));
       RICH_CHECK(stencil_apply(c, c->J7, Zj, k.w));
-      for (int pass = 0; pass < 2; ++pass) {
-        {
-          ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2));
-          k_multidot<<<nb, kBlock, 0, c->st>>>(n, j + 1, k.V, k.w, c->partials);
-        }
-        RICH_LAUNCH_CHECK();
-        RICH_CHECK(finish_sums(c, c->partials, nb, j + 1, s + 64 * pass));
-        {
-          ProfScope ps("multiaxpy", c->st, (double)n * 8.0 * (j + 3));
-          k_multiaxpy<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s + 64 * pass, -1.0, k.w);
-        }
-        RICH_LAUNCH_CHECK();
+      // Classical Gram-Schmidt with one re-orthogonalisation, three passes over V:
+      //   h1 = V^T w;  w' = w - V h1 with h2 = V^T w' and ||w'||^2 in the same pass;
+      //   V[j+1] = (w' - V h2) / hn, hn^2 = ||w'||^2 - ||h2||^2 (V orthonormal).
+      {
+        ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2));
+        launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
       }
-      RICH_CHECK(nrm2sq(c, k.w, n, s + 127));
+      RICH_LAUNCH_CHECK();
+      RICH_CHECK(finish_sums(c, c->partials, nb, j + 1, s));
+      {
+        ProfScope ps("orth_reorth", c->st, (double)n * 8.0 * (j + 3));  // V once, w read + written
+        launch_orth_pass2(nb, c->st, n, j + 1, k.V, s, k.w, c->partials);
+      }
+      RICH_LAUNCH_CHECK();
+      RICH_CHECK(finish_sums(c, c->partials, nb, j + 2, s + 64));
       RICH_CUDA(cudaMemcpyAsync(c->hsc, s, 128 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       RICH_CUDA(cudaStreamSynchronize(c->st));
-      for (int i = 0; i <= j; ++i) Hij(i, j) = c->hsc[i] + c->hsc[64 + i];
-      double hn = sqrt(c->hsc[127]);
+      double h2sq = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        Hij(i, j) = c->hsc[i] + c->hsc[64 + i];
+        h2sq += c->hsc[64 + i] * c->hsc[64 + i];
+      }
+      double wsq = c->hsc[64 + j + 1] - h2sq;
+      double hn = wsq > 0 ? sqrt(wsq) : 0.0;
       if (!std::isfinite(hn)) return RICH_ENONFINITE;
       Hij(j + 1, j) = hn;
-      if (hn > 0) {
-        k_scale<<<g, kBlock, 0, c->st>>>(n, k.w, 1.0 / hn, k.V + (long long)(j + 1) * n);
-        RICH_LAUNCH_CHECK();
+      {
+        ProfScope ps("orth_final", c->st, (double)n * 8.0 * (j + 3));
+        k_orth_final<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s + 64, k.w, hn > 0 ? 1.0 / hn : 0.0,
+                                             k.V + (long long)(j + 1) * n);
       }
+      RICH_LAUNCH_CHECK();
       for (int i = 0; i < j; ++i) {
         double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
         Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
@@ -586,16 +727,22 @@ static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
   int g = grid_for(n);
   memset(st, 0, sizeof(*st));
   st->min_lambda = 1.0;
-  double h[2];
+  // Converged when ||Phi|| <= max(rtol ||Phi_0||, atol, floor): the floor is
+  // eps times the norm of the per-cell magnitudes of the products summed into
+  // Phi, the accuracy to which Phi can be evaluated (a step that starts near
+  // steady state cannot be driven to rtol ||Phi_0|| below it).
+  const double kFloor = 2.220446049250313e-16;
+  double h[3];
   RICH_CHECK(rich_saturation(c, p, c->s_old));
   RICH_CHECK(residual_eval(c, p, c->s_old, dt, c->F, true));
-  RICH_CHECK(fetch_scalars(c, c->dsc, 1, h));
+  RICH_CHECK(fetch_scalars(c, c->dsc, 3, h));
   double fn = sqrt(h[0]);
+  double floor_ = kFloor * sqrt(h[2]);
   if (!std::isfinite(fn)) return RICH_ENONFINITE;
   st->res0 = st->res = fn;
   double tol = std::max(o->rtol * fn, o->atol);
   for (int r = 0;; ++r) {
-    if (fn <= tol) {
+    if (fn <= std::max(tol, floor_)) {
       st->converged = 1;
       break;
     }
@@ -630,14 +777,15 @@ static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
     double slope = h[0];
     if (!(slope < 0.0)) return RICH_ELINESEARCH;
     double f0 = 0.5 * fn * fn;
-    double lam = 1.0, ft = 0.0;
+    double lam = 1.0, ft = 0.0, floor_t = 0.0;
     for (;;) {
       k_axpby<<<g, kBlock, 0, c->st>>>(n, p, lam, c->d, c->ptrial);
       RICH_LAUNCH_CHECK();
       RICH_CHECK(residual_eval(c, c->ptrial, c->s_old, dt, c->Ft, true));
-      RICH_CHECK(fetch_scalars(c, c->dsc, 1, h));
+      RICH_CHECK(fetch_scalars(c, c->dsc, 3, h));
       st->line_search_evals++;
       ft = 0.5 * h[0];
+      floor_t = kFloor * sqrt(h[2]);
       if (!std::isfinite(ft)) return RICH_ENONFINITE;
       if (ft <= f0 + o->armijo_c * lam * slope) break;
       double lq = -slope * lam * lam / (2.0 * (ft - f0 - slope * lam));
@@ -647,6 +795,7 @@ static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
     RICH_CUDA(cudaMemcpyAsync(p, c->ptrial, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
     std::swap(c->F, c->Ft);
     fn = sqrt(2.0 * ft);
+    floor_ = floor_t;
     st->res = fn;
     st->newton_its++;
     st->min_lambda = std::min(st->min_lambda, lam);

@@ -31,7 +31,9 @@ BC_DIRICHLET = 1
 KMEAN_ARITH = 0
 KMEAN_UPSTREAM = 1
 KMEAN_HARMONIC = 2
-KMEAN_NAMES = {KMEAN_ARITH: "arithmetic", KMEAN_UPSTREAM: "upstream", KMEAN_HARMONIC: "harmonic"}
+KMEAN_GEOMETRIC = 3
+KMEAN_NAMES = {KMEAN_ARITH: "arithmetic", KMEAN_UPSTREAM: "upstream", KMEAN_HARMONIC: "harmonic",
+               KMEAN_GEOMETRIC: "geometric"}
 
 
 @dataclasses.dataclass(frozen=True)

@@ -101,11 +101,13 @@ def test_vcycle_parity_fp64_and_mixed(nu):
         ctx.close()
 
 
-def test_refresh_matches_oracle_galerkin_refresh():
+@pytest.mark.parametrize("dims,coarse_max", [((18, 16, 14), 150), ((40, 36, 32), 2000)])
+def test_refresh_matches_oracle_galerkin_refresh(dims, coarse_max):
+    # the larger grid has coarse rows with > 64 and > 1024 products (block and hash kernels)
     rb = _rb()
-    grid, p, ks, bc, dt, kmean = _problem((18, 16, 14), 8, 0)
+    grid, p, ks, bc, dt, kmean = _problem(dims, 8, 0)
     p2 = p + np.random.default_rng(4).uniform(0, 15, grid.n)
-    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, 150)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, coarse_max)
     ctx.jacobian(torch.tensor(p2, device="cuda"), 2.0 * dt)
     ctx.amg_update(rb.AMG_REFRESH)
     amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, p2, 2.0 * dt, ks))

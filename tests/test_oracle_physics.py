@@ -16,7 +16,7 @@ from oracle import discretization as disc
 from paper_2112_05051_gb300 import synth
 
 SOIL = synth.Soil()
-MEANS = [synth.KMEAN_ARITH, synth.KMEAN_UPSTREAM, synth.KMEAN_HARMONIC]
+MEANS = [synth.KMEAN_ARITH, synth.KMEAN_UPSTREAM, synth.KMEAN_HARMONIC, synth.KMEAN_GEOMETRIC]
 
 
 # ---------------------------------------------------------------- constitutive (eqs. (s(p)), (K(p)))
