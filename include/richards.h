@@ -152,6 +152,11 @@ typedef struct {
   int converged;           /* 1 if rtol/atol was met */
   double res0, res;        /* ||Phi||_2 at the start and at the end of the step */
   double min_lambda;       /* smallest accepted step length */
+  /* device time per phase (ms), the phases of the paper's time breakdown
+   * (Sec. 6): residual evaluations (Feval), Jacobian + diffusion-matrix
+   * assembly (Jacobian/Auxiliary), AMG setup or refresh (Setup), Krylov
+   * solves (LinSol); the rest of the step is Overhead (no Halo on one GPU). */
+  double ms_feval, ms_jacobian, ms_setup, ms_linsol, ms_total;
 } rich_step_stats;
 
 typedef struct {
@@ -187,6 +192,23 @@ int rich_saturation(rich_ctx* ctx, const double* p_dev, double* s_dev);
  * non-finite Phi returns RICH_ENONFINITE after writing F_dev. */
 int rich_residual(rich_ctx* ctx, const double* p_dev, const double* s_old_dev, double dt,
                   double* F_dev, double* norms_host);
+
+/* The residual of rich_residual without a context and without any device
+ * allocation.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory where they need a residual (a fixed,
+ * pre-reserved memory budget, an allocator that owns all device memory, or a
+ * loop that must not risk the synchronisation a cudaMalloc can cause).
+ * Inputs as for rich_create/rich_residual (soil->ks_field_dev is read in place,
+ * not copied); F_dev receives Phi; norms_host, if not NULL, receives
+ * {||Phi||_2, ||Phi||_inf} and the call then synchronises the stream.
+ * The only scratch is a file-scope device array of about 1 MB shared by all
+ * calls; grids above 134,217,728 cells (512^3) return RICH_ELIMIT.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  Calls that overlap on the
+ * GPU race on the shared array and must be serialised by the caller. */
+int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soil, int kmean, const rich_bc* bc,
+                          const double* p_dev, const double* s_old_dev, double dt, double* F_dev,
+                          double* norms_host, void* stream);
 
 /* ---- Sec. 3-4: Jacobian and diffusion-only preconditioner matrix ------- */
 /* Assemble J(p) = dPhi/dp (exact derivative of the residual; in the interior
@@ -250,6 +272,9 @@ int rich_profile_kernel(const char* name);
 /* Sum of the recorded launch durations (ms), number of recorded launches and
  * the algorithmic bytes those launches must move (synchronises the events). */
 int rich_profile_result(double* ms_total, long long* launches, double* bytes_total);
+/* With the target "*": per-kernel totals, one line "name launches ms bytes" each,
+ * written into buf (at most cap bytes, NUL-terminated). */
+int rich_profile_table(char* buf, int cap);
 
 /* Default option structs (as listed in the comments above). */
 void rich_default_newton_opts(rich_newton_opts* o);

@@ -69,7 +69,8 @@ class StepStats(ctypes.Structure):
     _fields_ = [("newton_its", ctypes.c_int), ("linear_its", ctypes.c_int), ("line_search_evals", ctypes.c_int),
                 ("fallbacks", ctypes.c_int), ("amg_setups", ctypes.c_int), ("amg_refreshes", ctypes.c_int),
                 ("converged", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
-                ("min_lambda", ctypes.c_double)]
+                ("min_lambda", ctypes.c_double), ("ms_feval", ctypes.c_double), ("ms_jacobian", ctypes.c_double),
+                ("ms_setup", ctypes.c_double), ("ms_linsol", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +93,14 @@ EXPORTS = {
     "rich_num_cells": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "rich_saturation": (ctypes.c_int, [_P, _P, _P]),
     "rich_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rich_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Soil), ctypes.c_int,
+                                             ctypes.POINTER(BC), _P, _P, ctypes.c_double, _P,
+                                             ctypes.POINTER(ctypes.c_double), _P]),
+    "rich_kernel_launches": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
+    "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
+    "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "rich_profile_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "rich_jacobian": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P]),
     "rich_jacobian_apply": (ctypes.c_int, [_P, _P, _P]),
     "amg_setup": (ctypes.c_int, [_P, ctypes.POINTER(AmgOpts), ctypes.POINTER(AmgInfo)]),
@@ -166,6 +175,33 @@ def default_amg_opts(**kw):
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def residual_noalloc(grid, soil, bc, kmean, p, s_old, dt, F, ks=None, norms=True):
+    """Phi(p) through rich_residual_noalloc (no context, no device allocation by the library).
+
+    ks, if given, must be a contiguous float64 CUDA tensor of n cells (read in place).
+    Returns the status code and (||Phi||_2, ||Phi||_inf) or None.
+    """
+    g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+    s = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
+             _ptr(ks) if ks is not None else None)
+    b = BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value))
+    arr = (ctypes.c_double * 2)() if norms else None
+    st = load().rich_residual_noalloc(ctypes.byref(g), ctypes.byref(s), kmean, ctypes.byref(b), _ptr(p),
+                                      _ptr(s_old), dt, _ptr(F), arr, _stream())
+    return st, ((arr[0], arr[1]) if norms else None)
+
+
+def profile_table():
+    """Per-kernel totals recorded under the "*" profiling target: {name: (launches, ms, bytes)}."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(load().rich_profile_table(buf, len(buf)), "rich_profile_table")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms, b = line.split()
+        out[name] = (int(n), float(ms), float(b))
+    return out
 
 
 class Context:
