@@ -267,6 +267,9 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     step_ms = sorted(marks[q].elapsed_time(marks[q + 1]) for q in range(args.steps))
+    phases = {k: sum(d[k] for d in stats) for k in ("ms_feval", "ms_jacobian", "ms_setup", "ms_linsol", "ms_total")}
+    phases["ms_overhead"] = phases["ms_total"] - sum(phases[k] for k in ("ms_feval", "ms_jacobian", "ms_setup",
+                                                                           "ms_linsol"))
     if dist:
         dist.barrier()
     elapsed = e0.elapsed_time(e1) / 1000.0
@@ -361,6 +364,7 @@ def run_ours(args):
                                          "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                                          "max": step_ms[-1]},
             "fp32_amg": mixed,
+            "phase_ms": {k[3:]: round(v, 3) for k, v in phases.items()},
             "parallelism": "replicas" if ws > 1 else "single"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)

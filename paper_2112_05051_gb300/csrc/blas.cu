@@ -13,28 +13,34 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- live kernel timing
 
-constexpr int kProfEvents = 16384;
-static std::string g_prof_target;
+constexpr int kProfEvents = 65536;
+static std::string g_prof_target;   // a kernel name, "*" for every named kernel, "" = off
 static std::vector<cudaEvent_t> g_prof_ev;
+static std::vector<const char*> g_prof_name;
+static std::vector<double> g_prof_b;
 static int g_prof_n = 0;          // recorded launch pairs
 static long long g_prof_seen = 0; // launches of the target (recorded or not)
 static double g_prof_bytes = 0.0;
 
 ProfScope::ProfScope(const char* name, cudaStream_t s, double b) : on(false), st(s), bytes(b) {
-  if (g_prof_target.empty() || g_prof_target != name) return;
+  if (g_prof_target.empty() || (g_prof_target != "*" && g_prof_target != name)) return;
   ++g_prof_seen;
   if (g_prof_n >= kProfEvents / 2) return;
   if (g_prof_ev.empty()) {
     g_prof_ev.resize(kProfEvents);
     for (auto& e : g_prof_ev) cudaEventCreate(&e);
+    g_prof_name.resize(kProfEvents / 2);
+    g_prof_b.resize(kProfEvents / 2);
   }
   on = true;
+  g_prof_name[g_prof_n] = name;
   cudaEventRecord(g_prof_ev[2 * g_prof_n], st);
 }
 
 ProfScope::~ProfScope() {
   if (!on) return;
   cudaEventRecord(g_prof_ev[2 * g_prof_n + 1], st);
+  g_prof_b[g_prof_n] = bytes;
   g_prof_bytes += bytes;
   ++g_prof_n;
 }
@@ -238,6 +244,35 @@ int rich_profile_result(double* ms_total, long long* launches, double* bytes_tot
   *ms_total = ms;
   *launches = rich::g_prof_n;
   *bytes_total = rich::g_prof_bytes;
+  return RICH_OK;
+}
+
+// Per-kernel totals of the recorded launches (profiling target "*"): writes up
+// to cap lines "name launches total_ms bytes" into buf (NUL-terminated).
+int rich_profile_table(char* buf, int cap) {
+  if (!buf || cap < 1) return RICH_EINVAL;
+  struct Acc { double ms = 0.0; long long n = 0; double bytes = 0.0; };
+  std::vector<std::pair<std::string, Acc>> tab;
+  for (int i = 0; i < rich::g_prof_n; ++i) {
+    cudaEventSynchronize(rich::g_prof_ev[2 * i + 1]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, rich::g_prof_ev[2 * i], rich::g_prof_ev[2 * i + 1]);
+    std::string nm = rich::g_prof_name[i];
+    size_t k = 0;
+    while (k < tab.size() && tab[k].first != nm) ++k;
+    if (k == tab.size()) tab.push_back({nm, Acc()});
+    tab[k].second.ms += t;
+    tab[k].second.n += 1;
+    tab[k].second.bytes += rich::g_prof_b[i];
+  }
+  int off = 0;
+  buf[0] = 0;
+  for (auto& e : tab) {
+    int w = snprintf(buf + off, cap - off, "%s %lld %.6f %.6e\n", e.first.c_str(), e.second.n, e.second.ms,
+                     e.second.bytes);
+    if (w < 0 || w >= cap - off) break;
+    off += w;
+  }
   return RICH_OK;
 }
 

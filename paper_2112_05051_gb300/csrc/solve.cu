@@ -721,20 +721,85 @@ static int ensure_newton(rich_ctx* c) {
   return RICH_OK;
 }
 
+// CUDA-event timers of the step's phases; ms accumulate into the target at resolve().
+struct PhaseTimers {
+  std::vector<cudaEvent_t> ev;
+  std::vector<double*> acc;
+  std::vector<char> closed;
+  cudaStream_t st;
+  explicit PhaseTimers(cudaStream_t s) : st(s) {}
+  ~PhaseTimers() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  int begin(double* target) {
+    int i = (int)acc.size();
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    ev.push_back(a);
+    ev.push_back(b);
+    acc.push_back(target);
+    closed.push_back(0);
+    cudaEventRecord(a, st);
+    return i;
+  }
+  void end(int i) {
+    cudaEventRecord(ev[2 * i + 1], st);
+    closed[i] = 1;
+  }
+  void resolve() {
+    for (size_t i = 0; i < acc.size(); ++i) {
+      if (!closed[i]) continue;
+      cudaEventSynchronize(ev[2 * i + 1]);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      *acc[i] += t;
+    }
+  }
+};
+
+// RAII phase: ends on scope exit, including early error returns.
+struct Phase {
+  PhaseTimers& pt;
+  int i;
+  Phase(PhaseTimers& p, double* target) : pt(p), i(p.begin(target)) {}
+  ~Phase() { pt.end(i); }
+};
+
+static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st,
+                     PhaseTimers& pt);
+
 static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) {
   RICH_CHECK(ensure_newton(c));
   long long n = c->g.n;
   int g = grid_for(n);
   memset(st, 0, sizeof(*st));
   st->min_lambda = 1.0;
+  PhaseTimers pt(c->st);
+  int rc;
+  {
+    Phase whole(pt, &st->ms_total);
+    rc = step_body(c, p, dt, o, st, pt);
+  }
+  pt.resolve();
+  return rc;
+}
+
+static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st,
+                     PhaseTimers& pt) {
+  long long n = c->g.n;
+  int g = grid_for(n);
   // Converged when ||Phi|| <= max(rtol ||Phi_0||, atol, floor): the floor is
   // eps times the norm of the per-cell magnitudes of the products summed into
   // Phi, the accuracy to which Phi can be evaluated (a step that starts near
   // steady state cannot be driven to rtol ||Phi_0|| below it).
   const double kFloor = 2.220446049250313e-16;
   double h[3];
-  RICH_CHECK(rich_saturation(c, p, c->s_old));
-  RICH_CHECK(residual_eval(c, p, c->s_old, dt, c->F, true));
+  {
+    Phase ph(pt, &st->ms_feval);
+    RICH_CHECK(rich_saturation(c, p, c->s_old));
+    RICH_CHECK(residual_eval(c, p, c->s_old, dt, c->F, true));
+  }
   RICH_CHECK(fetch_scalars(c, c->dsc, 3, h));
   double fn = sqrt(h[0]);
   double floor_ = kFloor * sqrt(h[2]);
@@ -747,18 +812,25 @@ static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
       break;
     }
     if (r == o->max_newton) return RICH_ENOTCONV_NEWTON;
-    RICH_CHECK(jacobian_eval(c, p, dt));
+    {
+      Phase ph(pt, &st->ms_jacobian);
+      RICH_CHECK(jacobian_eval(c, p, dt));
+    }
     bool rebuild = !c->H.built || (o->amg_policy == RICH_AMG_REBUILD_STEP && r == 0);
-    if (rebuild) {
-      RICH_CHECK(amg_build(c, &o->amg));
-      st->amg_setups++;
-    } else {
-      RICH_CHECK(o->amg_policy == RICH_AMG_SETUP_ONCE ? amg_update_fine(c) : amg_refresh(c));
-      st->amg_refreshes++;
+    {
+      Phase ph(pt, &st->ms_setup);
+      if (rebuild) {
+        RICH_CHECK(amg_build(c, &o->amg));
+        st->amg_setups++;
+      } else {
+        RICH_CHECK(o->amg_policy == RICH_AMG_SETUP_ONCE ? amg_update_fine(c) : amg_refresh(c));
+        st->amg_refreshes++;
+      }
     }
     k_scale<<<g, kBlock, 0, c->st>>>(n, c->F, -1.0, c->rhs);
     RICH_LAUNCH_CHECK();
     rich_krylov_stats ks;
+    int lin_phase = pt.begin(&st->ms_linsol);
     int s = krylov_run(c, c->rhs, c->d, &o->krylov, &ks);
     st->linear_its += ks.iterations;
     if (s == RICH_ENOTCONV_LIN && o->krylov.kind == RICH_KRYLOV_FCG) {
@@ -769,6 +841,7 @@ static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
       s = krylov_run(c, c->rhs, c->d, &fb, &ks);
       st->linear_its += ks.iterations;
     }
+    pt.end(lin_phase);
     if (s != RICH_OK) return s;
     // slope of f = 1/2 ||Phi||^2 along d: g = Phi . (J d)
     RICH_CHECK(stencil_apply(c, c->J7, c->d, c->Ft));
@@ -779,9 +852,12 @@ static int step_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
     double f0 = 0.5 * fn * fn;
     double lam = 1.0, ft = 0.0, floor_t = 0.0;
     for (;;) {
-      k_axpby<<<g, kBlock, 0, c->st>>>(n, p, lam, c->d, c->ptrial);
-      RICH_LAUNCH_CHECK();
-      RICH_CHECK(residual_eval(c, c->ptrial, c->s_old, dt, c->Ft, true));
+      {
+        Phase ph(pt, &st->ms_feval);
+        k_axpby<<<g, kBlock, 0, c->st>>>(n, p, lam, c->d, c->ptrial);
+        RICH_LAUNCH_CHECK();
+        RICH_CHECK(residual_eval(c, c->ptrial, c->s_old, dt, c->Ft, true));
+      }
       RICH_CHECK(fetch_scalars(c, c->dsc, 3, h));
       st->line_search_evals++;
       ft = 0.5 * h[0];
