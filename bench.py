@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="richards128_fp64")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="run the workload's settings on an n^3 grid instead (profiling captures); not a bench line")
     ap.add_argument("--roofline-kernel", default="multidot")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-AMG comparison run")
@@ -125,17 +127,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def workload_setup(name):
+def workload_setup(name, n=None):
     from paper_2112_05051_gb300 import synth
     w = synth.WORKLOADS[name]
-    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w)
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w, n)
     return w, grid, soil, bc, ks, p0, dts
 
 
 def newton_opts(rb, w):
     return rb.default_newton_opts(kind=rb.KRYLOV_FGMRES if w.krylov == "fgmres" else rb.KRYLOV_FCG,
                                   restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu, seed=w.amg_seed,
-                                  coarse_max=w.coarse_max, amg_policy=rb.AMG_REFRESH)
+                                  coarse_max=w.coarse_max, amg_policy=rb.AMG_REFRESH, smooth_levels=w.smooth_levels)
 
 
 def cpu_baseline(workload, budget, warm_only=False):
@@ -156,7 +158,8 @@ def oracle_sample_main(workload, budget, steps=None, warmup=None):
     w, grid, soil, bc, ks, p0, dts = workload_setup(workload)
     prob = newton.Problem(grid, soil, bc, w.kmean, ks)
     opt = newton.NewtonOptions(krylov=w.krylov, restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu,
-                               amg_seed=w.amg_seed, coarse_max=w.coarse_max, max_newton=1)
+                               amg_seed=w.amg_seed, coarse_max=w.coarse_max, max_newton=1,
+                               smooth_levels=w.smooth_levels)
     p = p0.copy()
     t0 = time.perf_counter()
     p, st = newton.step(prob, p, dts[0], opt)  # builds the hierarchy (not timed)
@@ -212,6 +215,8 @@ def workload_config(w, grid):
     return {"workload": w.name, "grid": [grid.nx, grid.ny, grid.nz], "dof": grid.n,
             "kmean": synth.KMEAN_NAMES[w.kmean], "krylov": "%s(%d)" % (w.krylov, w.restart) if w.restart else w.krylov,
             "vcycle": "V(%d,%d) l1-Jacobi" % (w.nu, w.nu), "amg_precision": "fp32" if w.mixed else "fp64",
+            "amg": "MIS-2 smoothed aggregation, P smoothed on the first %d levels, Galerkin refresh per Newton "
+                   "iteration" % w.smooth_levels,
             "newton_rtol": 1e-8, "eta": 1e-7, "dt": w.dt, "schedule_steps": w.steps,
             "l2": "working set > 129 MB L2 (7-diagonal Jacobian alone 118 MB, FGMRES basis 1 GB)"}
 
@@ -228,7 +233,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     lib = rb.load()
-    w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload)
+    w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload, args.grid)
     opts = newton_opts(rb, w)
     prec = rb.PREC_MIXED if w.mixed else rb.PREC_FP64
     stream = torch.cuda.current_stream()
@@ -236,14 +241,15 @@ def run_ours(args):
     ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
     pd = torch.tensor(p0, device="cuda")
     sched = lambda m: dts[m % len(dts)]
+    import ctypes
+    lw = ctypes.c_longlong()
+    lib.rich_kernel_launches(ctypes.byref(lw))
     for m in range(args.warmup):
         ctx.step(pd, sched(m), opts)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    import ctypes
-    lib.rich_profile_kernel.argtypes = [ctypes.c_char_p]
     lib.rich_profile_kernel(args.roofline_kernel.encode())
     l0 = ctypes.c_longlong()
     lib.rich_kernel_launches(ctypes.byref(l0))
@@ -358,7 +364,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, grid), "e2e": e2e,
-            "gpu_launches": int(l1.value - l0.value), "clocks": clocks, "roofline": roof,
+            "gpu_launches": int(l1.value - l0.value), "warmup_launches": int(l0.value - lw.value),
+            "clocks": clocks, "roofline": roof,
             "newton_its": newton_its, "linear_its": lin_its,
             "latency_ms_per_time_step": {"p50": step_ms[len(step_ms) // 2],
                                          "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],

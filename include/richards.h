@@ -114,6 +114,7 @@ typedef struct {
   int coarse_max;          /* stop coarsening below this many unknowns (2000) */
   int max_levels;          /* at most this many levels (10) */
   int nu1, nu2;            /* l1-Jacobi pre/post sweeps (1, 1) */
+  int smooth_levels;       /* levels 0..smooth_levels-1 smooth P; deeper ones use P = P_tent (10 = all) */
 } rich_amg_opts;
 
 typedef struct {

@@ -28,7 +28,9 @@ design notes):
                the pass-1 neighbour whose root has the largest key.
   prolongator  P = (I - omega D^-1 A) P_tent, P_tent[i, agg(i)] = 1,
                omega = 4 / (3 rho), rho = max_i sum_j |a_ij| / |a_ii|;
-               structural pattern, no dropping.
+               structural pattern, no dropping.  Only the first
+               smooth_levels levels smooth P (default: all); deeper levels
+               use P = P_tent, which keeps the coarsest operators sparse.
   coarse       A_c = R (A P) with R = P^T, structural pattern.  Coarsening
                stops when a level has fewer than coarse_max unknowns, the
                size ratio exceeds 0.8, or max_levels is reached; the last
@@ -214,7 +216,7 @@ class Hierarchy:
         return sum(lv.A.nnz for lv in self.levels) / self.levels[0].A.nnz
 
 
-def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8):
+def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, smooth_levels=10):
     """Build the hierarchy from a symmetric positive definite CSR matrix."""
     levels = [Level(A)]
     while True:
@@ -228,7 +230,8 @@ def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8):
         agg, nc = aggregate(S, state, keys)
         if nc > max_ratio * n:
             break
-        P, _ = smoothed_prolongator(lv.A, tentative_prolongator(agg, nc))
+        Pt = tentative_prolongator(agg, nc)
+        P = smoothed_prolongator(lv.A, Pt)[0] if len(levels) - 1 < smooth_levels else Pt
         R = transpose(P)
         Ac = spgemm(R, spgemm(lv.A, P))
         lv.S, lv.agg, lv.P, lv.R, lv.mis_rounds = S, agg, P, R, rounds

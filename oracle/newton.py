@@ -57,6 +57,7 @@ class NewtonOptions:
     amg_seed: int = 1
     coarse_max: int = 2000
     max_levels: int = 10
+    smooth_levels: int = 10
     armijo_c: float = 1e-4
     lambda_min: float = 1e-10
 
@@ -124,7 +125,8 @@ def step(prob, p, dt, opt):
         J = prob.jacobian(p, dt)
         A = prob.aux(p, dt)
         if prob.hierarchy is None or (opt.amg_policy == "rebuild_step" and r == 0):
-            prob.hierarchy = amg.setup(A, opt.theta, opt.amg_seed, opt.coarse_max, opt.max_levels)
+            prob.hierarchy = amg.setup(A, opt.theta, opt.amg_seed, opt.coarse_max, opt.max_levels,
+                                       smooth_levels=opt.smooth_levels)
         elif opt.amg_policy == "setup_once":
             amg.update_fine(prob.hierarchy, A)
         else:

@@ -478,24 +478,41 @@ __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const i
   }
 }
 
-// One block per row with more than kNumSmall products: the row's column list and
-// accumulators sit in shared memory (rows up to kNumLmax entries; longer rows
-// accumulate in global memory); products are spread over the block and added with
-// atomics (rounding-level order dependence).
+// One block per row with more than kNumSmall products.  The row's products are
+// flattened: a block scan of the B-row lengths over the row's A entries gives
+// each product index t an (A entry, B entry) pair, so every thread has work
+// however short the B rows are.  The row's column list and accumulators sit in
+// shared memory (rows up to kNumLmax entries; longer rows accumulate in global
+// memory); products are added with atomics (rounding-level order dependence).
 constexpr int kNumLmax = 4096;
+constexpr int kNumAmax = 2048;   // A entries per row staged at once
+constexpr int kNumThreads = 256;
+constexpr int kDenseCols = 8192; // C with at most this many columns: accumulate by column directly
 
-__global__ void __launch_bounds__(256) k_spgemm_numeric_block(
+// DENSE: the shared accumulator is indexed by column (C has <= kDenseCols columns),
+// so a product needs no search; otherwise the row's sorted column list is searched.
+template <bool DENSE>
+__global__ void __launch_bounds__(kNumThreads) k_spgemm_numeric_block(
     int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
     const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
     const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval,
-    const int* __restrict__ u) {
-  __shared__ int scol[kNumLmax];
-  __shared__ double sacc[kNumLmax];
+    const int* __restrict__ u, int ncols) {
+  // dynamic shared memory: sacc[kNumLmax] av[kNumAmax] (doubles), then scol[kNumLmax]
+  // off[kNumAmax + 1] bstart[kNumAmax] (ints)
+  extern __shared__ unsigned char dsm[];
+  double* sacc = reinterpret_cast<double*>(dsm);
+  double* av = sacc + (DENSE ? kDenseCols : kNumLmax);
+  int* scol = reinterpret_cast<int*>(av + kNumAmax);
+  int* off = scol + kNumLmax;         // prefix of B-row lengths over the staged A entries
+  int* bstart = off + kNumAmax + 1;
+  __shared__ int wsum[kNumThreads / 32];
   for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
     if (u[row] <= kNumSmall) continue;
     int c0 = crp[row], c1 = crp[row + 1], L = c1 - c0;
-    bool sh = L <= kNumLmax;
-    if (sh) {
+    bool sh = DENSE || L <= kNumLmax;
+    if (DENSE) {
+      for (int t = threadIdx.x; t < L; t += blockDim.x) sacc[ccol[c0 + t]] = 0.0;
+    } else if (sh) {
       for (int t = threadIdx.x; t < L; t += blockDim.x) {
         scol[t] = ccol[c0 + t];
         sacc[t] = 0.0;
@@ -504,13 +521,52 @@ __global__ void __launch_bounds__(256) k_spgemm_numeric_block(
       for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = 0.0;
     }
     __syncthreads();
-    for (int e = arp[row]; e < arp[row + 1]; ++e) {
-      int j = acol[e];
-      double a = aval[e];
-      for (int f = brp[j] + threadIdx.x; f < brp[j + 1]; f += blockDim.x) {
+    for (int e0 = arp[row]; e0 < arp[row + 1]; e0 += kNumAmax) {
+      int na = min(kNumAmax, arp[row + 1] - e0);
+      // stage A entries and the lengths of their B rows; block-wide exclusive scan
+      int per = (na + blockDim.x - 1) / blockDim.x;
+      int lo = threadIdx.x * per, hi = min(na, lo + per);
+      int local = 0;
+      for (int q = lo; q < hi; ++q) {
+        int j = acol[e0 + q];
+        int b0 = brp[j];
+        bstart[q] = b0;
+        av[q] = aval[e0 + q];
+        int len = brp[j + 1] - b0;
+        off[q] = local;
+        local += len;
+      }
+      // exclusive scan of the per-thread totals
+      int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      int inc = local;
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (lane == 31) wsum[wid] = inc;
+      __syncthreads();
+      int wbase = 0;
+      for (int q = 0; q < wid; ++q) wbase += wsum[q];
+      int tbase = wbase + inc - local;
+      for (int q = lo; q < hi; ++q) off[q] += tbase;
+      __syncthreads();
+      int total = 0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) total += wsum[q];
+      if (threadIdx.x == 0) off[na] = total;
+      __syncthreads();
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        // A entry q with off[q] <= t < off[q+1]
+        int lo2 = 0, hi2 = na;
+        while (hi2 - lo2 > 1) {
+          int mid = (lo2 + hi2) >> 1;
+          if (off[mid] <= t) lo2 = mid; else hi2 = mid;
+        }
+        int f = bstart[lo2] + (t - off[lo2]);
         int key = bcol[f];
-        double v = a * bval[f];
-        if (sh) {
+        double v = av[lo2] * bval[f];
+        if (DENSE) {
+          atomicAdd(&sacc[key], v);
+        } else if (sh) {
           int pos = find_col(scol, 0, L, key);
           atomicAdd(&sacc[pos], v);
         } else {
@@ -518,9 +574,11 @@ __global__ void __launch_bounds__(256) k_spgemm_numeric_block(
           atomicAdd(&cval[pos], v);
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
-    if (sh)
+    if (DENSE)
+      for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = sacc[ccol[c0 + t]];
+    else if (sh)
       for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = sacc[t];
     __syncthreads();
   }
@@ -636,14 +694,34 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
   return RICH_OK;
 }
 
-static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C, const int* u) {
-  ProfScope ps("spgemm_numeric", c->st, (double)A.nrows * 4 + A.nnz * 12.0 + (double)C.nrows * 4 + C.nnz * 12.0);
+static const char* kNumericName[2][16] = {
+    {"galerkin_ap_l0", "galerkin_ap_l1", "galerkin_ap_l2", "galerkin_ap_l3", "galerkin_ap_l4", "galerkin_ap_l5",
+     "galerkin_ap_l6", "galerkin_ap_l7", "galerkin_ap_l8", "galerkin_ap_l9", "galerkin_ap", "galerkin_ap",
+     "galerkin_ap", "galerkin_ap", "galerkin_ap", "galerkin_ap"},
+    {"galerkin_rap_l0", "galerkin_rap_l1", "galerkin_rap_l2", "galerkin_rap_l3", "galerkin_rap_l4",
+     "galerkin_rap_l5", "galerkin_rap_l6", "galerkin_rap_l7", "galerkin_rap_l8", "galerkin_rap_l9", "galerkin_rap",
+     "galerkin_rap", "galerkin_rap", "galerkin_rap", "galerkin_rap", "galerkin_rap"}};
+
+// which = 0 for A P, 1 for R (A P); level for the profile name
+static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C, const int* u,
+                          int which = 0, int level = 0) {
+  ProfScope ps(kNumericName[which][level & 15], c->st,
+               (double)A.nrows * 4 + A.nnz * 12.0 + (double)C.nrows * 4 + C.nnz * 12.0);
   k_spgemm_numeric<<<grid_for(A.nrows, 128), 128, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
                                                               B.val, C.rowptr, C.col, C.val, u);
   RICH_LAUNCH_CHECK();
-  int nb = A.nrows < 16 * kNumSM ? A.nrows : 16 * kNumSM;
-  k_spgemm_numeric_block<<<nb, 256, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
-                                               C.col, C.val, u);
+  int nb = A.nrows < 8 * kNumSM ? A.nrows : 8 * kNumSM;
+  if (C.ncols <= kDenseCols) {
+    const int dsm = (int)((kDenseCols + kNumAmax) * sizeof(double) + (kNumLmax + 2 * kNumAmax + 1) * sizeof(int));
+    RICH_CUDA(cudaFuncSetAttribute(k_spgemm_numeric_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    k_spgemm_numeric_block<true><<<nb, kNumThreads, dsm, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                                 B.val, C.rowptr, C.col, C.val, u, C.ncols);
+  } else {
+    const int dsm = (int)((kNumLmax + kNumAmax) * sizeof(double) + (kNumLmax + 2 * kNumAmax + 1) * sizeof(int));
+    RICH_CUDA(cudaFuncSetAttribute(k_spgemm_numeric_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    k_spgemm_numeric_block<false><<<nb, kNumThreads, dsm, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                                  B.val, C.rowptr, C.col, C.val, u, C.ncols);
+  }
   RICH_LAUNCH_CHECK();
   return RICH_OK;
 }
@@ -723,13 +801,18 @@ static int coarse_inverse(rich_ctx* c) {
   return RICH_OK;
 }
 
-__global__ void k_stencil4(long long n, const double* __restrict__ A7, double* __restrict__ d, double* __restrict__ wx,
-                           double* __restrict__ wy, double* __restrict__ wz, float* __restrict__ d32,
-                           float* __restrict__ wx32, float* __restrict__ wy32, float* __restrict__ wz32) {
+// Finest-level stencil arrays from the 7n diffusion stencil; dinv = 1 / (l1 row norm)
+// = 1 / (diag + sum of the six face weights).
+__global__ void k_stencil4(long long n, const double* __restrict__ A7, Stencil4<double> s64, Stencil4<float> s32) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double a = A7[i], x = -A7[2 * n + i], y = -A7[4 * n + i], z = -A7[6 * n + i];
-    if (d) { d[i] = a; wx[i] = x; wy[i] = y; wz[i] = z; }
-    if (d32) { d32[i] = (float)a; wx32[i] = (float)x; wy32[i] = (float)y; wz32[i] = (float)z; }
+    double l1 = a + ((-A7[1 * n + i] + x) + (-A7[3 * n + i] + y) + (-A7[5 * n + i] + z));
+    double r = 1.0 / l1;
+    if (s64.diag) { s64.diag[i] = a; s64.wx[i] = x; s64.wy[i] = y; s64.wz[i] = z; s64.dinv[i] = r; }
+    if (s32.diag) {
+      s32.diag[i] = (float)a; s32.wx[i] = (float)x; s32.wy[i] = (float)y; s32.wz[i] = (float)z;
+      s32.dinv[i] = (float)r;
+    }
   }
 }
 
@@ -743,15 +826,16 @@ static int fine_stencil(rich_ctx* c) {
     RICH_CHECK(dalloc(&H.st32.wx, n));
     RICH_CHECK(dalloc(&H.st32.wy, n));
     RICH_CHECK(dalloc(&H.st32.wz, n));
+    RICH_CHECK(dalloc(&H.st32.dinv, n));
   }
   if (!mp && !H.st64.diag) {
     RICH_CHECK(dalloc(&H.st64.diag, n));
     RICH_CHECK(dalloc(&H.st64.wx, n));
     RICH_CHECK(dalloc(&H.st64.wy, n));
     RICH_CHECK(dalloc(&H.st64.wz, n));
+    RICH_CHECK(dalloc(&H.st64.dinv, n));
   }
-  k_stencil4<<<grid_for(n), kBlock, 0, c->st>>>(n, c->A7, H.st64.diag, H.st64.wx, H.st64.wy, H.st64.wz, H.st32.diag,
-                                                H.st32.wx, H.st32.wy, H.st32.wz);
+  k_stencil4<<<grid_for(n), kBlock, 0, c->st>>>(n, c->A7, H.st64, H.st32);
   RICH_LAUNCH_CHECK();
   return RICH_OK;
 }
@@ -805,8 +889,8 @@ void amg_free(rich_ctx* c) {
   }
   H.lv.clear();
   H.nlev = 0;
-  dfree(H.st64.diag); dfree(H.st64.wx); dfree(H.st64.wy); dfree(H.st64.wz);
-  dfree(H.st32.diag); dfree(H.st32.wx); dfree(H.st32.wy); dfree(H.st32.wz);
+  dfree(H.st64.diag); dfree(H.st64.wx); dfree(H.st64.wy); dfree(H.st64.wz); dfree(H.st64.dinv);
+  dfree(H.st32.diag); dfree(H.st32.wx); dfree(H.st32.wy); dfree(H.st32.wz); dfree(H.st32.dinv);
   dfree(H.cdense);
   dfree(H.cinv32);
   dfree(H.cwork);
@@ -910,23 +994,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
     *stop = true;
     return RICH_OK;
   }
-  // prolongator
-  int nb = red_grid(n);
-  k_rowratio<<<nb, kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.val, d, c->partials);
-  RICH_LAUNCH_CHECK();
-  RICH_CHECK(finish_max(c, c->partials, nb, c->dsc));
-  double rho = 0.0;
-  RICH_CHECK(fetch_scalars(c, c->dsc, 1, &rho));
-  double omega = 4.0 / (3.0 * rho);
-  L.omega = omega;
-  Csr<double> Sm;
-  Sm.nrows = Sm.ncols = n;
-  Sm.nnz = L.A.nnz;
-  Sm.rowptr = L.A.rowptr;
-  Sm.col = L.A.col;
-  RICH_CHECK(dalloc(&Sm.val, L.A.nnz));
-  k_smoother_vals<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, omega, Sm.val);
-  RICH_LAUNCH_CHECK();
+  // prolongator: smoothed on the first smooth_levels levels, P_tent below
   Csr<double> Pt;
   Pt.nrows = n;
   Pt.ncols = nc;
@@ -936,8 +1004,39 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   RICH_LAUNCH_CHECK();
   Pt.col = L.agg;
   Pt.val = nullptr;
-  RICH_CHECK(spgemm_symbolic(c, Sm, Pt, L.P));
-  dfree(Sm.val);
+  if (l < o.smooth_levels) {
+    int nb = red_grid(n);
+    k_rowratio<<<nb, kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.val, d, c->partials);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(finish_max(c, c->partials, nb, c->dsc));
+    double rho = 0.0;
+    RICH_CHECK(fetch_scalars(c, c->dsc, 1, &rho));
+    double omega = 4.0 / (3.0 * rho);
+    L.omega = omega;
+    Csr<double> Sm;
+    Sm.nrows = Sm.ncols = n;
+    Sm.nnz = L.A.nnz;
+    Sm.rowptr = L.A.rowptr;
+    Sm.col = L.A.col;
+    RICH_CHECK(dalloc(&Sm.val, L.A.nnz));
+    k_smoother_vals<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, omega, Sm.val);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(spgemm_symbolic(c, Sm, Pt, L.P));
+    dfree(Sm.val);
+  } else {
+    // P = P_tent: identity rows onto the aggregates (pattern and unit values copied)
+    L.omega = 0.0;
+    L.P.nrows = n;
+    L.P.ncols = nc;
+    L.P.nnz = n;
+    RICH_CHECK(dalloc(&L.P.rowptr, (long long)n + 1));
+    RICH_CHECK(dalloc(&L.P.col, n));
+    RICH_CHECK(dalloc(&L.P.val, n));
+    RICH_CUDA(cudaMemcpyAsync(L.P.rowptr, Pt.rowptr, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, c->st));
+    RICH_CUDA(cudaMemcpyAsync(L.P.col, L.agg, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->st));
+    k_fill<<<grid_for(n), kBlock, 0, c->st>>>(n, 1.0, L.P.val);
+    RICH_LAUNCH_CHECK();
+  }
   dfree(Pt.rowptr);
   RICH_CHECK(transpose(c, L.P, L.R));
   RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP, &L.u_ap));
@@ -1006,8 +1105,8 @@ int amg_refresh(rich_ctx* c) {
   H.lv[0].A = c->A0;
   for (int l = 0; l + 1 < H.nlev; ++l) {
     Level& L = H.lv[l];
-    RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP, L.u_ap));
-    RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A, L.u_rap));
+    RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP, L.u_ap, 0, l));
+    RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A, L.u_rap, 1, l));
   }
   for (int l = 0; l < H.nlev; ++l) RICH_CHECK(level_diag_data(c, H.lv[l]));
   RICH_CHECK(fine_stencil(c));

@@ -123,7 +123,15 @@ struct Stencil4 {
   T* wx = nullptr;
   T* wy = nullptr;
   T* wz = nullptr;
+  T* dinv = nullptr;  // 1 / (diag + sum of the six face weights), the l1-Jacobi scaling
 };
+
+// Launch shape of the structured-grid kernels: one block row per (j, k) grid line,
+// blockIdx.y tiles the x direction; no 64-bit division per thread.
+constexpr int kLineThreads = 128;
+inline dim3 line_grid(const GridP& g) {
+  return dim3((unsigned)((long long)g.ny * g.nz), (unsigned)((g.nx + kLineThreads - 1) / kLineThreads), 1);
+}
 
 struct Hierarchy {
   Stencil4<double> st64;

@@ -177,25 +177,25 @@ __global__ void k_assemble(GridP g, SoilP so, BCP bc, int kmean, const double* _
 
 // y = A x for a 7n stencil.  The neighbour coefficient is zero outside the grid,
 // so the index is only guarded, never wrapped.
-__global__ void k_stencil_spmv(GridP g, const double* __restrict__ A7, const double* __restrict__ x,
-                               double* __restrict__ y) {
+__global__ void __launch_bounds__(kLineThreads) k_stencil_spmv(GridP g, const double* __restrict__ A7,
+                                                               const double* __restrict__ x, double* __restrict__ y) {
+  int i = blockIdx.y * kLineThreads + threadIdx.x;
+  if (i >= g.nx) return;
+  int r = blockIdx.x;
+  int j = r % g.ny;
+  int k = r / g.ny;
+  int nx = g.nx;
+  int sxy = g.nx * g.ny;
   long long n = g.n;
-  long long sxy = (long long)g.nx * g.ny;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(c % g.nx);
-    long long r = c / g.nx;
-    int j = (int)(r % g.ny);
-    int k = (int)(r / g.ny);
-    double s = A7[c] * x[c];
-    if (i > 0) s += A7[1 * n + c] * x[c - 1];
-    if (i < g.nx - 1) s += A7[2 * n + c] * x[c + 1];
-    if (j > 0) s += A7[3 * n + c] * x[c - g.nx];
-    if (j < g.ny - 1) s += A7[4 * n + c] * x[c + g.nx];
-    if (k > 0) s += A7[5 * n + c] * x[c - sxy];
-    if (k < g.nz - 1) s += A7[6 * n + c] * x[c + sxy];
-    y[c] = s;
-  }
+  int c = r * nx + i;
+  double s = A7[c] * x[c];
+  if (i > 0) s += A7[1 * n + c] * x[c - 1];
+  if (i < nx - 1) s += A7[2 * n + c] * x[c + 1];
+  if (j > 0) s += A7[3 * n + c] * x[c - nx];
+  if (j < g.ny - 1) s += A7[4 * n + c] * x[c + nx];
+  if (k > 0) s += A7[5 * n + c] * x[c - sxy];
+  if (k < g.nz - 1) s += A7[6 * n + c] * x[c + sxy];
+  y[c] = s;
 }
 
 // Finest-level CSR pattern of the 7-point stencil (sorted columns: -z,-y,-x,c,+x,+y,+z).
@@ -274,7 +274,7 @@ int jacobian_eval(rich_ctx* c, const double* p, double dt) {
 
 int stencil_apply(rich_ctx* c, const double* A7, const double* x, double* y) {
   ProfScope ps("stencil_spmv", c->st, (double)c->g.n * 72.0);
-  k_stencil_spmv<<<grid_for(c->g.n), kBlock, 0, c->st>>>(c->g, A7, x, y);
+  k_stencil_spmv<<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, A7, x, y);
   RICH_LAUNCH_CHECK();
   return RICH_OK;
 }
@@ -340,6 +340,7 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->max_levels = 10;
   o->nu1 = 1;
   o->nu2 = 1;
+  o->smooth_levels = 10;
 }
 
 void rich_default_newton_opts(rich_newton_opts* o) {

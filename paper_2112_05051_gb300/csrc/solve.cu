@@ -54,19 +54,21 @@ __global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict_
   }
 }
 
-// CSR row operation with one warp per row, for levels whose rows are long
-// (coarse Galerkin operators carry tens to hundreds of entries per row).
+// CSR row operation with G lanes per row (G = 4..32), for levels whose rows are
+// long (coarse Galerkin operators carry tens to hundreds of entries per row).
 // MODE 0: y = A x; 1: y += A x; 2: y = x + dinv (b - A x); 3: y = b - A x.
-template <class T, int MODE>
-__global__ void k_csr_warp(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
-                           const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
-                           T* __restrict__ y) {
-  int lane = threadIdx.x & 31;
-  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+template <class T, int MODE, int G>
+__global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+                          const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+                          T* __restrict__ y) {
+  int lane = threadIdx.x & (G - 1);
+  unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1)));
+  int rows_per_grid = (gridDim.x * blockDim.x) / G;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) / G; row < n; row += rows_per_grid) {
     T s = 0;
-    for (int e = rp[row] + lane; e < rp[row + 1]; e += 32) s += val[e] * x[col[e]];
+    for (int e = rp[row] + lane; e < rp[row + 1]; e += G) s += val[e] * x[col[e]];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(mask, s, o, G);
     if (lane == 0) {
       if (MODE == 0) y[row] = s;
       else if (MODE == 1) y[row] += s;
@@ -74,6 +76,16 @@ __global__ void k_csr_warp(int n, const int* __restrict__ rp, const int* __restr
       else y[row] = b[row] - s;
     }
   }
+}
+
+template <class T, int MODE>
+static void csr_op(cudaStream_t st, int n, long long nnz, const int* rp, const int* col, const T* val, const T* dinv,
+                   const T* b, const T* x, T* y) {
+  double avg = n > 0 ? (double)nnz / n : 0.0;
+  if (avg > 48) k_csr_grp<T, MODE, 32><<<grid_for((long long)n * 32), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else if (avg > 20) k_csr_grp<T, MODE, 16><<<grid_for((long long)n * 16), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else if (avg > 10) k_csr_grp<T, MODE, 8><<<grid_for((long long)n * 8), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else k_csr_grp<T, MODE, 4><<<grid_for((long long)n * 4), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
 }
 
 // x = M b for a dense row-major n x n matrix; one warp per row.
@@ -103,40 +115,31 @@ __global__ void k_f2d(long long n, const float* __restrict__ a, double* __restri
 // mode 0: xo = D_l1^-1 b (first sweep from x = 0); 1: xo = x + D_l1^-1 (b - A x);
 // 2: xo = b - A x (residual).
 template <class T, int MODE>
-__global__ void k_st_smooth(GridP g, Stencil4<T> A, const T* __restrict__ b, const T* __restrict__ x,
-                            T* __restrict__ xo) {
-  long long n = g.n;
-  long long sxy = (long long)g.nx * g.ny;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(c % g.nx);
-    long long r = c / g.nx;
-    int j = (int)(r % g.ny);
-    int k = (int)(r / g.ny);
-    T wxp = A.wx[c], wyp = A.wy[c], wzp = A.wz[c];
-    T wxm = i > 0 ? A.wx[c - 1] : T(0);
-    T wym = j > 0 ? A.wy[c - g.nx] : T(0);
-    T wzm = k > 0 ? A.wz[c - sxy] : T(0);
-    T d = A.diag[c];
-    if (MODE == 0) {
-      T l1 = d + ((wxm + wxp) + (wym + wyp) + (wzm + wzp));
-      xo[c] = b[c] / l1;
-      continue;
-    }
-    T xc = x[c];
-    T ax = d * xc;
-    if (i > 0) ax -= wxm * x[c - 1];
-    if (i < g.nx - 1) ax -= wxp * x[c + 1];
-    if (j > 0) ax -= wym * x[c - g.nx];
-    if (j < g.ny - 1) ax -= wyp * x[c + g.nx];
-    if (k > 0) ax -= wzm * x[c - sxy];
-    if (k < g.nz - 1) ax -= wzp * x[c + sxy];
-    if (MODE == 2) {
-      xo[c] = b[c] - ax;
-    } else {
-      T l1 = d + ((wxm + wxp) + (wym + wyp) + (wzm + wzp));
-      xo[c] = xc + (b[c] - ax) / l1;
-    }
+__global__ void __launch_bounds__(kLineThreads) k_st_smooth(GridP g, Stencil4<T> A, const T* __restrict__ b,
+                                                            const T* __restrict__ x, T* __restrict__ xo) {
+  int i = blockIdx.y * kLineThreads + threadIdx.x;
+  if (i >= g.nx) return;
+  int r = blockIdx.x;
+  int j = r % g.ny;
+  int k = r / g.ny;
+  int nx = g.nx;
+  int sxy = g.nx * g.ny;
+  int c = r * nx + i;
+  if (MODE == 0) {
+    xo[c] = A.dinv[c] * b[c];
+    return;
   }
+  T wxp = A.wx[c], wyp = A.wy[c], wzp = A.wz[c];
+  T xc = x[c];
+  T ax = A.diag[c] * xc;
+  if (i > 0) ax -= A.wx[c - 1] * x[c - 1];
+  if (i < nx - 1) ax -= wxp * x[c + 1];
+  if (j > 0) ax -= A.wy[c - nx] * x[c - nx];
+  if (j < g.ny - 1) ax -= wyp * x[c + nx];
+  if (k > 0) ax -= A.wz[c - sxy] * x[c - sxy];
+  if (k < g.nz - 1) ax -= wzp * x[c + sxy];
+  if (MODE == 2) xo[c] = b[c] - ax;
+  else xo[c] = xc + A.dinv[c] * (b[c] - ax);
 }
 
 template <class T>
@@ -203,12 +206,11 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   // finest level: stencil form (4 coefficient arrays + b + x in, x out)
   const bool st0 = (l == 0);
   // warp-per-row CSR kernels where rows are long
-  const bool wA = L.A.nnz > 12LL * n;
-  const int gw = grid_for((long long)n * 32);
-  const double st_bytes = (double)n * 7.0 * es;
+  const bool wA = L.A.nnz > 6LL * n;
+  const double st_bytes = (double)n * 8.0 * es;  // diag, 3 face weights, dinv, b, x in; x out
   if (nu1 > 0) {
     if (st0) {
-      k_st_smooth<T, 0><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, nullptr, x);
+      k_st_smooth<T, 0><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, nullptr, x);
     } else {
       k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
     }
@@ -216,8 +218,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     for (int s = 1; s < nu1; ++s) {
       {
         ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
-        if (st0) k_st_smooth<T, 1><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-        else if (wA) k_csr_warp<T, 2><<<gw, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+        if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
+        else if (wA) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
         else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
       }
       RICH_LAUNCH_CHECK();
@@ -225,8 +227,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     }
     {
       ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st, st0 ? st_bytes : sweep_bytes - (double)n * es);
-      if (st0) k_st_smooth<T, 2><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-      else if (wA) k_csr_warp<T, 3><<<gw, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, nullptr, b, x, (T*)L.r);
+      if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
+      else if (wA) csr_op<T, 3>(c->st, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r);
       else k_resid<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, b, x, (T*)L.r);
     }
     RICH_LAUNCH_CHECK();
@@ -237,9 +239,9 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   Level& C = H.lv[l + 1];
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
-    if (L.R.nnz > 8LL * C.n)
-      k_csr_warp<T, 0><<<grid_for((long long)C.n * 32), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, nullptr,
-                                                                            nullptr, (const T*)L.r, (T*)C.b);
+    if (L.R.nnz > 6LL * C.n)
+      csr_op<T, 0>(c->st, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr, (const T*)L.r,
+                   (T*)C.b);
     else
       k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
   }
@@ -248,8 +250,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    if (L.P.nnz > 8LL * n)
-      k_csr_warp<T, 1><<<gw, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, nullptr, nullptr, xc, x);
+    if (L.P.nnz > 6LL * n)
+      csr_op<T, 1>(c->st, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x);
     else
       k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
   }
@@ -257,8 +259,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   for (int s = 0; s < nu2; ++s) {
     {
       ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
-      if (st0) k_st_smooth<T, 1><<<g, kBlock, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-      else if (wA) k_csr_warp<T, 2><<<gw, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+      if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
+      else if (wA) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
       else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
     }
     RICH_LAUNCH_CHECK();
@@ -360,8 +362,29 @@ __global__ void k_multidot_rb(long long n, int nv, const double* __restrict__ V,
   }
 }
 
+// Batched dot products h[q] = V[q] . w: block (bx, q) reduces its share of one
+// vector; w is re-read per q from L2, V streams from HBM once.
+__global__ void k_bdot(long long n, const double* __restrict__ V, const double* __restrict__ w,
+                       double* __restrict__ partials) {
+  int q = blockIdx.y;
+  const double* v = V + (long long)q * n;
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc[0] += v[i] * w[i];
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[(long long)q * gridDim.x + blockIdx.x] = acc[0];
+}
+
+constexpr int kBdotBlocks = 2 * kNumSM;  // x-blocks per vector (fixed: deterministic summation order)
+
 static void launch_multidot(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* w,
                             double* partials) {
+  (void)nb;
+  k_bdot<<<dim3(kBdotBlocks, nv), kBlock, 0, st>>>(n, V, w, partials);
+}
+
+static void launch_multidot_regs(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* w,
+                                 double* partials) {
   if (nv <= 8) k_multidot_rb<8><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
   else if (nv <= 16) k_multidot_rb<16><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
   else if (nv <= 32) k_multidot_rb<32><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
@@ -437,6 +460,19 @@ static void launch_orth_pass2(int nb, cudaStream_t st, long long n, int nv, cons
   else if (nv <= 16) k_orth_pass2<16><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
   else if (nv <= 32) k_orth_pass2<32><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
   else k_orth_pass2<64><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
+}
+
+// w -= sum_q h[q] V[q], in place
+__global__ void k_orth_axpy(long long n, int nv, const double* __restrict__ V, const double* __restrict__ h,
+                            double* w) {
+  __shared__ double hs[64];
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) hs[q] = h[q];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double t = w[i];
+    for (int q = 0; q < nv; ++q) t -= hs[q] * V[(long long)q * n + i];
+    w[i] = t;
+  }
 }
 
 // out = f * (w - sum_q h2[q] V[q])
@@ -619,13 +655,19 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
         launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
       }
       RICH_LAUNCH_CHECK();
-      RICH_CHECK(finish_sums(c, c->partials, nb, j + 1, s));
+      RICH_CHECK(finish_sums(c, c->partials, kBdotBlocks, j + 1, s));
       {
-        ProfScope ps("orth_reorth", c->st, (double)n * 8.0 * (j + 3));  // V once, w read + written
-        launch_orth_pass2(nb, c->st, n, j + 1, k.V, s, k.w, c->partials);
+        ProfScope ps("orth_axpy", c->st, (double)n * 8.0 * (j + 3));  // w -= V h1 (w read and written)
+        k_orth_axpy<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s, k.w);
       }
       RICH_LAUNCH_CHECK();
-      RICH_CHECK(finish_sums(c, c->partials, nb, j + 2, s + 64));
+      {
+        ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2));
+        launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
+      }
+      RICH_LAUNCH_CHECK();
+      RICH_CHECK(finish_sums(c, c->partials, kBdotBlocks, j + 1, s + 64));
+      RICH_CHECK(nrm2sq(c, k.w, n, s + 64 + j + 1));
       RICH_CUDA(cudaMemcpyAsync(c->hsc, s, 128 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       RICH_CUDA(cudaStreamSynchronize(c->st));
       double h2sq = 0.0;

@@ -46,7 +46,8 @@ class BC(ctypes.Structure):
 
 class AmgOpts(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("coarse_max", ctypes.c_int),
-                ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int)]
+                ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("smooth_levels", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -162,7 +163,7 @@ def default_newton_opts(**kw):
     for k, v in kw.items():
         if k in ("kind", "restart", "eta", "maxit"):
             setattr(o.krylov, k, v)
-        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2"):
+        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)

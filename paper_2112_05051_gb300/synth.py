@@ -161,14 +161,17 @@ class Workload:
     ks_seed: int
     amg_seed: int
     coarse_max: int = 2000
+    smooth_levels: int = 10  # AMG levels whose prolongator is smoothed (10 = all)
 
 
 WORKLOADS = {
     "richards16_fp64": Workload("richards16_fp64", 16, KMEAN_ARITH, 5, "1", "fcg", 0, 1, False, 0.0, 0, 1),
     "richards128_fp64": Workload("richards128_fp64", 128, KMEAN_UPSTREAM, 20, "ramp1to30", "fgmres", 30, 2,
-                                 False, 0.0, 0, 2),
-    "richards256_mixed": Workload("richards256_mixed", 256, KMEAN_HARMONIC, 5, "1", "fcg", 0, 1, True, 1.5, 3, 3),
-    "richards512_mixed": Workload("richards512_mixed", 512, KMEAN_ARITH, 10, "10", "fcg", 0, 1, True, 2.0, 4, 4),
+                                 False, 0.0, 0, 2, smooth_levels=2),
+    "richards256_mixed": Workload("richards256_mixed", 256, KMEAN_HARMONIC, 5, "1", "fcg", 0, 1, True, 1.5, 3, 3,
+                                  smooth_levels=2),
+    "richards512_mixed": Workload("richards512_mixed", 512, KMEAN_ARITH, 10, "10", "fcg", 0, 1, True, 2.0, 4, 4,
+                                  smooth_levels=2),
 }
 
 

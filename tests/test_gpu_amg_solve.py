@@ -83,6 +83,18 @@ def test_hierarchy_bit_exact(dims, coarse_max, kmean):
     ctx.close()
 
 
+def test_hierarchy_with_unsmoothed_deep_levels():
+    rb = _rb()
+    grid, p, ks, bc, dt, _ = _problem((30, 28, 26), 6, 1)
+    ctx = rb.Context(grid, SOIL, bc, 1, ks)
+    ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+    info = ctx.amg_setup(rb.default_amg_opts(seed=5, coarse_max=100, smooth_levels=1))
+    h = amg.setup(disc.aux_matrix(grid, SOIL, bc, 1, p, dt, ks), 0.08, 5, 100, smooth_levels=1)
+    _compare_hierarchy(ctx, info, h)
+    assert info.levels >= 3
+    ctx.close()
+
+
 @pytest.mark.parametrize("nu", [1, 2])
 def test_vcycle_parity_fp64_and_mixed(nu):
     rb = _rb()
@@ -149,7 +161,8 @@ def _run_steps(workload, n, steps, prec=0, policy=0, opts_kw=None):
     w = synth.WORKLOADS[workload]
     grid, soil, bc, ks, p0, dts = synth.workload_inputs(w, n)
     kw = dict(kind=rb.KRYLOV_FGMRES if w.krylov == "fgmres" else rb.KRYLOV_FCG, restart=max(w.restart, 1),
-              nu1=w.nu, nu2=w.nu, seed=w.amg_seed, coarse_max=w.coarse_max, amg_policy=policy)
+              nu1=w.nu, nu2=w.nu, seed=w.amg_seed, coarse_max=w.coarse_max, amg_policy=policy,
+              smooth_levels=w.smooth_levels)
     kw.update(opts_kw or {})
     opts = rb.default_newton_opts(**kw)
     ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
@@ -160,7 +173,8 @@ def _run_steps(workload, n, steps, prec=0, policy=0, opts_kw=None):
     pol = {0: "refresh", 1: "setup_once", 2: "rebuild_step"}[policy]
     prob = newton.Problem(grid, soil, bc, w.kmean, ks)
     oopt = newton.NewtonOptions(krylov=w.krylov, restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu,
-                                amg_seed=w.amg_seed, coarse_max=w.coarse_max, amg_policy=pol)
+                                amg_seed=w.amg_seed, coarse_max=w.coarse_max, amg_policy=pol,
+                                smooth_levels=w.smooth_levels)
     for k, v in (opts_kw or {}).items():
         if k == "coarse_max":
             oopt.coarse_max = v
