@@ -478,6 +478,74 @@ __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const i
   }
 }
 
+// One warp per row with more than kNumSmall products and at most kWarpL output
+// entries: the row's columns and accumulators sit in the warp's slice of shared
+// memory; A entries are taken 32 at a time, a warp scan of their B-row lengths
+// flattens the products over the lanes.
+constexpr int kWarpL = 256;
+constexpr int kWarpRowsPerBlock = 8;
+
+__global__ void __launch_bounds__(32 * kWarpRowsPerBlock) k_spgemm_numeric_warp(
+    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
+    const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
+    const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval,
+    const int* __restrict__ u) {
+  __shared__ double sacc_all[kWarpRowsPerBlock][kWarpL];
+  __shared__ int scol_all[kWarpRowsPerBlock][kWarpL];
+  __shared__ int pre_all[kWarpRowsPerBlock][33];
+  __shared__ int bst_all[kWarpRowsPerBlock][32];
+  __shared__ double av_all[kWarpRowsPerBlock][32];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* sacc = sacc_all[w];
+  int* scol = scol_all[w];
+  int* pre = pre_all[w];
+  int nw = gridDim.x * kWarpRowsPerBlock;
+  for (int row = blockIdx.x * kWarpRowsPerBlock + w; row < nrows; row += nw) {
+    int c0 = crp[row], c1 = crp[row + 1], L = c1 - c0;
+    if (u[row] <= kNumSmall || L > kWarpL) continue;
+    for (int t = lane; t < L; t += 32) {
+      scol[t] = ccol[c0 + t];
+      sacc[t] = 0.0;
+    }
+    __syncwarp();
+    for (int e0 = arp[row]; e0 < arp[row + 1]; e0 += 32) {
+      int e = e0 + lane;
+      bool has = e < arp[row + 1];
+      int j = has ? acol[e] : 0;
+      double a = has ? aval[e] : 0.0;
+      int b0 = has ? brp[j] : 0;
+      int len = has ? brp[j + 1] - b0 : 0;
+      int inc = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      pre[lane + 1] = inc;
+      if (lane == 0) pre[0] = 0;
+      int total = __shfl_sync(0xffffffffu, inc, 31);
+      bst_all[w][lane] = b0;
+      av_all[w][lane] = a;
+      __syncwarp();
+      for (int t = lane; t < total; t += 32) {
+        int lo = 0, hi = 32;  // owner q of product t: pre[q] <= t < pre[q+1]
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (pre[mid] <= t) lo = mid; else hi = mid;
+        }
+        int f = bst_all[w][lo] + (t - pre[lo]);
+        int key = bcol[f];
+        double v = av_all[w][lo] * bval[f];
+        int pos = find_col(scol, 0, L, key);
+        atomicAdd(&sacc[pos], v);
+      }
+      __syncwarp();
+    }
+    for (int t = lane; t < L; t += 32) cval[c0 + t] = sacc[t];
+    __syncwarp();
+  }
+}
+
 // One block per row with more than kNumSmall products.  The row's products are
 // flattened: a block scan of the B-row lengths over the row's A entries gives
 // each product index t an (A entry, B entry) pair, so every thread has work
@@ -509,6 +577,7 @@ __global__ void __launch_bounds__(kNumThreads) k_spgemm_numeric_block(
   for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
     if (u[row] <= kNumSmall) continue;
     int c0 = crp[row], c1 = crp[row + 1], L = c1 - c0;
+    if (L <= kWarpL) continue;  // k_spgemm_numeric_warp
     bool sh = DENSE || L <= kNumLmax;
     if (DENSE) {
       for (int t = threadIdx.x; t < L; t += blockDim.x) sacc[ccol[c0 + t]] = 0.0;
@@ -710,6 +779,13 @@ static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& 
   k_spgemm_numeric<<<grid_for(A.nrows, 128), 128, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
                                                               B.val, C.rowptr, C.col, C.val, u);
   RICH_LAUNCH_CHECK();
+  {
+    int nwb = (A.nrows + kWarpRowsPerBlock - 1) / kWarpRowsPerBlock;
+    if (nwb > 32 * kNumSM) nwb = 32 * kNumSM;
+    k_spgemm_numeric_warp<<<nwb, 32 * kWarpRowsPerBlock, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr,
+                                                                     B.col, B.val, C.rowptr, C.col, C.val, u);
+    RICH_LAUNCH_CHECK();
+  }
   int nb = A.nrows < 8 * kNumSM ? A.nrows : 8 * kNumSM;
   if (C.ncols <= kDenseCols) {
     const int dsm = (int)((kDenseCols + kNumAmax) * sizeof(double) + (kNumLmax + 2 * kNumAmax + 1) * sizeof(int));

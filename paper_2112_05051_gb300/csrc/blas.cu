@@ -45,14 +45,13 @@ ProfScope::~ProfScope() {
   ++g_prof_n;
 }
 
+// one block per quantity: the same fixed reduction tree for each
 __global__ void k_finish_sums(const double* __restrict__ partials, int nb, int nq, double* __restrict__ dst) {
-  for (int q = 0; q < nq; ++q) {
-    double v[1] = {0.0};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v[0] += partials[(long long)q * nb + b];
-    block_sum<1>(v);
-    if (threadIdx.x == 0) dst[q] = v[0];
-    __syncthreads();
-  }
+  int q = blockIdx.x;
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v[0] += partials[(long long)q * nb + b];
+  block_sum<1>(v);
+  if (threadIdx.x == 0) dst[q] = v[0];
 }
 
 __global__ void k_finish_max(const double* __restrict__ partials, int nb, double* __restrict__ dst) {
@@ -66,7 +65,7 @@ __global__ void k_finish_max(const double* __restrict__ partials, int nb, double
 }
 
 int finish_sums(rich_ctx* c, const double* partials, int nb, int nq, double* dst) {
-  k_finish_sums<<<1, kBlock, 0, c->st>>>(partials, nb, nq, dst);
+  k_finish_sums<<<nq, kBlock, 0, c->st>>>(partials, nb, nq, dst);
   RICH_LAUNCH_CHECK();
   return RICH_OK;
 }

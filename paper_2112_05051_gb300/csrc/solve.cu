@@ -82,9 +82,9 @@ template <class T, int MODE>
 static void csr_op(cudaStream_t st, int n, long long nnz, const int* rp, const int* col, const T* val, const T* dinv,
                    const T* b, const T* x, T* y) {
   double avg = n > 0 ? (double)nnz / n : 0.0;
-  if (avg > 48) k_csr_grp<T, MODE, 32><<<grid_for((long long)n * 32), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else if (avg > 20) k_csr_grp<T, MODE, 16><<<grid_for((long long)n * 16), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else if (avg > 10) k_csr_grp<T, MODE, 8><<<grid_for((long long)n * 8), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  if (avg > 96) k_csr_grp<T, MODE, 32><<<grid_for((long long)n * 32), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else if (avg > 48) k_csr_grp<T, MODE, 16><<<grid_for((long long)n * 16), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else if (avg > 16) k_csr_grp<T, MODE, 8><<<grid_for((long long)n * 8), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
   else k_csr_grp<T, MODE, 4><<<grid_for((long long)n * 4), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
 }
 
