@@ -37,6 +37,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+# GB300 FP64: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s
+# (the nominal 1.25 TFLOP/s); ncu shows the FP64 smoother and dot products issue-bound
+# on this pipe, so FP64 kernels are reported against it.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the roofline kernel
 # (profiles/ summary of the same kernel and workload); None until captured.
 NCU_TRAFFIC_BYTES = {}
@@ -51,7 +55,7 @@ def parse():
     ap.add_argument("--workload", default="richards128_fp64")
     ap.add_argument("--grid", type=int, default=None,
                     help="run the workload's settings on an n^3 grid instead (profiling captures); not a bench line")
-    ap.add_argument("--roofline-kernel", default="multidot")
+    ap.add_argument("--roofline-kernel", default="l1jacobi")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-AMG comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -284,7 +288,8 @@ def run_ours(args):
     ms_k = ctypes.c_double()
     n_k = ctypes.c_longlong()
     by_k = ctypes.c_double()
-    lib.rich_profile_result(ctypes.byref(ms_k), ctypes.byref(n_k), ctypes.byref(by_k))
+    fl_k = ctypes.c_double()
+    lib.rich_profile_result(ctypes.byref(ms_k), ctypes.byref(n_k), ctypes.byref(by_k), ctypes.byref(fl_k))
     lib.rich_profile_kernel(None)
     clocks = clk.stop()
     work = float(grid.n) * newton_its
@@ -352,14 +357,24 @@ def run_ours(args):
         ctx3.close()
 
     peak, peak_kind = measured_peaks()
-    achieved = (by_k.value / (ms_k.value / 1000.0) / 1e9) if ms_k.value > 0 else None
+    secs = ms_k.value / 1000.0
+    gbs = (by_k.value / secs / 1e9) if secs > 0 else None
+    tfl = (fl_k.value / secs / 1e12) if secs > 0 else None
     per_launch_bytes = by_k.value / n_k.value if n_k.value else None
     traffic = NCU_TRAFFIC_BYTES.get((args.workload, args.roofline_kernel))
-    roof = {"kernel": args.roofline_kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes, "launches_timed": n_k.value,
-            "avg_launch_us": 1000.0 * ms_k.value / n_k.value if n_k.value else None,
-            "kernel_share_of_step": (ms_k.value / 1000.0) / elapsed if elapsed > 0 else None}
+    fp64_kernel = not (w.mixed or args.roofline_kernel.startswith("l1jacobi") and prec == rb.PREC_MIXED)
+    common = {"kernel": args.roofline_kernel, "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes,
+              "algorithmic_flops_per_launch": fl_k.value / n_k.value if n_k.value else None,
+              "launches_timed": n_k.value, "avg_launch_us": 1000.0 * ms_k.value / n_k.value if n_k.value else None,
+              "kernel_share_of_step": secs / elapsed if elapsed > 0 else None,
+              "hbm": {"achieved": gbs, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                      "frac": gbs / peak if gbs else None}}
+    if fp64_kernel and tfl:
+        roof = dict(common, bound="alu", achieved=tfl, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=tfl / FP64_PEAK_TFLOPS, peak_kind="derived FP64 (unit count x clock)")
+    else:
+        roof = dict(common, bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=gbs / peak if gbs else None,
+                    peak_kind=peak_kind)
     line = {"metric": "DOF*Newton-steps/s", "value": value, "unit": "DOF*Newton-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -270,9 +270,10 @@ int rich_kernel_launches(long long* out);
  * "restrict", "prolong", "coarse_gemv", "multidot", "multiaxpy", "fcg_update",
  * "spgemm_numeric". */
 int rich_profile_kernel(const char* name);
-/* Sum of the recorded launch durations (ms), number of recorded launches and
- * the algorithmic bytes those launches must move (synchronises the events). */
-int rich_profile_result(double* ms_total, long long* launches, double* bytes_total);
+/* Sum of the recorded launch durations (ms), number of recorded launches, the
+ * algorithmic bytes those launches must move and (flops_total may be NULL) their
+ * algorithmic floating-point operations (synchronises the events). */
+int rich_profile_result(double* ms_total, long long* launches, double* bytes_total, double* flops_total);
 /* With the target "*": per-kernel totals, one line "name launches ms bytes" each,
  * written into buf (at most cap bytes, NUL-terminated). */
 int rich_profile_table(char* buf, int cap);

@@ -21,8 +21,9 @@ static std::vector<double> g_prof_b;
 static int g_prof_n = 0;          // recorded launch pairs
 static long long g_prof_seen = 0; // launches of the target (recorded or not)
 static double g_prof_bytes = 0.0;
+static double g_prof_flops = 0.0;
 
-ProfScope::ProfScope(const char* name, cudaStream_t s, double b) : on(false), st(s), bytes(b) {
+ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(false), st(s), bytes(b), flops(f) {
   if (g_prof_target.empty() || (g_prof_target != "*" && g_prof_target != name)) return;
   ++g_prof_seen;
   if (g_prof_n >= kProfEvents / 2) return;
@@ -42,6 +43,7 @@ ProfScope::~ProfScope() {
   cudaEventRecord(g_prof_ev[2 * g_prof_n + 1], st);
   g_prof_b[g_prof_n] = bytes;
   g_prof_bytes += bytes;
+  g_prof_flops += flops;
   ++g_prof_n;
 }
 
@@ -228,11 +230,13 @@ int rich_profile_kernel(const char* name) {
   rich::g_prof_n = 0;
   rich::g_prof_seen = 0;
   rich::g_prof_bytes = 0.0;
+  rich::g_prof_flops = 0.0;
   return RICH_OK;
 }
 
-int rich_profile_result(double* ms_total, long long* launches, double* bytes_total) {
+int rich_profile_result(double* ms_total, long long* launches, double* bytes_total, double* flops_total) {
   if (!ms_total || !launches || !bytes_total) return RICH_EINVAL;
+  if (flops_total) *flops_total = rich::g_prof_flops;
   double ms = 0.0;
   for (int i = 0; i < rich::g_prof_n; ++i) {
     cudaEventSynchronize(rich::g_prof_ev[2 * i + 1]);

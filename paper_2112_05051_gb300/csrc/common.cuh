@@ -48,8 +48,8 @@ void count_launch();
 struct ProfScope {
   bool on;
   cudaStream_t st;
-  double bytes;
-  ProfScope(const char* name, cudaStream_t s, double algorithmic_bytes);
+  double bytes, flops;
+  ProfScope(const char* name, cudaStream_t s, double algorithmic_bytes, double algorithmic_flops = 0.0);
   ~ProfScope();
 };
 

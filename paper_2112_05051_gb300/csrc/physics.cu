@@ -273,7 +273,7 @@ int jacobian_eval(rich_ctx* c, const double* p, double dt) {
 }
 
 int stencil_apply(rich_ctx* c, const double* A7, const double* x, double* y) {
-  ProfScope ps("stencil_spmv", c->st, (double)c->g.n * 72.0);
+  ProfScope ps("stencil_spmv", c->st, (double)c->g.n * 72.0, (double)c->g.n * 13.0);
   k_stencil_spmv<<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, A7, x, y);
   RICH_LAUNCH_CHECK();
   return RICH_OK;

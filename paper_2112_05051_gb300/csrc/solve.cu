@@ -217,7 +217,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     RICH_LAUNCH_CHECK();
     for (int s = 1; s < nu1; ++s) {
       {
-        ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
+        ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
+                     st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
         if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
         else if (wA) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
         else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
@@ -258,7 +259,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < nu2; ++s) {
     {
-      ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes);
+      ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
+                   st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
       if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
       else if (wA) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
       else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
@@ -651,7 +653,7 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       //   h1 = V^T w;  w' = w - V h1 with h2 = V^T w' and ||w'||^2 in the same pass;
       //   V[j+1] = (w' - V h2) / hn, hn^2 = ||w'||^2 - ||h2||^2 (V orthonormal).
       {
-        ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2));
+        ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2), 2.0 * n * (j + 1));
         launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
       }
       RICH_LAUNCH_CHECK();
@@ -662,7 +664,7 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       }
       RICH_LAUNCH_CHECK();
       {
-        ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2));
+        ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2), 2.0 * n * (j + 1));
         launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
       }
       RICH_LAUNCH_CHECK();
