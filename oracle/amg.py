@@ -26,6 +26,10 @@ design notes):
                non-root with a strong root neighbour joins the one with the
                largest key; pass 2: a remaining node joins the aggregate of
                the pass-1 neighbour whose root has the largest key.
+               Isolated nodes (no strong neighbour) start OUT and join no
+               aggregate: their P_tent row is empty and the smoother alone
+               resolves them (strongly diagonally dominant rows, e.g. very
+               low-conductivity cells of a heterogeneous field).
   prolongator  P = (I - omega D^-1 A) P_tent, P_tent[i, agg(i)] = 1,
                omega = 4 / (3 rho), rho = max_i sum_j |a_ij| / |a_ii|;
                structural pattern, no dropping.  Only the first
@@ -34,7 +38,8 @@ design notes):
   coarse       A_c = R (A P) with R = P^T, structural pattern.  Coarsening
                stops when a level has fewer than coarse_max unknowns, the
                size ratio exceeds 0.8, or max_levels is reached; the last
-               level is solved by dense Cholesky.
+               level is solved by dense Cholesky, or, when coarsening stalled
+               above DENSE_MAX unknowns, by COARSE_SWEEPS l1-Jacobi sweeps.
   smoother     l1-Jacobi x <- x + D_l1^-1 (b - A x), D_l1,ii = sum_j |a_ij|.
 """
 import numpy as np
@@ -95,10 +100,14 @@ def _max_closed(Sc, v):
 
 
 def mis2(S, keys):
-    """Distance-2 maximal independent set by synchronous rounds; returns (state, rounds)."""
+    """Distance-2 maximal independent set by synchronous rounds; returns (state, rounds).
+
+    Isolated nodes (no strong neighbour) are OUT from the start.
+    """
     Sc = _closed(S)
     n = S.shape[0]
     state = np.full(n, STATE_UNDECIDED, dtype=np.uint64)
+    state[np.diff(S.indptr) == 0] = STATE_OUT
     rounds = 0
     while np.any(state == STATE_UNDECIDED):
         t = (state << np.uint64(62)) | keys
@@ -113,9 +122,10 @@ def mis2(S, keys):
 
 
 def aggregate(S, state, keys):
-    """Aggregate index per node (int64) and number of aggregates."""
+    """Aggregate index per node (int64, -1 for isolated nodes) and number of aggregates."""
     Sc = _closed(S)
     n = S.shape[0]
+    isolated = np.diff(S.indptr) == 0
     roots = state == STATE_IN
     agg_id = np.cumsum(roots) - 1
     agg = np.full(n, -1, dtype=np.int64)
@@ -133,7 +143,7 @@ def aggregate(S, state, keys):
     best2 = _max_closed(Sc, val2)
     take = rest & (best2 > 0)
     agg[take] = agg_id[((best2[take] - np.uint64(1)) & _LOW32).astype(np.int64)]
-    if np.any(agg < 0):
+    if np.any((agg < 0) & ~isolated):
         raise RuntimeError("aggregation left nodes unassigned")
     return agg, int(roots.sum())
 
@@ -168,8 +178,12 @@ def transpose(P):
 
 
 def tentative_prolongator(agg, nc):
+    """P_tent[i, agg(i)] = 1; rows of isolated nodes (agg = -1) are empty."""
     n = len(agg)
-    return sp.csr_matrix((np.ones(n), agg.astype(np.int64), np.arange(n + 1)), shape=(n, nc))
+    has = agg >= 0
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(has, out=indptr[1:])
+    return sp.csr_matrix((np.ones(int(has.sum())), agg[has].astype(np.int64), indptr), shape=(n, nc))
 
 
 def smoothed_prolongator(A, Pt):
@@ -190,6 +204,10 @@ def l1_diagonal(A):
     A = sp.csr_matrix(A)
     rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
     return np.bincount(rows, weights=np.abs(A.data), minlength=A.shape[0])
+
+
+DENSE_MAX = 8192
+COARSE_SWEEPS = 8
 
 
 class Level:
@@ -236,9 +254,13 @@ def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, 
         Ac = spgemm(R, spgemm(lv.A, P))
         lv.S, lv.agg, lv.P, lv.R, lv.mis_rounds = S, agg, P, R, rounds
         levels.append(Level(Ac))
-    Ac = levels[-1].A.toarray()
-    chol = np.linalg.cholesky(Ac)
-    return Hierarchy(levels, chol)
+    return Hierarchy(levels, _coarse_factor(levels[-1].A))
+
+
+def _coarse_factor(A):
+    if A.shape[0] > DENSE_MAX:
+        return None  # stalled coarsening: the coarsest level is smoothed, not factored
+    return np.linalg.cholesky(A.toarray())
 
 
 def update_fine(h, A):
@@ -251,7 +273,7 @@ def update_fine(h, A):
     lv.A = sp.csr_matrix(A)
     lv.dl1 = l1_diagonal(lv.A)
     if len(h.levels) == 1:
-        h.chol = np.linalg.cholesky(lv.A.toarray())
+        h.chol = _coarse_factor(lv.A)
 
 
 def refresh(h, A):
@@ -267,14 +289,19 @@ def refresh(h, A):
         Ac = spgemm(lv.R, spgemm(lv.A, lv.P))
         h.levels[l + 1].A = Ac
         h.levels[l + 1].dl1 = l1_diagonal(Ac)
-    h.chol = np.linalg.cholesky(h.levels[-1].A.toarray())
+    h.chol = _coarse_factor(h.levels[-1].A)
 
 
 def vcycle(h, b, nu1=1, nu2=1, level=0):
     """One symmetric V-cycle x = B b, zero initial guess (eq. (Vcycle))."""
     lv = h.levels[level]
     if level == len(h.levels) - 1:
-        return sla.cho_solve((h.chol, True), b)
+        if h.chol is not None:
+            return sla.cho_solve((h.chol, True), b)
+        x = np.zeros_like(b)
+        for _ in range(COARSE_SWEEPS):
+            x = x + (b - lv.A @ x) / lv.dl1
+        return x
     x = np.zeros_like(b)
     for _ in range(nu1):
         x = x + (b - lv.A @ x) / lv.dl1

@@ -93,9 +93,12 @@ __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restr
   }
 }
 
-__global__ void k_mis_init(int n, uint64_t seed, uint64_t* __restrict__ t) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    t[i] = (kUndecided << kStateShift) | prio_key(seed, i);
+// Isolated nodes (no strong neighbour) start OUT: they join no aggregate.
+__global__ void k_mis_init(int n, uint64_t seed, const int* __restrict__ srp, uint64_t* __restrict__ t) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bool isolated = srp[i + 1] == srp[i];
+    t[i] = (isolated ? 0ull : (kUndecided << kStateShift)) | prio_key(seed, i);
+  }
 }
 
 // m[i] = max of v over the closed strength neighbourhood of i
@@ -171,15 +174,24 @@ __global__ void k_val2(int n, const uint64_t* __restrict__ t, const int* __restr
   }
 }
 
-__global__ void k_agg_pass2(int n, const uint64_t* __restrict__ best2, const int* __restrict__ aggid,
-                            int* __restrict__ agg, int* __restrict__ unassigned) {
+__global__ void k_agg_pass2(int n, const int* __restrict__ srp, const uint64_t* __restrict__ best2,
+                            const int* __restrict__ aggid, int* __restrict__ agg, int* __restrict__ unassigned) {
   int miss = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (agg[i] >= 0) continue;
     if (best2[i] > 0) agg[i] = aggid[(int)((best2[i] - 1) & kLow32)];
-    else miss = 1;
+    else if (srp[i + 1] != srp[i]) miss = 1;  // isolated nodes stay unaggregated (agg = -1)
   }
   if (miss) atomicOr(unassigned, 1);
+}
+
+// P_tent: one unit entry per aggregated node, empty rows for isolated nodes
+__global__ void k_ptent_count(int n, const int* __restrict__ agg, int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) cnt[i] = agg[i] >= 0;
+}
+__global__ void k_ptent_fill(int n, const int* __restrict__ agg, const int* __restrict__ rp, int* __restrict__ col) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (agg[i] >= 0) col[rp[i]] = agg[i];
 }
 
 __global__ void k_rowratio(int n, const int* __restrict__ rp, const double* __restrict__ val,
@@ -857,6 +869,7 @@ static int transpose(rich_ctx* c, const Csr<double>& P, Csr<double>& R) {
 
 static int coarse_inverse(rich_ctx* c) {
   Hierarchy& H = c->H;
+  if (!H.dense) return RICH_OK;
   Level& L = H.lv[H.nlev - 1];
   int n = L.n;
   k_csr_to_dense<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, H.cdense);
@@ -973,7 +986,6 @@ void amg_free(rich_ctx* c) {
   H.built = false;
 }
 
-constexpr int kMaxCoarseDense = 8192;
 
 // Coarsen level L into a new level; returns RICH_OK with *stop = true when coarsening stops.
 static int coarsen(rich_ctx* c, int l, bool* stop) {
@@ -1004,7 +1016,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   uint64_t *t = nullptr, *m1 = nullptr;
   RICH_CHECK(dalloc(&t, n));
   RICH_CHECK(dalloc(&m1, n));
-  k_mis_init<<<grid_for(n), kBlock, 0, c->st>>>(n, o.seed, t);
+  k_mis_init<<<grid_for(n), kBlock, 0, c->st>>>(n, o.seed, S.rowptr, t);
   RICH_LAUNCH_CHECK();
   int rounds = 0;
   for (;;) {
@@ -1045,7 +1057,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
   RICH_LAUNCH_CHECK();
   RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
-  k_agg_pass2<<<grid_for(n), kBlock, 0, c->st>>>(n, best, aggid, L.agg, c->iflag);
+  k_agg_pass2<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, best, aggid, L.agg, c->iflag);
   RICH_LAUNCH_CHECK();
   RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   RICH_CUDA(cudaStreamSynchronize(c->st));
@@ -1074,11 +1086,16 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   Csr<double> Pt;
   Pt.nrows = n;
   Pt.ncols = nc;
-  Pt.nnz = n;
   RICH_CHECK(dalloc(&Pt.rowptr, (long long)n + 1));
-  k_seq<<<grid_for(n + 1), kBlock, 0, c->st>>>(n, Pt.rowptr);
+  k_ptent_count<<<grid_for(n), kBlock, 0, c->st>>>(n, L.agg, cnt);
   RICH_LAUNCH_CHECK();
-  Pt.col = L.agg;
+  RICH_CHECK(scan_exclusive_int(c, cnt, Pt.rowptr, n));
+  int ptnnz = 0;
+  RICH_CUDA(cudaMemcpy(&ptnnz, Pt.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+  Pt.nnz = ptnnz;
+  RICH_CHECK(dalloc(&Pt.col, ptnnz));
+  k_ptent_fill<<<grid_for(n), kBlock, 0, c->st>>>(n, L.agg, Pt.rowptr, Pt.col);
+  RICH_LAUNCH_CHECK();
   Pt.val = nullptr;
   if (l < o.smooth_levels) {
     int nb = red_grid(n);
@@ -1100,20 +1117,21 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
     RICH_CHECK(spgemm_symbolic(c, Sm, Pt, L.P));
     dfree(Sm.val);
   } else {
-    // P = P_tent: identity rows onto the aggregates (pattern and unit values copied)
+    // P = P_tent (pattern and unit values copied)
     L.omega = 0.0;
     L.P.nrows = n;
     L.P.ncols = nc;
-    L.P.nnz = n;
+    L.P.nnz = ptnnz;
     RICH_CHECK(dalloc(&L.P.rowptr, (long long)n + 1));
-    RICH_CHECK(dalloc(&L.P.col, n));
-    RICH_CHECK(dalloc(&L.P.val, n));
+    RICH_CHECK(dalloc(&L.P.col, ptnnz));
+    RICH_CHECK(dalloc(&L.P.val, ptnnz));
     RICH_CUDA(cudaMemcpyAsync(L.P.rowptr, Pt.rowptr, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, c->st));
-    RICH_CUDA(cudaMemcpyAsync(L.P.col, L.agg, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->st));
-    k_fill<<<grid_for(n), kBlock, 0, c->st>>>(n, 1.0, L.P.val);
+    RICH_CUDA(cudaMemcpyAsync(L.P.col, Pt.col, sizeof(int) * (size_t)ptnnz, cudaMemcpyDeviceToDevice, c->st));
+    k_fill<<<grid_for(ptnnz), kBlock, 0, c->st>>>(ptnnz, 1.0, L.P.val);
     RICH_LAUNCH_CHECK();
   }
   dfree(Pt.rowptr);
+  dfree(Pt.col);
   RICH_CHECK(transpose(c, L.P, L.R));
   RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP, &L.u_ap));
   Level nxt;
@@ -1155,19 +1173,19 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
   }
   H.nlev = (int)H.lv.size();
   H.cn = H.lv[H.nlev - 1].n;
-  if (H.cn > kMaxCoarseDense) {
-    amg_free(c);
-    return RICH_ELIMIT;
-  }
+  // coarsening stalled above the dense limit: the coarsest level is smoothed
+  H.dense = H.cn <= kMaxCoarseDense;
   for (int l = 0; l < H.nlev; ++l) {
     RICH_CHECK(level_alloc_vectors(c, H.lv[l]));
     RICH_CHECK(level_diag_data(c, H.lv[l]));
   }
   RICH_CHECK(fine_stencil(c));
-  RICH_CHECK(dalloc(&H.cdense, (long long)H.cn * H.cn));
-  RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn));
-  if (c->prec == RICH_PREC_MIXED) RICH_CHECK(dalloc(&H.cinv32, (long long)H.cn * H.cn));
-  RICH_CHECK(coarse_inverse(c));
+  if (H.dense) {
+    RICH_CHECK(dalloc(&H.cdense, (long long)H.cn * H.cn));
+    RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn));
+    if (c->prec == RICH_PREC_MIXED) RICH_CHECK(dalloc(&H.cinv32, (long long)H.cn * H.cn));
+    RICH_CHECK(coarse_inverse(c));
+  }
   RICH_CUDA(cudaStreamSynchronize(c->st));
   H.built = true;
   return RICH_OK;

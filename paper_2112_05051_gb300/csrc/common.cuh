@@ -144,7 +144,11 @@ struct Hierarchy {
   double* cwork = nullptr;        // Gauss-Jordan pivot row/column buffers (2 cn)
   rich_amg_opts opts{};
   bool built = false;
+  bool dense = true;              // coarsest level by dense inverse (else kCoarseSweeps l1-Jacobi sweeps)
 };
+
+constexpr int kMaxCoarseDense = 8192;  // largest coarsest level inverted densely
+constexpr int kCoarseSweeps = 8;       // l1-Jacobi sweeps on a stalled (larger) coarsest level
 
 struct KrylovWork {
   long long n = 0;

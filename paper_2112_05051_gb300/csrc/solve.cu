@@ -196,9 +196,20 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   // algorithmic bytes of one sweep over this level's CSR matrix (pattern + values + 4 vectors)
   const double sweep_bytes = (double)n * (4.0 + 4.0 * es) + (double)L.A.nnz * (4.0 + es);
   if (l == H.nlev - 1) {
-    ProfScope ps("coarse_gemv", c->st, (double)n * n * es + 2.0 * n * es);
-    k_gemv<T><<<grid_for((long long)n * 32), kBlock, 0, c->st>>>(n, coarse_inv<T>(c), b, x);
-    RICH_LAUNCH_CHECK();
+    if (H.dense) {
+      ProfScope ps("coarse_gemv", c->st, (double)n * n * es + 2.0 * n * es);
+      k_gemv<T><<<grid_for((long long)n * 32), kBlock, 0, c->st>>>(n, coarse_inv<T>(c), b, x);
+      RICH_LAUNCH_CHECK();
+    } else {  // stalled coarsening: l1-Jacobi sweeps from zero on the (large) coarsest level
+      k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
+      RICH_LAUNCH_CHECK();
+      for (int s = 1; s < kCoarseSweeps; ++s) {
+        if (L.A.nnz > 6LL * n) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
+        else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+        RICH_LAUNCH_CHECK();
+        std::swap(x, t);
+      }
+    }
     *xres = x;
     return RICH_OK;
   }

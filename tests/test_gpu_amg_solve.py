@@ -83,6 +83,46 @@ def test_hierarchy_bit_exact(dims, coarse_max, kmean):
     ctx.close()
 
 
+def test_hierarchy_with_isolated_nodes_from_extreme_heterogeneity():
+    # log10 Ks with std 2 spans ~16 decades: low-conductivity cells have no strong
+    # coupling and stay out of every aggregate (empty P_tent rows)
+    rb = _rb()
+    grid = synth.Grid(26, 24, 22)
+    ks = synth.ks_field(grid, 4, 2.0, (4.0, 4.0, 2.0))
+    p = np.full(grid.n, -40.0)
+    bc = synth.infiltration_bc()
+    ctx = rb.Context(grid, SOIL, bc, 0, ks)
+    ctx.jacobian(torch.tensor(p, device="cuda"), 10.0)
+    info = ctx.amg_setup(rb.default_amg_opts(seed=4, coarse_max=200))
+    A = disc.aux_matrix(grid, SOIL, bc, 0, p, 10.0, ks)
+    h = amg.setup(A, 0.08, 4, 200)
+    assert np.any(h.levels[0].agg < 0)
+    _compare_hierarchy(ctx, info, h)
+    r = np.random.default_rng(3).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= 1e-10
+    ctx.close()
+
+
+def test_stalled_coarsening_smooths_the_coarsest_level():
+    # a single 9600-unknown level exceeds the dense limit: the coarse "solve" is
+    # l1-Jacobi sweeps on both sides
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((24, 20, 20), 9, 0)
+    ctx = rb.Context(grid, SOIL, bc, kmean, ks)
+    ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+    info = ctx.amg_setup(rb.default_amg_opts(seed=2, max_levels=1))
+    assert info.levels == 1 and info.n[0] > amg.DENSE_MAX
+    h = amg.setup(disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks), 0.08, 2, 2000, max_levels=1)
+    assert h.chol is None
+    r = np.random.default_rng(8).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= 1e-10
+    ctx.close()
+
+
 def test_hierarchy_with_unsmoothed_deep_levels():
     rb = _rb()
     grid, p, ks, bc, dt, _ = _problem((30, 28, 26), 6, 1)

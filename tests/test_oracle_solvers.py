@@ -36,13 +36,16 @@ def _random_graph(n, p, seed):
 
 
 def _greedy_mis2(S, keys):
-    """Sequential greedy distance-2 independent set in decreasing key order (brute force)."""
+    """Sequential greedy distance-2 independent set in decreasing key order (brute force).
+
+    Isolated nodes (no neighbour) are left out, as the aggregation excludes them.
+    """
     n = S.shape[0]
     A = (S.toarray() != 0)
     A2 = A | (A.astype(int) @ A.astype(int) > 0)
     np.fill_diagonal(A2, False)
     chosen = np.zeros(n, bool)
-    blocked = np.zeros(n, bool)
+    blocked = ~A.any(axis=1)
     for i in sorted(range(n), key=lambda v: int(keys[v]), reverse=True):
         if not blocked[i]:
             chosen[i] = True
@@ -97,8 +100,10 @@ def test_aggregates_are_partition_with_radius_two(case):
     state, _ = amg.mis2(S, keys)
     agg, nc = amg.aggregate(S, state, keys)
     roots = np.flatnonzero(state == amg.STATE_IN)
+    isolated = np.diff(S.indptr) == 0
     assert nc == len(roots)
-    assert set(agg.tolist()) == set(range(nc))
+    assert np.all(agg[isolated] == -1) and np.all(agg[~isolated] >= 0)
+    assert set(agg[~isolated].tolist()) == set(range(nc))
     np.testing.assert_array_equal(agg[roots], np.arange(nc))  # numbered by root index
     for a, r in enumerate(roots):
         members = np.flatnonzero(agg == a)
