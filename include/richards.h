@@ -106,6 +106,13 @@ typedef struct {
 typedef struct {
   int kind[6];             /* RICH_BC_* per face */
   double value[6];         /* Dirichlet pressure head (cm) per face */
+  /* Optional per-cell Dirichlet values (device, NULL = the constant value[f]),
+   * one per boundary cell of the face, indexed i + nx*j on the z faces,
+   * i + nx*k on the y faces and j + ny*k on the x faces.  rich_create copies
+   * them; rich_residual_noalloc reads them in place.  Used for the paper's
+   * infiltration problem (Sec. 6): p = 0 on a centred square of the top face,
+   * h_r elsewhere. */
+  const double* value_field_dev[6];
 } rich_bc;
 
 typedef struct {

@@ -18,8 +18,9 @@ Readings where the paper is silent (all listed in the design notes):
     the +d side of the face, ties taking K_U; harmonic 2 K_L K_U/(K_L+K_U)
     (the abstract names it, no formula is printed); geometric sqrt(K_L K_U)
     (Sec. 2.1).
-  * Dirichlet face: the ghost node holds p = p_bc and K = K(p_bc) with the
-    Ks of the adjacent interior cell; T and G use it as a neighbour.
+  * Dirichlet face: the ghost node holds p = p_bc (a constant or a per-cell
+    value of the face) and K = K(p_bc) with the Ks of the adjacent interior
+    cell; T and G use it as a neighbour.
   * No-flux face: the whole face flux T + G is zero.
   * f = 0, rho_phi from the soil (1 by default).
 
@@ -131,11 +132,17 @@ class _Faces:
             bnd = _boundary_mask(shape, axis, side)
             kind = bc.kind[f]
             pbc = bc.value[f]
+            fld = bc.field(f) if hasattr(bc, "field") else None
             nb_p = _shift(p3, axis, side)
             nb_K = _shift(self.K3, axis, side)
             nb_dK = _shift(self.dK3, axis, side)
             if kind == BC_DIRICHLET:
                 ghost_p = np.full(shape, pbc)
+                if fld is not None:  # per-cell values of the face, broadcast along its normal
+                    ax = _np_axis(axis)
+                    fs = list(shape)
+                    fs[ax] = 1
+                    ghost_p = np.broadcast_to(np.asarray(fld, dtype=np.float64).reshape(fs), shape)
                 nb_p = np.where(bnd, ghost_p, nb_p)
                 nb_K = np.where(bnd, cst.conductivity(ghost_p, soil, ks3), nb_K)
             nb_dK = np.where(bnd, 0.0, nb_dK)

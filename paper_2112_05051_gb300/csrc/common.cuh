@@ -80,7 +80,18 @@ struct GridP {
 struct BCP {
   int kind[6];
   double value[6];
+  const double* field[6];  // per-cell Dirichlet values of the face, or nullptr
 };
+
+// Dirichlet value of face f at the boundary cell (i, j, k).
+__device__ __forceinline__ double bc_value(const BCP& bc, int f, int i, int j, int k, int nx, int ny) {
+  const double* fv = bc.field[f];
+  if (!fv) return bc.value[f];
+  int axis = f >> 1;
+  long long idx = axis == 2 ? (long long)i + (long long)nx * j : (axis == 1 ? (long long)i + (long long)nx * k
+                                                                          : (long long)j + (long long)ny * k);
+  return fv[idx];
+}
 
 template <class T>
 struct Csr {
@@ -204,6 +215,7 @@ struct rich_ctx {
   double* ptrial = nullptr;
   double* rhs = nullptr;
   double* pbuf = nullptr;      // device p for rich_step_host
+  double* bc_fields[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // owned per-cell BC values
   bool amg_ever = false;
 };
 

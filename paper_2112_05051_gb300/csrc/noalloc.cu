@@ -42,7 +42,7 @@ __device__ __forceinline__ bool noalloc_face(const GridP& g, const BCP& bc, cons
   bool bnd = side > 0 ? (coord == extent - 1) : (coord == 0);
   if (bnd) {
     if (bc.kind[f] == RICH_BC_NOFLUX) return false;
-    pn = bc.value[f];
+    pn = bc_value(bc, f, i, j, k, g.nx, g.ny);
     Kn = conductivity_only(pn, ksc, so);
     return true;
   }
@@ -170,6 +170,7 @@ extern "C" int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soi
   for (int f = 0; f < 6; ++f) {
     b.kind[f] = bc->kind[f];
     b.value[f] = bc->value[f];
+    b.field[f] = bc->value_field_dev[f];
   }
   cudaStream_t st = (cudaStream_t)stream;
   k_residual_noalloc<<<(int)nb, kNoAllocThreads, 0, st>>>(g, so, b, kmean, p_dev, s_old_dev, soil->ks_field_dev, dt,

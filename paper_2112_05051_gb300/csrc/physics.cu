@@ -61,7 +61,7 @@ __device__ __forceinline__ bool face_neighbour(const GridP& g, const BCP& bc, co
   bool bnd = side > 0 ? (coord == extent - 1) : (coord == 0);
   if (bnd) {
     if (bc.kind[f] == RICH_BC_NOFLUX) return false;
-    nb.p = bc.value[f];
+    nb.p = bc_value(bc, f, i, j, k, g.nx, g.ny);
     nb.K = conductivity_only(nb.p, ksc, so);
     nb.dK = 0.0;
     nb.idx = -1;
@@ -390,6 +390,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   for (int f = 0; f < 6; ++f) {
     c->bc.kind[f] = bc->kind[f];
     c->bc.value[f] = bc->value[f];
+    c->bc.field[f] = nullptr;
   }
   c->kmean = kmean;
   c->prec = precision;
@@ -410,6 +411,19 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   if (soil->ks_field_dev) {
     if ((s = dalloc(&c->ks, n))) return fail(s);
     if (cudaMemcpyAsync(c->ks, soil->ks_field_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st) !=
+        cudaSuccess)
+      return fail(RICH_ECUDA);
+  }
+  for (int f = 0; f < 6; ++f) {  // owned copies of per-cell Dirichlet values
+    if (!bc->value_field_dev[f]) continue;
+    int axis = f >> 1;
+    long long m = axis == 2 ? (long long)grid->nx * grid->ny
+                            : (axis == 1 ? (long long)grid->nx * grid->nz : (long long)grid->ny * grid->nz);
+    double* dst = nullptr;
+    if ((s = dalloc(&dst, m))) return fail(s);
+    c->bc_fields[f] = dst;
+    c->bc.field[f] = dst;
+    if (cudaMemcpyAsync(dst, bc->value_field_dev[f], m * sizeof(double), cudaMemcpyDeviceToDevice, c->st) !=
         cudaSuccess)
       return fail(RICH_ECUDA);
   }
@@ -442,6 +456,7 @@ int rich_destroy(rich_ctx* c) {
   dfree(c->ptrial);
   dfree(c->rhs);
   dfree(c->pbuf);
+  for (int f = 0; f < 6; ++f) dfree(c->bc_fields[f]);
   KrylovWork& k = c->kw;
   dfree(k.V);
   dfree(k.Z);

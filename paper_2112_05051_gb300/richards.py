@@ -41,7 +41,22 @@ class Soil(ctypes.Structure):
 
 
 class BC(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int * 6), ("value", ctypes.c_double * 6)]
+    _fields_ = [("kind", ctypes.c_int * 6), ("value", ctypes.c_double * 6), ("value_field_dev", ctypes.c_void_p * 6)]
+
+
+def _bc_struct(bc, keep):
+    """ctypes BC; per-face value arrays are uploaded to device tensors kept in `keep`."""
+    import torch
+    ptrs = []
+    for f in range(6):
+        fld = bc.field(f) if hasattr(bc, "field") else None
+        if fld is None:
+            ptrs.append(None)
+        else:
+            t = torch.as_tensor(fld, dtype=torch.float64).reshape(-1).cuda().contiguous()
+            keep.append(t)
+            ptrs.append(t.data_ptr())
+    return BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value), (ctypes.c_void_p * 6)(*ptrs))
 
 
 class AmgOpts(ctypes.Structure):
@@ -187,7 +202,8 @@ def residual_noalloc(grid, soil, bc, kmean, p, s_old, dt, F, ks=None, norms=True
     g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
     s = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
              _ptr(ks) if ks is not None else None)
-    b = BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value))
+    keep = []
+    b = _bc_struct(bc, keep)
     arr = (ctypes.c_double * 2)() if norms else None
     st = load().rich_residual_noalloc(ctypes.byref(g), ctypes.byref(s), kmean, ctypes.byref(b), _ptr(p),
                                       _ptr(s_old), dt, _ptr(F), arr, _stream())
@@ -218,7 +234,8 @@ class Context:
             self._ks = torch.as_tensor(ks, dtype=torch.float64).reshape(-1).cuda().contiguous()
         s = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
                  _ptr(self._ks) if self._ks is not None else None)
-        b = BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value))
+        self._bc_keep = []
+        b = _bc_struct(bc, self._bc_keep)
         h = ctypes.c_void_p()
         check(lib.rich_create(ctypes.byref(g), ctypes.byref(s), kmean, ctypes.byref(b), precision, _stream(),
                               ctypes.byref(h)), "rich_create")

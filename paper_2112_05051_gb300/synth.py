@@ -91,10 +91,19 @@ class Grid:
 
 @dataclasses.dataclass(frozen=True)
 class BC:
-    """Boundary condition per face in FACE_NAMES order."""
+    """Boundary condition per face in FACE_NAMES order.
+
+    ``fields`` optionally gives per-cell Dirichlet values of a face (a float64
+    array over the face's cells, flat index i + nx j on z faces, i + nx k on y
+    faces, j + ny k on x faces), or None per face for the constant ``value``.
+    """
 
     kind: Tuple[int, int, int, int, int, int]
     value: Tuple[float, float, float, float, float, float]
+    fields: Optional[Tuple] = None
+
+    def field(self, f):
+        return None if self.fields is None else self.fields[f]
 
 
 def infiltration_bc(p_top: float = -20.7) -> BC:
@@ -108,6 +117,22 @@ def all_dirichlet_bc(value: float) -> BC:
 
 def all_noflux_bc() -> BC:
     return BC(kind=(BC_NOFLUX,) * 6, value=(0.0,) * 6)
+
+
+def paper_infiltration_bc(grid: Grid, h_r: float) -> BC:
+    """The paper's infiltration test (Sec. 6): Dirichlet on every face, p = h_r except
+    p = 0 on the centred square [a/4, 3a/4] x [b/4, 3b/4] of the top face.
+
+    The paper's formula (1/alpha) ln[exp(alpha h_r) + (1 - exp(alpha h_r)) chi] is 0
+    where chi = 1 and h_r elsewhere for any alpha; cell (i, j) of the top face sits
+    at ((i+1) h_x, (j+1) h_y)."""
+    hx, hy, _ = grid.h
+    x = (np.arange(grid.nx) + 1) * hx
+    y = (np.arange(grid.ny) + 1) * hy
+    inside = ((x[None, :] >= grid.lx / 4) & (x[None, :] <= 3 * grid.lx / 4)
+              & (y[:, None] >= grid.ly / 4) & (y[:, None] <= 3 * grid.ly / 4))
+    top = np.where(inside, 0.0, h_r).reshape(-1)
+    return BC(kind=(BC_DIRICHLET,) * 6, value=(h_r,) * 6, fields=(None, None, None, None, None, top))
 
 
 P_INITIAL = -61.5
@@ -162,6 +187,7 @@ class Workload:
     amg_seed: int
     coarse_max: int = 2000
     smooth_levels: int = 10  # AMG levels whose prolongator is smoothed (10 = all)
+    problem: str = "column"  # "column": Dirichlet top, no-flux sides; "paper": Sec. 6 infiltration box
 
 
 WORKLOADS = {
@@ -172,12 +198,28 @@ WORKLOADS = {
                                   smooth_levels=2),
     "richards512_mixed": Workload("richards512_mixed", 512, KMEAN_ARITH, 10, "10", "fcg", 0, 1, True, 2.0, 4, 4,
                                   smooth_levels=2),
+    # Sec. 6 strong-scaling problem: [0,64]x[0,64]x[0,1] with 800x800x40 nodes
+    # (798x798x38 unknowns), upstream mean, GMRES(10), t in [0,2] with 10 steps;
+    # h_r (not given in the paper) read as the dry state -61.5 cm of Supplementary D
+    "paper_infiltration": Workload("paper_infiltration", 798, KMEAN_UPSTREAM, 10, "0.2", "fgmres", 10, 1, False,
+                                   0.0, 0, 6, smooth_levels=2, problem="paper"),
 }
+
+PAPER_H_R = -61.5
 
 
 def workload_inputs(w: Workload, n: Optional[int] = None):
-    """Grid, soil, BC, Ks field (or None for homogeneous), initial p, dt list."""
+    """Grid, soil, BC, Ks field (or None for homogeneous), initial p, dt list.
+
+    n overrides the grid size (n^3 for the column workloads; n x n x (38 n / 798)
+    cells on the paper's 64 x 64 x 1 box, at least 4 layers)."""
     nn = w.n if n is None else n
+    if w.problem == "paper":
+        nz = max(4, round(38 * nn / 798))
+        grid = Grid(nn, nn, nz, 64.0, 64.0, 1.0)
+        bc = paper_infiltration_bc(grid, PAPER_H_R)
+        p0 = np.full(grid.n, PAPER_H_R)
+        return grid, Soil(), bc, None, p0, dt_schedule(w.dt, w.steps)
     grid = Grid(nn, nn, nn)
     ks = ks_field(grid, w.ks_seed, w.ks_sigma) if w.ks_sigma > 0 else None
     p0 = np.full(grid.n, P_INITIAL)

@@ -245,6 +245,15 @@ def test_step_parity_richards128_shape_at_32():
         assert g.newton_its == o.newton_its
 
 
+def test_step_parity_paper_infiltration_small():
+    # the paper's Sec. 6 problem (Dirichlet box, p = 0 square on top, upstream mean,
+    # GMRES(10)) on a 32 x 32 x 4 grid of the 64 x 64 x 1 box
+    pg, po, gs, os_ = _run_steps("paper_infiltration", 32, 3)
+    np.testing.assert_allclose(pg, po, rtol=1e-8)
+    for g, o in zip(gs, os_):
+        assert g.converged and o.converged and g.newton_its == o.newton_its
+
+
 @pytest.mark.parametrize("workload,n,steps", [("richards512_mixed", 24, 1), ("richards16_fp64", None, 5)])
 def test_step_mixed_precision_matches_fp64_oracle(workload, n, steps):
     # FP32 hierarchy and V-cycle, FP64 residual/Jacobian/outer Krylov: the converged

@@ -33,7 +33,15 @@ BCS = {
     "infiltration": synth.infiltration_bc(-20.7),
     "dirichlet": synth.BC(kind=(1,) * 6, value=(-30.0, -35.0, -25.0, -40.0, -50.0, -20.0)),
     "mixed": synth.BC(kind=(1, 0, 0, 1, 1, 0), value=(-22.0, 0, 0, -44.0, -61.5, 0)),
+    "fields": None,
 }
+
+
+def _field_bc(grid):
+    rng = np.random.default_rng(23)
+    return synth.BC(kind=(1, 1, 0, 0, 0, 1), value=(-30.0, -40.0, 0, 0, 0, -20.0),
+                    fields=(rng.uniform(-60, -10, grid.ny * grid.nz), None, None, None, None,
+                            rng.uniform(-40, 0, grid.nx * grid.ny)))
 GRIDS = [(7, 5, 6), (16, 16, 16), (33, 17, 9), (1, 1, 23), (19, 1, 1), (1, 1, 1)]
 
 
@@ -52,7 +60,7 @@ def _inputs(grid, seed, het=True):
 def test_residual_jacobian_parity(kmean, bcname, dims):
     rb = _rb()
     grid = synth.Grid(*dims, lx=1.0, ly=0.9, lz=1.3)
-    bc = BCS[bcname]
+    bc = BCS[bcname] if bcname != "fields" else _field_bc(grid)
     p, ks, s_old = _inputs(grid, sum(dims) + kmean)
     dt = 0.8
     ctx = rb.Context(grid, SOIL, bc, kmean, ks)

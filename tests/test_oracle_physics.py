@@ -64,10 +64,20 @@ def _distinct_p(grid, seed):
     return -60.0 + 40.0 * rng.permutation(grid.n) / grid.n + rng.uniform(0, 1e-3, grid.n)
 
 
+def _field_bc(dims):
+    # per-cell Dirichlet values on the top face and on -x (the paper's Sec. 6 problem has a
+    # p = 0 square on top); value arrays follow the face index convention
+    rng = np.random.default_rng(17)
+    nx, ny, nz = dims
+    return synth.BC(kind=(1, 0, 0, 1, 0, 1), value=(-30.0, 0, 0, -45.0, 0, -20.0),
+                    fields=(rng.uniform(-50, -10, ny * nz), None, None, None, None, rng.uniform(-40, 0, nx * ny)))
+
+
 BCS = {
     "infiltration": synth.infiltration_bc(-20.7),
     "dirichlet": synth.BC(kind=(1,) * 6, value=(-30.0, -35.0, -25.0, -40.0, -50.0, -20.0)),
     "noflux": synth.all_noflux_bc(),
+    "fields": None,
 }
 
 
@@ -76,7 +86,7 @@ BCS = {
 @pytest.mark.parametrize("dims", [(4, 4, 4), (3, 4, 5)])
 def test_jacobian_matches_finite_differences(kmean, bcname, dims):
     grid = synth.Grid(*dims, lx=1.0, ly=1.3, lz=0.8)
-    bc = BCS[bcname]
+    bc = BCS[bcname] if bcname != "fields" else _field_bc(dims)
     p = _distinct_p(grid, 7)
     ks = synth.ks_field(grid, 3, 1.0, (2.0, 2.0, 1.0))
     s_old = cst.saturation(p + 1.0, SOIL)
@@ -255,6 +265,26 @@ def test_hydrostatic_state_has_zero_residual_with_arithmetic_mean():
     # so it does NOT vanish: flux (K_L - K_U)/2 per face.
     phi_up = disc.residual(grid, SOIL, bc, synth.KMEAN_UPSTREAM, p, s_old, 1.0, ks)
     assert np.abs(phi_up).max() > 1e-6 * kscale
+
+
+def test_face_field_equals_constant_value_when_uniform():
+    # a per-cell face array holding one value everywhere is the constant Dirichlet face
+    grid = synth.Grid(5, 4, 6)
+    p = _distinct_p(grid, 4)
+    s_old = cst.saturation(p, SOIL)
+    const = synth.BC(kind=(1, 0, 0, 0, 0, 1), value=(-33.0, 0, 0, 0, 0, -21.0))
+    fld = synth.BC(kind=(1, 0, 0, 0, 0, 1), value=(0.0, 0, 0, 0, 0, 0.0),
+                   fields=(np.full(4 * 6, -33.0), None, None, None, None, np.full(5 * 4, -21.0)))
+    for kmean in MEANS:
+        a = disc.residual(grid, SOIL, const, kmean, p, s_old, 0.5)
+        b = disc.residual(grid, SOIL, fld, kmean, p, s_old, 0.5)
+        np.testing.assert_array_equal(a, b)
+    # the paper's top-face pattern: 0 inside the centred square, h_r outside
+    g2 = synth.Grid(12, 8, 4, 64.0, 64.0, 1.0)
+    bc = synth.paper_infiltration_bc(g2, -61.5)
+    top = bc.field(5).reshape(g2.ny, g2.nx)
+    assert top.max() == 0.0 and top.min() == -61.5
+    assert top[g2.ny // 2, g2.nx // 2] == 0.0 and top[0, 0] == -61.5
 
 
 def test_aux_is_spd_and_equals_jacobian_without_conductivity_slope():
