@@ -475,9 +475,33 @@ __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const i
                                  const int* __restrict__ bcol, const double* __restrict__ bval,
                                  const int* __restrict__ crp, const int* __restrict__ ccol,
                                  double* __restrict__ cval, const int* __restrict__ u) {
+  constexpr int kReg = 32;  // rows with at most kReg entries accumulate in a per-thread array
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += gridDim.x * blockDim.x) {
     if (u[row] > kNumSmall) continue;
-    int c0 = crp[row], c1 = crp[row + 1];
+    int c0 = crp[row], c1 = crp[row + 1], L = c1 - c0;
+    if (L <= kReg) {
+      int cc[kReg];
+      double acc[kReg];
+#pragma unroll
+      for (int q = 0; q < kReg; ++q) {
+        cc[q] = q < L ? ccol[c0 + q] : -1;
+        acc[q] = 0.0;
+      }
+      for (int e = arp[row]; e < arp[row + 1]; ++e) {
+        int j = acol[e];
+        double a = aval[e];
+        for (int f = brp[j]; f < brp[j + 1]; ++f) {
+          int key = bcol[f];
+          double v = a * bval[f];
+          int pos = 0;
+#pragma unroll
+          for (int q = 0; q < kReg; ++q) pos = cc[q] == key ? q : pos;
+          acc[pos] += v;
+        }
+      }
+      for (int q = 0; q < L; ++q) cval[c0 + q] = acc[q];
+      continue;
+    }
     for (int q = c0; q < c1; ++q) cval[q] = 0.0;
     for (int e = arp[row]; e < arp[row + 1]; ++e) {
       int j = acol[e];
