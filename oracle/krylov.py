@@ -7,8 +7,9 @@ operator only in exact arithmetic and FP64), both solvers here are the
 flexible variants, which keep the preconditioned directions:
 
   fgmres   Saad's flexible GMRES(m): Arnoldi on J Z with Z = B V stored,
-           classical Gram-Schmidt with one re-orthogonalisation, Givens
-           rotations, restart every m iterations.
+           classical Gram-Schmidt with selective re-orthogonalisation (a
+           second pass when ||w'||^2 < ||w||^2 / 2, the DGKS criterion),
+           Givens rotations, restart every m iterations.
   fcg      Notay's flexible CG with truncation 1:
            z_k = B r_k, p_k = z_k - ((z_k, q_{k-1}) / (p_{k-1}, q_{k-1})) p_{k-1},
            q_k = J p_k, alpha_k = (p_k, r_k) / (p_k, q_k).
@@ -83,11 +84,14 @@ def fgmres(matvec, prec, b, eta, maxit, m):
         for j in range(m):
             Z[j] = prec(V[j])
             w = matvec(Z[j])
+            wn2 = float(w @ w)
             h1 = V[: j + 1] @ w
             w = w - h1 @ V[: j + 1]
-            h2 = V[: j + 1] @ w
-            w = w - h2 @ V[: j + 1]
-            H[: j + 1, j] = h1 + h2
+            if float(w @ w) < 0.5 * wn2:
+                h2 = V[: j + 1] @ w
+                w = w - h2 @ V[: j + 1]
+                h1 = h1 + h2
+            H[: j + 1, j] = h1
             hn = np.linalg.norm(w)
             H[j + 1, j] = hn
             if hn > 0.0:

@@ -891,9 +891,58 @@ static int transpose(rich_ctx* c, const Csr<double>& P, Csr<double>& R) {
   return RICH_OK;
 }
 
+static int coarse_inverse_launches(rich_ctx* c);
+
+// The coarsest inverse is n_c pivot launches; they are recorded once per hierarchy
+// into a CUDA graph (fixed buffers) and replayed on every refresh.
 static int coarse_inverse(rich_ctx* c) {
   Hierarchy& H = c->H;
   if (!H.dense) return RICH_OK;
+  if (H.gj_exec) {
+    RICH_CUDA(cudaGraphLaunch(H.gj_exec, c->st));
+    count_launches(H.gj_nodes);
+    return RICH_OK;
+  }
+  return coarse_inverse_launches(c);
+}
+
+static int capture_coarse_graph(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  if (!H.dense || H.gj_exec) return RICH_OK;
+  cudaStream_t cs;
+  RICH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = c->st;
+  RICH_CUDA(cudaStreamSynchronize(saved));
+  c->st = cs;
+  cudaGraph_t graph = nullptr;
+  long long before = 0;
+  rich_kernel_launches(&before);
+  int rc = RICH_OK;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = coarse_inverse_launches(c);
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  c->st = saved;
+  long long after = 0;
+  rich_kernel_launches(&after);
+  count_launches(before - after);  // recorded, not launched
+  if (e == cudaSuccess && rc == RICH_OK) {
+    e = cudaGraphInstantiate(&H.gj_exec, graph, 0);
+    if (e == cudaSuccess) H.gj_nodes = after - before;
+    else H.gj_exec = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // fall back to direct launches
+    H.gj_exec = nullptr;
+  }
+  return rc;
+}
+
+static int coarse_inverse_launches(rich_ctx* c) {
+  Hierarchy& H = c->H;
   Level& L = H.lv[H.nlev - 1];
   int n = L.n;
   k_csr_to_dense<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, H.cdense);
@@ -1007,6 +1056,9 @@ void amg_free(rich_ctx* c) {
   dfree(H.cdense);
   dfree(H.cinv32);
   dfree(H.cwork);
+  if (H.gj_exec) cudaGraphExecDestroy(H.gj_exec);
+  H.gj_exec = nullptr;
+  H.gj_nodes = 0;
   H.built = false;
 }
 
@@ -1209,6 +1261,7 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
     RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn));
     if (c->prec == RICH_PREC_MIXED) RICH_CHECK(dalloc(&H.cinv32, (long long)H.cn * H.cn));
     RICH_CHECK(coarse_inverse(c));
+    RICH_CHECK(capture_coarse_graph(c));
   }
   RICH_CUDA(cudaStreamSynchronize(c->st));
   H.built = true;

@@ -10,6 +10,7 @@ namespace rich {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- live kernel timing
 

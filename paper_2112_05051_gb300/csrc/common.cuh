@@ -37,6 +37,7 @@ void set_cuda_error(cudaError_t e, const char* where);
 
 // Every kernel launch is followed by RICH_LAUNCH_CHECK, which also counts it.
 void count_launch();
+void count_launches(long long k);  // k may be negative (launches recorded into a graph)
 #define RICH_LAUNCH_CHECK()        \
   do {                             \
     ::rich::count_launch();        \
@@ -156,6 +157,8 @@ struct Hierarchy {
   rich_amg_opts opts{};
   bool built = false;
   bool dense = true;              // coarsest level by dense inverse (else kCoarseSweeps l1-Jacobi sweeps)
+  cudaGraphExec_t gj_exec = nullptr;  // the coarsest inverse (one launch per pivot) as one graph
+  long long gj_nodes = 0;
 };
 
 constexpr int kMaxCoarseDense = 8192;  // largest coarsest level inverted densely

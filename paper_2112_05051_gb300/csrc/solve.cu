@@ -83,8 +83,8 @@ static void csr_op(cudaStream_t st, int n, long long nnz, const int* rp, const i
                    const T* b, const T* x, T* y) {
   double avg = n > 0 ? (double)nnz / n : 0.0;
   if (avg > 96) k_csr_grp<T, MODE, 32><<<grid_for((long long)n * 32), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else if (avg > 48) k_csr_grp<T, MODE, 16><<<grid_for((long long)n * 16), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else if (avg > 16) k_csr_grp<T, MODE, 8><<<grid_for((long long)n * 8), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else if (avg > 64) k_csr_grp<T, MODE, 16><<<grid_for((long long)n * 16), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+  else if (avg > 40) k_csr_grp<T, MODE, 8><<<grid_for((long long)n * 8), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
   else k_csr_grp<T, MODE, 4><<<grid_for((long long)n * 4), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
 }
 
@@ -378,8 +378,12 @@ __global__ void k_multidot_rb(long long n, int nv, const double* __restrict__ V,
 // Batched dot products h[q] = V[q] . w: block (bx, q) reduces its share of one
 // vector; w is re-read per q from L2, V streams from HBM once.
 __global__ void k_bdot(long long n, const double* __restrict__ V, const double* __restrict__ w,
-                       double* __restrict__ partials) {
+                       double* __restrict__ partials, const int* __restrict__ run) {
   int q = blockIdx.y;
+  if (run && !*run) {  // skipped pass: zero partials
+    if (threadIdx.x == 0) partials[(long long)q * gridDim.x + blockIdx.x] = 0.0;
+    return;
+  }
   const double* v = V + (long long)q * n;
   double acc[1] = {0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -391,9 +395,9 @@ __global__ void k_bdot(long long n, const double* __restrict__ V, const double* 
 constexpr int kBdotBlocks = 2 * kNumSM;  // x-blocks per vector (fixed: deterministic summation order)
 
 static void launch_multidot(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* w,
-                            double* partials) {
+                            double* partials, const int* run = nullptr) {
   (void)nb;
-  k_bdot<<<dim3(kBdotBlocks, nv), kBlock, 0, st>>>(n, V, w, partials);
+  k_bdot<<<dim3(kBdotBlocks, nv), kBlock, 0, st>>>(n, V, w, partials, run);
 }
 
 static void launch_multidot_regs(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* w,
@@ -488,10 +492,17 @@ __global__ void k_orth_axpy(long long n, int nv, const double* __restrict__ V, c
   }
 }
 
-// out = f * (w - sum_q h2[q] V[q])
+// DGKS decision on the device: run the second pass when ||w'||^2 < ||w||^2 / 2
+__global__ void k_dgks(const double* __restrict__ s, int i_w, int i_wp, int* __restrict__ run) {
+  *run = s[i_wp] < 0.5 * s[i_w] ? 1 : 0;
+}
+
+// out = f * (w - sum_q h2[q] V[q]); without a second pass (run == 0) out = f * w
 __global__ void k_orth_final(long long n, int nv, const double* __restrict__ V, const double* __restrict__ h2,
-                             const double* __restrict__ w, double f, double* __restrict__ out) {
+                             const double* __restrict__ w, double f, double* __restrict__ out,
+                             const int* __restrict__ run) {
   __shared__ double hs[64];
+  if (run && !*run) nv = 0;
   for (int q = threadIdx.x; q < nv; q += blockDim.x) hs[q] = h2[q];
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -660,9 +671,12 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       double* Zj = k.Z + (long long)j * n;
       RICH_CHECK(vcycle_apply(c, Vj, Zj));
       RICH_CHECK(stencil_apply(c, c->J7, Zj, k.w));
-      // Classical Gram-Schmidt with one re-orthogonalisation, three passes over V:
-      //   h1 = V^T w;  w' = w - V h1 with h2 = V^T w' and ||w'||^2 in the same pass;
+      // Classical Gram-Schmidt with selective re-orthogonalisation (DGKS):
+      //   h1 = V^T w; w' = w - V h1; if ||w'||^2 < ||w||^2/2: h2 = V^T w' (else 0);
       //   V[j+1] = (w' - V h2) / hn, hn^2 = ||w'||^2 - ||h2||^2 (V orthonormal).
+      // The decision stays on the device; one read-back per iteration.
+      int* run = c->iflag + 2;
+      RICH_CHECK(nrm2sq(c, k.w, n, s + 120));
       {
         ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2), 2.0 * n * (j + 1));
         launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
@@ -674,13 +688,15 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
         k_orth_axpy<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s, k.w);
       }
       RICH_LAUNCH_CHECK();
+      RICH_CHECK(nrm2sq(c, k.w, n, s + 121));
+      k_dgks<<<1, 1, 0, c->st>>>(s, 120, 121, run);
+      RICH_LAUNCH_CHECK();
       {
         ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2), 2.0 * n * (j + 1));
-        launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
+        launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials, run);
       }
       RICH_LAUNCH_CHECK();
       RICH_CHECK(finish_sums(c, c->partials, kBdotBlocks, j + 1, s + 64));
-      RICH_CHECK(nrm2sq(c, k.w, n, s + 64 + j + 1));
       RICH_CUDA(cudaMemcpyAsync(c->hsc, s, 128 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       RICH_CUDA(cudaStreamSynchronize(c->st));
       double h2sq = 0.0;
@@ -688,14 +704,14 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
         Hij(i, j) = c->hsc[i] + c->hsc[64 + i];
         h2sq += c->hsc[64 + i] * c->hsc[64 + i];
       }
-      double wsq = c->hsc[64 + j + 1] - h2sq;
+      double wsq = c->hsc[121] - h2sq;
       double hn = wsq > 0 ? sqrt(wsq) : 0.0;
       if (!std::isfinite(hn)) return RICH_ENONFINITE;
       Hij(j + 1, j) = hn;
       {
         ProfScope ps("orth_final", c->st, (double)n * 8.0 * (j + 3));
         k_orth_final<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s + 64, k.w, hn > 0 ? 1.0 / hn : 0.0,
-                                             k.V + (long long)(j + 1) * n);
+                                             k.V + (long long)(j + 1) * n, run);
       }
       RICH_LAUNCH_CHECK();
       for (int i = 0; i < j; ++i) {
