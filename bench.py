@@ -131,6 +131,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def aggregate_over_ranks(dist, elapsed, work, device):
+    """Whole-job numbers of an N-replica run: max elapsed time, summed work (DOF * Newton its)."""
+    if dist is None:
+        return elapsed, work
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    wk = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(wk, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(wk[0])
+
+
 def workload_setup(name, n=None):
     from paper_2112_05051_gb300 import synth
     w = synth.WORKLOADS[name]
@@ -293,12 +305,7 @@ def run_ours(args):
     lib.rich_profile_kernel(None)
     clocks = clk.stop()
     work = float(grid.n) * newton_its
-    if dist:
-        t = torch.tensor([elapsed, work], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        elapsed, work = float(tmax[0]), float(t[1])
+    elapsed, work = aggregate_over_ranks(dist, elapsed, work, "cuda")
     value = work / elapsed
 
     # end to end through the host-buffer entry point (fresh replica of the same run)
@@ -318,12 +325,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         el2 = time.perf_counter() - t0
         work2 = float(grid.n) * its2
-        if dist:
-            t = torch.tensor([el2, work2], dtype=torch.float64, device="cuda")
-            tmax = t.clone()
-            dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-            el2, work2 = float(tmax[0]), float(t[1])
+        el2, work2 = aggregate_over_ranks(dist, el2, work2, "cuda")
         e2e = {"value": work2 / el2, "unit": "DOF*Newton-steps/s", "h2d_bytes_per_step": 8 * grid.n,
                "d2h_bytes_per_step": 8 * grid.n}
         ctx2.close()
