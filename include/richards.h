@@ -122,6 +122,12 @@ typedef struct {
   int max_levels;          /* at most this many levels (10) */
   int nu1, nu2;            /* l1-Jacobi pre/post sweeps (1, 1) */
   int smooth_levels;       /* levels 0..smooth_levels-1 smooth P; deeper ones use P = P_tent (10 = all) */
+  int product_lists;       /* 1 (default): the first Galerkin refresh records, per entry of A P and of
+                              R (A P), the list of (A entry, B entry) pairs summed into it, and every
+                              refresh sums those lists (about 8 bytes per scalar product of device
+                              memory; used only while it fits in half the free device memory).
+                              0: every refresh searches
+                              each product's output position instead (no extra memory). */
 } rich_amg_opts;
 
 typedef struct {
@@ -245,7 +251,9 @@ int amg_update(rich_ctx* ctx, int policy);
 int amg_vcycle(rich_ctx* ctx, const double* r_dev, double* z_dev);
 /* Export level l for inspection (host buffers sized from rich_amg_info):
  * aggregate index per node of level l (n[l] ints, level < levels-1), and the
- * CSR of A_l (rowptr n[l]+1, col nnz, val nnz).  Any pointer may be NULL. */
+ * CSR of A_l (rowptr n[l]+1, col nnz, val nnz).  Any pointer may be NULL.
+ * In MIXED precision, levels below the finest return the FP32 values the
+ * V-cycle uses (the Galerkin refresh runs in FP32 there), widened to double. */
 int amg_export_level(rich_ctx* ctx, int level, int* agg_host, int* rowptr_host, int* col_host,
                      double* val_host);
 /* Export P_l (n[l] x n[l+1]) as CSR to host buffers; nnz via nnz_out. */

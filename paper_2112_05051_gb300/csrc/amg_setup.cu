@@ -235,6 +235,14 @@ __global__ void k_l1dinv(int n, const int* __restrict__ rp, const double* __rest
   }
 }
 
+__global__ void k_l1dinv32(int n, const int* __restrict__ rp, const float* __restrict__ val, float* __restrict__ dinv32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s += fabsf(val[e]);
+    dinv32[i] = 1.0f / s;
+  }
+}
+
 __global__ void k_cast(long long n, const double* __restrict__ a, float* __restrict__ b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -470,29 +478,30 @@ __global__ void __launch_bounds__(kHashThreads) k_spgemm_hash(
 // pass).  Larger rows: k_spgemm_numeric_block.
 constexpr int kNumSmall = 64;
 
+template <class T>
 __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const int* __restrict__ acol,
-                                 const double* __restrict__ aval, const int* __restrict__ brp,
-                                 const int* __restrict__ bcol, const double* __restrict__ bval,
+                                 const T* __restrict__ aval, const int* __restrict__ brp,
+                                 const int* __restrict__ bcol, const T* __restrict__ bval,
                                  const int* __restrict__ crp, const int* __restrict__ ccol,
-                                 double* __restrict__ cval, const int* __restrict__ u) {
+                                 T* __restrict__ cval, const int* __restrict__ u) {
   constexpr int kReg = 32;  // rows with at most kReg entries accumulate in a per-thread array
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += gridDim.x * blockDim.x) {
     if (u[row] > kNumSmall) continue;
     int c0 = crp[row], c1 = crp[row + 1], L = c1 - c0;
     if (L <= kReg) {
       int cc[kReg];
-      double acc[kReg];
+      T acc[kReg];
 #pragma unroll
       for (int q = 0; q < kReg; ++q) {
         cc[q] = q < L ? ccol[c0 + q] : -1;
-        acc[q] = 0.0;
+        acc[q] = T(0);
       }
       for (int e = arp[row]; e < arp[row + 1]; ++e) {
         int j = acol[e];
-        double a = aval[e];
+        T a = aval[e];
         for (int f = brp[j]; f < brp[j + 1]; ++f) {
           int key = bcol[f];
-          double v = a * bval[f];
+          T v = a * bval[f];
           int pos = 0;
 #pragma unroll
           for (int q = 0; q < kReg; ++q) pos = cc[q] == key ? q : pos;
@@ -502,10 +511,10 @@ __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const i
       for (int q = 0; q < L; ++q) cval[c0 + q] = acc[q];
       continue;
     }
-    for (int q = c0; q < c1; ++q) cval[q] = 0.0;
+    for (int q = c0; q < c1; ++q) cval[q] = T(0);
     for (int e = arp[row]; e < arp[row + 1]; ++e) {
       int j = acol[e];
-      double a = aval[e];
+      T a = aval[e];
       for (int f = brp[j]; f < brp[j + 1]; ++f) {
         int pos = find_col(ccol, c0, c1, bcol[f]);
         cval[pos] += a * bval[f];
@@ -521,18 +530,19 @@ __global__ void k_spgemm_numeric(int nrows, const int* __restrict__ arp, const i
 constexpr int kWarpL = 256;
 constexpr int kWarpRowsPerBlock = 8;
 
+template <class T>
 __global__ void __launch_bounds__(32 * kWarpRowsPerBlock) k_spgemm_numeric_warp(
-    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
-    const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
-    const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval,
+    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const T* __restrict__ aval,
+    const int* __restrict__ brp, const int* __restrict__ bcol, const T* __restrict__ bval,
+    const int* __restrict__ crp, const int* __restrict__ ccol, T* __restrict__ cval,
     const int* __restrict__ u) {
-  __shared__ double sacc_all[kWarpRowsPerBlock][kWarpL];
+  __shared__ T sacc_all[kWarpRowsPerBlock][kWarpL];
   __shared__ int scol_all[kWarpRowsPerBlock][kWarpL];
   __shared__ int pre_all[kWarpRowsPerBlock][33];
   __shared__ int bst_all[kWarpRowsPerBlock][32];
-  __shared__ double av_all[kWarpRowsPerBlock][32];
+  __shared__ T av_all[kWarpRowsPerBlock][32];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* sacc = sacc_all[w];
+  T* sacc = sacc_all[w];
   int* scol = scol_all[w];
   int* pre = pre_all[w];
   int nw = gridDim.x * kWarpRowsPerBlock;
@@ -541,14 +551,14 @@ __global__ void __launch_bounds__(32 * kWarpRowsPerBlock) k_spgemm_numeric_warp(
     if (u[row] <= kNumSmall || L > kWarpL) continue;
     for (int t = lane; t < L; t += 32) {
       scol[t] = ccol[c0 + t];
-      sacc[t] = 0.0;
+      sacc[t] = T(0);
     }
     __syncwarp();
     for (int e0 = arp[row]; e0 < arp[row + 1]; e0 += 32) {
       int e = e0 + lane;
       bool has = e < arp[row + 1];
       int j = has ? acol[e] : 0;
-      double a = has ? aval[e] : 0.0;
+      T a = has ? aval[e] : T(0);
       int b0 = has ? brp[j] : 0;
       int len = has ? brp[j + 1] - b0 : 0;
       int inc = len;
@@ -571,7 +581,7 @@ __global__ void __launch_bounds__(32 * kWarpRowsPerBlock) k_spgemm_numeric_warp(
         }
         int f = bst_all[w][lo] + (t - pre[lo]);
         int key = bcol[f];
-        double v = av_all[w][lo] * bval[f];
+        T v = av_all[w][lo] * bval[f];
         int pos = find_col(scol, 0, L, key);
         atomicAdd(&sacc[pos], v);
       }
@@ -595,17 +605,17 @@ constexpr int kDenseCols = 8192; // C with at most this many columns: accumulate
 
 // DENSE: the shared accumulator is indexed by column (C has <= kDenseCols columns),
 // so a product needs no search; otherwise the row's sorted column list is searched.
-template <bool DENSE>
+template <class T, bool DENSE>
 __global__ void __launch_bounds__(kNumThreads) k_spgemm_numeric_block(
-    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
-    const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
-    const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval,
+    int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const T* __restrict__ aval,
+    const int* __restrict__ brp, const int* __restrict__ bcol, const T* __restrict__ bval,
+    const int* __restrict__ crp, const int* __restrict__ ccol, T* __restrict__ cval,
     const int* __restrict__ u, int ncols) {
   // dynamic shared memory: sacc[kNumLmax] av[kNumAmax] (doubles), then scol[kNumLmax]
   // off[kNumAmax + 1] bstart[kNumAmax] (ints)
   extern __shared__ unsigned char dsm[];
-  double* sacc = reinterpret_cast<double*>(dsm);
-  double* av = sacc + (DENSE ? kDenseCols : kNumLmax);
+  T* sacc = reinterpret_cast<T*>(dsm);
+  T* av = sacc + (DENSE ? kDenseCols : kNumLmax);
   int* scol = reinterpret_cast<int*>(av + kNumAmax);
   int* off = scol + kNumLmax;         // prefix of B-row lengths over the staged A entries
   int* bstart = off + kNumAmax + 1;
@@ -616,14 +626,14 @@ __global__ void __launch_bounds__(kNumThreads) k_spgemm_numeric_block(
     if (L <= kWarpL) continue;  // k_spgemm_numeric_warp
     bool sh = DENSE || L <= kNumLmax;
     if (DENSE) {
-      for (int t = threadIdx.x; t < L; t += blockDim.x) sacc[ccol[c0 + t]] = 0.0;
+      for (int t = threadIdx.x; t < L; t += blockDim.x) sacc[ccol[c0 + t]] = T(0);
     } else if (sh) {
       for (int t = threadIdx.x; t < L; t += blockDim.x) {
         scol[t] = ccol[c0 + t];
-        sacc[t] = 0.0;
+        sacc[t] = T(0);
       }
     } else {
-      for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = 0.0;
+      for (int t = threadIdx.x; t < L; t += blockDim.x) cval[c0 + t] = T(0);
     }
     __syncthreads();
     for (int e0 = arp[row]; e0 < arp[row + 1]; e0 += kNumAmax) {
@@ -668,7 +678,7 @@ __global__ void __launch_bounds__(kNumThreads) k_spgemm_numeric_block(
         }
         int f = bstart[lo2] + (t - off[lo2]);
         int key = bcol[f];
-        double v = av[lo2] * bval[f];
+        T v = av[lo2] * bval[f];
         if (DENSE) {
           atomicAdd(&sacc[key], v);
         } else if (sh) {
@@ -689,13 +699,138 @@ __global__ void __launch_bounds__(kNumThreads) k_spgemm_numeric_block(
   }
 }
 
+// ---------------------------------------------------------------- Galerkin refresh by product lists
+// The patterns of A P and R (A P) do not change between refreshes, so the pair
+// (A entry, B entry) behind each scalar product, and the C entry it adds to, are
+// the same every time.  k_plist enumerates the products of each row (one warp
+// per row, A entries 32 at a time, a warp scan of their B-row lengths spreads
+// the products over the lanes) and either counts the products of every C entry
+// or files each pair into its C entry's segment; k_plist_sort then orders each
+// segment by A entry, which is the order a row-by-row product sums in.
+constexpr int kPlWarps = 8;
+
+template <bool FILL>
+__global__ void __launch_bounds__(32 * kPlWarps) k_plist(int nrows, const int* __restrict__ arp,
+                                                         const int* __restrict__ acol, const int* __restrict__ brp,
+                                                         const int* __restrict__ bcol, const int* __restrict__ crp,
+                                                         const int* __restrict__ ccol, int* __restrict__ cnt,
+                                                         const int* __restrict__ seg,
+                                                         const long long* __restrict__ base, int* __restrict__ pa,
+                                                         int* __restrict__ pb) {
+  __shared__ int pre_all[kPlWarps][33];
+  __shared__ int bst_all[kPlWarps][32];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* pre = pre_all[w];
+  int* bst = bst_all[w];
+  int nw = gridDim.x * kPlWarps;
+  for (int row = blockIdx.x * kPlWarps + w; row < nrows; row += nw) {
+    int c0 = crp[row], c1 = crp[row + 1];
+    int a1 = arp[row + 1];
+    for (int e0 = arp[row]; e0 < a1; e0 += 32) {
+      int e = e0 + lane;
+      bool has = e < a1;
+      int j = has ? acol[e] : 0;
+      int b0 = has ? brp[j] : 0;
+      int len = has ? brp[j + 1] - b0 : 0;
+      int inc = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      int total = __shfl_sync(0xffffffffu, inc, 31);
+      pre[lane + 1] = inc;
+      if (lane == 0) pre[0] = 0;
+      bst[lane] = b0;
+      __syncwarp();
+      for (int t = lane; t < total; t += 32) {
+        int lo = 0, hi = 32;  // owner q of product t: pre[q] <= t < pre[q+1]
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (pre[mid] <= t) lo = mid; else hi = mid;
+        }
+        int f = bst[lo] + (t - pre[lo]);
+        int q = find_col(ccol, c0, c1, bcol[f]);
+        int slot = atomicAdd(&cnt[q], 1);
+        if (FILL) {
+          long long at = base[q >> kPlShift] + seg[q] + slot;
+          pa[at] = e0 + lo;
+          pb[at] = f;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// 64-bit segment starts -> chunk bases and 32-bit remainders.
+__global__ void k_plist_split(int nnz, const long long* __restrict__ segll, int* __restrict__ seg,
+                              long long* __restrict__ base) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= nnz; q += gridDim.x * blockDim.x) {
+    long long b = segll[(q >> kPlShift) << kPlShift];
+    seg[q] = (int)(segll[q] - b);
+    if ((q & ((1 << kPlShift) - 1)) == 0) base[q >> kPlShift] = b;
+  }
+}
+
+__device__ __forceinline__ long long plist_start(const int* __restrict__ seg, const long long* __restrict__ base,
+                                                 int q) {
+  return base[q >> kPlShift] + seg[q];
+}
+
+// Insertion sort of each segment by A entry (segments hold tens of pairs).
+__global__ void k_plist_sort(int nnz, const int* __restrict__ seg, const long long* __restrict__ base,
+                             int* __restrict__ pa, int* __restrict__ pb) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+    long long s0 = plist_start(seg, base, q), s1 = plist_start(seg, base, q + 1);
+    for (long long t = s0 + 1; t < s1; ++t) {
+      int ka = pa[t], kb = pb[t];
+      long long v = t - 1;
+      while (v >= s0 && pa[v] > ka) {
+        pa[v + 1] = pa[v];
+        pb[v + 1] = pb[v];
+        --v;
+      }
+      pa[v + 1] = ka;
+      pb[v + 1] = kb;
+    }
+  }
+}
+
+__global__ void k_sum_rows_ll(int n, const int* __restrict__ u, unsigned long long* __restrict__ out) {
+  unsigned long long s = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += (unsigned)u[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// c[q] = sum over the segment of q of a[pa] * b[pb], in segment order: no
+// search, no atomics, the same sum every refresh.  One thread per entry keeps
+// the threads of a warp on neighbouring entries of one C row, whose pairs read
+// neighbouring B entries (a lane group per entry was measured slower: its
+// gathers from B, too large for L2, lose that locality).
+template <class T>
+__global__ void __launch_bounds__(256) k_galerkin_lists(int nnz, const int* __restrict__ seg,
+                                                        const long long* __restrict__ base,
+                                                        const int* __restrict__ pa, const int* __restrict__ pb,
+                                                        const T* __restrict__ aval, const T* __restrict__ bval,
+                                                        T* __restrict__ cval) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+    long long s0 = plist_start(seg, base, q), s1 = plist_start(seg, base, q + 1);
+    T acc = T(0);
+    for (long long t = s0; t < s1; ++t) acc += aval[pa[t]] * bval[pb[t]];
+    cval[q] = acc;
+  }
+}
+
 // ---------------------------------------------------------------- coarsest level: dense inverse
 
+template <class T>
 __global__ void k_csr_to_dense(int n, const int* __restrict__ rp, const int* __restrict__ col,
-                               const double* __restrict__ val, double* __restrict__ dense) {
+                               const T* __restrict__ val, double* __restrict__ dense) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     for (int j = 0; j < n; ++j) dense[(long long)i * n + j] = 0.0;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) dense[(long long)i * n + col[e]] = val[e];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) dense[(long long)i * n + col[e]] = (double)val[e];
   }
 }
 
@@ -807,35 +942,108 @@ static const char* kNumericName[2][16] = {
      "galerkin_rap_l5", "galerkin_rap_l6", "galerkin_rap_l7", "galerkin_rap_l8", "galerkin_rap_l9", "galerkin_rap",
      "galerkin_rap", "galerkin_rap", "galerkin_rap", "galerkin_rap", "galerkin_rap"}};
 
-// which = 0 for A P, 1 for R (A P); level for the profile name
-static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C, const int* u,
-                          int which = 0, int level = 0) {
+static void plist_free(ProdList& pl) {
+  dfree(pl.seg);
+  dfree(pl.base);
+  dfree(pl.pa);
+  dfree(pl.pb);
+  pl.np = 0;
+}
+
+// Product lists of C = A B (u = products per row).  Leaves pl empty, and
+// returns RICH_OK, when the lists would not fit in half the free device
+// memory; the refresh then falls back to the searching kernels.
+static int plist_build(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, const Csr<double>& C, const int* u,
+                       ProdList& pl) {
+  plist_free(pl);
+  unsigned long long* dsum = reinterpret_cast<unsigned long long*>(c->iflag + 4);  // slots 4-5, 16-byte aligned
+  RICH_CUDA(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), c->st));
+  k_sum_rows_ll<<<red_grid(A.nrows), kBlock, 0, c->st>>>(A.nrows, u, dsum);
+  RICH_LAUNCH_CHECK();
+  unsigned long long np = 0;
+  RICH_CUDA(cudaMemcpyAsync(&np, dsum, sizeof(np), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  size_t fr = 0, tot = 0;
+  RICH_CUDA(cudaMemGetInfo(&fr, &tot));
+  double need = 8.0 * (double)np + 24.0 * ((double)C.nnz + 1);  // lists, offsets and the build's scratch
+  if (need > 0.5 * (double)fr) return RICH_OK;
+  int* cnt = nullptr;
+  long long* segll = nullptr;
+  RICH_CHECK(dalloc(&cnt, (long long)C.nnz + 1));
+  RICH_CHECK(dalloc(&segll, (long long)C.nnz + 1));
+  RICH_CHECK(dalloc(&pl.seg, (long long)C.nnz + 1));
+  RICH_CHECK(dalloc(&pl.base, ((long long)C.nnz >> kPlShift) + 1));
+  RICH_CHECK(dalloc(&pl.pa, (long long)np + 1));
+  RICH_CHECK(dalloc(&pl.pb, (long long)np + 1));
+  pl.np = (long long)np;
+  int nwb = (A.nrows + kPlWarps - 1) / kPlWarps;
+  if (nwb > 64 * kNumSM) nwb = 64 * kNumSM;
+  RICH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)C.nnz + 1), c->st));
+  k_plist<false><<<nwb, 32 * kPlWarps, 0, c->st>>>(A.nrows, A.rowptr, A.col, B.rowptr, B.col, C.rowptr, C.col, cnt,
+                                                   nullptr, nullptr, nullptr, nullptr);
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(scan_exclusive_int_ll(c, cnt, segll, C.nnz));
+  k_plist_split<<<grid_for((long long)C.nnz + 1), kBlock, 0, c->st>>>(C.nnz, segll, pl.seg, pl.base);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)C.nnz + 1), c->st));
+  k_plist<true><<<nwb, 32 * kPlWarps, 0, c->st>>>(A.nrows, A.rowptr, A.col, B.rowptr, B.col, C.rowptr, C.col, cnt,
+                                                  pl.seg, pl.base, pl.pa, pl.pb);
+  RICH_LAUNCH_CHECK();
+  k_plist_sort<<<grid_for(C.nnz), kBlock, 0, c->st>>>(C.nnz, pl.seg, pl.base, pl.pa, pl.pb);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  dfree(cnt);
+  dfree(segll);
+  return RICH_OK;
+}
+
+// C = A B on C's pattern with values of type T (aval/bval/cval); which = 0 for
+// A P, 1 for R (A P); level for the profile name.  pl, if it holds lists, is used.
+template <class T>
+static int spgemm_numeric_t(rich_ctx* c, const Csr<double>& A, const T* aval, const Csr<double>& B, const T* bval,
+                            const Csr<double>& C, T* cval, const int* u, int which, int level,
+                            const ProdList* pl = nullptr) {
+  if (pl && pl->seg) {
+    ProfScope ps(kNumericName[which][level & 15], c->st,
+                 4.0 * ((double)C.nnz + 1) + 8.0 * (double)pl->np +
+                     (double)sizeof(T) * ((double)A.nnz + (double)B.nnz + (double)C.nnz),
+                 2.0 * (double)pl->np);
+    k_galerkin_lists<T><<<grid_for(C.nnz, 256), 256, 0, c->st>>>(C.nnz, pl->seg, pl->base, pl->pa, pl->pb, aval,
+                                                                  bval, cval);
+    RICH_LAUNCH_CHECK();
+    return RICH_OK;
+  }
   ProfScope ps(kNumericName[which][level & 15], c->st,
-               (double)A.nrows * 4 + A.nnz * 12.0 + (double)C.nrows * 4 + C.nnz * 12.0);
-  k_spgemm_numeric<<<grid_for(A.nrows, 128), 128, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                              B.val, C.rowptr, C.col, C.val, u);
+               (double)A.nrows * 4 + A.nnz * (4.0 + sizeof(T)) + (double)C.nrows * 4 + C.nnz * (4.0 + sizeof(T)));
+  k_spgemm_numeric<T><<<grid_for(A.nrows, 128), 128, 0, c->st>>>(A.nrows, A.rowptr, A.col, aval, B.rowptr, B.col,
+                                                                 bval, C.rowptr, C.col, cval, u);
   RICH_LAUNCH_CHECK();
   {
     int nwb = (A.nrows + kWarpRowsPerBlock - 1) / kWarpRowsPerBlock;
     if (nwb > 32 * kNumSM) nwb = 32 * kNumSM;
-    k_spgemm_numeric_warp<<<nwb, 32 * kWarpRowsPerBlock, 0, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr,
-                                                                     B.col, B.val, C.rowptr, C.col, C.val, u);
+    k_spgemm_numeric_warp<T><<<nwb, 32 * kWarpRowsPerBlock, 0, c->st>>>(A.nrows, A.rowptr, A.col, aval, B.rowptr,
+                                                                        B.col, bval, C.rowptr, C.col, cval, u);
     RICH_LAUNCH_CHECK();
   }
   int nb = A.nrows < 8 * kNumSM ? A.nrows : 8 * kNumSM;
   if (C.ncols <= kDenseCols) {
     const int dsm = (int)((kDenseCols + kNumAmax) * sizeof(double) + (kNumLmax + 2 * kNumAmax + 1) * sizeof(int));
-    RICH_CUDA(cudaFuncSetAttribute(k_spgemm_numeric_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
-    k_spgemm_numeric_block<true><<<nb, kNumThreads, dsm, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                                 B.val, C.rowptr, C.col, C.val, u, C.ncols);
+    RICH_CUDA(cudaFuncSetAttribute(k_spgemm_numeric_block<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    k_spgemm_numeric_block<T, true><<<nb, kNumThreads, dsm, c->st>>>(A.nrows, A.rowptr, A.col, aval, B.rowptr, B.col,
+                                                                    bval, C.rowptr, C.col, cval, u, C.ncols);
   } else {
     const int dsm = (int)((kNumLmax + kNumAmax) * sizeof(double) + (kNumLmax + 2 * kNumAmax + 1) * sizeof(int));
-    RICH_CUDA(cudaFuncSetAttribute(k_spgemm_numeric_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
-    k_spgemm_numeric_block<false><<<nb, kNumThreads, dsm, c->st>>>(A.nrows, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                                  B.val, C.rowptr, C.col, C.val, u, C.ncols);
+    RICH_CUDA(cudaFuncSetAttribute(k_spgemm_numeric_block<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    k_spgemm_numeric_block<T, false><<<nb, kNumThreads, dsm, c->st>>>(A.nrows, A.rowptr, A.col, aval, B.rowptr,
+                                                                     B.col, bval, C.rowptr, C.col, cval, u, C.ncols);
   }
   RICH_LAUNCH_CHECK();
   return RICH_OK;
+}
+
+static int spgemm_numeric(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C, const int* u,
+                          int which = 0, int level = 0, const ProdList* pl = nullptr) {
+  return spgemm_numeric_t<double>(c, A, A.val, B, B.val, C, C.val, u, which, level, pl);
 }
 
 static void csr_free(Csr<double>& m, bool pattern = true) {
@@ -945,7 +1153,11 @@ static int coarse_inverse_launches(rich_ctx* c) {
   Hierarchy& H = c->H;
   Level& L = H.lv[H.nlev - 1];
   int n = L.n;
-  k_csr_to_dense<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, H.cdense);
+  // in MIXED precision the refreshed coarse values are the FP32 ones
+  if (c->prec == RICH_PREC_MIXED && H.nlev > 1)
+    k_csr_to_dense<float><<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A32, H.cdense);
+  else
+    k_csr_to_dense<double><<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, H.cdense);
   RICH_LAUNCH_CHECK();
   k_gj_prepare<<<grid_for(n), kBlock, 0, c->st>>>(n, H.cdense, H.cwork);
   RICH_LAUNCH_CHECK();
@@ -1042,6 +1254,10 @@ void amg_free(rich_ctx* c) {
     dfree(L.agg);
     dfree(L.P32);
     dfree(L.R32);
+    dfree(L.AP32);
+    plist_free(L.pl_ap);
+    plist_free(L.pl_rap);
+    L.pl_tried = false;
     dfree(L.u_ap);
     dfree(L.u_rap);
     if (L.x) cudaFree(L.x);
@@ -1216,6 +1432,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   if (c->prec == RICH_PREC_MIXED) {
     RICH_CHECK(dalloc(&L.P32, L.P.nnz));
     RICH_CHECK(dalloc(&L.R32, L.R.nnz));
+    RICH_CHECK(dalloc(&L.AP32, L.AP.nnz));
     k_cast<<<grid_for(L.P.nnz), kBlock, 0, c->st>>>(L.P.nnz, L.P.val, L.P32);
     RICH_LAUNCH_CHECK();
     k_cast<<<grid_for(L.R.nnz), kBlock, 0, c->st>>>(L.R.nnz, L.R.val, L.R32);
@@ -1276,10 +1493,32 @@ int amg_refresh(rich_ctx* c) {
   H.lv[0].A = c->A0;
   for (int l = 0; l + 1 < H.nlev; ++l) {
     Level& L = H.lv[l];
-    RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP, L.u_ap, 0, l));
-    RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A, L.u_rap, 1, l));
+    if (L.pl_tried || !H.opts.product_lists) continue;
+    L.pl_tried = true;
+    RICH_CHECK(plist_build(c, L.A, L.P, L.AP, L.u_ap, L.pl_ap));
+    if (L.pl_ap.seg) RICH_CHECK(plist_build(c, L.R, L.AP, H.lv[l + 1].A, L.u_rap, L.pl_rap));
   }
-  for (int l = 0; l < H.nlev; ++l) RICH_CHECK(level_diag_data(c, H.lv[l]));
+  if (c->prec == RICH_PREC_MIXED) {
+    // The V-cycle runs in FP32, so the Galerkin products do too: A32_{l+1} =
+    // R32 (A32_l P32), on the patterns kept from the setup.  The FP64 values of
+    // the coarse levels keep their setup-time content and are not read again.
+    RICH_CHECK(level_diag_data(c, H.lv[0]));
+    for (int l = 0; l + 1 < H.nlev; ++l) {
+      Level& L = H.lv[l];
+      Level& N = H.lv[l + 1];
+      RICH_CHECK(spgemm_numeric_t<float>(c, L.A, L.A32, L.P, L.P32, L.AP, L.AP32, L.u_ap, 0, l, &L.pl_ap));
+      RICH_CHECK(spgemm_numeric_t<float>(c, L.R, L.R32, L.AP, L.AP32, N.A, N.A32, L.u_rap, 1, l, &L.pl_rap));
+      k_l1dinv32<<<grid_for(N.n), kBlock, 0, c->st>>>(N.n, N.A.rowptr, N.A32, N.dinv32);
+      RICH_LAUNCH_CHECK();
+    }
+  } else {
+    for (int l = 0; l + 1 < H.nlev; ++l) {
+      Level& L = H.lv[l];
+      RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP, L.u_ap, 0, l, &L.pl_ap));
+      RICH_CHECK(spgemm_numeric(c, L.R, L.AP, H.lv[l + 1].A, L.u_rap, 1, l, &L.pl_rap));
+    }
+    for (int l = 0; l < H.nlev; ++l) RICH_CHECK(level_diag_data(c, H.lv[l]));
+  }
   RICH_CHECK(fine_stencil(c));
   return coarse_inverse(c);
 }
@@ -1342,7 +1581,16 @@ int amg_export_level(rich_ctx* c, int level, int* agg, int* rp, int* col, double
   }
   if (rp) RICH_CUDA(cudaMemcpy(rp, L.A.rowptr, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost));
   if (col) RICH_CUDA(cudaMemcpy(col, L.A.col, sizeof(int) * L.A.nnz, cudaMemcpyDeviceToHost));
-  if (val) RICH_CUDA(cudaMemcpy(val, L.A.val, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost));
+  if (val) {
+    if (c->prec == RICH_PREC_MIXED && level > 0) {
+      // the FP32 values the V-cycle uses (refreshed in FP32), widened
+      std::vector<float> v32((size_t)L.A.nnz);
+      RICH_CUDA(cudaMemcpy(v32.data(), L.A32, sizeof(float) * L.A.nnz, cudaMemcpyDeviceToHost));
+      for (long long e = 0; e < L.A.nnz; ++e) val[e] = (double)v32[(size_t)e];
+    } else {
+      RICH_CUDA(cudaMemcpy(val, L.A.val, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost));
+    }
+  }
   return RICH_OK;
 }
 

@@ -212,6 +212,9 @@ static int scan_impl(rich_ctx* c, const TI* in, TO* out, long long n) {
 }
 
 int scan_exclusive_int(rich_ctx* c, const int* in, int* out, long long n) { return scan_impl<int, int>(c, in, out, n); }
+int scan_exclusive_int_ll(rich_ctx* c, const int* in, long long* out, long long n) {
+  return scan_impl<int, long long>(c, in, out, n);
+}
 int scan_exclusive_ll(rich_ctx* c, const long long* in, long long* out, long long n) {
   return scan_impl<long long, long long>(c, in, out, n);
 }

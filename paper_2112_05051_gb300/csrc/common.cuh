@@ -105,6 +105,19 @@ struct Csr {
 
 // One level of the AMG hierarchy.  Level 0 holds the diffusion matrix of the
 // finest grid; levels 1.. hold Galerkin products.  FP32 copies exist in MIXED mode.
+// Galerkin refresh by product lists: entry q of C = A B is the sum over
+// t in [start(q), start(q+1)) of a[pa[t]] * b[pb[t]], the pairs sorted by A
+// entry; start(q) = base[q >> kPlShift] + seg[q] (64-bit pair offsets stored as
+// one base per 2^kPlShift entries plus a 32-bit remainder).
+constexpr int kPlShift = 10;
+struct ProdList {
+  int* seg = nullptr;        // nnz(C) + 1 offsets within the entry's chunk
+  long long* base = nullptr; // (nnz(C) >> kPlShift) + 1 chunk offsets
+  int* pa = nullptr;         // A entry of each pair
+  int* pb = nullptr;         // B entry of each pair
+  long long np = 0;          // pairs (= scalar products of C = A B)
+};
+
 struct Level {
   int n = 0;
   Csr<double> A;
@@ -117,6 +130,9 @@ struct Level {
   int* u_rap = nullptr;
   float* P32 = nullptr;            // values of P/R in FP32
   float* R32 = nullptr;
+  float* AP32 = nullptr;           // values of A P in FP32 (MIXED-precision refresh)
+  ProdList pl_ap, pl_rap;          // product lists of A P and R (A P), built at the first refresh
+  bool pl_tried = false;
   int mis_rounds = 0;
   double omega = 0.0;
   // V-cycle work vectors, typed by the hierarchy precision (double or float)
@@ -337,6 +353,7 @@ int finish_max(rich_ctx* c, const double* partials, int nb, double* dst);
 int fetch_scalars(rich_ctx* c, const double* dsrc, int count, double* host);
 int scan_exclusive_int(rich_ctx* c, const int* in, int* out, long long n);         // out[n] = total
 int scan_exclusive_ll(rich_ctx* c, const long long* in, long long* out, long long n);
+int scan_exclusive_int_ll(rich_ctx* c, const int* in, long long* out, long long n);
 int dot(rich_ctx* c, const double* x, const double* y, long long n, double* dst_dev);
 int nrm2sq(rich_ctx* c, const double* x, long long n, double* dst_dev);
 

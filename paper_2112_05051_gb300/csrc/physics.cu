@@ -341,6 +341,7 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->nu1 = 1;
   o->nu2 = 1;
   o->smooth_levels = 10;
+  o->product_lists = 1;
 }
 
 void rich_default_newton_opts(rich_newton_opts* o) {

@@ -62,7 +62,7 @@ def _bc_struct(bc, keep):
 class AmgOpts(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("coarse_max", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("smooth_levels", ctypes.c_int)]
+                ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -178,7 +178,7 @@ def default_newton_opts(**kw):
     for k, v in kw.items():
         if k in ("kind", "restart", "eta", "maxit"):
             setattr(o.krylov, k, v)
-        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels"):
+        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)

@@ -44,12 +44,12 @@ def _problem(dims, seed, kmean=0, het=True, dt=1.0, bc=None):
     return grid, p, ks, bc, dt, kmean
 
 
-def _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, seed=7, prec=0):
+def _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, seed=7, prec=0, lists=1):
     rb = _rb()
     ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
     pd = torch.tensor(p, device="cuda")
     ctx.jacobian(pd, dt)
-    info = ctx.amg_setup(rb.default_amg_opts(seed=seed, coarse_max=coarse_max))
+    info = ctx.amg_setup(rb.default_amg_opts(seed=seed, coarse_max=coarse_max, product_lists=lists))
     A = disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks)
     h = amg.setup(A, 0.08, seed, coarse_max)
     return ctx, info, h
@@ -153,21 +153,49 @@ def test_vcycle_parity_fp64_and_mixed(nu):
         ctx.close()
 
 
+@pytest.mark.parametrize("lists", [1, 0])
 @pytest.mark.parametrize("dims,coarse_max", [((18, 16, 14), 150), ((40, 36, 32), 2000)])
-def test_refresh_matches_oracle_galerkin_refresh(dims, coarse_max):
-    # the larger grid has coarse rows with > 64 and > 1024 products (block and hash kernels)
+def test_refresh_matches_oracle_galerkin_refresh(dims, coarse_max, lists):
+    # lists=1: summed product lists; lists=0: the searching kernels (the larger
+    # grid has coarse rows with > 64 and > 1024 products: warp and block kernels)
     rb = _rb()
     grid, p, ks, bc, dt, kmean = _problem(dims, 8, 0)
     p2 = p + np.random.default_rng(4).uniform(0, 15, grid.n)
-    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, coarse_max)
-    ctx.jacobian(torch.tensor(p2, device="cuda"), 2.0 * dt)
-    ctx.amg_update(rb.AMG_REFRESH)
-    amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, p2, 2.0 * dt, ks))
-    _compare_hierarchy(ctx, info, h)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, lists=lists)
+    for k in range(2):  # the second refresh reuses the lists the first one built
+        pk = p2 + 3.0 * k
+        ctx.jacobian(torch.tensor(pk, device="cuda"), 2.0 * dt)
+        ctx.amg_update(rb.AMG_REFRESH)
+        amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, pk, 2.0 * dt, ks))
+        _compare_hierarchy(ctx, info, h)
     r = np.random.default_rng(1).standard_normal(grid.n)
     z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
     ctx.vcycle(torch.tensor(r, device="cuda"), z)
     assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,coarse_max", [((18, 16, 14), 150), ((40, 36, 32), 2000)])
+@pytest.mark.parametrize("lists", [1, 0])
+def test_mixed_precision_refresh_runs_galerkin_in_fp32(dims, coarse_max, lists):
+    # MIXED: the refreshed coarse operators are FP32 products of the FP32 fine
+    # matrix and prolongators; they agree with the FP64 oracle to FP32 rounding
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem(dims, 8, 0)
+    p2 = p + np.random.default_rng(4).uniform(0, 15, grid.n)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, prec=1, lists=lists)
+    ctx.jacobian(torch.tensor(p2, device="cuda"), 2.0 * dt)
+    ctx.amg_update(rb.AMG_REFRESH)
+    amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, p2, 2.0 * dt, ks))
+    for l, lv in enumerate(h.levels):
+        _, rp, col, val = ctx.export_level(l, info)
+        np.testing.assert_array_equal(rp, lv.A.indptr)
+        np.testing.assert_array_equal(col, lv.A.indices)
+        assert _nrel(val, lv.A.data) <= (1e-10 if l == 0 else 1e-5)
+    r = np.random.default_rng(1).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= 1e-4
     ctx.close()
 
 
