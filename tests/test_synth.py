@@ -25,3 +25,39 @@ def test_dt_ramp_schedule():
     d = synth.dt_schedule("ramp1to30", 20)
     assert d[0] == 1.0 and d[-1] == 30.0 and len(d) == 20
     assert all(b > a for a, b in zip(d, d[1:]))
+
+
+def test_soil_and_paper_workload_match_printed_constants():
+    # tests/golden/paper_constants.txt: the values the paper prints (Fig. 1
+    # caption, Sec. 6, Supplementary D), each with its citation
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    g = {ln.split()[0]: float(ln.split()[1]) for ln in open(path) if ln.strip() and not ln.startswith("#")}
+    soil = synth.Soil()
+    for k in ("alpha", "beta", "theta_s", "theta_r", "a", "gamma", "ks"):
+        assert getattr(soil, k) == g[k]
+    w = synth.WORKLOADS["paper_infiltration"]
+    grid, _, bc, ks, p0, dts = synth.workload_inputs(w)
+    # unknowns on the interior nodes: n = N - 2 per direction
+    assert (grid.nx, grid.ny, grid.nz) == (g["nodes_x"] - 2, g["nodes_y"] - 2, g["nodes_z"] - 2)
+    assert (grid.lx, grid.ly, grid.lz) == (g["domain_x"], g["domain_y"], g["domain_z"])
+    assert len(dts) == g["time_steps"] and abs(sum(dts) - g["t_end"]) < 1e-12
+    assert w.krylov == "fgmres" and w.restart == g["gmres_restart"]
+    assert synth.P_TOP == g["p_top"] and synth.P_INITIAL == g["p_dry"] and np.all(p0 == g["p_dry"])
+
+
+def test_solver_defaults_match_printed_linear_settings():
+    # eta and the iteration limit of Sec. 6, in the oracle and in the library's defaults
+    import os
+    from oracle import newton
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    g = {ln.split()[0]: float(ln.split()[1]) for ln in open(path) if ln.strip() and not ln.startswith("#")}
+    o = newton.NewtonOptions()
+    assert o.eta == g["eta"] and o.maxit == g["max_linear_its"]
+    try:
+        from paper_2112_05051_gb300 import richards as rb
+        rb.load()
+    except Exception:  # library not built in this environment
+        return
+    d = rb.default_newton_opts()
+    assert d.krylov.eta == g["eta"] and d.krylov.maxit == g["max_linear_its"]
