@@ -76,6 +76,12 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-AMG comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
+    ap.add_argument("--serving-requests", type=int, default=512)
+    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--serving-lists", type=int, default=0,
+                    help="Galerkin product lists for served one-step requests (0: searching refresh)")
+    ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
     return ap.parse_args()
 
 
@@ -240,6 +246,104 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "DOF*Newton-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def serving_run(args, rb):
+    """Request stream: one-step solves of mixed size and soil through the request server.
+
+    Each request is one backward-Euler step (dt = 1 s) of an n^3 column, n drawn
+    from {24, 32, 48, 64, 96}, with its own seeded log-normal K_s field (sigma
+    uniform in [1, 2], field seed 1000 + id) and K-mean kind (arithmetic,
+    upstream or harmonic), FP32 AMG with FP64 residual and outer FCG.  A closed
+    burst of all requests measures the capacity mu (requests / s); then the same
+    requests arrive as a Poisson stream at 0.8 mu (seed 5) and the latency
+    submit -> result on the host is reported.  Finally one request of each size
+    is rerun alone and compared with its result in the mix.
+    """
+    import numpy as np
+    from paper_2112_05051_gb300 import synth
+    rng = np.random.default_rng(5)
+    n_req = args.serving_requests
+    sizes = [24, 32, 48, 64, 96]
+    soil = synth.Soil()
+    bc = synth.infiltration_bc(synth.P_TOP)
+    reqs = []
+    p0s = {}
+    for i in range(n_req):
+        n = sizes[int(rng.integers(len(sizes)))]
+        sigma = float(rng.uniform(1.0, 2.0))
+        kmean = int(rng.integers(3))
+        grid = synth.Grid(n, n, n)
+        ks = synth.ks_field(grid, 1000 + i, sigma)
+        p0s.setdefault(n, np.full(grid.n, synth.P_INITIAL))
+        reqs.append((grid, ks, kmean, n))
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
+                                  product_lists=args.serving_lists)
+
+    def submit(srv, q):
+        grid, ks, kmean, n = q
+        return srv.submit(grid, soil, bc, kmean, 1.0, p0=p0s[n], ks=ks, precision=rb.PREC_MIXED, opts=opts)
+
+    srv = rb.Server(slots=args.serving_slots)
+    # warm-up: one request of each size (library kernels loaded, memory pool primed)
+    for n in sizes:
+        k = next((j for j, q in enumerate(reqs) if q[3] == n), None)
+        if k is not None:
+            srv.wait(submit(srv, reqs[k]))
+    t0 = time.perf_counter()
+    ids = [submit(srv, q) for q in reqs]
+    burst = [srv.wait(i) for i in ids]
+    t_burst = time.perf_counter() - t0
+    mu = n_req / t_burst
+    lam = 0.8 * mu
+    gaps = rng.exponential(1.0 / lam, n_req)
+    t1 = time.perf_counter()
+    due = t1
+    ids = []
+    for q, g in zip(reqs, gaps):
+        due += g
+        wait = due - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(submit(srv, q))
+    stream = [srv.wait(i) for i in ids]
+    t_stream = time.perf_counter() - t1
+    cnt = srv.counters()
+    srv.close()
+    lat = sorted(1e3 * (r["t_done"] - r["t_submit"]) for r in stream)
+    lat_ok = sorted(1e3 * (r["t_done"] - r["t_submit"]) for r in stream if r["status"] == 0)
+    work_b = sum(q[0].n * r["stats"]["newton_its"] for q, r in zip(reqs, burst) if r["status"] == 0)
+    work_s = sum(q[0].n * r["stats"]["newton_its"] for q, r in zip(reqs, stream) if r["status"] == 0)
+    fails = {}
+    for r in stream:
+        if r["status"] != 0:
+            key = rb.ERRORS.get(r["status"], str(r["status"]))
+            fails[key] = fails.get(key, 0) + 1
+    # the same requests alone (one slot, nothing else in flight) against their results in the mix
+    alone = rb.Server(slots=1)
+    dev = 0.0
+    checked = 0
+    for n in sizes:
+        k = next((j for j, q in enumerate(reqs) if q[3] == n and stream[j]["status"] == 0), None)
+        if k is None:
+            continue
+        r = alone.wait(submit(alone, reqs[k]))
+        if r["status"] == 0:
+            dev = max(dev, float(np.abs(r["p"] - stream[k]["p"]).max() / np.abs(stream[k]["p"]).max()))
+            checked += 1
+    alone.close()
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))] if v else None
+    return {"requests": n_req, "slots": args.serving_slots, "sizes": sizes, "sigma": [1.0, 2.0],
+            "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
+            "capacity_rps": mu, "burst_s": t_burst,
+            "burst_dof_newton_per_s": work_b / t_burst, "rate_rps": lam, "arrivals": "Poisson, seed 5",
+            "stream_s": t_stream, "stream_dof_newton_per_s": work_s / t_stream,
+            "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "mean": sum(lat) / len(lat),
+                           "max": lat[-1]},
+            "latency_ms_converged": {"p50": pct(lat_ok, 0.5), "p99": pct(lat_ok, 0.99)},
+            "failed": fails, "max_in_flight": cnt["max_in_flight"],
+            "mix_vs_alone_max_rel_dev": dev, "mix_vs_alone_checked": checked,
+            "admission": "FIFO, a free slot and the request's device-memory estimate within 80% of free HBM"}
 
 
 def workload_config(w, grid):
@@ -426,6 +530,8 @@ def run_ours(args):
             "parallelism": "replicas" if ws > 1 else "single"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
+    if not args.no_serving and ws == 1:
+        line["serving"] = serving_run(args, rb)
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
@@ -443,6 +549,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving_only:
+        from paper_2112_05051_gb300 import richards as rb
+        rb.load()
+        print(json.dumps(serving_run(args, rb)))
+        return 0
     return run_ours(args)
 
 

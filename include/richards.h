@@ -49,6 +49,7 @@ extern "C" {
 #define RICH_ENONFINITE       -7  /* NaN or Inf in a residual or Krylov scalar */
 #define RICH_ESTATE           -8  /* call made before its prerequisite (e.g. no Jacobian yet) */
 #define RICH_ELIMIT           -9  /* a size limit of the implementation was exceeded */
+#define RICH_EBUSY           -10  /* request server: the request has not finished yet */
 
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
@@ -296,6 +297,76 @@ int rich_profile_table(char* buf, int cap);
 /* Default option structs (as listed in the comments above). */
 void rich_default_newton_opts(rich_newton_opts* o);
 void rich_default_amg_opts(rich_amg_opts* o);
+
+/* ---- request server (serving many time-step solves at once) -------------- */
+/* A server takes time-step requests of any grid size and soil as they arrive
+ * and runs up to `slots` of them on the device at once: each slot is a host
+ * worker thread with its own CUDA stream, so the kernels of different requests
+ * overlap on the GPU.  A request is admitted, in arrival order, as soon as a
+ * slot is free and its device-memory estimate fits in the budget next to the
+ * requests in flight and the resident sessions (least recently used idle
+ * sessions are evicted to make room).  Device memory is stream-ordered, so
+ * admitting or finishing one request never waits for another.  Each request
+ * runs the same kernels, in the same order, as a lone rich_step on its own
+ * context, so its result does not depend on what else is in flight.  The
+ * paper has no serving layer; this is the deployment form of Sec. 3's step. */
+typedef struct rich_server rich_server;
+
+typedef struct {
+  int slots;               /* requests in flight at once (8) */
+  double mem_budget_bytes; /* device bytes requests and sessions may hold; <= 0: 80 % of the free memory at creation */
+  int max_sessions;        /* resident sessions kept at most (64) */
+} rich_server_opts;
+
+typedef struct {
+  rich_grid grid;
+  rich_soil soil;              /* ks_field_dev is ignored: see ks_field_host */
+  const double* ks_field_host; /* n cells of K_s (host), or NULL for soil.ks_const */
+  int kmean;                   /* RICH_KMEAN_* */
+  rich_bc bc;                  /* constant face values (value_field_dev must be NULL) */
+  int precision;               /* RICH_PREC_* */
+  double dt;                   /* time step */
+  rich_newton_opts opts;
+  const double* p0_host;       /* n cells of p^{l-1}; NULL continues the session's resident pressure */
+  double* p_out_host;          /* n cells, receives p^l when the request finishes (may be NULL); after a
+                                  failed step, the last accepted Newton iterate */
+  long long session;           /* 0: one-off.  Otherwise the server keeps this problem's context (pressure,
+                                  AMG hierarchy) on the device for later requests with the same id, which
+                                  must have the same grid, soil, kmean, bc and precision (else RICH_EINVAL);
+                                  once evicted, a request with p0_host NULL returns RICH_ESTATE */
+} rich_request;
+
+typedef struct {
+  int status;                  /* the step's status (RICH_OK or an error code) */
+  rich_step_stats stats;
+  double t_submit, t_admit, t_done; /* seconds since the server was created */
+  int slot;                    /* worker slot that ran it */
+  double mem_estimate;         /* device bytes reserved for it at admission */
+  double mem_in_flight;        /* bytes reserved by all admitted requests and sessions, itself included */
+} rich_request_result;
+
+void rich_default_server_opts(rich_server_opts* o);
+/* Starts the worker threads on the current device.  RICH_EINVAL for slots < 1
+ * or max_sessions < 0. */
+int rich_server_create(const rich_server_opts* opts, rich_server** out);
+/* Queues a request (the struct is copied; the host arrays it points to must stay
+ * valid until the request has finished) and returns its id (> 0).  RICH_EINVAL
+ * for a malformed request, RICH_ELIMIT if its estimate exceeds the whole budget. */
+int rich_server_submit(rich_server* s, const rich_request* req, long long* id_out);
+/* RICH_OK with *out filled once request id has finished (the id is then
+ * released), RICH_EBUSY while it is queued or running, RICH_EINVAL for an
+ * unknown id. */
+int rich_server_poll(rich_server* s, long long id, rich_request_result* out);
+/* Blocks until request id has finished; then as rich_server_poll. */
+int rich_server_wait(rich_server* s, long long id, rich_request_result* out);
+/* Blocks until every submitted request has finished. */
+int rich_server_drain(rich_server* s);
+/* Requests admitted so far, the most that were in flight at once, and the
+ * device bytes reserved now (any pointer may be NULL). */
+int rich_server_counters(rich_server* s, long long* admitted, int* max_in_flight, double* reserved_bytes);
+/* Finishes the queued and running requests, stops the workers and frees every
+ * resident session. */
+int rich_server_destroy(rich_server* s);
 
 #ifdef __cplusplus
 }

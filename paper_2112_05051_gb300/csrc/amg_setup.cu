@@ -964,6 +964,8 @@ static int plist_build(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, 
   RICH_CUDA(cudaMemcpyAsync(&np, dsum, sizeof(np), cudaMemcpyDeviceToHost, c->st));
   RICH_CUDA(cudaStreamSynchronize(c->st));
   size_t fr = 0, tot = 0;
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  pool_trim();  // blocks freed into the pool count as free here
   RICH_CUDA(cudaMemGetInfo(&fr, &tot));
   double need = 8.0 * (double)np + 24.0 * ((double)C.nnz + 1);  // lists, offsets and the build's scratch
   if (need > 0.5 * (double)fr) return RICH_OK;
@@ -1107,6 +1109,7 @@ static int coarse_inverse(rich_ctx* c) {
   Hierarchy& H = c->H;
   if (!H.dense) return RICH_OK;
   if (H.gj_exec) {
+    ProfScope ps("coarse_inverse", c->st, 8.0 * (double)H.cn * H.cn * 2.0);
     RICH_CUDA(cudaGraphLaunch(H.gj_exec, c->st));
     count_launches(H.gj_nodes);
     return RICH_OK;
@@ -1228,10 +1231,12 @@ static int level_diag_data(rich_ctx* c, Level& L) {
 static int level_alloc_vectors(rich_ctx* c, Level& L) {
   size_t es = c->prec == RICH_PREC_MIXED ? sizeof(float) : sizeof(double);
   long long n = L.n > 0 ? L.n : 1;
-  RICH_CUDA(cudaMalloc(&L.x, es * n));
-  RICH_CUDA(cudaMalloc(&L.b, es * n));
-  RICH_CUDA(cudaMalloc(&L.r, es * n));
-  RICH_CUDA(cudaMalloc(&L.t, es * n));
+  void** vecs[4] = {&L.x, &L.b, &L.r, &L.t};
+  for (void** v : vecs) {
+    char* m = nullptr;
+    RICH_CHECK(dalloc(&m, (long long)es * n));
+    *v = m;
+  }
   RICH_CHECK(dalloc(&L.dinv, n));
   if (c->prec == RICH_PREC_MIXED) {
     RICH_CHECK(dalloc(&L.dinv32, n));
@@ -1260,10 +1265,12 @@ void amg_free(rich_ctx* c) {
     L.pl_tried = false;
     dfree(L.u_ap);
     dfree(L.u_rap);
-    if (L.x) cudaFree(L.x);
-    if (L.b) cudaFree(L.b);
-    if (L.r) cudaFree(L.r);
-    if (L.t) cudaFree(L.t);
+    void** vecs[4] = {&L.x, &L.b, &L.r, &L.t};
+    for (void** v : vecs) {
+      char* m = static_cast<char*>(*v);
+      dfree(m);
+      *v = nullptr;
+    }
   }
   H.lv.clear();
   H.nlev = 0;
@@ -1543,6 +1550,7 @@ extern "C" {
 
 int amg_setup(rich_ctx* c, const rich_amg_opts* o, rich_amg_info* info) {
   if (!c) return RICH_EINVAL;
+  AllocStream guard(c->st);
   RICH_CHECK(amg_build(c, o));
   if (info) {
     Hierarchy& H = c->H;
@@ -1563,6 +1571,7 @@ int amg_setup(rich_ctx* c, const rich_amg_opts* o, rich_amg_info* info) {
 
 int amg_update(rich_ctx* c, int policy) {
   if (!c) return RICH_EINVAL;
+  AllocStream guard(c->st);
   if (policy == RICH_AMG_SETUP_ONCE) return amg_update_fine(c);
   if (policy == RICH_AMG_REFRESH) return amg_refresh(c);
   return RICH_EINVAL;
@@ -1570,6 +1579,7 @@ int amg_update(rich_ctx* c, int policy) {
 
 int amg_export_level(rich_ctx* c, int level, int* agg, int* rp, int* col, double* val) {
   if (!c) return RICH_EINVAL;
+  AllocStream guard(c->st);
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
   if (level < 0 || level >= H.nlev) return RICH_EINVAL;
@@ -1596,6 +1606,7 @@ int amg_export_level(rich_ctx* c, int level, int* agg, int* rp, int* col, double
 
 int amg_export_prolongator(rich_ctx* c, int level, long long* nnz, int* rp, int* col, double* val) {
   if (!c) return RICH_EINVAL;
+  AllocStream guard(c->st);
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
   if (level < 0 || level + 1 >= H.nlev) return RICH_EINVAL;

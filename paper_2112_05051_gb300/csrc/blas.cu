@@ -1,12 +1,62 @@
 // Deterministic reductions, scans and dot products.  Every reduction writes one
 // partial per block of a fixed grid and a second single-block kernel sums the
 // partials in block order, so FP64 results reproduce bit for bit run to run.
+#include <mutex>
+
 #include "common.cuh"
 
 #include <atomic>
 #include <string>
 
 namespace rich {
+
+thread_local cudaStream_t t_alloc_stream = 0;
+
+static std::mutex g_pool_mu;
+static bool g_pool_done[64] = {false};
+
+void pool_setup() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (g_pool_done[dev]) return;
+  g_pool_done[dev] = true;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  unsigned long long keep = ~0ULL;  // keep freed blocks for the next allocation
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
+void pool_trim() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  cudaMemPoolTrimTo(pool, 0);
+}
+
+static std::mutex g_pinned_mu;
+static std::vector<void*> g_pinned_free;
+
+void* pinned_get() {
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      void* b = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return b;
+    }
+  }
+  void* b = nullptr;
+  if (cudaMallocHost(&b, kPinnedBlock) != cudaSuccess) return nullptr;
+  return b;
+}
+
+void pinned_put(void* b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.push_back(b);
+}
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -357,12 +357,32 @@ int scan_exclusive_int_ll(rich_ctx* c, const int* in, long long* out, long long 
 int dot(rich_ctx* c, const double* x, const double* y, long long n, double* dst_dev);
 int nrm2sq(rich_ctx* c, const double* x, long long n, double* dst_dev);
 
+// Device memory is stream-ordered: cudaMallocAsync / cudaFreeAsync on the
+// stream of the context being worked on, so allocating or freeing never waits
+// for the work of other streams (the request server runs several contexts at
+// once).  Every entry point that may allocate names its stream with an
+// AllocStream guard; outside one the legacy default stream is used, which is
+// ordered with every blocking stream.  Freed blocks stay in the device's pool
+// for reuse (release threshold raised once per device, see pool_setup).
+extern thread_local cudaStream_t t_alloc_stream;
+struct AllocStream {
+  cudaStream_t prev;
+  explicit AllocStream(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+  ~AllocStream() { t_alloc_stream = prev; }
+};
+void pool_setup();         // keeps freed device memory in the current device's pool
+void pool_trim();          // returns the pool's unused memory (before free-memory queries)
+void* pinned_get();        // a 2 KB pinned host block from a process-wide free list
+void pinned_put(void* b);  // back to the list (never cudaFreeHost: that synchronises the device)
+constexpr size_t kPinnedBlock = 2048;
+
 template <class T>
 int dalloc(T** p, long long count) {
   if (count <= 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+  pool_setup();
+  cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * (size_t)count, t_alloc_stream);
   if (e != cudaSuccess) {
-    set_cuda_error(e, "cudaMalloc");
+    set_cuda_error(e, "cudaMallocAsync");
     *p = nullptr;
     return RICH_ENOMEM;
   }
@@ -370,7 +390,7 @@ int dalloc(T** p, long long count) {
 }
 template <class T>
 void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+  if (p) cudaFreeAsync((void*)p, t_alloc_stream);
   p = nullptr;
 }
 

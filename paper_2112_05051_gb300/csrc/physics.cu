@@ -397,6 +397,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   c->prec = precision;
   c->st = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
+  AllocStream guard(c->st);
   int s = RICH_OK;
   auto fail = [&](int st_) {
     rich_destroy(c);
@@ -406,9 +407,13 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
       (s = dalloc(&c->J7, 7 * n)) || (s = dalloc(&c->A7, 7 * n)) || (s = dalloc(&c->partials, (long long)kRedBlocks * 64)) ||
       (s = dalloc(&c->dsc, 128)) || (s = dalloc(&c->iflag, 16)))
     return fail(s);
-  if (cudaMallocHost((void**)&c->hsc, 128 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->hflag, 16 * sizeof(int)) != cudaSuccess)
-    return fail(RICH_ENOMEM);
+  {
+    // 128 doubles then 16 ints of pinned host memory from the process-wide pool
+    char* blk = static_cast<char*>(pinned_get());
+    if (!blk) return fail(RICH_ENOMEM);
+    c->hsc = reinterpret_cast<double*>(blk);
+    c->hflag = reinterpret_cast<int*>(blk + 128 * sizeof(double));
+  }
   if (soil->ks_field_dev) {
     if ((s = dalloc(&c->ks, n))) return fail(s);
     if (cudaMemcpyAsync(c->ks, soil->ks_field_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st) !=
@@ -435,7 +440,8 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
 
 int rich_destroy(rich_ctx* c) {
   if (!c) return RICH_OK;
-  if (c->st) cudaStreamSynchronize(c->st);
+  AllocStream guard(c->st);
+  cudaStreamSynchronize(c->st);
   amg_free(c);
   dfree(c->ks);
   dfree(c->K);
@@ -469,14 +475,14 @@ int rich_destroy(rich_ctx* c) {
   dfree(k.z);
   dfree(k.w);
   dfree(k.hcoef);
-  if (c->hsc) cudaFreeHost(c->hsc);
-  if (c->hflag) cudaFreeHost(c->hflag);
+  pinned_put(c->hsc);
   delete c;
   return RICH_OK;
 }
 
 int rich_saturation(rich_ctx* c, const double* p, double* s) {
   if (!c || !p || !s) return RICH_EINVAL;
+  AllocStream guard(c->st);
   k_saturation<<<grid_for(c->g.n), kBlock, 0, c->st>>>(c->g.n, c->soil, p, s);
   RICH_LAUNCH_CHECK();
   return RICH_OK;
@@ -484,6 +490,7 @@ int rich_saturation(rich_ctx* c, const double* p, double* s) {
 
 int rich_residual(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, double* norms) {
   if (!c || !p || !s_old || !F || !(dt > 0)) return RICH_EINVAL;
+  AllocStream guard(c->st);
   RICH_CHECK(residual_eval(c, p, s_old, dt, F, norms != nullptr));
   if (norms) {
     double h[2];
@@ -497,6 +504,7 @@ int rich_residual(rich_ctx* c, const double* p, const double* s_old, double dt, 
 
 int rich_jacobian(rich_ctx* c, const double* p, double dt, double* J7, double* A7) {
   if (!c || !p || !(dt > 0)) return RICH_EINVAL;
+  AllocStream guard(c->st);
   RICH_CHECK(jacobian_eval(c, p, dt));
   long long bytes = 7 * c->g.n * (long long)sizeof(double);
   if (J7) RICH_CUDA(cudaMemcpyAsync(J7, c->J7, bytes, cudaMemcpyDeviceToDevice, c->st));
@@ -506,6 +514,7 @@ int rich_jacobian(rich_ctx* c, const double* p, double dt, double* J7, double* A
 
 int rich_jacobian_apply(rich_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return RICH_EINVAL;
+  AllocStream guard(c->st);
   if (!c->have_jac) return RICH_ESTATE;
   return stencil_apply(c, c->J7, x, y);
 }

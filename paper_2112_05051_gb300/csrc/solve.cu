@@ -958,11 +958,13 @@ extern "C" {
 
 int amg_vcycle(rich_ctx* c, const double* r, double* z) {
   if (!c || !r || !z) return RICH_EINVAL;
+  AllocStream guard(c->st);
   return vcycle_apply(c, r, z);
 }
 
 int krylov_solve(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
   if (!c || !b || !x || !o) return RICH_EINVAL;
+  AllocStream guard(c->st);
   if (!c->have_jac || !c->H.built) return RICH_ESTATE;
   rich_krylov_stats tmp;
   return krylov_run(c, b, x, o, st ? st : &tmp);
@@ -970,6 +972,7 @@ int krylov_solve(rich_ctx* c, const double* b, double* x, const rich_krylov_opts
 
 int rich_step(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) {
   if (!c || !p || !(dt > 0)) return RICH_EINVAL;
+  AllocStream guard(c->st);
   rich_newton_opts def;
   if (!o) {
     rich_default_newton_opts(&def);
@@ -981,6 +984,7 @@ int rich_step(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich
 
 int rich_step_host(rich_ctx* c, double* p_host, double dt, const rich_newton_opts* o, rich_step_stats* st) {
   if (!c || !p_host || !(dt > 0)) return RICH_EINVAL;
+  AllocStream guard(c->st);
   long long n = c->g.n;
   if (!c->pbuf) RICH_CHECK(dalloc(&c->pbuf, n));
   RICH_CUDA(cudaMemcpyAsync(c->pbuf, p_host, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));

@@ -19,7 +19,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 ERRORS = {-1: "RICH_EINVAL", -2: "RICH_ENOMEM", -3: "RICH_ECUDA", -4: "RICH_ENOTCONV_LIN",
           -5: "RICH_ENOTCONV_NEWTON", -6: "RICH_ELINESEARCH", -7: "RICH_ENONFINITE", -8: "RICH_ESTATE",
-          -9: "RICH_ELIMIT"}
+          -9: "RICH_ELIMIT", -10: "RICH_EBUSY"}
+RICH_EBUSY = -10
 
 
 class RichError(RuntimeError):
@@ -92,6 +93,22 @@ class StepStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double), ("max_sessions", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("soil", Soil), ("ks_field_host", ctypes.c_void_p), ("kmean", ctypes.c_int),
+                ("bc", BC), ("precision", ctypes.c_int), ("dt", ctypes.c_double), ("opts", NewtonOpts),
+                ("p0_host", ctypes.c_void_p), ("p_out_host", ctypes.c_void_p), ("session", ctypes.c_longlong)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("stats", StepStats), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("slot", ctypes.c_int),
+                ("mem_estimate", ctypes.c_double), ("mem_in_flight", ctypes.c_double)]
+
+
 class AmgInfo(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("n", ctypes.c_int * 16), ("nnz", ctypes.c_longlong * 16),
                 ("mis_rounds", ctypes.c_int * 16), ("omega", ctypes.c_double * 16),
@@ -130,6 +147,15 @@ EXPORTS = {
                                       ctypes.POINTER(StepStats)]),
     "rich_default_newton_opts": (None, [ctypes.POINTER(NewtonOpts)]),
     "rich_default_amg_opts": (None, [ctypes.POINTER(AmgOpts)]),
+    "rich_default_server_opts": (None, [ctypes.POINTER(ServerOpts)]),
+    "rich_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)]),
+    "rich_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
+    "rich_server_poll": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(RequestResult)]),
+    "rich_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(RequestResult)]),
+    "rich_server_drain": (ctypes.c_int, [_P]),
+    "rich_server_counters": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "rich_server_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -329,3 +355,105 @@ class Context:
         check(load().rich_step_host(self.h, ptr, dt, ctypes.byref(opts) if opts is not None else None,
                                     ctypes.byref(st)), "rich_step_host")
         return st
+
+
+def default_server_opts(**kw):
+    o = ServerOpts()
+    load().rich_default_server_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Request server (rich_server_*): time-step solves of any size, several in flight at once.
+
+    submit() takes host numpy arrays (float64); they stay referenced until the
+    request's result has been collected with wait() or poll().  A result holds
+    the step's status and statistics, host timestamps (seconds since the server
+    started) and the output pressure (after a failed step: the last accepted
+    Newton iterate).
+    """
+
+    def __init__(self, slots=8, mem_budget_bytes=0.0, max_sessions=64):
+        self._lib = load()
+        self.h = ctypes.c_void_p()
+        o = default_server_opts(slots=slots, mem_budget_bytes=float(mem_budget_bytes), max_sessions=max_sessions)
+        check(self._lib.rich_server_create(ctypes.byref(o), ctypes.byref(self.h)), "rich_server_create")
+        self._keep = {}
+
+    def submit(self, grid, soil, bc, kmean, dt, p0=None, ks=None, precision=PREC_MIXED, opts=None, session=0,
+               want_output=True):
+        import numpy as np
+        if any(bc.field(f) is not None for f in range(6)):
+            raise ValueError("the request server takes constant boundary values only")
+        r = Request()
+        r.grid = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        r.soil = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
+                      None)
+        keep = []
+        if ks is not None:
+            ks = np.ascontiguousarray(ks, dtype=np.float64)
+            keep.append(ks)
+            r.ks_field_host = ks.ctypes.data
+        r.kmean = kmean
+        r.bc = BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value), (ctypes.c_void_p * 6)())
+        r.precision = precision
+        r.dt = dt
+        r.opts = opts if opts is not None else default_newton_opts()
+        if p0 is not None:
+            p0 = np.ascontiguousarray(p0, dtype=np.float64)
+            keep.append(p0)
+            r.p0_host = p0.ctypes.data
+        out = None
+        if want_output:
+            out = np.full(grid.n, np.nan)
+            keep.append(out)
+            r.p_out_host = out.ctypes.data
+        r.session = session
+        rid = ctypes.c_longlong()
+        check(self._lib.rich_server_submit(self.h, ctypes.byref(r), ctypes.byref(rid)), "rich_server_submit")
+        self._keep[rid.value] = (keep, out)
+        return rid.value
+
+    def _result(self, rid, res):
+        keep, out = self._keep.pop(rid)
+        return {"status": res.status, "stats": res.stats.as_dict(), "t_submit": res.t_submit,
+                "t_admit": res.t_admit, "t_done": res.t_done, "slot": res.slot, "mem_estimate": res.mem_estimate,
+                "mem_in_flight": res.mem_in_flight, "p": out}
+
+    def wait(self, rid):
+        res = RequestResult()
+        check(self._lib.rich_server_wait(self.h, rid, ctypes.byref(res)), "rich_server_wait")
+        return self._result(rid, res)
+
+    def poll(self, rid):
+        res = RequestResult()
+        st = self._lib.rich_server_poll(self.h, rid, ctypes.byref(res))
+        if st == RICH_EBUSY:
+            return None
+        check(st, "rich_server_poll")
+        return self._result(rid, res)
+
+    def drain(self):
+        check(self._lib.rich_server_drain(self.h), "rich_server_drain")
+
+    def counters(self):
+        a = ctypes.c_longlong()
+        m = ctypes.c_int()
+        b = ctypes.c_double()
+        check(self._lib.rich_server_counters(self.h, ctypes.byref(a), ctypes.byref(m), ctypes.byref(b)),
+              "rich_server_counters")
+        return {"admitted": a.value, "max_in_flight": m.value, "reserved_bytes": b.value}
+
+    def close(self):
+        if self.h:
+            self._lib.rich_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

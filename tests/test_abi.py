@@ -49,3 +49,17 @@ def test_host_only_calls_work_without_a_gpu(lib):
     assert lib.rich_strerror(-4) == b"Krylov solver did not converge"
     # argument validation happens before any device work
     assert lib.rich_create(None, None, 0, None, 0, None, None) == -1
+
+
+def test_server_options_and_argument_checks_without_a_gpu(lib):
+    import ctypes as C
+    from paper_2112_05051_gb300 import richards as rb
+    rb.load()
+    o = rb.default_server_opts()
+    assert o.slots == 8 and o.mem_budget_bytes == 0.0 and o.max_sessions == 64
+    h = C.c_void_p()
+    bad = rb.default_server_opts(slots=0)
+    assert lib.rich_server_create(C.byref(bad), C.byref(h)) == -1 and not h.value
+    assert lib.rich_server_submit(None, None, None) == -1
+    assert lib.rich_server_poll(None, 1, None) == -1
+    assert lib.rich_server_destroy(None) == 0
