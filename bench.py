@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--serving-lists", type=int, default=0,
                     help="Galerkin product lists for served one-step requests (0: searching refresh)")
     ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
+    ap.add_argument("--serving-coarse-max", type=int, default=500)
     return ap.parse_args()
 
 
@@ -254,7 +255,8 @@ def serving_run(args, rb):
     Each request is one backward-Euler step (dt = 1 s) of an n^3 column, n drawn
     from {24, 32, 48, 64, 96}, with its own seeded log-normal K_s field (sigma
     uniform in [1, 2], field seed 1000 + id) and K-mean kind (arithmetic,
-    upstream or harmonic), FP32 AMG with FP64 residual and outer FCG.  A closed
+    upstream or harmonic), FP32 AMG (coarsest level < 500 unknowns) with FP64
+    residual and outer FCG.  A closed
     burst of all requests measures the capacity mu (requests / s); then the same
     requests arrive as a Poisson stream at 0.8 mu (seed 5) and the latency
     submit -> result on the host is reported.  Finally one request of each size
@@ -277,8 +279,10 @@ def serving_run(args, rb):
         ks = synth.ks_field(grid, 1000 + i, sigma)
         p0s.setdefault(n, np.full(grid.n, synth.P_INITIAL))
         reqs.append((grid, ks, kmean, n))
+    # coarsest level below 500 unknowns: its dense inverse is redone at every
+    # refresh, and a short one-step request refreshes ~10 times
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
-                                  product_lists=args.serving_lists)
+                                  product_lists=args.serving_lists, coarse_max=args.serving_coarse_max)
 
     def submit(srv, q):
         grid, ks, kmean, n = q
@@ -334,6 +338,7 @@ def serving_run(args, rb):
     alone.close()
     pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))] if v else None
     return {"requests": n_req, "slots": args.serving_slots, "sizes": sizes, "sigma": [1.0, 2.0],
+            "coarse_max": args.serving_coarse_max, "product_lists": args.serving_lists,
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
             "capacity_rps": mu, "burst_s": t_burst,
             "burst_dof_newton_per_s": work_b / t_burst, "rate_rps": lam, "arrivals": "Poisson, seed 5",

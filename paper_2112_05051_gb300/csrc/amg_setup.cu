@@ -834,34 +834,42 @@ __global__ void k_csr_to_dense(int n, const int* __restrict__ rp, const int* __r
   }
 }
 
+// Work buffer layout (4n + 2 doubles): two parity copies of [pivot row | pivot
+// column] (2n each), then the reciprocal of the pivot of each parity.
 __global__ void k_gj_prepare(int n, const double* __restrict__ a, double* __restrict__ buf) {
-  // buf[0..n): row 0, buf[n..2n): column 0 (parity 0 buffers)
+  // parity 0: row 0, column 0 and 1 / a_00
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     buf[t] = a[t];
     buf[n + t] = a[(long long)t * n];
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) buf[4 * n] = 1.0 / a[0];
 }
 
-// One Gauss-Jordan pivot step (no pivoting: the matrix is SPD).  Row k and column k
-// before the step come from the parity buffer; the updated row/column k+1 are
-// written to the other parity buffer for the next step.
+// One Gauss-Jordan pivot step (no pivoting: the matrix is SPD), one block row
+// per matrix row (blockIdx.y).  Row k, column k and 1/a_kk before the step come
+// from the parity-k buffers; the updated row/column k+1 and the reciprocal of
+// the next pivot go to the other parity for the next step, so every element
+// costs one FMA and no division.
 __global__ void k_gj_step(int n, int k, double* __restrict__ a, double* __restrict__ buf) {
   const double* rowk = buf + (k & 1) * 2 * n;
   const double* colk = rowk + n;
   double* rown = buf + ((k + 1) & 1) * 2 * n;
   double* coln = rown + n;
-  double piv = rowk[k];
-  long long nn = (long long)n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t / n), j = (int)(t % n);
+  const double inv = buf[4 * n + (k & 1)];
+  const int i = blockIdx.y;
+  const double ci = colk[i] * inv;
+  double* ai = a + (long long)i * n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double v;
-    if (i == k && j == k) v = 1.0 / piv;
-    else if (i == k) v = rowk[j] / piv;
-    else if (j == k) v = -colk[i] / piv;
-    else v = a[t] - colk[i] * rowk[j] / piv;
-    a[t] = v;
+    if (i == k) v = (j == k) ? inv : rowk[j] * inv;
+    else if (j == k) v = -ci;
+    else v = fma(-ci, rowk[j], ai[j]);
+    ai[j] = v;
     if (j == k + 1) coln[i] = v;
-    if (i == k + 1) rown[j] = v;
+    if (i == k + 1) {
+      rown[j] = v;
+      if (j == k + 1) buf[4 * n + ((k + 1) & 1)] = 1.0 / v;
+    }
   }
 }
 
@@ -1165,8 +1173,7 @@ static int coarse_inverse_launches(rich_ctx* c) {
   k_gj_prepare<<<grid_for(n), kBlock, 0, c->st>>>(n, H.cdense, H.cwork);
   RICH_LAUNCH_CHECK();
   long long nn = (long long)n * n;
-  int g = grid_for(nn);
-  if (g > 4 * kNumSM) g = 4 * kNumSM;
+  dim3 g((unsigned)((n + kBlock - 1) / kBlock), (unsigned)n);
   for (int k = 0; k < n; ++k) {
     k_gj_step<<<g, kBlock, 0, c->st>>>(n, k, H.cdense, H.cwork);
     RICH_LAUNCH_CHECK();
@@ -1482,7 +1489,7 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
   RICH_CHECK(fine_stencil(c));
   if (H.dense) {
     RICH_CHECK(dalloc(&H.cdense, (long long)H.cn * H.cn));
-    RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn));
+    RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn + 2));
     if (c->prec == RICH_PREC_MIXED) RICH_CHECK(dalloc(&H.cinv32, (long long)H.cn * H.cn));
     RICH_CHECK(coarse_inverse(c));
     RICH_CHECK(capture_coarse_graph(c));
