@@ -79,8 +79,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
     ap.add_argument("--serving-requests", type=int, default=512)
     ap.add_argument("--serving-slots", type=int, default=8)
-    ap.add_argument("--serving-lists", type=int, default=0,
-                    help="Galerkin product lists for served one-step requests (0: searching refresh)")
+    ap.add_argument("--serving-lists", type=int, default=1,
+                    help="Galerkin product lists for served requests (0: searching refresh, whose shared-memory "
+                         "atomics make results differ from run to run at rounding level)")
     ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
     ap.add_argument("--serving-coarse-max", type=int, default=500)
     return ap.parse_args()
