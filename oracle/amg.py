@@ -206,6 +206,115 @@ def l1_diagonal(A):
     return np.bincount(rows, weights=np.abs(A.data), minlength=A.shape[0])
 
 
+# ---------------------------------------------------------------- matching aggregation
+# The paper's second coarsening (SMATCH, Sec. 5.2, with aggregates of at most 8
+# dofs in its runs) is coupled aggregation by weighted graph matching, named
+# without formulas.  The oracle fixes it as follows:
+#   weights   for the smooth vector of ones, the compatible weight of the edge
+#             {i, j} is w_ij = 1 - (a_ij + a_ji) / (a_ii + a_jj), taken over the
+#             negative couplings (a_ij + a_ji < 0) and rounded to FP32, so that
+#             rounding-order differences of the FP64 matrices cannot reorder two
+#             equal weights.  Edges are ordered by weight (larger first), then by
+#             (min(i, j), max(i, j)) (smaller first): a strict total order.
+#   matching  locally dominant: in synchronous rounds every unmatched node
+#             proposes to its best unmatched neighbour, mutual proposals are
+#             matched; rounds repeat while a proposal exists.  With a strict
+#             total order this equals the sequential greedy matching (edges by
+#             decreasing order, kept when both ends are free).
+#   pairs     each matched pair, and each unmatched node alone, becomes a node
+#             of the pair graph, numbered by its smallest member; the pair
+#             graph's matrix is P_p^T A P_p with P_p the 0/1 pairing.
+#   aggregates  log2(max_size) pairing passes (3 for aggregates of at most 8),
+#             composed; the prolongator then follows the smoothed-aggregation
+#             rule of the MIS-2 path.
+
+def matching_weights(A):
+    """Per stored entry: the FP32 compatible weight, or -inf where {i, j} is no edge."""
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    n = A.shape[0]
+    At = sp.csr_matrix(A.T)
+    At.sort_indices()
+    if not (np.array_equal(At.indptr, A.indptr) and np.array_equal(At.indices, A.indices)):
+        raise ValueError("matching needs a structurally symmetric matrix")
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    cols = A.indices
+    d = A.diagonal()
+    s = A.data + At.data  # a_ij + a_ji, the same value seen from i and from j
+    edge = (cols != rows) & (s < 0)
+    w = np.full(len(cols), -np.inf, dtype=np.float32)
+    w[edge] = (1.0 - s[edge] / (d[rows[edge]] + d[cols[edge]])).astype(np.float32)
+    return rows, cols, w
+
+
+def match(A):
+    """Locally dominant matching in synchronous rounds; returns (mate, rounds), mate = -1 if unmatched."""
+    rows, cols, w = matching_weights(A)
+    n = A.shape[0]
+    lo = np.minimum(rows, cols)
+    hi = np.maximum(rows, cols)
+    mate = np.full(n, -1, dtype=np.int64)
+    rounds = 0
+    while True:
+        ok = np.isfinite(w) & (mate[rows] < 0) & (mate[cols] < 0)
+        if not np.any(ok):
+            break
+        r, c, ww, l, h = rows[ok], cols[ok], w[ok], lo[ok], hi[ok]
+        order = np.lexsort((h, l, -ww.astype(np.float64), r))  # by row, then best edge first
+        first = np.ones(len(order), dtype=bool)
+        first[1:] = r[order][1:] != r[order][:-1]
+        cand = np.full(n, -1, dtype=np.int64)
+        cand[r[order][first]] = c[order][first]
+        i = np.flatnonzero(cand >= 0)
+        mutual = i[cand[cand[i]] == i]
+        mate[mutual] = cand[mutual]
+        rounds += 1
+    return mate, rounds
+
+
+def greedy_matching(A):
+    """Sequential greedy matching in the same edge order (the pin of match())."""
+    rows, cols, w = matching_weights(A)
+    n = A.shape[0]
+    keep = np.isfinite(w) & (rows < cols)
+    r, c, ww = rows[keep], cols[keep], w[keep]
+    mate = np.full(n, -1, dtype=np.int64)
+    for e in np.lexsort((c, r, -ww.astype(np.float64))):
+        if mate[r[e]] < 0 and mate[c[e]] < 0:
+            mate[r[e]] = c[e]
+            mate[c[e]] = r[e]
+    return mate
+
+
+def pair_ids(mate):
+    """Pair-graph node of every node (pairs and singletons numbered by their smallest member)."""
+    n = len(mate)
+    idx = np.arange(n)
+    first = (mate < 0) | (idx < mate)
+    ids = np.cumsum(first) - 1
+    rep = np.where(mate < 0, idx, np.minimum(idx, mate))
+    return ids[rep].astype(np.int64), int(first.sum())
+
+
+def matching_aggregate(A, max_size=8):
+    """Aggregates of at most max_size nodes by log2(max_size) pairing passes; (agg, nc, rounds)."""
+    passes = int(np.floor(np.log2(max_size)))
+    n = A.shape[0]
+    agg = np.arange(n, dtype=np.int64)
+    nc = n
+    Ak = sp.csr_matrix(A)
+    rounds = 0
+    for _ in range(passes):
+        mate, r = match(Ak)
+        rounds += r
+        ids, nk = pair_ids(mate)
+        Pp = tentative_prolongator(ids, nk)
+        Ak = spgemm(transpose(Pp), spgemm(Ak, Pp))
+        agg = ids[agg]
+        nc = nk
+    return agg, nc, rounds
+
+
 DENSE_MAX = 8192
 COARSE_SWEEPS = 8
 
@@ -234,18 +343,27 @@ class Hierarchy:
         return sum(lv.A.nnz for lv in self.levels) / self.levels[0].A.nnz
 
 
-def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, smooth_levels=10):
-    """Build the hierarchy from a symmetric positive definite CSR matrix."""
+def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, smooth_levels=10,
+          aggregation="mis2", max_agg_size=8):
+    """Build the hierarchy from a symmetric positive definite CSR matrix.
+
+    aggregation: "mis2" (strength graph + MIS-2 roots) or "matching"
+    (compatible weighted matching, aggregates of at most max_agg_size).
+    """
     levels = [Level(A)]
     while True:
         lv = levels[-1]
         n = lv.A.shape[0]
         if n < coarse_max or len(levels) >= max_levels:
             break
-        S = strength(lv.A, theta * 0.5 ** (len(levels) - 1))
-        keys = priority_keys(n, seed)
-        state, rounds = mis2(S, keys)
-        agg, nc = aggregate(S, state, keys)
+        if aggregation == "matching":
+            S = None
+            agg, nc, rounds = matching_aggregate(lv.A, max_agg_size)
+        else:
+            S = strength(lv.A, theta * 0.5 ** (len(levels) - 1))
+            keys = priority_keys(n, seed)
+            state, rounds = mis2(S, keys)
+            agg, nc = aggregate(S, state, keys)
         if nc > max_ratio * n:
             break
         Pt = tentative_prolongator(agg, nc)

@@ -58,6 +58,8 @@ class NewtonOptions:
     coarse_max: int = 2000
     max_levels: int = 10
     smooth_levels: int = 10
+    aggregation: str = "mis2"     # or "matching" (the paper's SMATCH-style coarsening)
+    max_agg_size: int = 8
     armijo_c: float = 1e-4
     lambda_min: float = 1e-10
 
@@ -126,7 +128,8 @@ def step(prob, p, dt, opt):
         A = prob.aux(p, dt)
         if prob.hierarchy is None or (opt.amg_policy == "rebuild_step" and r == 0):
             prob.hierarchy = amg.setup(A, opt.theta, opt.amg_seed, opt.coarse_max, opt.max_levels,
-                                       smooth_levels=opt.smooth_levels)
+                                       smooth_levels=opt.smooth_levels, aggregation=opt.aggregation,
+                                       max_agg_size=opt.max_agg_size)
         elif opt.amg_policy == "setup_once":
             amg.update_fine(prob.hierarchy, A)
         else:

@@ -875,6 +875,16 @@ __global__ void k_gj_step(int n, int k, double* __restrict__ a, double* __restri
 
 // ---------------------------------------------------------------- host side
 
+// One int from the device, on the context's stream only (a plain cudaMemcpy would
+// run on the legacy default stream and wait for every blocking stream, e.g. the
+// other request-server slots).
+static int read_dev_int(rich_ctx* c, const int* src, int* out) {
+  RICH_CUDA(cudaMemcpyAsync(c->hflag + 8, src, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  *out = c->hflag[8];
+  return RICH_OK;
+}
+
 static int spgemm_upper(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, int* u, int* umax) {
   int n = A.nrows;
   k_spgemm_upper<<<grid_for(n), kBlock, 0, c->st>>>(n, A.rowptr, A.col, B.rowptr, u);
@@ -917,7 +927,7 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
     if (mode == 1) {
       RICH_CHECK(scan_exclusive_int(c, cnt, C.rowptr, n));
       int nnz = 0;
-      RICH_CUDA(cudaMemcpy(&nnz, C.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+      RICH_CHECK(read_dev_int(c, C.rowptr + n, &nnz));
       if (nnz < 0) return RICH_ELIMIT;
       C.nnz = nnz;
       RICH_CHECK(dalloc(&C.col, nnz));
@@ -1314,7 +1324,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   RICH_CHECK(dalloc(&S.rowptr, (long long)n + 1));
   RICH_CHECK(scan_exclusive_int(c, cnt, S.rowptr, n));
   int snnz = 0;
-  RICH_CUDA(cudaMemcpy(&snnz, S.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+  RICH_CHECK(read_dev_int(c, S.rowptr + n, &snnz));
   RICH_CHECK(dalloc(&S.col, snnz));
   k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, S.rowptr, nullptr, S.col);
   RICH_LAUNCH_CHECK();
@@ -1351,7 +1361,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   RICH_LAUNCH_CHECK();
   RICH_CHECK(scan_exclusive_int(c, isroot, aggid, n));
   int nc = 0;
-  RICH_CUDA(cudaMemcpy(&nc, aggid + n, sizeof(int), cudaMemcpyDeviceToHost));
+  RICH_CHECK(read_dev_int(c, aggid + n, &nc));
   k_rootval<<<grid_for(n), kBlock, 0, c->st>>>(n, t, rv);
   RICH_LAUNCH_CHECK();
   k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
@@ -1397,7 +1407,7 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   RICH_LAUNCH_CHECK();
   RICH_CHECK(scan_exclusive_int(c, cnt, Pt.rowptr, n));
   int ptnnz = 0;
-  RICH_CUDA(cudaMemcpy(&ptnnz, Pt.rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+  RICH_CHECK(read_dev_int(c, Pt.rowptr + n, &ptnnz));
   Pt.nnz = ptnnz;
   RICH_CHECK(dalloc(&Pt.col, ptnnz));
   k_ptent_fill<<<grid_for(n), kBlock, 0, c->st>>>(n, L.agg, Pt.rowptr, Pt.col);

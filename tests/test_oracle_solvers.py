@@ -302,3 +302,85 @@ def test_converged_pressure_is_independent_of_solver_choices():
         res.append(p)
     for q in res[1:]:
         np.testing.assert_allclose(q, res[0], rtol=1e-8)
+
+
+# ---------------------------------------------------------------- matching aggregation
+
+def _random_spd_graph(n, p, seed, levels=4):
+    """Symmetric M-matrix on a random graph with few distinct coupling values (many tied weights)."""
+    rng = np.random.default_rng(seed)
+    m = np.triu(rng.random((n, n)) < p, 1)
+    vals = -rng.integers(1, levels + 1, size=(n, n)).astype(float)
+    off = np.where(m, vals, 0.0)
+    off = off + off.T
+    d = -off.sum(axis=1) + 1.0
+    return sp.csr_matrix(off + np.diag(d))
+
+
+def test_compatible_weight_of_a_two_node_laplacian():
+    # w = 1 - (a_12 + a_21)/(a_11 + a_22) = 1 - (-2)/4 = 1.5 for [[2, -1], [-1, 2]]
+    rows, cols, w = amg.matching_weights(sp.csr_matrix(np.array([[2.0, -1.0], [-1.0, 2.0]])))
+    off = rows != cols
+    assert np.all(w[off] == np.float32(1.5)) and np.all(np.isneginf(w[~off]))
+    # positive couplings are not edges
+    _, _, w2 = amg.matching_weights(sp.csr_matrix(np.array([[2.0, 0.5], [0.5, 2.0]])))
+    assert np.all(np.isneginf(w2))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+@pytest.mark.parametrize("n,p", [(30, 0.15), (80, 0.05), (150, 0.03)])
+def test_locally_dominant_matching_equals_sequential_greedy(n, p, seed):
+    A = _random_spd_graph(n, p, seed)
+    mate, rounds = amg.match(A)
+    assert np.array_equal(mate, amg.greedy_matching(A))
+    # a valid, maximal matching of the negative couplings
+    m = np.flatnonzero(mate >= 0)
+    assert np.all(mate[mate[m]] == m) and np.all(mate[m] != m)
+    D = A.toarray()
+    assert np.all(D[m, mate[m]] < 0)
+    free = mate < 0
+    assert not np.any((D[np.ix_(free, free)] < 0) & ~np.eye(int(free.sum()), dtype=bool))
+
+
+def test_matching_on_the_grid_laplacian_pairs_every_node_along_x():
+    # equal weights everywhere: ties go to the smallest index pair, so the greedy
+    # order pairs (0,1), (2,3), ... along x on an even grid
+    grid = synth.Grid(6, 4, 3)
+    st = np.zeros((grid.n, 7))
+    st[:, 0] = 6.0
+    st[:, 1:] = -1.0
+    A = disc._stencil_to_csr(grid, st)
+    mate, _ = amg.match(A)
+    idx = np.arange(grid.n)
+    assert np.array_equal(mate, idx ^ 1)
+
+
+@pytest.mark.parametrize("max_size", [2, 4, 8])
+def test_matching_aggregates_partition_with_bounded_size(max_size):
+    grid = synth.Grid(14, 12, 10)
+    ks = synth.ks_field(grid, 5, 1.0, (4.0, 4.0, 2.0))
+    A = disc.aux_matrix(grid, SOIL, synth.infiltration_bc(), 0, np.full(grid.n, -40.0), 1.0, ks)
+    agg, nc, rounds = amg.matching_aggregate(A, max_size)
+    assert agg.min() == 0 and agg.max() == nc - 1
+    sizes = np.bincount(agg, minlength=nc)
+    assert sizes.min() >= 1 and sizes.max() <= max_size
+    assert nc < grid.n / (0.6 * max_size)  # most nodes are matched at every pass
+    # every aggregate is connected through negative couplings
+    G = (A < 0).astype(int)
+    for a in np.unique(agg)[:200]:
+        nodes = np.flatnonzero(agg == a)
+        if len(nodes) > 1:
+            sub = G[nodes][:, nodes]
+            ncomp, _ = sp.csgraph.connected_components(sub, directed=False)
+            assert ncomp == 1
+
+
+def test_matching_hierarchy_gives_a_convergent_vcycle():
+    grid = synth.Grid(20, 18, 16)
+    ks = synth.ks_field(grid, 7, 1.5, (4.0, 4.0, 2.0))
+    A = disc.aux_matrix(grid, SOIL, synth.infiltration_bc(), 1, np.full(grid.n, -50.0), 1.0, ks)
+    h = amg.setup(A, 0.08, 1, 100, smooth_levels=2, aggregation="matching")
+    assert len(h.levels) >= 3
+    b = np.random.default_rng(2).standard_normal(grid.n)
+    x, its, ok, _ = krylov.fgmres(lambda v: A @ v, lambda v: amg.vcycle(h, v), b, 1e-10, 100, 30)
+    assert ok and its < 40
