@@ -51,6 +51,9 @@ extern "C" {
 #define RICH_ELIMIT           -9  /* a size limit of the implementation was exceeded */
 #define RICH_EBUSY           -10  /* request server: the request has not finished yet */
 
+#define RICH_AGG_MIS2          0
+#define RICH_AGG_MATCHING      1
+
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
  * (eq. (upstream_mean)) K_U if p_U - p_L >= 0 else K_L with U the +d cell;
@@ -129,6 +132,12 @@ typedef struct {
                               memory; used only while it fits in half the free device memory).
                               0: every refresh searches
                               each product's output position instead (no extra memory). */
+  int aggregation;         /* RICH_AGG_MIS2 (default): strength graph + MIS-2 roots.  RICH_AGG_MATCHING:
+                              the paper's SMATCH-style coupled aggregation (Sec. 5.2): compatible weights
+                              w_ij = 1 - (a_ij + a_ji)/(a_ii + a_jj) of the negative couplings (FP32),
+                              locally dominant matching, log2(max_agg_size) pairing passes on the
+                              successive pair graphs */
+  int max_agg_size;        /* largest aggregate of the matching (8, as in the paper's runs) */
 } rich_amg_opts;
 
 typedef struct {

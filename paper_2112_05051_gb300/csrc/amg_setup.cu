@@ -17,6 +17,8 @@
 // sums each column's products in product order, so patterns are structural
 // and values deterministic.  The numeric refresh recomputes values on the kept
 // patterns with one thread per row in the same product order.
+#include <math_constants.h>
+
 #include "common.cuh"
 
 namespace rich {
@@ -873,6 +875,96 @@ __global__ void k_gj_step(int n, int k, double* __restrict__ a, double* __restri
   }
 }
 
+// ---------------------------------------------------------------- matching aggregation
+// Coupled aggregation by compatible weighted matching (the paper's SMATCH
+// coarsening, Sec. 5.2).  Edge {i, j} of a negative coupling has the weight
+// w_ij = 1 - (a_ij + a_ji) / (a_ii + a_jj) (smooth vector of ones), rounded to
+// FP32 so that rounding-order differences of the FP64 matrices do not reorder
+// equal weights; edges are ordered by weight, then by (min, max) index pair.
+// The matching is locally dominant: synchronous rounds in which every unmatched
+// node proposes to its best unmatched neighbour and mutual proposals match.
+
+__device__ __forceinline__ bool match_better(float w1, int lo1, int hi1, float w2, int lo2, int hi2) {
+  if (w1 != w2) return w1 > w2;
+  if (lo1 != lo2) return lo1 < lo2;
+  return hi1 < hi2;
+}
+
+__global__ void k_match_weights(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ d,
+                                float* __restrict__ w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      int j = col[e];
+      float wv = -CUDART_INF_F;
+      if (j != i) {
+        int q = find_col(col, rp[j], rp[j + 1], i);  // a_ji (the pattern is symmetric)
+        if (q < rp[j + 1] && col[q] == i) {
+          double sum = val[e] + val[q];
+          if (sum < 0.0) wv = (float)(1.0 - sum / (d[i] + d[j]));
+        }
+      }
+      w[e] = wv;
+    }
+  }
+}
+
+// Proposals of one round; *any = 1 if some node proposed.
+__global__ void k_match_propose(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const float* __restrict__ w, const int* __restrict__ mate, int* __restrict__ cand,
+                                int* __restrict__ any) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int best = -1;
+    float bw = -CUDART_INF_F;
+    int blo = 0, bhi = 0;
+    if (mate[i] < 0) {
+      for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int j = col[e];
+        float we = w[e];
+        if (we == -CUDART_INF_F || mate[j] >= 0) continue;
+        int lo = min(i, j), hi = max(i, j);
+        if (best < 0 || match_better(we, lo, hi, bw, blo, bhi)) {
+          best = j;
+          bw = we;
+          blo = lo;
+          bhi = hi;
+        }
+      }
+    }
+    cand[i] = best;
+    if (best >= 0) *any = 1;
+  }
+}
+
+__global__ void k_match_commit(int n, const int* __restrict__ cand, int* __restrict__ mate) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int j = cand[i];
+    if (j >= 0 && cand[j] == i) mate[i] = j;
+  }
+}
+
+// 1 for the smallest member of each pair and for every unmatched node.
+__global__ void k_pair_first(int n, const int* __restrict__ mate, int* __restrict__ first) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    first[i] = mate[i] < 0 || i < mate[i];
+}
+
+__global__ void k_pair_ids(int n, const int* __restrict__ mate, const int* __restrict__ pos, int* __restrict__ ids) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int m = mate[i];
+    ids[i] = pos[m < 0 ? i : min(i, m)];
+  }
+}
+
+// agg[i] = ids[agg[i]] (composition of the pairing passes).
+__global__ void k_compose(int n, const int* __restrict__ ids, int* __restrict__ agg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) agg[i] = ids[agg[i]];
+}
+
+__global__ void k_iota(int n, int* __restrict__ a) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
 // ---------------------------------------------------------------- host side
 
 // One int from the device, on the context's stream only (a plain cudaMemcpy would
@@ -1304,6 +1396,94 @@ void amg_free(rich_ctx* c) {
 
 
 // Coarsen level L into a new level; returns RICH_OK with *stop = true when coarsening stops.
+// Aggregates of at most max_size nodes by log2(max_size) matching passes on A
+// (the first pass) and on the successive pair graphs P_p^T A P_p.  agg (n ints)
+// receives the aggregate of every node, *nc their number, *rounds the matching
+// rounds summed over the passes.
+static int matching_aggregate(rich_ctx* c, const Csr<double>& A, int max_size, int* agg, int* nc, int* rounds) {
+  int n = A.nrows;
+  int passes = 0;
+  while ((2 << passes) <= max_size) ++passes;
+  k_iota<<<grid_for(n), kBlock, 0, c->st>>>(n, agg);
+  RICH_LAUNCH_CHECK();
+  *nc = n;
+  *rounds = 0;
+  Csr<double> Ak = A;  // the first pass reads A itself
+  bool own = false;
+  for (int pass = 0; pass < passes; ++pass) {
+    int m = Ak.nrows;
+    double* d = nullptr;
+    float* w = nullptr;
+    int *mate = nullptr, *cand = nullptr, *first = nullptr, *pos = nullptr, *ids = nullptr;
+    RICH_CHECK(dalloc(&d, m));
+    RICH_CHECK(dalloc(&w, Ak.nnz));
+    RICH_CHECK(dalloc(&mate, m));
+    RICH_CHECK(dalloc(&cand, m));
+    RICH_CHECK(dalloc(&first, m));
+    RICH_CHECK(dalloc(&pos, (long long)m + 1));
+    RICH_CHECK(dalloc(&ids, m));
+    k_diag<<<grid_for(m), kBlock, 0, c->st>>>(m, Ak.rowptr, Ak.col, Ak.val, d);
+    RICH_LAUNCH_CHECK();
+    k_match_weights<<<grid_for(m), kBlock, 0, c->st>>>(m, Ak.rowptr, Ak.col, Ak.val, d, w);
+    RICH_LAUNCH_CHECK();
+    RICH_CUDA(cudaMemsetAsync(mate, 0xff, sizeof(int) * (size_t)m, c->st));  // -1: unmatched
+    for (;;) {
+      RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
+      k_match_propose<<<grid_for(m), kBlock, 0, c->st>>>(m, Ak.rowptr, Ak.col, w, mate, cand, c->iflag);
+      RICH_LAUNCH_CHECK();
+      int any = 0;
+      RICH_CHECK(read_dev_int(c, c->iflag, &any));
+      if (!any) break;
+      k_match_commit<<<grid_for(m), kBlock, 0, c->st>>>(m, cand, mate);
+      RICH_LAUNCH_CHECK();
+      ++*rounds;
+      if (*rounds > 1000000) return RICH_ELIMIT;  // every round matches the globally best free edge
+    }
+    k_pair_first<<<grid_for(m), kBlock, 0, c->st>>>(m, mate, first);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(scan_exclusive_int(c, first, pos, m));
+    int mc = 0;
+    RICH_CHECK(read_dev_int(c, pos + m, &mc));
+    k_pair_ids<<<grid_for(m), kBlock, 0, c->st>>>(m, mate, pos, ids);
+    RICH_LAUNCH_CHECK();
+    k_compose<<<grid_for(n), kBlock, 0, c->st>>>(n, ids, agg);
+    RICH_LAUNCH_CHECK();
+    *nc = mc;
+    if (pass + 1 < passes) {  // the pair graph's matrix for the next pass
+      Csr<double> Pp, Rp, AP, Ac;
+      Pp.nrows = m;
+      Pp.ncols = mc;
+      Pp.nnz = m;
+      RICH_CHECK(dalloc(&Pp.rowptr, (long long)m + 1));
+      RICH_CHECK(dalloc(&Pp.col, m));
+      RICH_CHECK(dalloc(&Pp.val, m));
+      k_iota<<<grid_for((long long)m + 1), kBlock, 0, c->st>>>(m + 1, Pp.rowptr);
+      RICH_LAUNCH_CHECK();
+      RICH_CUDA(cudaMemcpyAsync(Pp.col, ids, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, c->st));
+      k_fill<<<grid_for(m), kBlock, 0, c->st>>>(m, 1.0, Pp.val);
+      RICH_LAUNCH_CHECK();
+      RICH_CHECK(transpose(c, Pp, Rp));
+      RICH_CHECK(spgemm_symbolic(c, Ak, Pp, AP));
+      RICH_CHECK(spgemm_symbolic(c, Rp, AP, Ac));
+      csr_free(Pp);
+      csr_free(Rp);
+      csr_free(AP);
+      if (own) csr_free(Ak);
+      Ak = Ac;
+      own = true;
+    }
+    dfree(d);
+    dfree(w);
+    dfree(mate);
+    dfree(cand);
+    dfree(first);
+    dfree(pos);
+    dfree(ids);
+  }
+  if (own) csr_free(Ak);
+  return RICH_OK;
+}
+
 static int coarsen(rich_ctx* c, int l, bool* stop) {
   Hierarchy& H = c->H;
   const rich_amg_opts& o = H.opts;
@@ -1317,72 +1497,79 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   RICH_CHECK(dalloc(&cnt, n));
   k_diag<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d);
   RICH_LAUNCH_CHECK();
-  double theta_l = o.theta * std::ldexp(1.0, -l);
-  double theta2 = theta_l * theta_l;
-  k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, nullptr, cnt, nullptr);
-  RICH_LAUNCH_CHECK();
-  RICH_CHECK(dalloc(&S.rowptr, (long long)n + 1));
-  RICH_CHECK(scan_exclusive_int(c, cnt, S.rowptr, n));
-  int snnz = 0;
-  RICH_CHECK(read_dev_int(c, S.rowptr + n, &snnz));
-  RICH_CHECK(dalloc(&S.col, snnz));
-  k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, S.rowptr, nullptr, S.col);
-  RICH_LAUNCH_CHECK();
-  // MIS-2
-  uint64_t *t = nullptr, *m1 = nullptr;
-  RICH_CHECK(dalloc(&t, n));
-  RICH_CHECK(dalloc(&m1, n));
-  k_mis_init<<<grid_for(n), kBlock, 0, c->st>>>(n, o.seed, S.rowptr, t);
-  RICH_LAUNCH_CHECK();
   int rounds = 0;
-  for (;;) {
+  int nc = 0;
+  int* aggid = nullptr;
+  bool unassigned = false;
+  if (o.aggregation == RICH_AGG_MATCHING) {
+    RICH_CHECK(dalloc(&L.agg, n));
+    RICH_CHECK(dalloc(&aggid, 1));
+    RICH_CHECK(matching_aggregate(c, L.A, o.max_agg_size, L.agg, &nc, &rounds));
+  } else {
+    double theta_l = o.theta * std::ldexp(1.0, -l);
+    double theta2 = theta_l * theta_l;
+    k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, nullptr, cnt, nullptr);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(dalloc(&S.rowptr, (long long)n + 1));
+    RICH_CHECK(scan_exclusive_int(c, cnt, S.rowptr, n));
+    int snnz = 0;
+    RICH_CHECK(read_dev_int(c, S.rowptr + n, &snnz));
+    RICH_CHECK(dalloc(&S.col, snnz));
+    k_strength<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, d, theta2, S.rowptr, nullptr, S.col);
+    RICH_LAUNCH_CHECK();
+    // MIS-2
+    uint64_t *t = nullptr, *m1 = nullptr;
+    RICH_CHECK(dalloc(&t, n));
+    RICH_CHECK(dalloc(&m1, n));
+    k_mis_init<<<grid_for(n), kBlock, 0, c->st>>>(n, o.seed, S.rowptr, t);
+    RICH_LAUNCH_CHECK();
+    for (;;) {
+      RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
+      k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, t, m1);
+      RICH_LAUNCH_CHECK();
+      k_mis_update<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, m1, t, c->iflag);
+      RICH_LAUNCH_CHECK();
+      ++rounds;
+      RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      RICH_CUDA(cudaStreamSynchronize(c->st));
+      if (!c->hflag[0]) break;
+      if (rounds > 100000) return RICH_ELIMIT;  // a round always decides the largest undecided key
+    }
+    // aggregates
+    int* isroot = cnt;
+    int* p1root = nullptr;
+    uint64_t* rv = m1;
+    uint64_t* best = nullptr;
+    RICH_CHECK(dalloc(&aggid, (long long)n + 1));
+    RICH_CHECK(dalloc(&p1root, n));
+    RICH_CHECK(dalloc(&best, n));
+    RICH_CHECK(dalloc(&L.agg, n));
+    k_is_root<<<grid_for(n), kBlock, 0, c->st>>>(n, t, isroot);
+    RICH_LAUNCH_CHECK();
+    RICH_CHECK(scan_exclusive_int(c, isroot, aggid, n));
+    RICH_CHECK(read_dev_int(c, aggid + n, &nc));
+    k_rootval<<<grid_for(n), kBlock, 0, c->st>>>(n, t, rv);
+    RICH_LAUNCH_CHECK();
+    k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
+    RICH_LAUNCH_CHECK();
+    k_agg_pass1<<<grid_for(n), kBlock, 0, c->st>>>(n, t, best, aggid, L.agg, p1root);
+    RICH_LAUNCH_CHECK();
+    k_val2<<<grid_for(n), kBlock, 0, c->st>>>(n, t, p1root, rv);
+    RICH_LAUNCH_CHECK();
+    k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
+    RICH_LAUNCH_CHECK();
     RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
-    k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, t, m1);
+    k_agg_pass2<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, best, aggid, L.agg, c->iflag);
     RICH_LAUNCH_CHECK();
-    k_mis_update<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, m1, t, c->iflag);
-    RICH_LAUNCH_CHECK();
-    ++rounds;
     RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     RICH_CUDA(cudaStreamSynchronize(c->st));
-    if (!c->hflag[0]) break;
-    if (rounds > 100000) return RICH_ELIMIT;  // a round always decides the largest undecided key
+    unassigned = c->hflag[0] != 0;
+    dfree(t);
+    dfree(m1);
+    dfree(p1root);
+    dfree(best);
+    csr_free(S);
   }
-  // aggregates
-  int* isroot = cnt;
-  int* aggid = nullptr;
-  int* p1root = nullptr;
-  uint64_t* rv = m1;
-  uint64_t* best = nullptr;
-  RICH_CHECK(dalloc(&aggid, (long long)n + 1));
-  RICH_CHECK(dalloc(&p1root, n));
-  RICH_CHECK(dalloc(&best, n));
-  RICH_CHECK(dalloc(&L.agg, n));
-  k_is_root<<<grid_for(n), kBlock, 0, c->st>>>(n, t, isroot);
-  RICH_LAUNCH_CHECK();
-  RICH_CHECK(scan_exclusive_int(c, isroot, aggid, n));
-  int nc = 0;
-  RICH_CHECK(read_dev_int(c, aggid + n, &nc));
-  k_rootval<<<grid_for(n), kBlock, 0, c->st>>>(n, t, rv);
-  RICH_LAUNCH_CHECK();
-  k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
-  RICH_LAUNCH_CHECK();
-  k_agg_pass1<<<grid_for(n), kBlock, 0, c->st>>>(n, t, best, aggid, L.agg, p1root);
-  RICH_LAUNCH_CHECK();
-  k_val2<<<grid_for(n), kBlock, 0, c->st>>>(n, t, p1root, rv);
-  RICH_LAUNCH_CHECK();
-  k_max_closed<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, S.col, rv, best);
-  RICH_LAUNCH_CHECK();
-  RICH_CUDA(cudaMemsetAsync(c->iflag, 0, sizeof(int), c->st));
-  k_agg_pass2<<<grid_for(n), kBlock, 0, c->st>>>(n, S.rowptr, best, aggid, L.agg, c->iflag);
-  RICH_LAUNCH_CHECK();
-  RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  RICH_CUDA(cudaStreamSynchronize(c->st));
-  bool unassigned = c->hflag[0] != 0;
-  dfree(t);
-  dfree(m1);
-  dfree(p1root);
-  dfree(best);
-  csr_free(S);
   if (unassigned) {
     dfree(d);
     dfree(cnt);
@@ -1475,6 +1662,9 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
   Hierarchy& H = c->H;
   if (o) H.opts = *o; else rich_default_amg_opts(&H.opts);
   if (H.opts.max_levels < 1 || H.opts.max_levels > 16 || H.opts.nu1 < 0 || H.opts.nu2 < 0 || H.opts.coarse_max < 1)
+    return RICH_EINVAL;
+  if (H.opts.aggregation != RICH_AGG_MIS2 && H.opts.aggregation != RICH_AGG_MATCHING) return RICH_EINVAL;
+  if (H.opts.aggregation == RICH_AGG_MATCHING && (H.opts.max_agg_size < 2 || H.opts.max_agg_size > 1024))
     return RICH_EINVAL;
   RICH_CHECK(refresh_a0_values(c));
   Level L0;

@@ -342,6 +342,8 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->nu2 = 1;
   o->smooth_levels = 10;
   o->product_lists = 1;
+  o->aggregation = RICH_AGG_MIS2;
+  o->max_agg_size = 8;
 }
 
 void rich_default_newton_opts(rich_newton_opts* o) {

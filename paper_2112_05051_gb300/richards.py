@@ -16,6 +16,7 @@ RICH_OK = 0
 KRYLOV_FCG, KRYLOV_FGMRES = 0, 1
 AMG_REFRESH, AMG_SETUP_ONCE, AMG_REBUILD_STEP = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+AGG_MIS2, AGG_MATCHING = 0, 1
 
 ERRORS = {-1: "RICH_EINVAL", -2: "RICH_ENOMEM", -3: "RICH_ECUDA", -4: "RICH_ENOTCONV_LIN",
           -5: "RICH_ENOTCONV_NEWTON", -6: "RICH_ELINESEARCH", -7: "RICH_ENONFINITE", -8: "RICH_ESTATE",
@@ -63,7 +64,8 @@ def _bc_struct(bc, keep):
 class AmgOpts(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("coarse_max", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int)]
+                ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int), ("aggregation", ctypes.c_int),
+                ("max_agg_size", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -204,7 +206,8 @@ def default_newton_opts(**kw):
     for k, v in kw.items():
         if k in ("kind", "restart", "eta", "maxit"):
             setattr(o.krylov, k, v)
-        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists"):
+        elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
+                   "aggregation", "max_agg_size"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)

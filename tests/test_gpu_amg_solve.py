@@ -44,14 +44,16 @@ def _problem(dims, seed, kmean=0, het=True, dt=1.0, bc=None):
     return grid, p, ks, bc, dt, kmean
 
 
-def _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, seed=7, prec=0, lists=1):
+def _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, seed=7, prec=0, lists=1, aggregation=0, smooth_levels=10):
     rb = _rb()
     ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
     pd = torch.tensor(p, device="cuda")
     ctx.jacobian(pd, dt)
-    info = ctx.amg_setup(rb.default_amg_opts(seed=seed, coarse_max=coarse_max, product_lists=lists))
+    info = ctx.amg_setup(rb.default_amg_opts(seed=seed, coarse_max=coarse_max, product_lists=lists,
+                                             aggregation=aggregation, smooth_levels=smooth_levels))
     A = disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks)
-    h = amg.setup(A, 0.08, seed, coarse_max)
+    h = amg.setup(A, 0.08, seed, coarse_max, smooth_levels=smooth_levels,
+                  aggregation="matching" if aggregation else "mis2")
     return ctx, info, h
 
 
@@ -288,3 +290,47 @@ def test_step_mixed_precision_matches_fp64_oracle(workload, n, steps):
     # pressure is the FP64 oracle's to the Newton tolerance.
     pg, po, gs, os_ = _run_steps(workload, n, steps, prec=1)
     np.testing.assert_allclose(pg, po, rtol=1e-8)
+
+
+# ---------------------------------------------------------------- matching aggregation (SMATCH-style)
+
+@pytest.mark.parametrize("dims,coarse_max,kmean,het", [((24, 24, 24), 300, 1, False), ((20, 18, 16), 150, 0, True),
+                                                         ((33, 17, 9), 100, 2, True), ((40, 36, 32), 2000, 1, True)])
+def test_matching_hierarchy_bit_exact(dims, coarse_max, kmean, het):
+    grid, p, ks, bc, dt, _ = _problem(dims, 4, kmean, het=het)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, coarse_max, aggregation=1, smooth_levels=2)
+    assert info.levels == len(h.levels) >= 2
+    _compare_hierarchy(ctx, info, h)
+    r = np.random.default_rng(5).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= 1e-10
+    # the refresh reuses the matching aggregates
+    rb = _rb()
+    p2 = p + np.random.default_rng(6).uniform(0, 10, grid.n)
+    ctx.jacobian(torch.tensor(p2, device="cuda"), dt)
+    ctx.amg_update(rb.AMG_REFRESH)
+    amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, p2, dt, ks))
+    _compare_hierarchy(ctx, info, h)
+    ctx.close()
+
+
+def test_matching_newton_step_matches_oracle():
+    rb = _rb()
+    w = synth.WORKLOADS["richards16_fp64"]
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w)
+    ks = synth.ks_field(grid, 9, 1.0, (4.0, 4.0, 2.0))
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=1, smooth_levels=2, coarse_max=200,
+                                  aggregation=rb.AGG_MATCHING)
+    ctx = rb.Context(grid, soil, bc, 0, ks)
+    pd = torch.tensor(p0, device="cuda")
+    po = p0.copy()
+    prob = newton.Problem(grid, soil, bc, 0, ks)
+    oopt = newton.NewtonOptions(krylov="fcg", nu1=1, nu2=1, amg_seed=1, smooth_levels=2, coarse_max=200,
+                                aggregation="matching")
+    for m in range(2):
+        st = ctx.step(pd, dts[m], opts)
+        po, ost = newton.step(prob, po, dts[m], oopt)
+        assert st.converged and ost.converged
+    assert _nrel(pd.cpu().numpy(), po) <= 1e-8
+    ctx.close()
