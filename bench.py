@@ -84,6 +84,7 @@ def parse():
                          "atomics make results differ from run to run at rounding level)")
     ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
     ap.add_argument("--serving-coarse-max", type=int, default=500)
+    ap.add_argument("--serving-aggregation", type=int, default=0, help="0: MIS-2, 1: matching (SMATCH-style)")
     return ap.parse_args()
 
 
@@ -283,7 +284,8 @@ def serving_run(args, rb):
     # coarsest level below 500 unknowns: its dense inverse is redone at every
     # refresh, and a short one-step request refreshes ~10 times
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
-                                  product_lists=args.serving_lists, coarse_max=args.serving_coarse_max)
+                                  product_lists=args.serving_lists, coarse_max=args.serving_coarse_max,
+                                  aggregation=args.serving_aggregation)
 
     def submit(srv, q):
         grid, ks, kmean, n = q
@@ -340,6 +342,7 @@ def serving_run(args, rb):
     pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))] if v else None
     return {"requests": n_req, "slots": args.serving_slots, "sizes": sizes, "sigma": [1.0, 2.0],
             "coarse_max": args.serving_coarse_max, "product_lists": args.serving_lists,
+            "aggregation": "matching" if args.serving_aggregation else "MIS-2",
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
             "capacity_rps": mu, "burst_s": t_burst,
             "burst_dof_newton_per_s": work_b / t_burst, "rate_rps": lam, "arrivals": "Poisson, seed 5",
