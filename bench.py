@@ -41,9 +41,11 @@ FALLBACK_HBM_GBS = 6800.0
 # (the nominal 1.25 TFLOP/s); ncu shows the FP64 smoother and dot products issue-bound
 # on this pipe, so FP64 kernels are reported against it.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the roofline kernel
-# (profiles/ summary of the same kernel and workload); None until captured.
-NCU_TRAFFIC_BYTES = {}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the roofline kernel,
+# averaged over the launches it covers in one V-cycle (profiles/ summary of the
+# same kernel and workload): the coarse-level l1-Jacobi sweep of the 128^3 FP64
+# bench runs 3 sweeps on level 1 (79.9 MB each) and 3 on level 2 (10.65 MB each).
+NCU_TRAFFIC_BYTES = {("richards128_fp64", "l1jacobi"): 45.28e6}
 
 
 def nvtx_push(name):
