@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=None,
                     help="run the workload's settings on an n^3 grid instead (profiling captures); not a bench line")
     ap.add_argument("--roofline-kernel", default="l1jacobi")
+    ap.add_argument("--amg-precision", default=None, choices=["fp64", "fp32"],
+                    help="override the workload's AMG precision for the timed run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-AMG comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -381,6 +383,9 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     lib = rb.load()
     w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload, args.grid)
+    if args.amg_precision is not None:
+        import dataclasses
+        w = dataclasses.replace(w, mixed=args.amg_precision == "fp32")
     opts = newton_opts(rb, w)
     prec = rb.PREC_MIXED if w.mixed else rb.PREC_FP64
     stream = torch.cuda.current_stream()
