@@ -295,6 +295,13 @@ int rich_kernel_launches(long long* out);
  * "restrict", "prolong", "coarse_gemv", "multidot", "multiaxpy", "fcg_update",
  * "spgemm_numeric". */
 int rich_profile_kernel(const char* name);
+/* Time only every stride-th launch of the profiling target (1 = every launch,
+ * the default); the events around each timed launch cost a few microseconds of
+ * host and device time, so a stride keeps a long run's timing close to an
+ * unprofiled one.  A stride coprime with the period of the launch pattern
+ * (e.g. 7 for the V-cycle's six sweeps) samples every position of it.
+ * RICH_EINVAL for stride < 1. */
+int rich_profile_stride(int stride);
 /* Sum of the recorded launch durations (ms), number of recorded launches, the
  * algorithmic bytes those launches must move and (flops_total may be NULL) their
  * algorithmic floating-point operations (synchronises the events). */

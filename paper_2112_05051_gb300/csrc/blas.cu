@@ -71,12 +71,13 @@ static std::vector<const char*> g_prof_name;
 static std::vector<double> g_prof_b;
 static int g_prof_n = 0;          // recorded launch pairs
 static long long g_prof_seen = 0; // launches of the target (recorded or not)
+static long long g_prof_stride = 1;  // record every stride-th launch of the target
 static double g_prof_bytes = 0.0;
 static double g_prof_flops = 0.0;
 
 ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(false), st(s), bytes(b), flops(f) {
   if (g_prof_target.empty() || (g_prof_target != "*" && g_prof_target != name)) return;
-  ++g_prof_seen;
+  if (g_prof_seen++ % g_prof_stride != 0) return;  // only every stride-th launch is timed
   if (g_prof_n >= kProfEvents / 2) return;
   if (g_prof_ev.empty()) {
     g_prof_ev.resize(kProfEvents);
@@ -285,6 +286,12 @@ int rich_profile_kernel(const char* name) {
   rich::g_prof_seen = 0;
   rich::g_prof_bytes = 0.0;
   rich::g_prof_flops = 0.0;
+  return RICH_OK;
+}
+
+int rich_profile_stride(int stride) {
+  if (stride < 1) return RICH_EINVAL;
+  rich::g_prof_stride = stride;
   return RICH_OK;
 }
 

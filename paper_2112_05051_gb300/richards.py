@@ -136,6 +136,7 @@ EXPORTS = {
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "rich_profile_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
+    "rich_profile_stride": (ctypes.c_int, [ctypes.c_int]),
     "rich_jacobian": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P]),
     "rich_jacobian_apply": (ctypes.c_int, [_P, _P, _P]),
     "amg_setup": (ctypes.c_int, [_P, ctypes.POINTER(AmgOpts), ctypes.POINTER(AmgInfo)]),
