@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # bench runs 3 sweeps on level 1 (79.9 MB each) and 3 on level 2 (10.65 MB each).
 NCU_TRAFFIC_BYTES = {("richards128_fp64", "l1jacobi"): 45.28e6}
 # the roofline kernel's launches are timed with CUDA events one in PROFILE_STRIDE
-PROFILE_STRIDE = 7
+PROFILE_STRIDE = 29
 
 
 def nvtx_push(name):
@@ -404,7 +404,7 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    # every 7th launch of the roofline kernel is timed with events (7 is coprime
+    # every 29th launch of the roofline kernel is timed with events (29 is coprime
     # with the V-cycle's six sweeps per cycle, so every position is sampled)
     lib.rich_profile_stride(PROFILE_STRIDE)
     lib.rich_profile_kernel(args.roofline_kernel.encode())
