@@ -348,33 +348,6 @@ __global__ void k_fcg_update(long long n, double* __restrict__ x, double* __rest
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
 }
 
-// partials[q*nb + b] = sum over block b of V[q] . w  for q < nv: a single pass in
-// which each element's V values are consumed as they arrive (NVMAX >= nv).
-template <int NVMAX>
-__global__ void k_multidot_rb(long long n, int nv, const double* __restrict__ V, const double* __restrict__ w,
-                              double* __restrict__ partials) {
-  double acc[NVMAX];
-#pragma unroll
-  for (int q = 0; q < NVMAX; ++q) acc[q] = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double wi = w[i];
-#pragma unroll
-    for (int q = 0; q < NVMAX; ++q)
-      if (q < nv) acc[q] += V[(long long)q * n + i] * wi;
-  }
-#pragma unroll
-  for (int q0 = 0; q0 < NVMAX; q0 += 4) {
-    if (q0 >= nv) break;
-    double v[4] = {acc[q0], acc[q0 + 1], acc[q0 + 2], acc[q0 + 3]};
-    block_sum<4>(v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
-    }
-  }
-}
-
 // Batched dot products h[q] = V[q] . w: block (bx, q) reduces its share of one
 // vector; w is re-read per q from L2, V streams from HBM once.
 __global__ void k_bdot(long long n, const double* __restrict__ V, const double* __restrict__ w,
@@ -398,85 +371,6 @@ static void launch_multidot(int nb, cudaStream_t st, long long n, int nv, const 
                             double* partials, const int* run = nullptr) {
   (void)nb;
   k_bdot<<<dim3(kBdotBlocks, nv), kBlock, 0, st>>>(n, V, w, partials, run);
-}
-
-static void launch_multidot_regs(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* w,
-                                 double* partials) {
-  if (nv <= 8) k_multidot_rb<8><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
-  else if (nv <= 16) k_multidot_rb<16><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
-  else if (nv <= 32) k_multidot_rb<32><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
-  else k_multidot_rb<64><<<nb, kBlock, 0, st>>>(n, nv, V, w, partials);
-}
-
-// partials[q*nb + b] = sum over block b of V[q] . w  for q < nv
-__global__ void k_multidot(long long n, int nv, const double* __restrict__ V, const double* __restrict__ w,
-                           double* __restrict__ partials) {
-  for (int q0 = 0; q0 < nv; q0 += 4) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-      double wi = w[i];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (q0 + u < nv) v[u] += V[(long long)(q0 + u) * n + i] * wi;
-    }
-    block_sum<4>(v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
-    }
-    __syncthreads();
-  }
-}
-
-// w' = w - sum_q h1[q] V[q] (written back to w), with the partial sums of V^T w'
-// (nv of them) and of ||w'||^2 from the same single pass over V: each element's
-// V values stay in registers (NVMAX >= nv, a compile-time bound).
-template <int NVMAX>
-__global__ void k_orth_pass2(long long n, int nv, const double* __restrict__ V, const double* __restrict__ h1,
-                             double* __restrict__ w, double* __restrict__ partials) {
-  __shared__ double hs[NVMAX];
-  for (int q = threadIdx.x; q < NVMAX; q += blockDim.x) hs[q] = q < nv ? h1[q] : 0.0;
-  __syncthreads();
-  double acc[NVMAX];
-  double nrm = 0.0;
-#pragma unroll
-  for (int q = 0; q < NVMAX; ++q) acc[q] = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double vq[NVMAX];
-    double t = w[i];
-#pragma unroll
-    for (int q = 0; q < NVMAX; ++q) {
-      vq[q] = q < nv ? V[(long long)q * n + i] : 0.0;
-      t -= hs[q] * vq[q];
-    }
-    w[i] = t;
-    nrm += t * t;
-#pragma unroll
-    for (int q = 0; q < NVMAX; ++q) acc[q] += vq[q] * t;
-  }
-  double nr[1] = {nrm};
-  block_sum<1>(nr);
-  if (threadIdx.x == 0) partials[(long long)nv * gridDim.x + blockIdx.x] = nr[0];
-#pragma unroll
-  for (int q0 = 0; q0 < NVMAX; q0 += 4) {
-    if (q0 >= nv) break;
-    double v[4] = {acc[q0], acc[q0 + 1], acc[q0 + 2], acc[q0 + 3]};
-    block_sum<4>(v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (q0 + u < nv) partials[(long long)(q0 + u) * gridDim.x + blockIdx.x] = v[u];
-    }
-  }
-}
-
-static void launch_orth_pass2(int nb, cudaStream_t st, long long n, int nv, const double* V, const double* h1,
-                              double* w, double* partials) {
-  if (nv <= 8) k_orth_pass2<8><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
-  else if (nv <= 16) k_orth_pass2<16><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
-  else if (nv <= 32) k_orth_pass2<32><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
-  else k_orth_pass2<64><<<nb, kBlock, 0, st>>>(n, nv, V, h1, w, partials);
 }
 
 // w -= sum_q h[q] V[q], in place
