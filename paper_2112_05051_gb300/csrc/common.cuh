@@ -396,8 +396,11 @@ void dfree(T*& p) {
 
 // physics.cu
 int constit_eval(rich_ctx* c, const double* p);
-int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms);
-int jacobian_eval(rich_ctx* c, const double* p, double dt);
+// constit_current: the context's K, K', s, s' already hold the values of this p
+// (the last constitutive evaluation was at the same pressure), so they are reused.
+int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms,
+                  bool constit_current = false);
+int jacobian_eval(rich_ctx* c, const double* p, double dt, bool constit_current = false);
 int stencil_apply(rich_ctx* c, const double* A7, const double* x, double* y);
 int refresh_a0_values(rich_ctx* c);
 

@@ -242,8 +242,9 @@ int constit_eval(rich_ctx* c, const double* p) {
   return RICH_OK;
 }
 
-int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms) {
-  RICH_CHECK(constit_eval(c, p));
+int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms,
+                  bool constit_current) {
+  if (!constit_current) RICH_CHECK(constit_eval(c, p));
   int nb = red_grid(c->g.n);
   {
     ProfScope ps("residual", c->st, (double)c->g.n * (32.0 + (c->ks ? 8.0 : 0.0)));
@@ -259,8 +260,8 @@ int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, 
   return RICH_OK;
 }
 
-int jacobian_eval(rich_ctx* c, const double* p, double dt) {
-  RICH_CHECK(constit_eval(c, p));
+int jacobian_eval(rich_ctx* c, const double* p, double dt, bool constit_current) {
+  if (!constit_current) RICH_CHECK(constit_eval(c, p));
   {
     ProfScope ps("assemble", c->st, (double)c->g.n * (8.0 + (c->ks ? 8.0 : 0.0) + 14 * 8.0));
     k_assemble<<<grid_for(c->g.n), kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->dK, c->dS,

@@ -762,8 +762,10 @@ static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
   double h[3];
   {
     Phase ph(pt, &st->ms_feval);
-    RICH_CHECK(rich_saturation(c, p, c->s_old));
-    RICH_CHECK(residual_eval(c, p, c->s_old, dt, c->F, true));
+    // s_old = s(p^{l-1}) is the saturation the constitutive pass computes at p
+    RICH_CHECK(constit_eval(c, p));
+    RICH_CUDA(cudaMemcpyAsync(c->s_old, c->S, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    RICH_CHECK(residual_eval(c, p, c->s_old, dt, c->F, true, true));
   }
   RICH_CHECK(fetch_scalars(c, c->dsc, 3, h));
   double fn = sqrt(h[0]);
@@ -779,7 +781,8 @@ static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
     if (r == o->max_newton) return RICH_ENOTCONV_NEWTON;
     {
       Phase ph(pt, &st->ms_jacobian);
-      RICH_CHECK(jacobian_eval(c, p, dt));
+      // the last residual evaluation was at this p (the start or the accepted trial point)
+      RICH_CHECK(jacobian_eval(c, p, dt, true));
     }
     bool rebuild = !c->H.built || (o->amg_policy == RICH_AMG_REBUILD_STEP && r == 0);
     {
