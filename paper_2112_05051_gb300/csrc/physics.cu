@@ -82,6 +82,7 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
                            double* __restrict__ F, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
   double amax = 0.0;
+  const double rdt = so.rho_phi / dt;  // one division per thread, not per cell
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.n;
        c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % g.nx);
@@ -91,8 +92,8 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
     double pc = p[c], Kc = K[c];
     double ksc = ks ? ks[c] : so.ks;
     double sc = S[c], so_c = s_old[c];
-    double phi = so.rho_phi * (sc - so_c) / dt;
-    double mag = so.rho_phi * (fabs(sc) + fabs(so_c)) / dt;
+    double phi = (sc - so_c) * rdt;
+    double mag = (fabs(sc) + fabs(so_c)) * rdt;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       FaceNb nb;
@@ -130,6 +131,7 @@ __global__ void k_assemble(GridP g, SoilP so, BCP bc, int kmean, const double* _
                            const double* __restrict__ K, const double* __restrict__ dK,
                            const double* __restrict__ dS, const double* __restrict__ ks, double dt,
                            double* __restrict__ J7, double* __restrict__ A7) {
+  const double rdt = so.rho_phi / dt;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.n;
        c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % g.nx);
@@ -138,7 +140,7 @@ __global__ void k_assemble(GridP g, SoilP so, BCP bc, int kmean, const double* _
     int k = (int)(r / g.ny);
     double pc = p[c], Kc = K[c], dKc = dK[c];
     double ksc = ks ? ks[c] : so.ks;
-    double dj = so.rho_phi * dS[c] / dt;
+    double dj = dS[c] * rdt;
     double da = dj;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
