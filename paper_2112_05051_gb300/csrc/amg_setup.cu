@@ -836,43 +836,95 @@ __global__ void k_csr_to_dense(int n, const int* __restrict__ rp, const int* __r
   }
 }
 
-// Work buffer layout (4n + 2 doubles): two parity copies of [pivot row | pivot
-// column] (2n each), then the reciprocal of the pivot of each parity.
-__global__ void k_gj_prepare(int n, const double* __restrict__ a, double* __restrict__ buf) {
-  // parity 0: row 0, column 0 and 1 / a_00
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    buf[t] = a[t];
-    buf[n + t] = a[(long long)t * n];
+// Blocked Gauss-Jordan inversion in place (no pivoting: the matrix is SPD).
+// For a panel P of kGjB consecutive pivots and the other indices O, one block
+// step turns [[A_PP, A_PO], [A_OP, A_OO]] into
+//   [[A_PP^-1, A_PP^-1 A_PO], [-A_OP A_PP^-1, A_OO - A_OP A_PP^-1 A_PO]];
+// after every panel the matrix holds A^-1.  Three launches per panel:
+// k_gj_panel inverts A_PP in shared memory; k_gj_rows forms the new panel rows
+// and saves the old panel columns; k_gj_update applies the rank-kGjB update as
+// a shared-memory tiled product.  Work buffer (2 kGjB n + kGjB^2 doubles):
+// R[p][j] (new panel rows; for j in P the panel inverse), C[p][i] (old panel
+// columns), Pinv (kGjB x kGjB).
+constexpr int kGjB = 32;
+
+__global__ void __launch_bounds__(kGjB* kGjB) k_gj_panel(int n, int K, int bs, double* __restrict__ a,
+                                                        double* __restrict__ pinv) {
+  __shared__ double m[kGjB][kGjB + 1];
+  __shared__ double rowk[kGjB], colk[kGjB];  // pivot row, and pivot column scaled by 1/pivot
+  __shared__ double inv;
+  const int r = threadIdx.y, q = threadIdx.x;  // element (r, q) of the bs x bs panel block
+  const bool in = r < bs && q < bs;
+  if (in) m[r][q] = a[(long long)(K + r) * n + K + q];
+  __syncthreads();
+  for (int k = 0; k < bs; ++k) {
+    if (r == 0 && q == 0) inv = 1.0 / m[k][k];  // the step's one division
+    if (in && r == k) rowk[q] = m[k][q];
+    __syncthreads();
+    if (in && q == k) colk[r] = m[r][k] * inv;
+    __syncthreads();
+    if (in) {
+      double v;
+      if (r == k) v = (q == k) ? inv : rowk[q] * inv;
+      else if (q == k) v = -colk[r];
+      else v = fma(-colk[r], rowk[q], m[r][q]);
+      m[r][q] = v;
+    }
+    __syncthreads();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) buf[4 * n] = 1.0 / a[0];
+  if (in) a[(long long)(K + r) * n + K + q] = m[r][q];
+  pinv[r * kGjB + q] = in ? m[r][q] : 0.0;  // zeros outside a partial last panel
 }
 
-// One Gauss-Jordan pivot step (no pivoting: the matrix is SPD), one block row
-// per matrix row (blockIdx.y).  Row k, column k and 1/a_kk before the step come
-// from the parity-k buffers; the updated row/column k+1 and the reciprocal of
-// the next pivot go to the other parity for the next step, so every element
-// costs one FMA and no division.
-__global__ void k_gj_step(int n, int k, double* __restrict__ a, double* __restrict__ buf) {
-  const double* rowk = buf + (k & 1) * 2 * n;
-  const double* colk = rowk + n;
-  double* rown = buf + ((k + 1) & 1) * 2 * n;
-  double* coln = rown + n;
-  const double inv = buf[4 * n + (k & 1)];
-  const int i = blockIdx.y;
-  const double ci = colk[i] * inv;
-  double* ai = a + (long long)i * n;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double v;
-    if (i == k) v = (j == k) ? inv : rowk[j] * inv;
-    else if (j == k) v = -ci;
-    else v = fma(-ci, rowk[j], ai[j]);
-    ai[j] = v;
-    if (j == k + 1) coln[i] = v;
-    if (i == k + 1) {
-      rown[j] = v;
-      if (j == k + 1) buf[4 * n + ((k + 1) & 1)] = 1.0 / v;
-    }
+// Columns j0 .. j0+7 per block, thread (p, jj): R[p][j] = (Pinv A_P,j)_p written
+// back to panel row p (j outside P), or the panel inverse's entry (j in P); the
+// same thread saves row i = j's old panel entry C[p][i] = a_i,K+p (i outside P).
+constexpr int kGjCols = 8;
+
+__global__ void __launch_bounds__(kGjB* kGjCols) k_gj_rows(int n, int K, int bs, double* __restrict__ a,
+                                                          const double* __restrict__ pinv, double* __restrict__ R,
+                                                          double* __restrict__ C) {
+  __shared__ double ps[kGjB][kGjB + 1];
+  __shared__ double cs[kGjB][kGjCols];
+  const int p = threadIdx.x, jj = threadIdx.y;
+  for (int t = jj; t < kGjB; t += kGjCols) ps[t][p] = pinv[t * kGjB + p];
+  const int j = blockIdx.x * kGjCols + jj;
+  const bool inP = j >= K && j < K + bs;
+  cs[p][jj] = (j < n && p < bs && !inP) ? a[(long long)(K + p) * n + j] : 0.0;
+  __syncthreads();
+  if (j >= n || p >= bs) return;
+  if (inP) {
+    R[(long long)p * n + j] = ps[p][j - K];
+    return;
   }
+  double v = 0.0;
+#pragma unroll
+  for (int q = 0; q < kGjB; ++q) v = fma(ps[p][q], cs[q][jj], v);
+  R[(long long)p * n + j] = v;
+  a[(long long)(K + p) * n + j] = v;
+  C[(long long)p * n + j] = a[(long long)j * n + K + p];
+}
+
+// a_ij <- (j in P ? 0 : a_ij) - sum_p C[p][i] R[p][j] for rows i outside P; one
+// kGjB x kGjB tile of (i, j) per block.
+__global__ void __launch_bounds__(kGjB* kGjB) k_gj_update(int n, int K, int bs, double* __restrict__ a,
+                                                         const double* __restrict__ R, const double* __restrict__ C) {
+  __shared__ double cs[kGjB][kGjB + 1];  // cs[p][ti]
+  __shared__ double rs[kGjB][kGjB + 1];  // rs[p][tj]
+  const int ti = threadIdx.y, tj = threadIdx.x;
+  const int i0 = blockIdx.y * kGjB, j0 = blockIdx.x * kGjB;
+  for (int p = ti; p < kGjB; p += blockDim.y) {
+    const int i = i0 + tj, j = j0 + tj;
+    cs[p][tj] = (p < bs && i < n) ? C[(long long)p * n + i] : 0.0;
+    rs[p][tj] = (p < bs && j < n) ? R[(long long)p * n + j] : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + ti, j = j0 + tj;
+  if (i >= n || j >= n || (i >= K && i < K + bs)) return;
+  double acc = (j >= K && j < K + bs) ? 0.0 : a[(long long)i * n + j];
+#pragma unroll 8
+  for (int p = 0; p < kGjB; ++p) acc = fma(-cs[p][ti], rs[p][tj], acc);
+  a[(long long)i * n + j] = acc;
 }
 
 // ---------------------------------------------------------------- matching aggregation
@@ -1272,12 +1324,19 @@ static int coarse_inverse_launches(rich_ctx* c) {
   else
     k_csr_to_dense<double><<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, H.cdense);
   RICH_LAUNCH_CHECK();
-  k_gj_prepare<<<grid_for(n), kBlock, 0, c->st>>>(n, H.cdense, H.cwork);
-  RICH_LAUNCH_CHECK();
   long long nn = (long long)n * n;
-  dim3 g((unsigned)((n + kBlock - 1) / kBlock), (unsigned)n);
-  for (int k = 0; k < n; ++k) {
-    k_gj_step<<<g, kBlock, 0, c->st>>>(n, k, H.cdense, H.cwork);
+  double* R = H.cwork;
+  double* C = R + (long long)kGjB * n;
+  double* pinv = C + (long long)kGjB * n;
+  const dim3 tile(kGjB, kGjB);
+  const dim3 tiles((unsigned)((n + kGjB - 1) / kGjB), (unsigned)((n + kGjB - 1) / kGjB));
+  for (int K = 0; K < n; K += kGjB) {
+    const int bs = n - K < kGjB ? n - K : kGjB;
+    k_gj_panel<<<1, tile, 0, c->st>>>(n, K, bs, H.cdense, pinv);
+    RICH_LAUNCH_CHECK();
+    k_gj_rows<<<(n + kGjCols - 1) / kGjCols, dim3(kGjB, kGjCols), 0, c->st>>>(n, K, bs, H.cdense, pinv, R, C);
+    RICH_LAUNCH_CHECK();
+    k_gj_update<<<tiles, tile, 0, c->st>>>(n, K, bs, H.cdense, R, C);
     RICH_LAUNCH_CHECK();
   }
   if (H.cinv32) {
@@ -1689,7 +1748,7 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
   RICH_CHECK(fine_stencil(c));
   if (H.dense) {
     RICH_CHECK(dalloc(&H.cdense, (long long)H.cn * H.cn));
-    RICH_CHECK(dalloc(&H.cwork, 4LL * H.cn + 2));
+    RICH_CHECK(dalloc(&H.cwork, 2LL * kGjB * H.cn + kGjB * kGjB));
     if (c->prec == RICH_PREC_MIXED) RICH_CHECK(dalloc(&H.cinv32, (long long)H.cn * H.cn));
     RICH_CHECK(coarse_inverse(c));
     RICH_CHECK(capture_coarse_graph(c));

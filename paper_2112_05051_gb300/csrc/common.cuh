@@ -169,7 +169,7 @@ struct Hierarchy {
   int cn = 0;                     // coarsest size
   double* cdense = nullptr;       // coarsest matrix, dense, then its inverse (cn x cn)
   float* cinv32 = nullptr;
-  double* cwork = nullptr;        // Gauss-Jordan pivot row/column buffers and pivot reciprocals (4 cn + 2)
+  double* cwork = nullptr;        // blocked Gauss-Jordan work: panel rows, old panel columns, panel inverse
   rich_amg_opts opts{};
   bool built = false;
   bool dense = true;              // coarsest level by dense inverse (else kCoarseSweeps l1-Jacobi sweeps)
