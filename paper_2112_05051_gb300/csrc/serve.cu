@@ -173,6 +173,8 @@ static void srv_run(SrvRequest* q, SrvSession* se, cudaStream_t st) {
     c = se->ctx;
     c->st = st;
     p = se->p;
+  } else if (!r.p0_host) {
+    status = RICH_ESTATE;  // nothing to continue from (the session was evicted or never ran)
   } else {
     double* ks = nullptr;
     if (r.ks_field_host) {
@@ -191,7 +193,6 @@ static void srv_run(SrvRequest* q, SrvSession* se, cudaStream_t st) {
       se->p = p;
     }
   }
-  if (!status && !r.p0_host && !resident) status = RICH_ESTATE;  // nothing to continue from
   if (!status && r.p0_host &&
       cudaMemcpyAsync(p, r.p0_host, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
     status = RICH_ECUDA;
@@ -247,14 +248,22 @@ static void srv_worker(rich_server* s, int slot) {
       continue;
     }
     srv_run(q, se, st);
+    SrvSession* dead = nullptr;
     {
       std::lock_guard<std::mutex> lock(s->mu);
       if (!q->r.session) s->reserved -= q->est;
+      if (se && !se->ctx) {  // the session's first request failed before creating its state
+        s->sessions.erase(se->id);
+        s->reserved -= se->est;
+        dead = se;
+        se = nullptr;
+      }
       if (se) se->busy = false;
       --s->in_flight;
       q->res.t_done = srv_now(s);
       q->done = true;
     }
+    delete dead;
     s->cv_done.notify_all();
     s->cv_work.notify_all();
   }

@@ -156,3 +156,29 @@ def test_admission_keeps_reserved_memory_within_the_budget():
         assert e.value.status == -9
     finally:
         srv2.close()
+
+
+def test_sessions_beyond_the_limit_are_evicted_least_recently_used_first():
+    rb = _rb()
+    grid = synth.Grid(12, 12, 12)
+    ks = synth.ks_field(grid, 3, 1.0, (4.0, 4.0, 2.0))
+    p0 = np.full(grid.n, synth.P_INITIAL)
+    bc = synth.infiltration_bc()
+    srv = rb.Server(slots=1, max_sessions=1)
+
+    def run(session, first):
+        return srv.wait(srv.submit(grid, SOIL, bc, 0, 1.0, p0=p0 if first else None, ks=ks if first else None,
+                                   opts=_opts(rb), session=session))
+
+    assert run(1, True)["status"] == 0
+    assert run(1, False)["status"] == 0          # session 1 resident: continues
+    assert run(2, True)["status"] == 0           # a second session evicts session 1
+    assert run(1, False)["status"] == -8         # RICH_ESTATE: nothing left to continue from
+    r = run(2, False)                            # the failed request kept nothing: session 2 was evicted
+    assert r["status"] == -8
+    r1 = run(1, True)                            # starting again from p0 works
+    r2 = run(1, False)
+    srv.close()
+    assert r1["status"] == 0 and r2["status"] == 0
+    q = dict(grid=grid, ks=ks, kmean=0, prec=1, p0=p0, dt=1.0)
+    assert _rel(r2["p"], _alone(rb, q, steps=2)) <= 1e-12
