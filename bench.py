@@ -18,6 +18,16 @@ e2e     = the same metric through rich_step_host: each step copies p from pinned
 The AMG hierarchy (aggregates, P, R) is built in the first warm-up step and
 refreshed numerically on every Newton iteration afterwards.
 
+The line also carries: the roofline of the dominant kernel (the coarse-level
+l1-Jacobi sweep, one launch in PROFILE_STRIDE timed with CUDA events; FP64
+kernels against the FP64 ALU peak, DRAM traffic from an ncu capture), the same
+schedule with the FP32 AMG hierarchy (`fp32_amg`), per-step latency, the
+phase split, the oracle timed on the host (`cpu_baseline`) and a request
+stream through the request server (`serving`: 512 one-step requests of mixed
+size, soil and mean; capacity, p50/p99 latency, failures, mix-versus-alone
+check).  --amg-precision fp32 times the workload itself with the FP32
+hierarchy; --serving-only prints only the request stream.
+
 --impl reference times the CPU oracle (the plain FP64 numpy/scipy restatement)
 on the same workload: each step is one Newton iteration of the first time step
 (a bounded sample; the AMG setup happens in the first warm-up step).
