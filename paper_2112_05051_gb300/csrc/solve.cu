@@ -220,11 +220,9 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   const bool wA = L.A.nnz > 6LL * n;
   const double st_bytes = (double)n * 8.0 * es;  // diag, 3 face weights, dinv, b, x in; x out
   if (nu1 > 0) {
-    if (st0) {
-      k_st_smooth<T, 0><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, nullptr, x);
-    } else {
-      k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
-    }
+    // first sweep from x = 0: x = D_l1^-1 b, elementwise on every level (on the
+    // finest level the stencil copy's 1/l1 array)
+    k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, st0 ? fine<T>(c).dinv : v.dinv, b, x);
     RICH_LAUNCH_CHECK();
     for (int s = 1; s < nu1; ++s) {
       {
