@@ -402,6 +402,8 @@ def run_ours(args):
     prec = rb.PREC_MIXED if w.mixed else rb.PREC_FP64
     stream = torch.cuda.current_stream()
 
+    rb.memory_peak(reset=True)
+    torch.cuda.reset_peak_memory_stats()
     ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
     pd = torch.tensor(p0, device="cuda")
     sched = lambda m: dts[m % len(dts)]
@@ -459,6 +461,10 @@ def run_ours(args):
     lib.rich_profile_kernel(None)
     lib.rich_profile_stride(1)
     clocks = clk.stop()
+    # peak device memory of the main run: the library's pool and torch's tensors
+    lib_used, lib_reserved = rb.memory_peak()
+    peak_mem = {"library_pool_used_high_bytes": lib_used, "library_pool_reserved_high_bytes": lib_reserved,
+                "torch_max_allocated_bytes": int(torch.cuda.max_memory_allocated())}
     work = float(grid.n) * newton_its
     elapsed, work = aggregate_over_ranks(dist, elapsed, work, "cuda")
     value = work / elapsed
@@ -559,6 +565,7 @@ def run_ours(args):
                                          "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                                          "max": step_ms[-1]},
             "fp32_amg": mixed,
+            "peak_device_memory": peak_mem,
             "phase_ms": {k[3:]: round(v, 3) for k, v in phases.items()},
             "parallelism": "replicas" if ws > 1 else "single"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -310,6 +310,12 @@ int rich_profile_result(double* ms_total, long long* launches, double* bytes_tot
  * written into buf (at most cap bytes, NUL-terminated). */
 int rich_profile_table(char* buf, int cap);
 
+/* Peak device memory of the library on the current device: every allocation it
+ * makes comes from that device's stream-ordered pool, whose high-water marks of
+ * bytes in use and bytes reserved are returned (either pointer may be NULL).
+ * reset != 0 restarts both marks from the current usage. */
+int rich_memory_peak(long long* used_high, long long* reserved_high, int reset);
+
 /* Default option structs (as listed in the comments above). */
 void rich_default_newton_opts(rich_newton_opts* o);
 void rich_default_amg_opts(rich_amg_opts* o);

@@ -289,6 +289,24 @@ int rich_profile_kernel(const char* name) {
   return RICH_OK;
 }
 
+int rich_memory_peak(long long* used_high, long long* reserved_high, int reset) {
+  int dev = 0;
+  RICH_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  RICH_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t u = 0, r = 0;  // the attribute values are 64-bit
+  RICH_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &u));
+  RICH_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &r));
+  if (used_high) *used_high = (long long)u;
+  if (reserved_high) *reserved_high = (long long)r;
+  if (reset) {
+    uint64_t zero = 0;
+    RICH_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    RICH_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &zero));
+  }
+  return RICH_OK;
+}
+
 int rich_profile_stride(int stride) {
   if (stride < 1) return RICH_EINVAL;
   rich::g_prof_stride = stride;

@@ -112,8 +112,8 @@ __global__ void k_f2d(long long n, const float* __restrict__ a, double* __restri
 
 // Finest-level l1-Jacobi sweep and residual on the stencil form.  The l1 row norm
 // is diag + sum of the six face weights (all couplings are -w with w >= 0).
-// mode 0: xo = D_l1^-1 b (first sweep from x = 0); 1: xo = x + D_l1^-1 (b - A x);
-// 2: xo = b - A x (residual).
+// mode 1: xo = x + D_l1^-1 (b - A x); 2: xo = b - A x (residual).  The first
+// sweep from x = 0 (x = D_l1^-1 b) is the elementwise k_jacobi0.
 template <class T, int MODE>
 __global__ void __launch_bounds__(kLineThreads) k_st_smooth(GridP g, Stencil4<T> A, const T* __restrict__ b,
                                                             const T* __restrict__ x, T* __restrict__ xo) {
@@ -125,10 +125,6 @@ __global__ void __launch_bounds__(kLineThreads) k_st_smooth(GridP g, Stencil4<T>
   int nx = g.nx;
   int sxy = g.nx * g.ny;
   int c = r * nx + i;
-  if (MODE == 0) {
-    xo[c] = A.dinv[c] * b[c];
-    return;
-  }
   T wxp = A.wx[c], wyp = A.wy[c], wzp = A.wz[c];
   T xc = x[c];
   T ax = A.diag[c] * xc;

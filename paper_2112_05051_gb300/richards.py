@@ -137,6 +137,8 @@ EXPORTS = {
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "rich_profile_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "rich_profile_stride": (ctypes.c_int, [ctypes.c_int]),
+    "rich_memory_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.c_int]),
     "rich_jacobian": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P]),
     "rich_jacobian_apply": (ctypes.c_int, [_P, _P, _P]),
     "amg_setup": (ctypes.c_int, [_P, ctypes.POINTER(AmgOpts), ctypes.POINTER(AmgInfo)]),
@@ -461,3 +463,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def memory_peak(reset=False):
+    """(bytes in use, bytes reserved) high-water marks of the library's device memory pool."""
+    u = ctypes.c_longlong()
+    r = ctypes.c_longlong()
+    check(load().rich_memory_peak(ctypes.byref(u), ctypes.byref(r), 1 if reset else 0), "rich_memory_peak")
+    return u.value, r.value
