@@ -300,3 +300,56 @@ def test_aux_is_spd_and_equals_jacobian_without_conductivity_slope():
         J = disc.jacobian(grid, flat, synth.infiltration_bc(), kmean, p, 0.5).toarray()
         A = disc.aux_matrix(grid, flat, synth.infiltration_bc(), kmean, p, 0.5).toarray()
         assert np.abs(J - A).max() <= 1e-14 * np.abs(A).max()
+
+
+def test_face_means_obey_the_mean_inequality_and_the_upstream_rule():
+    # harmonic <= geometric <= arithmetic, all between min and max, all equal to K
+    # when both sides agree (the textbook inequality of the three Pythagorean means)
+    rng = np.random.default_rng(17)
+    kl = 10.0 ** rng.uniform(-8, 0, 2000)
+    ku = 10.0 ** rng.uniform(-8, 0, 2000)
+    pl = rng.uniform(-70, -10, 2000)
+    pu = rng.uniform(-70, -10, 2000)
+    a = disc.face_mean(disc.KMEAN_ARITH, kl, ku, pl, pu)
+    g = disc.face_mean(disc.KMEAN_GEOMETRIC, kl, ku, pl, pu)
+    h = disc.face_mean(disc.KMEAN_HARMONIC, kl, ku, pl, pu)
+    lo, hi = np.minimum(kl, ku), np.maximum(kl, ku)
+    tol = 1e-14 * hi
+    assert np.all(h <= g + tol) and np.all(g <= a + tol)
+    assert np.all(lo - tol <= h) and np.all(a <= hi + tol)
+    for m in (disc.KMEAN_ARITH, disc.KMEAN_UPSTREAM, disc.KMEAN_HARMONIC, disc.KMEAN_GEOMETRIC):
+        np.testing.assert_allclose(disc.face_mean(m, kl, kl, pl, pu), kl, rtol=1e-15)
+    # upstream: the conductivity of the cell with the higher head, the upper cell on a tie
+    u = disc.face_mean(disc.KMEAN_UPSTREAM, kl, ku, pl, pu)
+    assert np.array_equal(u, np.where(pu >= pl, ku, kl))
+    assert np.array_equal(disc.face_mean(disc.KMEAN_UPSTREAM, kl, ku, pl, pl), ku)
+
+
+@pytest.mark.parametrize("kmean", [0, 1, 2, 3])
+def test_face_mean_partials_match_central_differences(kmean):
+    rng = np.random.default_rng(3 + kmean)
+    kl = 10.0 ** rng.uniform(-6, -1, 200)
+    ku = 10.0 ** rng.uniform(-6, -1, 200)
+    pl = rng.uniform(-70, -10, 200)
+    pu = pl + rng.choice([-1.0, 1.0], 200) * rng.uniform(1, 5, 200)  # away from upstream ties
+    dl, du = disc.face_mean_partials(kmean, kl, ku, pl, pu)
+    for k_var, d in ((0, dl), (1, du)):
+        e = 1e-4 * (kl if k_var == 0 else ku)  # central differences: O(e^2) truncation
+        if k_var == 0:
+            fd = (disc.face_mean(kmean, kl + e, ku, pl, pu) - disc.face_mean(kmean, kl - e, ku, pl, pu)) / (2 * e)
+        else:
+            fd = (disc.face_mean(kmean, kl, ku + e, pl, pu) - disc.face_mean(kmean, kl, ku - e, pl, pu)) / (2 * e)
+        np.testing.assert_allclose(d, fd, rtol=1e-5, atol=1e-9)
+
+
+def test_all_means_give_the_same_residual_where_neighbour_conductivities_agree():
+    # a uniform head on a homogeneous soil makes K equal on both sides of every
+    # interior face (Dirichlet ghosts at the same head too): the four means coincide
+    grid = synth.Grid(6, 5, 7)
+    bc = synth.all_dirichlet_bc(-35.0)
+    p = np.full(grid.n, -35.0)
+    s_old = cst.saturation(p + 3.0, SOIL)
+    ref = disc.residual(grid, SOIL, bc, disc.KMEAN_ARITH, p, s_old, 0.7)
+    for m in (disc.KMEAN_UPSTREAM, disc.KMEAN_HARMONIC, disc.KMEAN_GEOMETRIC):
+        np.testing.assert_allclose(disc.residual(grid, SOIL, bc, m, p, s_old, 0.7), ref, rtol=1e-13,
+                                   atol=1e-13 * np.abs(ref).max())
