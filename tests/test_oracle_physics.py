@@ -353,3 +353,33 @@ def test_all_means_give_the_same_residual_where_neighbour_conductivities_agree()
     for m in (disc.KMEAN_UPSTREAM, disc.KMEAN_HARMONIC, disc.KMEAN_GEOMETRIC):
         np.testing.assert_allclose(disc.residual(grid, SOIL, bc, m, p, s_old, 0.7), ref, rtol=1e-13,
                                    atol=1e-13 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- the pins catch planted mistakes
+# Each test plants one plausible mistake in the oracle (on the CPU, for the
+# duration of the test) and checks that the pin above it fails.
+
+def test_pins_catch_a_geometric_mean_without_its_root(monkeypatch):
+    orig = disc.face_mean
+    monkeypatch.setattr(disc, "face_mean", lambda m, kl, ku, pl, pu: kl * ku if m == disc.KMEAN_GEOMETRIC
+                        else orig(m, kl, ku, pl, pu))
+    with pytest.raises(AssertionError):
+        test_face_means_obey_the_mean_inequality_and_the_upstream_rule()
+
+
+def test_pins_catch_a_harmonic_mean_without_its_factor_two(monkeypatch):
+    orig = disc.face_mean
+    monkeypatch.setattr(disc, "face_mean", lambda m, kl, ku, pl, pu: kl * ku / (kl + ku) if m == disc.KMEAN_HARMONIC
+                        else orig(m, kl, ku, pl, pu))
+    with pytest.raises(AssertionError):
+        test_face_means_obey_the_mean_inequality_and_the_upstream_rule()
+
+
+def test_pins_catch_a_saturation_derivative_with_the_wrong_exponent(monkeypatch):
+    def bad(p, soil):
+        ap = np.abs(p)
+        pb = ap ** soil.beta
+        return soil.alpha * soil.beta * pb * (soil.theta_s - soil.theta_r) / (soil.alpha + pb) ** 2  # |p|^beta
+    monkeypatch.setattr(cst, "dsaturation", bad)
+    with pytest.raises(AssertionError):
+        test_derivatives_match_central_differences(-61.5)

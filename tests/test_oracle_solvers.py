@@ -384,3 +384,27 @@ def test_matching_hierarchy_gives_a_convergent_vcycle():
     b = np.random.default_rng(2).standard_normal(grid.n)
     x, its, ok, _ = krylov.fgmres(lambda v: A @ v, lambda v: amg.vcycle(h, v), b, 1e-10, 100, 30)
     assert ok and its < 40
+
+
+# ---------------------------------------------------------------- the pins catch planted mistakes
+
+def test_pins_catch_an_mis2_that_takes_the_smallest_key(monkeypatch):
+    monkeypatch.setattr(amg, "_max_closed", lambda Sc, v: np.minimum.reduceat(v[Sc.indices], Sc.indptr[:-1]))
+    with pytest.raises(AssertionError):
+        test_mis2_equals_sequential_greedy("rand40", 1)
+
+
+def test_pins_catch_an_unsymmetrised_compatible_weight(monkeypatch):
+    def bad(A):
+        A = sp.csr_matrix(A)
+        n = A.shape[0]
+        rows = np.repeat(np.arange(n), np.diff(A.indptr))
+        cols = A.indices
+        d = A.diagonal()
+        edge = (cols != rows) & (A.data < 0)
+        w = np.full(len(cols), -np.inf, dtype=np.float32)
+        w[edge] = (1.0 - A.data[edge] / (d[rows[edge]] + d[cols[edge]])).astype(np.float32)  # a_ij only
+        return rows, cols, w
+    monkeypatch.setattr(amg, "matching_weights", bad)
+    with pytest.raises(AssertionError):
+        test_compatible_weight_of_a_two_node_laplacian()
