@@ -383,3 +383,14 @@ def test_pins_catch_a_saturation_derivative_with_the_wrong_exponent(monkeypatch)
     monkeypatch.setattr(cst, "dsaturation", bad)
     with pytest.raises(AssertionError):
         test_derivatives_match_central_differences(-61.5)
+
+
+def test_pins_catch_swapped_harmonic_mean_partials(monkeypatch):
+    orig = disc.face_mean_partials
+
+    def bad(m, kl, ku, pl, pu):
+        dl, du = orig(m, kl, ku, pl, pu)
+        return (du, dl) if m == disc.KMEAN_HARMONIC else (dl, du)
+    monkeypatch.setattr(disc, "face_mean_partials", bad)
+    with pytest.raises(AssertionError):
+        test_jacobian_matches_finite_differences(disc.KMEAN_HARMONIC, list(BCS)[0], (4, 4, 4))

@@ -408,3 +408,27 @@ def test_pins_catch_an_unsymmetrised_compatible_weight(monkeypatch):
     monkeypatch.setattr(amg, "matching_weights", bad)
     with pytest.raises(AssertionError):
         test_compatible_weight_of_a_two_node_laplacian()
+
+
+def test_pins_catch_a_wrong_smoothing_weight(monkeypatch):
+    orig = amg.smoothed_prolongator
+
+    def bad(A, Pt):  # omega = 2 / (3 rho) instead of 4 / (3 rho)
+        A = sp.csr_matrix(A)
+        n = A.shape[0]
+        d = A.diagonal()
+        rows = np.repeat(np.arange(n), np.diff(A.indptr))
+        rho = np.max(np.bincount(rows, weights=np.abs(A.data), minlength=n) / np.abs(d))
+        omega = 2.0 / (3.0 * rho)
+        vals = -omega * A.data / d[rows] + (A.indices == rows)
+        return amg.spgemm(sp.csr_matrix((vals, A.indices.copy(), A.indptr.copy()), shape=A.shape), Pt), omega
+    monkeypatch.setattr(amg, "smoothed_prolongator", bad)
+    with pytest.raises(AssertionError):
+        test_prolongator_and_galerkin_product_against_dense_algebra()
+
+
+def test_pins_catch_a_vcycle_without_post_smoothing(monkeypatch):
+    orig = amg.vcycle
+    monkeypatch.setattr(amg, "vcycle", lambda h, b, nu1=1, nu2=1, level=0: orig(h, b, nu1, 0, level))
+    with pytest.raises(AssertionError):
+        test_hierarchy_coarsens_and_vcycle_is_symmetric_positive_contraction()
