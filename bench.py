@@ -267,6 +267,29 @@ def run_reference(args):
     return 0
 
 
+def percentile(sorted_values, q):
+    """The q-quantile of an ascending list by the nearest-rank rule (None if empty)."""
+    if not sorted_values:
+        return None
+    return sorted_values[min(len(sorted_values) - 1, int(q * len(sorted_values)))]
+
+
+def stream_stats(results, dofs, seconds, error_names):
+    """Latency percentiles (ms, submit -> done), converged work per second and failures by status name."""
+    lat = sorted(1e3 * (r["t_done"] - r["t_submit"]) for r in results)
+    lat_ok = sorted(1e3 * (r["t_done"] - r["t_submit"]) for r in results if r["status"] == 0)
+    work = sum(n * r["stats"]["newton_its"] for n, r in zip(dofs, results) if r["status"] == 0)
+    failed = {}
+    for r in results:
+        if r["status"] != 0:
+            key = error_names.get(r["status"], str(r["status"]))
+            failed[key] = failed.get(key, 0) + 1
+    return {"latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
+                           "mean": sum(lat) / len(lat) if lat else None, "max": lat[-1] if lat else None},
+            "latency_ms_converged": {"p50": percentile(lat_ok, 0.5), "p99": percentile(lat_ok, 0.99)},
+            "dof_newton_per_s": work / seconds if seconds > 0 else None, "failed": failed}
+
+
 def serving_run(args, rb):
     """Request stream: one-step solves of mixed size and soil through the request server.
 
@@ -333,15 +356,8 @@ def serving_run(args, rb):
     t_stream = time.perf_counter() - t1
     cnt = srv.counters()
     srv.close()
-    lat = sorted(1e3 * (r["t_done"] - r["t_submit"]) for r in stream)
-    lat_ok = sorted(1e3 * (r["t_done"] - r["t_submit"]) for r in stream if r["status"] == 0)
-    work_b = sum(q[0].n * r["stats"]["newton_its"] for q, r in zip(reqs, burst) if r["status"] == 0)
-    work_s = sum(q[0].n * r["stats"]["newton_its"] for q, r in zip(reqs, stream) if r["status"] == 0)
-    fails = {}
-    for r in stream:
-        if r["status"] != 0:
-            key = rb.ERRORS.get(r["status"], str(r["status"]))
-            fails[key] = fails.get(key, 0) + 1
+    st_b = stream_stats(burst, [q[0].n for q in reqs], t_burst, rb.ERRORS)
+    st_s = stream_stats(stream, [q[0].n for q in reqs], t_stream, rb.ERRORS)
     # the same requests alone (one slot, nothing else in flight) against their results in the mix
     alone = rb.Server(slots=1)
     dev = 0.0
@@ -355,18 +371,15 @@ def serving_run(args, rb):
             dev = max(dev, float(np.abs(r["p"] - stream[k]["p"]).max() / np.abs(stream[k]["p"]).max()))
             checked += 1
     alone.close()
-    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))] if v else None
     return {"requests": n_req, "slots": args.serving_slots, "sizes": sizes, "sigma": [1.0, 2.0],
             "coarse_max": args.serving_coarse_max, "product_lists": args.serving_lists,
             "aggregation": "matching" if args.serving_aggregation else "MIS-2",
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
             "capacity_rps": mu, "burst_s": t_burst,
-            "burst_dof_newton_per_s": work_b / t_burst, "rate_rps": lam, "arrivals": "Poisson, seed 5",
-            "stream_s": t_stream, "stream_dof_newton_per_s": work_s / t_stream,
-            "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "mean": sum(lat) / len(lat),
-                           "max": lat[-1]},
-            "latency_ms_converged": {"p50": pct(lat_ok, 0.5), "p99": pct(lat_ok, 0.99)},
-            "failed": fails, "max_in_flight": cnt["max_in_flight"],
+            "burst_dof_newton_per_s": st_b["dof_newton_per_s"], "rate_rps": lam, "arrivals": "Poisson, seed 5",
+            "stream_s": t_stream, "stream_dof_newton_per_s": st_s["dof_newton_per_s"],
+            "latency_ms": st_s["latency_ms"], "latency_ms_converged": st_s["latency_ms_converged"],
+            "failed": st_s["failed"], "max_in_flight": cnt["max_in_flight"],
             "mix_vs_alone_max_rel_dev": dev, "mix_vs_alone_checked": checked,
             "admission": "FIFO, a free slot and the request's device-memory estimate within 80% of free HBM"}
 
@@ -571,7 +584,10 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
     if not args.no_serving and ws == 1:
-        line["serving"] = serving_run(args, rb)
+        try:
+            line["serving"] = serving_run(args, rb)
+        except Exception as e:  # the main measurement stands on its own
+            line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
     ctx.close()
     if rank == 0:
         print(json.dumps(line))

@@ -53,3 +53,58 @@ def test_single_rank_passthrough():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate_over_ranks(None, 3.0, 7.0, "cpu") == (3.0, 7.0)
+
+
+def test_request_stream_statistics():
+    import bench
+    assert bench.percentile([], 0.5) is None
+    v = list(range(1, 101))  # 1 .. 100
+    assert bench.percentile(v, 0.5) == 51 and bench.percentile(v, 0.99) == 100 and bench.percentile(v, 0.0) == 1
+    res = [{"t_submit": 0.0, "t_done": 0.010 * (k + 1), "status": 0 if k % 4 else -4,
+            "stats": {"newton_its": 3}} for k in range(8)]
+    st = bench.stream_stats(res, [1000] * 8, 2.0, {-4: "RICH_ENOTCONV_LIN"})
+    assert st["failed"] == {"RICH_ENOTCONV_LIN": 2}
+    assert st["dof_newton_per_s"] == 6 * 1000 * 3 / 2.0          # converged work only
+    assert abs(st["latency_ms"]["max"] - 80.0) < 1e-9 and abs(st["latency_ms"]["mean"] - 45.0) < 1e-9
+    assert abs(st["latency_ms_converged"]["p50"] - 60.0) < 1e-9  # 20,30,40,60,70,80 -> nearest rank 4
+
+
+def test_serving_run_end_to_end_against_a_fake_server(monkeypatch):
+    # the request-stream driver with a stand-in for the request server (no GPU):
+    # every request "converges" in 2 Newton iterations, 5 ms after submission
+    import types
+    import numpy as np
+    import bench
+    from paper_2112_05051_gb300 import synth
+
+    class FakeServer:
+        def __init__(self, slots=8, **kw):
+            self.t = 0.0
+            self.out = {}
+
+        def submit(self, grid, soil, bc, kmean, dt, p0=None, ks=None, precision=1, opts=None, session=0):
+            rid = len(self.out) + 1
+            self.t += 0.001
+            self.out[rid] = {"status": 0 if kmean != 2 else -4, "stats": {"newton_its": 2}, "t_submit": self.t,
+                             "t_done": self.t + 0.005, "p": np.full(grid.n, -61.5)}
+            return rid
+
+        def wait(self, rid):
+            return self.out.pop(rid)
+
+        def counters(self):
+            return {"admitted": 0, "max_in_flight": 3, "reserved_bytes": 0.0}
+
+        def close(self):
+            pass
+
+    fake = types.SimpleNamespace(Server=FakeServer, PREC_MIXED=1, KRYLOV_FCG=0, ERRORS={-4: "RICH_ENOTCONV_LIN"},
+                                 default_newton_opts=lambda **kw: None)
+    monkeypatch.setattr(synth, "ks_field", lambda grid, seed, sigma, *a, **k: np.ones(grid.n))
+    args = types.SimpleNamespace(serving_requests=12, serving_slots=3, serving_lists=1, serving_coarse_max=500,
+                                 serving_aggregation=0)
+    out = bench.serving_run(args, fake)
+    assert out["requests"] == 12 and out["max_in_flight"] == 3
+    assert out["capacity_rps"] > 0 and out["latency_ms"]["p50"] == pytest.approx(5.0, abs=1e-6)
+    assert set(out["failed"]) <= {"RICH_ENOTCONV_LIN"}
+    assert out["mix_vs_alone_max_rel_dev"] == 0.0
