@@ -26,10 +26,18 @@ design notes):
                non-root with a strong root neighbour joins the one with the
                largest key; pass 2: a remaining node joins the aggregate of
                the pass-1 neighbour whose root has the largest key.
-               Isolated nodes (no strong neighbour) start OUT and join no
-               aggregate: their P_tent row is empty and the smoother alone
-               resolves them (strongly diagonally dominant rows, e.g. very
-               low-conductivity cells of a heterogeneous field).
+               Isolated nodes (no strong neighbour) start OUT of MIS-2.
+               pass 3: an isolated node whose row is not diagonally dominant
+               (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
+               aggregated matrix neighbour j with the largest
+               (fp32(|a_ij|), key(j)); the others (dominant rows, e.g. cells
+               under a Dirichlet face) join no aggregate, their P_tent row is
+               empty and the smoother alone resolves them.  On high-contrast
+               fields a low-conductivity cell between cells that carry much
+               larger couplings elsewhere has only weak couplings by the
+               symmetric measure, yet its row sums to about zero (its error is
+               the average of its neighbours'); left out of the coarse space,
+               it costs the V-cycle most of its contraction.
   prolongator  P = (I - omega D^-1 A) P_tent, P_tent[i, agg(i)] = 1,
                omega = 4 / (3 rho), rho = max_i sum_j |a_ij| / |a_ii|;
                structural pattern, no dropping.  Only the first
@@ -121,8 +129,12 @@ def mis2(S, keys):
     return state, rounds
 
 
-def aggregate(S, state, keys):
-    """Aggregate index per node (int64, -1 for isolated nodes) and number of aggregates."""
+def aggregate(S, state, keys, A=None):
+    """Aggregate index per node (int64, -1 for nodes left out) and number of aggregates.
+
+    With the matrix A given, pass 3 places the isolated nodes whose row is not
+    diagonally dominant (module docstring); without it every isolated node is
+    left out."""
     Sc = _closed(S)
     n = S.shape[0]
     isolated = np.diff(S.indptr) == 0
@@ -145,7 +157,39 @@ def aggregate(S, state, keys):
     agg[take] = agg_id[((best2[take] - np.uint64(1)) & _LOW32).astype(np.int64)]
     if np.any((agg < 0) & ~isolated):
         raise RuntimeError("aggregation left nodes unassigned")
+    if A is not None:
+        agg = join_isolated(A, agg, keys)
     return agg, int(roots.sum())
+
+
+def join_isolated(A, agg, keys):
+    """Pass 3: every node left out (agg = -1) whose row is not diagonally dominant,
+    a_ii < 2 sum_{j != i} |a_ij|, joins the aggregate of the neighbour j with
+    agg(j) >= 0 that has the largest (fp32(|a_ij|), key(j)); one synchronous pass
+    over the aggregates of passes 1-2.  Rounding |a_ij| to FP32 keeps couplings that
+    are equal in exact arithmetic equal whatever the order their FP64 values were
+    summed in, so the key decides between them."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    out = agg.copy()
+    d = A.diagonal()
+    for i in np.flatnonzero(agg < 0):
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        cols = A.indices[lo:hi]
+        vals = A.data[lo:hi]
+        off = cols != i
+        if not np.any(off) or not abs(d[i]) < 2.0 * np.sum(np.abs(vals[off])):
+            continue
+        best = None
+        for j, v in zip(cols[off], vals[off]):
+            if agg[j] < 0:
+                continue
+            cand = (np.float32(abs(v)), int(keys[j]))
+            if best is None or cand > best[0]:
+                best = (cand, j)
+        if best is not None:
+            out[i] = agg[best[1]]
+    return out
 
 
 def spgemm(A, B):
@@ -344,11 +388,12 @@ class Hierarchy:
 
 
 def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, smooth_levels=10,
-          aggregation="mis2", max_agg_size=8):
+          aggregation="mis2", max_agg_size=8, isolated_join=True):
     """Build the hierarchy from a symmetric positive definite CSR matrix.
 
     aggregation: "mis2" (strength graph + MIS-2 roots) or "matching"
     (compatible weighted matching, aggregates of at most max_agg_size).
+    isolated_join: pass 3 of the MIS-2 aggregation (module docstring).
     """
     levels = [Level(A)]
     while True:
@@ -363,7 +408,7 @@ def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, 
             S = strength(lv.A, theta * 0.5 ** (len(levels) - 1))
             keys = priority_keys(n, seed)
             state, rounds = mis2(S, keys)
-            agg, nc = aggregate(S, state, keys)
+            agg, nc = aggregate(S, state, keys, lv.A if isolated_join else None)
         if nc > max_ratio * n:
             break
         Pt = tentative_prolongator(agg, nc)

@@ -22,7 +22,11 @@ then retries the solve with FGMRES(30).
 import numpy as np
 
 
-def fcg(matvec, prec, b, eta, maxit):
+def fcg(matvec, prec, b, eta, maxit, info=None):
+    """Returns (x, iterations, converged, residual history); info, if a dict, receives
+    the reason of a failure: "maxit", "curvature" ((p, q) <= 0) or "growth"."""
+    if info is None:
+        info = {}
     b = np.asarray(b, dtype=np.float64)
     bnorm = np.linalg.norm(b)
     x = np.zeros_like(b)
@@ -43,6 +47,7 @@ def fcg(matvec, prec, b, eta, maxit):
         q = matvec(p)
         pq = np.dot(p, q)
         if not pq > 0.0:
+            info["reason"] = "curvature"
             return x, k, False, hist
         alpha = np.dot(p, r) / pq
         x = x + alpha * p
@@ -52,9 +57,11 @@ def fcg(matvec, prec, b, eta, maxit):
         if rn <= target:
             return x, k, True, hist
         if rn > 10.0 * best:
+            info["reason"] = "growth"
             return x, k, False, hist
         best = min(best, rn)
         p_prev, q_prev, pq_prev = p, q, pq
+    info["reason"] = "maxit"
     return x, maxit, False, hist
 
 

@@ -29,8 +29,11 @@ no constants; the readings used here (shared with the CUDA path) are:
     failure.
 """
 import dataclasses
+import math
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import amg
 from . import constitutive as cst
@@ -62,6 +65,8 @@ class NewtonOptions:
     max_agg_size: int = 8
     armijo_c: float = 1e-4
     lambda_min: float = 1e-10
+    isolated_join: bool = True    # pass 3 of the MIS-2 aggregation (amg module docstring)
+    max_dt_halvings: int = 0      # time-step control (advance); 0 = off
 
 
 @dataclasses.dataclass
@@ -76,6 +81,10 @@ class StepStats:
     lambdas: list = dataclasses.field(default_factory=list)
     lin_its: list = dataclasses.field(default_factory=list)
     res_hist: list = dataclasses.field(default_factory=list)
+    line_searches: list = dataclasses.field(default_factory=list)  # (f0, slope, [(lam, f(lam)), ...]) per iteration
+    substeps: int = 1             # backward-Euler steps taken to cover dt (advance)
+    dt_min: float = 0.0           # smallest of them
+    dt_failures: int = 0          # attempts that failed and were retried with half the step
 
 
 class Problem:
@@ -94,14 +103,53 @@ class Problem:
         return disc.aux_matrix(self.grid, self.soil, self.bc, self.kmean, p, dt, self.ks)
 
 
+class LineSearchError(RuntimeError):
+    pass
+
+
+class LinearSolveError(RuntimeError):
+    pass
+
+
+def armijo_backtrack(merit, f0, slope, c, lambda_min):
+    """Armijo backtracking along a descent direction (Sec. 3, the line search of KINSOL's
+    inexact Newton method; constants in the module docstring).
+
+    merit(lam) returns (f(lam), extra) with f(lam) = 1/2 ||Phi(p + lam d)||^2; f0 = f(0)
+    and slope = f'(0) < 0.  The trial steps start at lam = 1.  A trial is accepted
+    when f(lam) <= f0 + c lam slope; otherwise the next trial minimises the quadratic
+    that matches f(0), f'(0) and f(lam), clamped to [0.1 lam, 0.5 lam] (quadratic
+    backtracking).  Returns (lam, f(lam), extra, trials) with trials the list of
+    (lam, f(lam)) evaluated in order; raises LineSearchError once lam < lambda_min.
+    """
+    lam = 1.0
+    trials = []
+    while True:
+        ft, extra = merit(lam)
+        trials.append((lam, ft))
+        if ft <= f0 + c * lam * slope:
+            return lam, ft, extra, trials
+        lq = -slope * lam * lam / (2.0 * (ft - f0 - slope * lam))
+        lam = min(max(lq, 0.1 * lam), 0.5 * lam)
+        if lam < lambda_min:
+            raise LineSearchError("line search failed")
+
+
 def linear_solve(J, h, rhs, opt, stats):
+    if opt.krylov == "direct":  # exact correction (tests: separates Newton from the preconditioner)
+        return spla.spsolve(sp.csc_matrix(J), rhs), 0, True
     prec = lambda v: amg.vcycle(h, v, opt.nu1, opt.nu2)
     mv = lambda v: J @ v
     if opt.krylov == "fcg":
-        d, its, ok, _ = krylov.fcg(mv, prec, rhs, opt.eta, opt.maxit)
+        info = {}
+        d, its, ok, _ = krylov.fcg(mv, prec, rhs, opt.eta, opt.maxit, info=info)
         stats.linear_its += its
         if ok:
             return d, its, True
+        if opt.max_dt_halvings > 0 and info.get("reason") == "curvature":
+            # under time-step control a Jacobian that is not positive definite along
+            # a preconditioned direction ends the attempt: the step is retried shorter
+            return d, its, False
         stats.fallbacks += 1
     d, its, ok, _ = krylov.fgmres(mv, prec, rhs, opt.eta, opt.maxit, opt.restart)
     stats.linear_its += its
@@ -129,7 +177,7 @@ def step(prob, p, dt, opt):
         if prob.hierarchy is None or (opt.amg_policy == "rebuild_step" and r == 0):
             prob.hierarchy = amg.setup(A, opt.theta, opt.amg_seed, opt.coarse_max, opt.max_levels,
                                        smooth_levels=opt.smooth_levels, aggregation=opt.aggregation,
-                                       max_agg_size=opt.max_agg_size)
+                                       max_agg_size=opt.max_agg_size, isolated_join=opt.isolated_join)
         elif opt.amg_policy == "setup_once":
             amg.update_fine(prob.hierarchy, A)
         else:
@@ -137,22 +185,19 @@ def step(prob, p, dt, opt):
         d, its, ok = linear_solve(J, prob.hierarchy, -F, opt, st)
         st.lin_its.append(its)
         if not ok:
-            raise RuntimeError("linear solver did not converge")
+            raise LinearSolveError("linear solver did not converge")
         g = float(F @ (J @ d))
         if not g < 0.0:
-            raise RuntimeError("non-descent Newton direction")
+            raise LineSearchError("non-descent Newton direction")
         f0 = 0.5 * fn * fn
-        lam = 1.0
-        while True:
+
+        def merit(lam):
             Ft, scale_t = prob.residual(p + lam * d, s_old, dt, with_scale=True)
-            st.line_search_evals += 1
-            ft = 0.5 * float(Ft @ Ft)
-            if ft <= f0 + opt.armijo_c * lam * g:
-                break
-            lq = -g * lam * lam / (2.0 * (ft - f0 - g * lam))
-            lam = min(max(lq, 0.1 * lam), 0.5 * lam)
-            if lam < opt.lambda_min:
-                raise RuntimeError("line search failed")
+            return 0.5 * float(Ft @ Ft), (Ft, scale_t)
+
+        lam, ft, (Ft, scale_t), trials = armijo_backtrack(merit, f0, g, opt.armijo_c, opt.lambda_min)
+        st.line_search_evals += len(trials)
+        st.line_searches.append((f0, g, trials))
         p = p + lam * d
         F, scale = Ft, scale_t
         fn = np.linalg.norm(F)
@@ -161,3 +206,64 @@ def step(prob, p, dt, opt):
         st.newton_its += 1
     st.res = fn
     return p, st
+
+
+def advance(prob, p, dt, opt):
+    """Cover one time step dt with backward-Euler steps under time-step control.
+
+    The paper fixes dt per step (Sec. 6) and gives no control; this is the usual
+    host-side remedy when Newton fails at a steep wetting front.  With
+    opt.max_dt_halvings = H > 0 the step is tried whole; an attempt that fails
+    (Krylov, line search or Newton non-convergence) is discarded and retried
+    with half its length, down to dt / 2^H; after each accepted substep the
+    length doubles again whenever the time reached is a multiple of the doubled
+    length, so the substeps land exactly on dt.  Lengths are dt / 2^k (exact in
+    binary floating point).  Returns (p_new, stats) with the Newton and Krylov
+    counts summed over accepted and failed attempts; raises the last failure
+    when a step of dt / 2^H fails.
+    """
+    H = int(opt.max_dt_halvings)
+    if H <= 0:
+        return step(prob, p, dt, opt)
+    total = 1 << H          # dt in units of dt / 2^H
+    t = 0                   # time reached, in those units
+    k = 0                   # current substep length dt / 2^k = 2^(H-k) units
+    acc = StepStats(substeps=0, dt_min=dt)
+    acc.res0 = None
+    p = np.array(p, dtype=np.float64)
+    while t < total:
+        h = math.ldexp(dt, -k)
+        length = 1 << (H - k)
+        try:
+            p_new, st = step(prob, p, h, opt)
+            ok = st.converged
+            err = None if ok else RuntimeError("Newton did not converge")
+        except (LinearSolveError, LineSearchError) as e:
+            st, ok, err = None, False, e
+        if st is not None:
+            acc.newton_its += st.newton_its
+            acc.linear_its += st.linear_its
+            acc.line_search_evals += st.line_search_evals
+            acc.fallbacks += st.fallbacks
+            acc.lambdas += st.lambdas
+            acc.lin_its += st.lin_its
+            acc.line_searches += st.line_searches
+            if acc.res0 is None:
+                acc.res0 = st.res0
+            acc.res = st.res
+        if not ok:
+            acc.dt_failures += 1
+            if k == H:
+                raise err
+            k += 1
+            continue
+        p = p_new
+        t += length
+        acc.substeps += 1
+        acc.dt_min = min(acc.dt_min, h)
+        if k > 0 and t % (2 * length) == 0:
+            k -= 1
+    acc.converged = True
+    if acc.res0 is None:
+        acc.res0 = 0.0
+    return p, acc
