@@ -36,6 +36,7 @@ With torchrun (N > 1) every rank runs an independent replica of the workload
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -268,10 +269,12 @@ def run_reference(args):
 
 
 def percentile(sorted_values, q):
-    """The q-quantile of an ascending list by the nearest-rank rule (None if empty)."""
+    """The q-quantile of an ascending list by the nearest-rank rule: the smallest value
+    with at least a fraction q of the values at or below it (None if empty)."""
     if not sorted_values:
         return None
-    return sorted_values[min(len(sorted_values) - 1, int(q * len(sorted_values)))]
+    n = len(sorted_values)
+    return sorted_values[min(n - 1, max(0, math.ceil(q * n) - 1))]
 
 
 def stream_stats(results, dofs, seconds, error_names):

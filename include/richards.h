@@ -62,6 +62,12 @@ extern "C" {
 #define RICH_KMEAN_UPSTREAM   1
 #define RICH_KMEAN_HARMONIC   2
 #define RICH_KMEAN_GEOMETRIC  3
+/* Sec. 2.1 also allows two different means, one for the horizontal and one for
+ * the vertical direction: RICH_KMEAN_SPLIT(h, v) applies mean h on the x and y
+ * faces and mean v on the z faces (h, v among the four above).  Every entry point
+ * that takes a kmean accepts these codes. */
+#define RICH_KMEAN_SPLIT_FLAG 0x100
+#define RICH_KMEAN_SPLIT(h, v) (RICH_KMEAN_SPLIT_FLAG | ((h) << 4) | (v))
 
 #define RICH_BC_NOFLUX     0  /* the whole face flux (diffusion + gravity) is zero */
 #define RICH_BC_DIRICHLET  1  /* ghost node at p = value, K from the adjacent cell's K_s */
@@ -138,6 +144,10 @@ typedef struct {
                               locally dominant matching, log2(max_agg_size) pairing passes on the
                               successive pair graphs */
   int max_agg_size;        /* largest aggregate of the matching (8, as in the paper's runs) */
+  int isolated_join;       /* MIS-2 pass 3 (1, default): a node without strong neighbours whose row is not
+                              diagonally dominant (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
+                              aggregated neighbour j with the largest (fp32 |a_ij|, key(j)); dominant rows
+                              (e.g. under a Dirichlet face) stay out.  0: every such node stays out */
 } rich_amg_opts;
 
 typedef struct {
@@ -164,6 +174,15 @@ typedef struct {
   double armijo_c;         /* sufficient-decrease constant (1e-4) */
   double lambda_min;       /* smallest line-search step (1e-10) */
   int fcg_fallback_restart;/* FGMRES(m) retry after an FCG failure (30) */
+  int max_dt_halvings;     /* time-step control (0 = off, default).  H > 0: rich_step covers dt with
+                              backward-Euler steps of length dt / 2^k: an attempt that fails with
+                              RICH_ENOTCONV_LIN, RICH_ENOTCONV_NEWTON or RICH_ELINESEARCH is discarded
+                              (p restored) and retried with half its length, down to dt / 2^H; after an
+                              accepted substep the length doubles back whenever the time reached is a
+                              multiple of the doubled length, so the substeps end exactly at dt.  Under
+                              control an FCG solve that meets (p, J p) <= 0 fails the attempt at once
+                              instead of falling back to FGMRES.  The paper fixes dt per step (Sec. 6);
+                              this is host-side control for steep wetting fronts */
 } rich_newton_opts;
 
 typedef struct {
@@ -181,6 +200,9 @@ typedef struct {
    * assembly (Jacobian/Auxiliary), AMG setup or refresh (Setup), Krylov
    * solves (LinSol); the rest of the step is Overhead (no Halo on one GPU). */
   double ms_feval, ms_jacobian, ms_setup, ms_linsol, ms_total;
+  int substeps;            /* backward-Euler steps that covered dt (1 without time-step control) */
+  int dt_failures;         /* attempts discarded and retried with half the step */
+  double dt_min;           /* shortest accepted substep */
 } rich_step_stats;
 
 typedef struct {
@@ -277,8 +299,10 @@ int krylov_solve(rich_ctx* ctx, const double* b_dev, double* x_dev, const rich_k
 
 /* ---- Sec. 3: one backward-Euler step ------------------------------------ */
 /* p_dev holds p^{l-1} on entry and p^l on return (or the last accepted
- * Newton iterate on error).  opts NULL = defaults.  The first call of a
- * context builds the AMG hierarchy. */
+ * Newton iterate on error; under time-step control, the pressure at the start
+ * of the substep that failed at the shortest length).  opts NULL = defaults.
+ * The first call of a context builds the AMG hierarchy.  Counts in stats_host
+ * cover every attempt, discarded ones included. */
 int rich_step(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_opts* opts,
               rich_step_stats* stats_host);
 /* The same step on a host array: copies p_host to the device, steps, and

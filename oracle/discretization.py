@@ -17,7 +17,8 @@ Readings where the paper is silent (all listed in the design notes):
     (upstream_mean)) K_U if p_U - p_L >= 0 else K_L, where U is the cell on
     the +d side of the face, ties taking K_U; harmonic 2 K_L K_U/(K_L+K_U)
     (the abstract names it, no formula is printed); geometric sqrt(K_L K_U)
-    (Sec. 2.1).
+    (Sec. 2.1); or a split of two of them, one on the horizontal (x, y) and
+    one on the vertical (z) faces (Sec. 2.1, axis_kmean).
   * Dirichlet face: the ghost node holds p = p_bc (a constant or a per-cell
     value of the face) and K = K(p_bc) with the Ks of the adjacent interior
     cell; T and G use it as a neighbour.
@@ -75,6 +76,16 @@ def _boundary_mask(shape, axis, side):
     idx[ax] = -1 if side > 0 else 0
     m[tuple(idx)] = True
     return m
+
+
+def axis_kmean(kmean, axis):
+    """The mean used on the faces normal to axis.  Sec. 2.1 allows "two different
+    means, one for the horizontal and another for the vertical direction": such a
+    split mean is coded 0x100 | (horizontal << 4) | vertical and applies the
+    horizontal mean on the x and y faces, the vertical one on the z faces."""
+    if kmean & 0x100:
+        return kmean & 0xF if axis == 2 else (kmean >> 4) & 0xF
+    return kmean
 
 
 def face_mean(kmean, k_lo, k_up, p_lo, p_up):
@@ -174,7 +185,7 @@ def residual(grid, soil, bc, kmean, p, s_old, dt, ks=None, with_scale=False):
     for axis, side, nb_p, nb_K, nb_dK, interior, active in fd.faces:
         h = fd.h[axis]
         k_lo, k_up, p_lo, p_up = fd.lower_upper(side, nb_p, nb_K)
-        kav = face_mean(kmean, k_lo, k_up, p_lo, p_up)
+        kav = face_mean(axis_kmean(kmean, axis), k_lo, k_up, p_lo, p_up)
         t = kav * (fd.p3 - nb_p) / (h * h)
         m = kav * (np.abs(fd.p3) + np.abs(nb_p)) / (h * h)
         if axis == 2:
@@ -214,8 +225,8 @@ def jacobian_stencil(grid, soil, bc, kmean, p, dt, ks=None):
     for f, (axis, side, nb_p, nb_K, nb_dK, interior, active) in enumerate(fd.faces):
         h = fd.h[axis]
         k_lo, k_up, p_lo, p_up = fd.lower_upper(side, nb_p, nb_K)
-        kav = face_mean(kmean, k_lo, k_up, p_lo, p_up)
-        d_lo, d_up = face_mean_partials(kmean, k_lo, k_up, p_lo, p_up)
+        kav = face_mean(axis_kmean(kmean, axis), k_lo, k_up, p_lo, p_up)
+        d_lo, d_up = face_mean_partials(axis_kmean(kmean, axis), k_lo, k_up, p_lo, p_up)
         d_self, d_nb = (d_lo, d_up) if side > 0 else (d_up, d_lo)
         dp = (fd.p3 - nb_p) / (h * h)
         dd = d_self * fd.dK3 * dp + kav / (h * h)
@@ -243,7 +254,7 @@ def aux_stencil(grid, soil, bc, kmean, p, dt, ks=None):
     for f, (axis, side, nb_p, nb_K, nb_dK, interior, active) in enumerate(fd.faces):
         h = fd.h[axis]
         k_lo, k_up, p_lo, p_up = fd.lower_upper(side, nb_p, nb_K)
-        w = face_mean(kmean, k_lo, k_up, p_lo, p_up) / (h * h)
+        w = face_mean(axis_kmean(kmean, axis), k_lo, k_up, p_lo, p_up) / (h * h)
         diag = diag + np.where(active, w, 0.0)
         st[:, 1 + f] = np.where(interior, -w, 0.0).reshape(-1)
     st[:, 0] = diag.reshape(-1)

@@ -27,6 +27,9 @@ no constants; the readings used here (shared with the CUDA path) are:
     lambda <- clamp(-g lambda^2 / (2 (f(lambda) - f(0) - g lambda)),
     0.1 lambda, 0.5 lambda); fail below 1e-10.  A non-negative slope is a
     failure.
+  * time-step control (advance, off unless max_dt_halvings > 0): a failed
+    step is retried with half its length, down to dt / 2^H, and the length
+    doubles back once the time reached allows it.
 """
 import dataclasses
 import math
@@ -111,6 +114,10 @@ class LinearSolveError(RuntimeError):
     pass
 
 
+class NewtonError(RuntimeError):
+    pass
+
+
 def armijo_backtrack(merit, f0, slope, c, lambda_min):
     """Armijo backtracking along a descent direction (Sec. 3, the line search of KINSOL's
     inexact Newton method; constants in the module docstring).
@@ -157,10 +164,22 @@ def linear_solve(J, h, rhs, opt, stats):
 
 
 def step(prob, p, dt, opt):
-    """Advance p by one backward-Euler step of size dt; returns (p_new, stats)."""
+    """Advance p by one backward-Euler step of size dt; returns (p_new, stats).
+
+    A failure raises LinearSolveError or LineSearchError carrying the statistics
+    gathered until then (attribute stats); Newton non-convergence returns with
+    stats.converged False."""
+    st = StepStats()
+    try:
+        return _step(prob, p, dt, opt, st)
+    except (LinearSolveError, LineSearchError) as e:
+        e.stats = st
+        raise
+
+
+def _step(prob, p, dt, opt, st):
     p = np.array(p, dtype=np.float64)
     s_old = cst.saturation(p, prob.soil)
-    st = StepStats()
     F, scale = prob.residual(p, s_old, dt, with_scale=True)
     fn = np.linalg.norm(F)
     st.res0 = fn
@@ -237,9 +256,9 @@ def advance(prob, p, dt, opt):
         try:
             p_new, st = step(prob, p, h, opt)
             ok = st.converged
-            err = None if ok else RuntimeError("Newton did not converge")
+            err = None if ok else NewtonError("Newton did not converge")
         except (LinearSolveError, LineSearchError) as e:
-            st, ok, err = None, False, e
+            st, ok, err = getattr(e, "stats", None), False, e
         if st is not None:
             acc.newton_its += st.newton_its
             acc.linear_its += st.linear_its

@@ -187,6 +187,42 @@ __global__ void k_agg_pass2(int n, const int* __restrict__ srp, const uint64_t* 
   if (miss) atomicOr(unassigned, 1);
 }
 
+// Pass 3: a node left out by passes 1-2 (no strong neighbour) whose row is not
+// diagonally dominant (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
+// aggregated neighbour j with the largest (fp32 |a_ij|, key(j)).  On high-contrast
+// fields such a row sums to about zero although every coupling is weak relative to
+// the neighbours' diagonals; left out, its error is corrected by the smoother alone.
+// Reads the aggregates of passes 1-2 (agg_in) only, so the pass is synchronous.
+__global__ void k_agg_pass3(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, uint64_t seed, const int* __restrict__ agg_in,
+                            int* __restrict__ agg_out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int a = agg_in[i];
+    if (a >= 0) continue;
+    double diag = 0.0, off = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      if (col[e] == i) diag = val[e];
+      else off += fabs(val[e]);
+    }
+    if (!(fabs(diag) < 2.0 * off)) continue;
+    int bj = -1;
+    float bw = 0.0f;
+    uint64_t bk = 0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      int j = col[e];
+      if (j == i || agg_in[j] < 0) continue;
+      float w = (float)fabs(val[e]);
+      uint64_t kj = prio_key(seed, j);
+      if (bj < 0 || w > bw || (w == bw && kj > bk)) {
+        bj = j;
+        bw = w;
+        bk = kj;
+      }
+    }
+    if (bj >= 0) agg_out[i] = agg_in[bj];
+  }
+}
+
 // P_tent: one unit entry per aggregated node, empty rows for isolated nodes
 __global__ void k_ptent_count(int n, const int* __restrict__ agg, int* __restrict__ cnt) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) cnt[i] = agg[i] >= 0;
@@ -1069,10 +1105,19 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
   RICH_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c->st));
   for (int mode = 0; mode < 2; ++mode) {
     if (mode == 1) {
+      // the row offsets are 32-bit: check the total in 64 bits before the scan
+      unsigned long long* dsum = reinterpret_cast<unsigned long long*>(c->iflag + 4);  // slots 4-5
+      RICH_CUDA(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), c->st));
+      k_sum_rows_ll<<<red_grid(n), kBlock, 0, c->st>>>(n, cnt, dsum);
+      RICH_LAUNCH_CHECK();
+      unsigned long long total = 0;
+      RICH_CUDA(cudaMemcpyAsync(&total, dsum, sizeof(total), cudaMemcpyDeviceToHost, c->st));
+      RICH_CUDA(cudaStreamSynchronize(c->st));
+      if (total > 2147483647ull) return RICH_ELIMIT;
       RICH_CHECK(scan_exclusive_int(c, cnt, C.rowptr, n));
       int nnz = 0;
       RICH_CHECK(read_dev_int(c, C.rowptr + n, &nnz));
-      if (nnz < 0) return RICH_ELIMIT;
+      if (nnz < 0 || (unsigned long long)nnz != total) return RICH_ELIMIT;
       C.nnz = nnz;
       RICH_CHECK(dalloc(&C.col, nnz));
       RICH_CHECK(dalloc(&C.val, nnz));
@@ -1623,6 +1668,12 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
     RICH_CUDA(cudaMemcpyAsync(c->hflag, c->iflag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     RICH_CUDA(cudaStreamSynchronize(c->st));
     unassigned = c->hflag[0] != 0;
+    if (!unassigned && o.isolated_join) {
+      int* agg_in = p1root;  // pass-1 scratch, free now
+      RICH_CUDA(cudaMemcpyAsync(agg_in, L.agg, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->st));
+      k_agg_pass3<<<grid_for(n), kBlock, 0, c->st>>>(n, L.A.rowptr, L.A.col, L.A.val, o.seed, agg_in, L.agg);
+      RICH_LAUNCH_CHECK();
+    }
     dfree(t);
     dfree(m1);
     dfree(p1root);

@@ -193,6 +193,7 @@ struct KrylovWork {
   double* z = nullptr;
   double* w = nullptr;
   double* hcoef = nullptr;  // device coefficients (m+1)
+  int fail_reason = 0;      // last FCG failure: 0 none, 1 maxit, 2 (p, J p) <= 0, 3 residual growth
 };
 
 }  // namespace rich
@@ -234,6 +235,7 @@ struct rich_ctx {
   double* ptrial = nullptr;
   double* rhs = nullptr;
   double* pbuf = nullptr;      // device p for rich_step_host
+  double* psave = nullptr;     // p at the start of a substep (time-step control)
   double* bc_fields[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // owned per-cell BC values
   bool amg_ever = false;
 };
@@ -271,6 +273,18 @@ __device__ __forceinline__ void constit(double p, double ks, const SoilP& so, do
 __device__ __forceinline__ double conductivity_only(double p, double ks, const SoilP& so) {
   if (p < 0.0) return ks * so.a / (so.a + exp(so.gamma * log(-p)));
   return ks;
+}
+
+// The mean used on the faces normal to axis: a split code (RICH_KMEAN_SPLIT) takes
+// its horizontal mean on the x and y faces and its vertical mean on the z faces.
+__host__ __device__ __forceinline__ int axis_mean(int kmean, int axis) {
+  if (kmean & RICH_KMEAN_SPLIT_FLAG) return axis == 2 ? (kmean & 0xF) : ((kmean >> 4) & 0xF);
+  return kmean;
+}
+inline bool kmean_valid(int kmean) {
+  if (kmean >= 0 && kmean <= 3) return true;
+  if ((kmean & ~0x1FF) != 0 || !(kmean & RICH_KMEAN_SPLIT_FLAG)) return false;
+  return ((kmean >> 4) & 0xF) <= 3 && (kmean & 0xF) <= 3;
 }
 
 // Face mean between the lower (L) and upper (+d side, U) cell and its partials.

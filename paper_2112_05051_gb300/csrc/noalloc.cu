@@ -28,6 +28,8 @@ constexpr int kNoAllocItems = 8;  // cells per thread
 constexpr long long kNoAllocCells = (long long)kNoAllocThreads * kNoAllocItems;
 constexpr int kNoAllocMaxBlocks = 65536;
 constexpr int kNoAllocSlots = 2 * kNoAllocMaxBlocks + 8;  // partials, then the two results
+// block_sum / block_max size their shared arrays and final warp pass by kBlock
+static_assert(kNoAllocThreads == kBlock, "the norm reductions assume kBlock threads per block");
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
 
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_residual_noalloc(
       int axis = f >> 1;
       double side = (f & 1) ? 1.0 : -1.0;
       double dL, dU;
-      double ka = (f & 1) ? face_mean(kmean, Kc, Kn, pc, pn, dL, dU) : face_mean(kmean, Kn, Kc, pn, pc, dL, dU);
+      const int km = axis_mean(kmean, f >> 1);
+      double ka = (f & 1) ? face_mean(km, Kc, Kn, pc, pn, dL, dU) : face_mean(km, Kn, Kc, pn, pc, dL, dU);
       double tt = ka * (pc - pn) * g.inv_h2[axis];
       if (axis == 2) tt -= side * (Kc + Kn) * 0.5 * g.inv_h[2];
       phi += tt;
@@ -146,7 +149,7 @@ extern "C" int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soi
   if (!grid || !soil || !bc || !p_dev || !s_old_dev || !F_dev || !(dt > 0)) return RICH_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0 && grid->ly > 0 && grid->lz > 0))
     return RICH_EINVAL;
-  if (kmean < 0 || kmean > 3) return RICH_EINVAL;
+  if (!kmean_valid(kmean)) return RICH_EINVAL;
   for (int f = 0; f < 6; ++f)
     if (bc->kind[f] != RICH_BC_NOFLUX && bc->kind[f] != RICH_BC_DIRICHLET) return RICH_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;

@@ -101,8 +101,8 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
       int axis = f >> 1;
       double side = (f & 1) ? 1.0 : -1.0;
       double dL, dU;
-      double ka = (f & 1) ? face_mean(kmean, Kc, nb.K, pc, nb.p, dL, dU)
-                          : face_mean(kmean, nb.K, Kc, nb.p, pc, dL, dU);
+      double ka = (f & 1) ? face_mean(axis_mean(kmean, axis), Kc, nb.K, pc, nb.p, dL, dU)
+                          : face_mean(axis_mean(kmean, axis), nb.K, Kc, nb.p, pc, dL, dU);
       double t = ka * (pc - nb.p) * g.inv_h2[axis];
       double m = ka * (fabs(pc) + fabs(nb.p)) * g.inv_h2[axis];
       if (axis == 2) {
@@ -150,8 +150,8 @@ __global__ void k_assemble(GridP g, SoilP so, BCP bc, int kmean, const double* _
         int axis = f >> 1;
         double side = (f & 1) ? 1.0 : -1.0;
         double dL, dU;
-        double ka = (f & 1) ? face_mean(kmean, Kc, nb.K, pc, nb.p, dL, dU)
-                            : face_mean(kmean, nb.K, Kc, nb.p, pc, dL, dU);
+        double ka = (f & 1) ? face_mean(axis_mean(kmean, axis), Kc, nb.K, pc, nb.p, dL, dU)
+                            : face_mean(axis_mean(kmean, axis), nb.K, Kc, nb.p, pc, dL, dU);
         double dself = (f & 1) ? dL : dU;
         double dnb = (f & 1) ? dU : dL;
         double w = ka * g.inv_h2[axis];
@@ -347,6 +347,7 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->product_lists = 1;
   o->aggregation = RICH_AGG_MIS2;
   o->max_agg_size = 8;
+  o->isolated_join = 1;
 }
 
 void rich_default_newton_opts(rich_newton_opts* o) {
@@ -362,6 +363,7 @@ void rich_default_newton_opts(rich_newton_opts* o) {
   o->armijo_c = 1e-4;
   o->lambda_min = 1e-10;
   o->fcg_fallback_restart = 30;
+  o->max_dt_halvings = 0;
 }
 
 int rich_num_cells(const rich_ctx* c, long long* n) {
@@ -376,7 +378,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   *out = nullptr;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return RICH_EINVAL;
   if (!(grid->lx > 0 && grid->ly > 0 && grid->lz > 0)) return RICH_EINVAL;
-  if (kmean < 0 || kmean > 3 || (precision != RICH_PREC_FP64 && precision != RICH_PREC_MIXED)) return RICH_EINVAL;
+  if (!kmean_valid(kmean) || (precision != RICH_PREC_FP64 && precision != RICH_PREC_MIXED)) return RICH_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   if (n > 2147483647LL / 8) return RICH_ELIMIT;  // 32-bit CSR indices of the 7-point pattern
   for (int f = 0; f < 6; ++f)
@@ -468,6 +470,7 @@ int rich_destroy(rich_ctx* c) {
   dfree(c->ptrial);
   dfree(c->rhs);
   dfree(c->pbuf);
+  dfree(c->psave);
   for (int f = 0; f < 6; ++f) dfree(c->bc_fields[f]);
   KrylovWork& k = c->kw;
   dfree(k.V);

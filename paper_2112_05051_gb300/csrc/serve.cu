@@ -321,7 +321,7 @@ int rich_server_submit(rich_server* s, const rich_request* req, long long* id_ou
   const rich_request& r = *req;
   if (r.grid.nx < 1 || r.grid.ny < 1 || r.grid.nz < 1 || !(r.grid.lx > 0 && r.grid.ly > 0 && r.grid.lz > 0))
     return RICH_EINVAL;
-  if (!(r.dt > 0) || r.kmean < 0 || r.kmean > 3) return RICH_EINVAL;
+  if (!(r.dt > 0) || !kmean_valid(r.kmean)) return RICH_EINVAL;
   if (r.precision != RICH_PREC_FP64 && r.precision != RICH_PREC_MIXED) return RICH_EINVAL;
   for (int f = 0; f < 6; ++f) {
     if (r.bc.kind[f] != RICH_BC_NOFLUX && r.bc.kind[f] != RICH_BC_DIRICHLET) return RICH_EINVAL;

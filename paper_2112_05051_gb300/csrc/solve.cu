@@ -471,6 +471,7 @@ static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* 
   st->res = bn;
   st->iterations = 0;
   st->converged = 0;
+  k.fail_reason = 0;
   RICH_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, c->st));
   if (!(bn > 0)) {
     st->converged = std::isfinite(bn) ? 1 : 0;
@@ -507,15 +508,22 @@ static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* 
     st->iterations = it;
     st->res = rn;
     if (!std::isfinite(rn) || !std::isfinite(h[2])) return RICH_ENONFINITE;
-    if (!(h[2] > 0)) return RICH_ENOTCONV_LIN;
+    if (!(h[2] > 0)) {
+      k.fail_reason = 2;
+      return RICH_ENOTCONV_LIN;
+    }
     if (rn <= target) {
       st->converged = 1;
       return RICH_OK;
     }
-    if (rn > 10.0 * best) return RICH_ENOTCONV_LIN;
+    if (rn > 10.0 * best) {
+      k.fail_reason = 3;
+      return RICH_ENOTCONV_LIN;
+    }
     best = std::min(best, rn);
     std::swap(q, qprev);
   }
+  k.fail_reason = 1;
   return RICH_ENOTCONV_LIN;
 }
 
@@ -795,7 +803,9 @@ static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
     int lin_phase = pt.begin(&st->ms_linsol);
     int s = krylov_run(c, c->rhs, c->d, &o->krylov, &ks);
     st->linear_its += ks.iterations;
-    if (s == RICH_ENOTCONV_LIN && o->krylov.kind == RICH_KRYLOV_FCG) {
+    // under time-step control, (p, J p) <= 0 in FCG ends the attempt: the step is retried shorter
+    const bool indefinite = o->max_dt_halvings > 0 && c->kw.fail_reason == 2;
+    if (s == RICH_ENOTCONV_LIN && o->krylov.kind == RICH_KRYLOV_FCG && !indefinite) {
       rich_krylov_opts fb = o->krylov;
       fb.kind = RICH_KRYLOV_FGMRES;
       fb.restart = o->fcg_fallback_restart;
@@ -841,6 +851,65 @@ static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
   return RICH_OK;
 }
 
+// Time-step control: cover dt with backward-Euler substeps of length dt / 2^k.  A
+// substep that fails to converge is discarded (p restored) and retried with half
+// its length, down to dt / 2^H; after an accepted substep the length doubles back
+// whenever the time reached (counted in units of dt / 2^H) is a multiple of the
+// doubled length, so the substeps end exactly at dt.
+static bool retryable(int s) {
+  return s == RICH_ENOTCONV_LIN || s == RICH_ENOTCONV_NEWTON || s == RICH_ELINESEARCH;
+}
+
+static int advance_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) {
+  const int H = o->max_dt_halvings;
+  if (H > 40) return RICH_EINVAL;
+  long long n = c->g.n;
+  if (!c->psave) RICH_CHECK(dalloc(&c->psave, n));
+  memset(st, 0, sizeof(*st));
+  st->min_lambda = 1.0;
+  st->dt_min = dt;
+  const long long total = 1LL << H;
+  long long t = 0;
+  int k = 0;
+  bool first = true;
+  while (t < total) {
+    const double h = std::ldexp(dt, -k);
+    const long long len = 1LL << (H - k);
+    RICH_CUDA(cudaMemcpyAsync(c->psave, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    rich_step_stats sub;
+    int s = step_impl(c, p, h, o, &sub);
+    st->newton_its += sub.newton_its;
+    st->linear_its += sub.linear_its;
+    st->line_search_evals += sub.line_search_evals;
+    st->fallbacks += sub.fallbacks;
+    st->amg_setups += sub.amg_setups;
+    st->amg_refreshes += sub.amg_refreshes;
+    st->ms_feval += sub.ms_feval;
+    st->ms_jacobian += sub.ms_jacobian;
+    st->ms_setup += sub.ms_setup;
+    st->ms_linsol += sub.ms_linsol;
+    st->ms_total += sub.ms_total;
+    if (first) st->res0 = sub.res0;
+    first = false;
+    st->res = sub.res;
+    if (s != RICH_OK) {
+      if (!retryable(s)) return s;
+      st->dt_failures++;
+      RICH_CUDA(cudaMemcpyAsync(p, c->psave, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+      if (k == H) return s;
+      ++k;
+      continue;
+    }
+    st->min_lambda = std::min(st->min_lambda, sub.min_lambda);
+    t += len;
+    st->substeps++;
+    st->dt_min = std::min(st->dt_min, h);
+    if (k > 0 && t % (2 * len) == 0) --k;
+  }
+  st->converged = 1;
+  return RICH_OK;
+}
+
 }  // namespace rich
 
 using namespace rich;
@@ -870,7 +939,13 @@ int rich_step(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich
     o = &def;
   }
   rich_step_stats tmp;
-  return step_impl(c, p, dt, o, st ? st : &tmp);
+  if (!st) st = &tmp;
+  if (o->max_dt_halvings < 0) return RICH_EINVAL;
+  if (o->max_dt_halvings > 0) return advance_impl(c, p, dt, o, st);
+  int s = step_impl(c, p, dt, o, st);
+  st->substeps = s == RICH_OK ? 1 : 0;
+  st->dt_min = dt;
+  return s;
 }
 
 int rich_step_host(rich_ctx* c, double* p_host, double dt, const rich_newton_opts* o, rich_step_stats* st) {

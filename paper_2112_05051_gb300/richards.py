@@ -65,7 +65,7 @@ class AmgOpts(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("seed", ctypes.c_uint64), ("coarse_max", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int), ("aggregation", ctypes.c_int),
-                ("max_agg_size", ctypes.c_int)]
+                ("max_agg_size", ctypes.c_int), ("isolated_join", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -81,7 +81,8 @@ class KrylovStats(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("krylov", KrylovOpts), ("amg", AmgOpts), ("amg_policy", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("armijo_c", ctypes.c_double),
-                ("lambda_min", ctypes.c_double), ("fcg_fallback_restart", ctypes.c_int)]
+                ("lambda_min", ctypes.c_double), ("fcg_fallback_restart", ctypes.c_int),
+                ("max_dt_halvings", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -89,7 +90,8 @@ class StepStats(ctypes.Structure):
                 ("fallbacks", ctypes.c_int), ("amg_setups", ctypes.c_int), ("amg_refreshes", ctypes.c_int),
                 ("converged", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double),
                 ("min_lambda", ctypes.c_double), ("ms_feval", ctypes.c_double), ("ms_jacobian", ctypes.c_double),
-                ("ms_setup", ctypes.c_double), ("ms_linsol", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("ms_setup", ctypes.c_double), ("ms_linsol", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("substeps", ctypes.c_int), ("dt_failures", ctypes.c_int), ("dt_min", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -210,7 +212,7 @@ def default_newton_opts(**kw):
         if k in ("kind", "restart", "eta", "maxit"):
             setattr(o.krylov, k, v)
         elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
-                   "aggregation", "max_agg_size"):
+                   "aggregation", "max_agg_size", "isolated_join"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)

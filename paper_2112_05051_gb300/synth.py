@@ -34,6 +34,18 @@ KMEAN_HARMONIC = 2
 KMEAN_GEOMETRIC = 3
 KMEAN_NAMES = {KMEAN_ARITH: "arithmetic", KMEAN_UPSTREAM: "upstream", KMEAN_HARMONIC: "harmonic",
                KMEAN_GEOMETRIC: "geometric"}
+KMEAN_SPLIT_FLAG = 0x100
+
+
+def kmean_split(horizontal: int, vertical: int) -> int:
+    """Code of a split face mean (Sec. 2.1): one mean on the x and y faces, another on the z faces."""
+    return KMEAN_SPLIT_FLAG | (horizontal << 4) | vertical
+
+
+def kmean_name(code: int) -> str:
+    if code & KMEAN_SPLIT_FLAG:
+        return "%s horizontal, %s vertical" % (KMEAN_NAMES[(code >> 4) & 0xF], KMEAN_NAMES[code & 0xF])
+    return KMEAN_NAMES[code]
 
 
 @dataclasses.dataclass(frozen=True)

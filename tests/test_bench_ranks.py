@@ -59,14 +59,17 @@ def test_request_stream_statistics():
     import bench
     assert bench.percentile([], 0.5) is None
     v = list(range(1, 101))  # 1 .. 100
-    assert bench.percentile(v, 0.5) == 51 and bench.percentile(v, 0.99) == 100 and bench.percentile(v, 0.0) == 1
+    # nearest rank: p50 of 1..100 is the 50th value, p99 the 99th, p100 the maximum
+    assert bench.percentile(v, 0.5) == 50 and bench.percentile(v, 0.99) == 99 and bench.percentile(v, 0.0) == 1
+    assert bench.percentile(v, 1.0) == 100 and bench.percentile(v, 0.505) == 51
+    assert bench.percentile([7.0], 0.99) == 7.0
     res = [{"t_submit": 0.0, "t_done": 0.010 * (k + 1), "status": 0 if k % 4 else -4,
             "stats": {"newton_its": 3}} for k in range(8)]
     st = bench.stream_stats(res, [1000] * 8, 2.0, {-4: "RICH_ENOTCONV_LIN"})
     assert st["failed"] == {"RICH_ENOTCONV_LIN": 2}
     assert st["dof_newton_per_s"] == 6 * 1000 * 3 / 2.0          # converged work only
     assert abs(st["latency_ms"]["max"] - 80.0) < 1e-9 and abs(st["latency_ms"]["mean"] - 45.0) < 1e-9
-    assert abs(st["latency_ms_converged"]["p50"] - 60.0) < 1e-9  # 20,30,40,60,70,80 -> nearest rank 4
+    assert abs(st["latency_ms_converged"]["p50"] - 40.0) < 1e-9  # 20,30,40,60,70,80 -> nearest rank 3
 
 
 def test_serving_run_end_to_end_against_a_fake_server(monkeypatch):

@@ -85,9 +85,12 @@ def test_hierarchy_bit_exact(dims, coarse_max, kmean):
     ctx.close()
 
 
-def test_hierarchy_with_isolated_nodes_from_extreme_heterogeneity():
-    # log10 Ks with std 2 spans ~16 decades: low-conductivity cells have no strong
-    # coupling and stay out of every aggregate (empty P_tent rows)
+@pytest.mark.parametrize("join", [1, 0])
+def test_hierarchy_with_isolated_nodes_from_extreme_heterogeneity(join):
+    # log10 Ks with std 2 spans ~16 decades: many cells have no strong coupling.
+    # join=1 (pass 3): those whose row is not diagonally dominant join the aggregate of
+    # their strongest aggregated neighbour; the dominant rows under the Dirichlet top
+    # (and, with join=0, all of them) stay out of every aggregate (empty P_tent rows)
     rb = _rb()
     grid = synth.Grid(26, 24, 22)
     ks = synth.ks_field(grid, 4, 2.0, (4.0, 4.0, 2.0))
@@ -95,10 +98,13 @@ def test_hierarchy_with_isolated_nodes_from_extreme_heterogeneity():
     bc = synth.infiltration_bc()
     ctx = rb.Context(grid, SOIL, bc, 0, ks)
     ctx.jacobian(torch.tensor(p, device="cuda"), 10.0)
-    info = ctx.amg_setup(rb.default_amg_opts(seed=4, coarse_max=200))
+    info = ctx.amg_setup(rb.default_amg_opts(seed=4, coarse_max=200, isolated_join=join))
     A = disc.aux_matrix(grid, SOIL, bc, 0, p, 10.0, ks)
-    h = amg.setup(A, 0.08, 4, 200)
+    h = amg.setup(A, 0.08, 4, 200, isolated_join=bool(join))
     assert np.any(h.levels[0].agg < 0)
+    if join:
+        h0 = amg.setup(A, 0.08, 4, 200, isolated_join=False)
+        assert np.sum(h.levels[0].agg < 0) < np.sum(h0.levels[0].agg < 0)
     _compare_hierarchy(ctx, info, h)
     r = np.random.default_rng(3).standard_normal(grid.n)
     z = torch.empty(grid.n, dtype=torch.float64, device="cuda")

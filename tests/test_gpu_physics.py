@@ -54,7 +54,7 @@ def _inputs(grid, seed, het=True):
     return p, ks, s_old
 
 
-@pytest.mark.parametrize("kmean", [0, 1, 2, 3])
+@pytest.mark.parametrize("kmean", [0, 1, 2, 3, synth.kmean_split(1, 2), synth.kmean_split(3, 0)])
 @pytest.mark.parametrize("bcname", list(BCS))
 @pytest.mark.parametrize("dims", GRIDS)
 def test_residual_jacobian_parity(kmean, bcname, dims):

@@ -1,0 +1,91 @@
+"""GPU parity at the bench's scale: the 128^3 hierarchy, V-cycle and FGMRES(30) solve of
+the upstream-mean workload, and a mixed-precision step of the 512^3 workload's
+settings (sigma 2 field, arithmetic mean, dt = 10 s) on 48^3, against the FP64 oracle.
+
+Bars: aggregates and patterns bit-exact; FP64 values and one V(2,2) application
+normwise 1e-10; the FGMRES(30) correction within one iteration of the oracle's
+count and 1e-8 of its solution; the mixed-precision converged pressure 1e-8.
+The oracle builds the 128^3 hierarchy in about ten seconds on one host core.
+"""
+import numpy as np
+import pytest
+
+from oracle import amg, krylov, newton
+from oracle import constitutive as cst
+from oracle import discretization as disc
+from paper_2112_05051_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _rb():
+    from paper_2112_05051_gb300 import richards as rb
+    rb.load()
+    return rb
+
+
+def _nrel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_bench_scale_hierarchy_vcycle_and_fgmres_128():
+    rb = _rb()
+    w = synth.WORKLOADS["richards128_fp64"]
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w)
+    dt = dts[0]
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks)
+    pd = torch.tensor(p0, device="cuda")
+    ctx.jacobian(pd, dt)
+    info = ctx.amg_setup(rb.default_amg_opts(seed=w.amg_seed, coarse_max=w.coarse_max, nu1=w.nu, nu2=w.nu,
+                                             smooth_levels=w.smooth_levels))
+    A = disc.aux_matrix(grid, soil, bc, w.kmean, p0, dt, ks)
+    h = amg.setup(A, 0.08, w.amg_seed, w.coarse_max, smooth_levels=w.smooth_levels)
+    assert info.levels == len(h.levels) >= 3
+    for l, lv in enumerate(h.levels):
+        assert info.n[l] == lv.A.shape[0]
+        agg, rp, col, val = ctx.export_level(l, info)
+        np.testing.assert_array_equal(rp, lv.A.indptr)
+        np.testing.assert_array_equal(col, lv.A.indices)
+        assert _nrel(val, lv.A.data) <= 1e-10
+        if l < info.levels - 1:
+            np.testing.assert_array_equal(agg, lv.agg)
+            prp, pcol, pval = ctx.export_prolongator(l, info)
+            np.testing.assert_array_equal(prp, lv.P.indptr)
+            np.testing.assert_array_equal(pcol, lv.P.indices)
+            assert _nrel(pval, lv.P.data) <= 1e-10
+    # one V(2,2) application
+    r = np.random.default_rng(7).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r, w.nu, w.nu)) <= 1e-10
+    # the first Newton correction J d = -Phi by FGMRES(30)
+    F = disc.residual(grid, soil, bc, w.kmean, p0, cst.saturation(p0, soil), dt, ks)
+    J = disc.jacobian(grid, soil, bc, w.kmean, p0, dt, ks)
+    x = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    s, st = ctx.krylov_solve(torch.tensor(-F, device="cuda"), x, kind=rb.KRYLOV_FGMRES, restart=30, eta=1e-7,
+                             maxit=200)
+    xr, its, ok, _ = krylov.fgmres(lambda v: J @ v, lambda v: amg.vcycle(h, v, w.nu, w.nu), -F, 1e-7, 200, 30)
+    assert ok and st.converged and abs(st.iterations - its) <= 1
+    assert _nrel(x.cpu().numpy(), xr) <= 1e-8
+    ctx.close()
+
+
+def test_mixed_step_of_the_512_workload_at_48_matches_fp64_oracle():
+    rb = _rb()
+    w = synth.WORKLOADS["richards512_mixed"]
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w, 48)
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=w.nu, nu2=w.nu, seed=w.amg_seed, coarse_max=w.coarse_max,
+                                  smooth_levels=w.smooth_levels)
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_MIXED)
+    pd = torch.tensor(p0, device="cuda")
+    st = ctx.step(pd, dts[0], opts)
+    prob = newton.Problem(grid, soil, bc, w.kmean, ks)
+    po, ost = newton.step(prob, p0, dts[0], newton.NewtonOptions(krylov="fcg", nu1=w.nu, nu2=w.nu,
+                                                                  amg_seed=w.amg_seed, coarse_max=w.coarse_max,
+                                                                  smooth_levels=w.smooth_levels))
+    assert st.converged and ost.converged
+    assert _nrel(pd.cpu().numpy(), po) <= 1e-8
+    # the FP32 hierarchy costs at most a few Krylov iterations over the FP64 one
+    assert st.linear_its <= 1.25 * ost.linear_its + 5
+    ctx.close()

@@ -81,7 +81,11 @@ BCS = {
 }
 
 
-@pytest.mark.parametrize("kmean", MEANS)
+SPLITS = [synth.kmean_split(synth.KMEAN_UPSTREAM, synth.KMEAN_HARMONIC),
+          synth.kmean_split(synth.KMEAN_GEOMETRIC, synth.KMEAN_ARITH)]
+
+
+@pytest.mark.parametrize("kmean", MEANS + SPLITS)
 @pytest.mark.parametrize("bcname", list(BCS))
 @pytest.mark.parametrize("dims", [(4, 4, 4), (3, 4, 5)])
 def test_jacobian_matches_finite_differences(kmean, bcname, dims):
@@ -394,3 +398,47 @@ def test_pins_catch_swapped_harmonic_mean_partials(monkeypatch):
     monkeypatch.setattr(disc, "face_mean_partials", bad)
     with pytest.raises(AssertionError):
         test_jacobian_matches_finite_differences(disc.KMEAN_HARMONIC, list(BCS)[0], (4, 4, 4))
+
+
+# ---------------------------------------------------------------- split horizontal/vertical mean (Sec. 2.1)
+
+@pytest.mark.parametrize("kmean", MEANS)
+def test_split_mean_of_one_kind_is_that_mean(kmean):
+    grid = synth.Grid(5, 4, 6)
+    p = _distinct_p(grid, 2)
+    ks = synth.ks_field(grid, 4, 1.0, (2.0, 2.0, 1.0))
+    s_old = cst.saturation(p + 0.5, SOIL)
+    bc = synth.BC(kind=(1, 0, 1, 0, 1, 1), value=(-30.0, 0, -35.0, 0, -50.0, -20.0))
+    sp_ = synth.kmean_split(kmean, kmean)
+    np.testing.assert_array_equal(disc.residual(grid, SOIL, bc, sp_, p, s_old, 0.9, ks),
+                                  disc.residual(grid, SOIL, bc, kmean, p, s_old, 0.9, ks))
+    np.testing.assert_array_equal(disc.jacobian_stencil(grid, SOIL, bc, sp_, p, 0.9, ks),
+                                  disc.jacobian_stencil(grid, SOIL, bc, kmean, p, 0.9, ks))
+    np.testing.assert_array_equal(disc.aux_stencil(grid, SOIL, bc, sp_, p, 0.9, ks),
+                                  disc.aux_stencil(grid, SOIL, bc, kmean, p, 0.9, ks))
+
+
+@pytest.mark.parametrize("h,v", [(synth.KMEAN_UPSTREAM, synth.KMEAN_HARMONIC), (synth.KMEAN_GEOMETRIC, synth.KMEAN_ARITH)])
+def test_split_mean_takes_the_horizontal_mean_across_x_y_faces_and_the_vertical_one_across_z(h, v):
+    sp_ = synth.kmean_split(h, v)
+    # a single horizontal layer with closed z faces has only x and y faces
+    layer = synth.Grid(6, 5, 1)
+    p = _distinct_p(layer, 5)
+    s_old = cst.saturation(p + 0.5, SOIL)
+    bc = synth.BC(kind=(1, 1, 1, 0, 0, 0), value=(-30.0, -20.0, -40.0, 0, 0, 0))
+    np.testing.assert_array_equal(disc.residual(layer, SOIL, bc, sp_, p, s_old, 0.9),
+                                  disc.residual(layer, SOIL, bc, h, p, s_old, 0.9))
+    # a vertical column with closed side faces has only z faces
+    col = synth.Grid(1, 1, 9)
+    p = _distinct_p(col, 6)
+    s_old = cst.saturation(p + 0.5, SOIL)
+    bc = synth.infiltration_bc(-20.7)
+    np.testing.assert_array_equal(disc.residual(col, SOIL, bc, sp_, p, s_old, 0.9),
+                                  disc.residual(col, SOIL, bc, v, p, s_old, 0.9))
+    # in 3D the split differs from both of its parts
+    g3 = synth.Grid(4, 4, 4)
+    p = _distinct_p(g3, 7)
+    s_old = cst.saturation(p + 0.5, SOIL)
+    r = disc.residual(g3, SOIL, synth.infiltration_bc(), sp_, p, s_old, 0.9)
+    assert not np.allclose(r, disc.residual(g3, SOIL, synth.infiltration_bc(), h, p, s_old, 0.9))
+    assert not np.allclose(r, disc.residual(g3, SOIL, synth.infiltration_bc(), v, p, s_old, 0.9))
