@@ -54,6 +54,16 @@ extern "C" {
 #define RICH_AGG_MIS2          0
 #define RICH_AGG_MATCHING      1
 
+/* V-cycle smoother (Sec. 5.2).  L1JACOBI: x <- x + D_l1^-1 (b - A x), D_l1 the row
+ * l1 norms.  HYBRID_GS: the paper's hybrid backward/forward Gauss-Seidel (Sec. 6:
+ * backward sweeps before, forward sweeps after the coarse correction) -- Gauss-Seidel
+ * inside the block of unknowns one GPU thread (or lane group) owns, Jacobi between
+ * blocks, scaled by a_ii + sum of |a_ij| over couplings to other blocks (the l1 form,
+ * convergent for any blocks); blocks are vertical column segments on the finest grid
+ * and runs of consecutive rows on coarser levels. */
+#define RICH_SMOOTH_L1JACOBI   0
+#define RICH_SMOOTH_HYBRID_GS  1
+
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
  * (eq. (upstream_mean)) K_U if p_U - p_L >= 0 else K_L with U the +d cell;
@@ -144,6 +154,10 @@ typedef struct {
                               locally dominant matching, log2(max_agg_size) pairing passes on the
                               successive pair graphs */
   int max_agg_size;        /* largest aggregate of the matching (8, as in the paper's runs) */
+  int smoother;            /* RICH_SMOOTH_L1JACOBI (default) or RICH_SMOOTH_HYBRID_GS */
+  int hgs_seg;             /* hybrid Gauss-Seidel blocks on the finest grid: segments of this many cells of
+                              one vertical column (16) */
+  int hgs_block;           /* hybrid Gauss-Seidel blocks on coarser levels: this many consecutive rows (16) */
   int isolated_join;       /* MIS-2 pass 3 (1, default): a node without strong neighbours whose row is not
                               diagonally dominant (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
                               aggregated neighbour j with the largest (fp32 |a_ij|, key(j)); dominant rows

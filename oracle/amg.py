@@ -378,6 +378,10 @@ class Hierarchy:
     def __init__(self, levels, chol):
         self.levels = levels
         self.chol = chol  # lower Cholesky factor of the coarsest matrix
+        self.smoother = "l1jacobi"
+        self.grid = None        # (nx, ny, nz) of level 0, for the hybrid GS blocks there
+        self.hgs_seg = 16
+        self.hgs_block = 16
 
     @property
     def sizes(self):
@@ -388,12 +392,15 @@ class Hierarchy:
 
 
 def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, smooth_levels=10,
-          aggregation="mis2", max_agg_size=8, isolated_join=True):
+          aggregation="mis2", max_agg_size=8, isolated_join=True, smoother="l1jacobi", grid=None,
+          hgs_seg=16, hgs_block=16):
     """Build the hierarchy from a symmetric positive definite CSR matrix.
 
     aggregation: "mis2" (strength graph + MIS-2 roots) or "matching"
     (compatible weighted matching, aggregates of at most max_agg_size).
     isolated_join: pass 3 of the MIS-2 aggregation (module docstring).
+    smoother: "l1jacobi" or "hgs" (hybrid Gauss-Seidel, hybrid_blocks and
+    hybrid_gs_sweep; grid = (nx, ny, nz) of the finest level).
     """
     levels = [Level(A)]
     while True:
@@ -417,7 +424,9 @@ def setup(A, theta=0.08, seed=1, coarse_max=2000, max_levels=10, max_ratio=0.8, 
         Ac = spgemm(R, spgemm(lv.A, P))
         lv.S, lv.agg, lv.P, lv.R, lv.mis_rounds = S, agg, P, R, rounds
         levels.append(Level(Ac))
-    return Hierarchy(levels, _coarse_factor(levels[-1].A))
+    h = Hierarchy(levels, _coarse_factor(levels[-1].A))
+    h.smoother, h.grid, h.hgs_seg, h.hgs_block = smoother, grid, hgs_seg, hgs_block
+    return h
 
 
 def _coarse_factor(A):
@@ -455,8 +464,68 @@ def refresh(h, A):
     h.chol = _coarse_factor(h.levels[-1].A)
 
 
+# ---------------------------------------------------------------- hybrid Gauss-Seidel smoother
+# The paper's AMG smoother (Sec. 5.2 and the setup of Sec. 6) is one sweep of
+# "hybrid" backward/forward Gauss-Seidel as pre/post-smoother: Gauss-Seidel
+# within the block of unknowns one process owns, Jacobi between blocks.  Here a
+# block is what one GPU thread (or lane group) owns:
+#   level 0 (the 7-point grid): a segment of hgs_seg consecutive cells of one
+#           vertical column, (i, j, k0 .. k0 + hgs_seg - 1), k0 a multiple of hgs_seg;
+#   coarser levels: hgs_block consecutive rows.
+# Inside a block the unknowns are visited in increasing (forward) or decreasing
+# (backward) index order and use the values already updated in this sweep;
+# unknowns of other blocks enter with their values from before the sweep.  The
+# scaling is the l1 form of hybrid Gauss-Seidel (Baker, Falgout, Kolev, Yang,
+# "Multigrid smoothers for ultraparallel computing", SIAM J. Sci. Comput. 2011):
+# a_ii + sum over couplings to other blocks of |a_ij|, which makes every sweep
+# convergent for SPD matrices whatever the blocks.  With pre = backward and post =
+# forward sweeps the V-cycle stays a symmetric operator.
+
+def hybrid_blocks(n, level, grid=None, seg=16, block=16):
+    """(block id, position inside the block) of every node of a level."""
+    idx = np.arange(n, dtype=np.int64)
+    if level == 0 and grid is not None:
+        nx, ny, nz = grid
+        plane = nx * ny
+        k = idx // plane
+        return (idx % plane) + plane * (k // seg), k % seg
+    return idx // block, idx % block
+
+
+def hybrid_gs_sweep(A, b, x, block_id, pos, forward):
+    """One hybrid Gauss-Seidel sweep from x (x = None: from zero); returns the new x."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    same = block_id[rows] == block_id[A.indices]
+    A_in = sp.csr_matrix((np.where(same, A.data, 0.0), A.indices, A.indptr), shape=A.shape)
+    A_off = sp.csr_matrix((np.where(same, 0.0, A.data), A.indices, A.indptr), shape=A.shape)
+    d = A.diagonal() + np.bincount(rows, weights=np.where(same, 0.0, np.abs(A.data)), minlength=n)
+    x_old = np.zeros(n) if x is None else np.asarray(x, dtype=np.float64)
+    x_new = x_old.copy()
+    positions = range(int(pos.max()) + 1) if n else range(0)
+    for t in (positions if forward else reversed(positions)):
+        R = np.flatnonzero(pos == t)
+        r = b[R] - A_in[R] @ x_new - A_off[R] @ x_old
+        x_new[R] = x_new[R] + r / d[R]
+    return x_new
+
+
+def _smooth(h, level, b, x, forward):
+    lv = h.levels[level]
+    if h.smoother == "hgs":
+        bid, pos = hybrid_blocks(lv.A.shape[0], level, h.grid, h.hgs_seg, h.hgs_block)
+        return hybrid_gs_sweep(lv.A, b, x, bid, pos, forward)
+    if x is None:
+        return b / lv.dl1
+    return x + (b - lv.A @ x) / lv.dl1
+
+
 def vcycle(h, b, nu1=1, nu2=1, level=0):
-    """One symmetric V-cycle x = B b, zero initial guess (eq. (Vcycle))."""
+    """One symmetric V-cycle x = B b, zero initial guess (eq. (Vcycle)).
+
+    Pre-smoothing: nu1 l1-Jacobi sweeps, or nu1 backward hybrid Gauss-Seidel
+    sweeps; post-smoothing: nu2 sweeps (forward for hybrid Gauss-Seidel)."""
     lv = h.levels[level]
     if level == len(h.levels) - 1:
         if h.chol is not None:
@@ -465,12 +534,14 @@ def vcycle(h, b, nu1=1, nu2=1, level=0):
         for _ in range(COARSE_SWEEPS):
             x = x + (b - lv.A @ x) / lv.dl1
         return x
-    x = np.zeros_like(b)
+    x = None
     for _ in range(nu1):
-        x = x + (b - lv.A @ x) / lv.dl1
+        x = _smooth(h, level, b, x, forward=False)
+    if x is None:
+        x = np.zeros_like(b)
     r = b - lv.A @ x
     xc = vcycle(h, lv.R @ r, nu1, nu2, level + 1)
     x = x + lv.P @ xc
     for _ in range(nu2):
-        x = x + (b - lv.A @ x) / lv.dl1
+        x = _smooth(h, level, b, x, forward=True)
     return x

@@ -69,6 +69,9 @@ class NewtonOptions:
     armijo_c: float = 1e-4
     lambda_min: float = 1e-10
     isolated_join: bool = True    # pass 3 of the MIS-2 aggregation (amg module docstring)
+    smoother: str = "l1jacobi"    # or "hgs": hybrid backward/forward Gauss-Seidel (amg module)
+    hgs_seg: int = 16
+    hgs_block: int = 16
     max_dt_halvings: int = 0      # time-step control (advance); 0 = off
 
 
@@ -196,7 +199,9 @@ def _step(prob, p, dt, opt, st):
         if prob.hierarchy is None or (opt.amg_policy == "rebuild_step" and r == 0):
             prob.hierarchy = amg.setup(A, opt.theta, opt.amg_seed, opt.coarse_max, opt.max_levels,
                                        smooth_levels=opt.smooth_levels, aggregation=opt.aggregation,
-                                       max_agg_size=opt.max_agg_size, isolated_join=opt.isolated_join)
+                                       max_agg_size=opt.max_agg_size, isolated_join=opt.isolated_join,
+                                       smoother=opt.smoother, grid=(prob.grid.nx, prob.grid.ny, prob.grid.nz),
+                                       hgs_seg=opt.hgs_seg, hgs_block=opt.hgs_block)
         elif opt.amg_policy == "setup_once":
             amg.update_fine(prob.hierarchy, A)
         else:

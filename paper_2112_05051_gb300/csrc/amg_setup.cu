@@ -1774,6 +1774,10 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
   if (H.opts.max_levels < 1 || H.opts.max_levels > 16 || H.opts.nu1 < 0 || H.opts.nu2 < 0 || H.opts.coarse_max < 1)
     return RICH_EINVAL;
   if (H.opts.aggregation != RICH_AGG_MIS2 && H.opts.aggregation != RICH_AGG_MATCHING) return RICH_EINVAL;
+  if (H.opts.smoother != RICH_SMOOTH_L1JACOBI && H.opts.smoother != RICH_SMOOTH_HYBRID_GS) return RICH_EINVAL;
+  if (H.opts.smoother == RICH_SMOOTH_HYBRID_GS && (H.opts.hgs_seg < 1 || H.opts.hgs_block < 1 ||
+                                                  H.opts.hgs_block > 4096))
+    return RICH_EINVAL;
   if (H.opts.aggregation == RICH_AGG_MATCHING && (H.opts.max_agg_size < 2 || H.opts.max_agg_size > 1024))
     return RICH_EINVAL;
   RICH_CHECK(refresh_a0_values(c));

@@ -347,6 +347,9 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->product_lists = 1;
   o->aggregation = RICH_AGG_MIS2;
   o->max_agg_size = 8;
+  o->smoother = RICH_SMOOTH_L1JACOBI;
+  o->hgs_seg = 16;
+  o->hgs_block = 16;
   o->isolated_join = 1;
 }
 

@@ -138,6 +138,106 @@ __global__ void __launch_bounds__(kLineThreads) k_st_smooth(GridP g, Stencil4<T>
   else xo[c] = xc + A.dinv[c] * (b[c] - ax);
 }
 
+// Hybrid Gauss-Seidel (the paper's smoother, Sec. 5.2 / Sec. 6): Gauss-Seidel inside
+// the block one thread (or lane group) owns, Jacobi between blocks, scaled by
+// a_ii + sum over couplings to other blocks of |a_ij| (the l1 form).  x == nullptr
+// sweeps from zero; xo receives the new values (blocks read only x for each other).
+//
+// Finest level: a block is a segment of `seg` cells of one vertical column; the
+// thread walks it upward (FWD) or downward carrying the new value of the cell just
+// updated, so the in-block coupling costs no extra load.  Launch: blockIdx.x over
+// (j, segment), blockIdx.y over x tiles, threadIdx.x = i (coalesced in x).
+template <class T, bool FWD>
+__global__ void __launch_bounds__(kLineThreads) k_hgs_st(GridP g, Stencil4<T> A, int seg, const T* __restrict__ b,
+                                                         const T* __restrict__ x, T* __restrict__ xo) {
+  int i = blockIdx.y * kLineThreads + threadIdx.x;
+  if (i >= g.nx) return;
+  int r = blockIdx.x;
+  int j = r % g.ny;
+  int k0 = (r / g.ny) * seg;
+  int k1 = min(g.nz, k0 + seg);
+  int nx = g.nx;
+  int sxy = g.nx * g.ny;
+  T carry = T(0);
+  for (int q = 0; q < k1 - k0; ++q) {
+    int k = FWD ? k0 + q : k1 - 1 - q;
+    int c = (k * g.ny + j) * nx + i;
+    T xc = x ? x[c] : T(0);
+    T ax = A.diag[c] * xc;
+    T d = A.diag[c];
+    T w;
+    if (i > 0) { w = A.wx[c - 1]; ax -= w * (x ? x[c - 1] : T(0)); d += w; }
+    if (i < nx - 1) { w = A.wx[c]; ax -= w * (x ? x[c + 1] : T(0)); d += w; }
+    if (j > 0) { w = A.wy[c - nx]; ax -= w * (x ? x[c - nx] : T(0)); d += w; }
+    if (j < g.ny - 1) { w = A.wy[c]; ax -= w * (x ? x[c + nx] : T(0)); d += w; }
+    if (k > 0) {
+      w = A.wz[c - sxy];
+      if (k - 1 >= k0) ax -= w * (FWD ? carry : (x ? x[c - sxy] : T(0)));  // in block: new below (FWD)
+      else { ax -= w * (x ? x[c - sxy] : T(0)); d += w; }
+    }
+    if (k < g.nz - 1) {
+      w = A.wz[c];
+      if (k + 1 < k1) ax -= w * (FWD ? (x ? x[c + sxy] : T(0)) : carry);  // in block: new above (backward)
+      else { ax -= w * (x ? x[c + sxy] : T(0)); d += w; }
+    }
+    T xn = xc + (b[c] - ax) / d;
+    xo[c] = xn;
+    carry = xn;
+  }
+}
+
+// Coarser levels: a block is `bs` consecutive rows, walked by one group of G lanes
+// (rows of tens to hundreds of entries); lane 0 writes each new value and the group
+// synchronises before the next row reads it.
+template <class T, bool FWD, int G>
+__global__ void k_hgs_csr(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+                          int bs, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo) {
+  int lane = threadIdx.x & (G - 1);
+  unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1)));
+  int nblk = (n + bs - 1) / bs;
+  int groups = (gridDim.x * blockDim.x) / G;
+  for (int blk = (blockIdx.x * blockDim.x + threadIdx.x) / G; blk < nblk; blk += groups) {
+    int r0 = blk * bs;
+    int r1 = min(n, r0 + bs);
+    for (int q = 0; q < r1 - r0; ++q) {
+      int i = FWD ? r0 + q : r1 - 1 - q;
+      T s = 0, d = 0;
+      for (int e = rp[i] + lane; e < rp[i + 1]; e += G) {
+        int jj = col[e];
+        T a = val[e];
+        T xv;
+        if (jj >= r0 && jj < r1) {
+          bool updated = FWD ? jj < i : jj > i;
+          xv = updated ? xo[jj] : (x ? x[jj] : T(0));
+          if (jj == i) d += a;
+        } else {
+          xv = x ? x[jj] : T(0);
+          d += a < T(0) ? -a : a;
+        }
+        s += a * xv;
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        s += __shfl_down_sync(mask, s, o, G);
+        d += __shfl_down_sync(mask, d, o, G);
+      }
+      if (lane == 0) xo[i] = (x ? x[i] : T(0)) + (b[i] - s) / d;
+      __syncwarp(mask);
+    }
+  }
+}
+
+template <class T, bool FWD>
+static void hgs_csr(cudaStream_t st, int n, long long nnz, const int* rp, const int* col, const T* val, int bs,
+                    const T* b, const T* x, T* y) {
+  double avg = n > 0 ? (double)nnz / n : 0.0;
+  long long nblk = (n + bs - 1) / bs;
+  if (avg > 64) k_hgs_csr<T, FWD, 32><<<grid_for(nblk * 32), kBlock, 0, st>>>(n, rp, col, val, bs, b, x, y);
+  else if (avg > 24) k_hgs_csr<T, FWD, 16><<<grid_for(nblk * 16), kBlock, 0, st>>>(n, rp, col, val, bs, b, x, y);
+  else if (avg > 10) k_hgs_csr<T, FWD, 8><<<grid_for(nblk * 8), kBlock, 0, st>>>(n, rp, col, val, bs, b, x, y);
+  else k_hgs_csr<T, FWD, 4><<<grid_for(nblk * 4), kBlock, 0, st>>>(n, rp, col, val, bs, b, x, y);
+}
+
 template <class T>
 static const Stencil4<T>& fine(rich_ctx* c);
 template <>
@@ -178,6 +278,90 @@ const double* coarse_inv<double>(rich_ctx* c) { return c->H.cdense; }
 template <>
 const float* coarse_inv<float>(rich_ctx* c) { return c->H.cinv32; }
 
+template <class T>
+static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres);
+
+// One hybrid Gauss-Seidel sweep on level l (x == nullptr: from zero) into xo.
+template <class T>
+static int hgs_sweep(rich_ctx* c, int l, bool forward, const T* b, const T* x, T* xo) {
+  Hierarchy& H = c->H;
+  Level& L = H.lv[l];
+  const double es = sizeof(T);
+  if (l == 0) {
+    const GridP& g = c->g;
+    int nseg = (g.nz + H.opts.hgs_seg - 1) / H.opts.hgs_seg;
+    dim3 grid((unsigned)((long long)g.ny * nseg), (unsigned)((g.nx + kLineThreads - 1) / kLineThreads), 1);
+    ProfScope ps("hgs_l0", c->st, (double)g.n * (x ? 8.0 : 7.0) * es, 20.0 * (double)g.n);
+    if (forward) k_hgs_st<T, true><<<grid, kLineThreads, 0, c->st>>>(g, fine<T>(c), H.opts.hgs_seg, b, x, xo);
+    else k_hgs_st<T, false><<<grid, kLineThreads, 0, c->st>>>(g, fine<T>(c), H.opts.hgs_seg, b, x, xo);
+  } else {
+    LevelView<T> v = view<T>(c, l);
+    ProfScope ps("hgs", c->st, (double)L.n * (4.0 + 3.0 * es) + (double)L.A.nnz * (4.0 + es), 4.0 * L.A.nnz);
+    if (forward) hgs_csr<T, true>(c->st, L.n, L.A.nnz, v.rp, v.col, v.val, H.opts.hgs_block, b, x, xo);
+    else hgs_csr<T, false>(c->st, L.n, L.A.nnz, v.rp, v.col, v.val, H.opts.hgs_block, b, x, xo);
+  }
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+// V-cycle level with hybrid Gauss-Seidel: nu1 backward sweeps (the first from zero),
+// residual, restriction, coarse correction, nu2 forward sweeps.
+template <class T>
+static int vcycle_level_hgs(rich_ctx* c, int l, const T* b, T** xres) {
+  Hierarchy& H = c->H;
+  Level& L = H.lv[l];
+  LevelView<T> v = view<T>(c, l);
+  int n = v.n;
+  int g = grid_for(n);
+  T* x = (T*)L.x;
+  T* t = (T*)L.t;
+  const double es = sizeof(T);
+  const bool st0 = (l == 0);
+  for (int s = 0; s < H.opts.nu1; ++s) {
+    RICH_CHECK(hgs_sweep<T>(c, l, false, b, s == 0 ? (const T*)nullptr : (const T*)x, t));
+    std::swap(x, t);
+  }
+  if (H.opts.nu1 == 0) RICH_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, c->st));
+  {
+    ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st,
+                 st0 ? (double)n * 7.0 * es : (double)n * (4.0 + 3.0 * es) + (double)L.A.nnz * (4.0 + es));
+    if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
+    else if (L.A.nnz > 6LL * n) csr_op<T, 3>(c->st, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r);
+    else k_resid<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, b, x, (T*)L.r);
+  }
+  RICH_LAUNCH_CHECK();
+  Level& C = H.lv[l + 1];
+  {
+    ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
+    if (L.R.nnz > 6LL * C.n)
+      csr_op<T, 0>(c->st, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr, (const T*)L.r,
+                   (T*)C.b);
+    else
+      k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
+  }
+  RICH_LAUNCH_CHECK();
+  T* xc = nullptr;
+  RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
+  {
+    ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
+    if (L.P.nnz > 6LL * n)
+      csr_op<T, 1>(c->st, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x);
+    else
+      k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
+  }
+  RICH_LAUNCH_CHECK();
+  for (int s = 0; s < H.opts.nu2; ++s) {
+    RICH_CHECK(hgs_sweep<T>(c, l, true, b, x, t));
+    std::swap(x, t);
+  }
+  if (x != (T*)L.x) {
+    L.t = L.x;
+    L.x = x;
+  }
+  *xres = x;
+  return RICH_OK;
+}
+
 // b is the level's right-hand side, the result is left in *xres (one of the level's buffers).
 template <class T>
 static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
@@ -212,6 +396,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   int nu1 = H.opts.nu1, nu2 = H.opts.nu2;
   // finest level: stencil form (4 coefficient arrays + b + x in, x out)
   const bool st0 = (l == 0);
+  if (H.opts.smoother == RICH_SMOOTH_HYBRID_GS) return vcycle_level_hgs<T>(c, l, b, xres);
   // warp-per-row CSR kernels where rows are long
   const bool wA = L.A.nnz > 6LL * n;
   const double st_bytes = (double)n * 8.0 * es;  // diag, 3 face weights, dinv, b, x in; x out

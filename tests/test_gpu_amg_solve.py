@@ -340,3 +340,47 @@ def test_matching_newton_step_matches_oracle():
         assert st.converged and ost.converged
     assert _nrel(pd.cpu().numpy(), po) <= 1e-8
     ctx.close()
+
+
+# ---------------------------------------------------------------- hybrid Gauss-Seidel smoother
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("dims,seg,block", [((18, 16, 20), 16, 16), ((33, 17, 9), 4, 5), ((12, 11, 40), 7, 16)])
+def test_hybrid_gs_vcycle_parity(prec, tol, dims, seg, block):
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem(dims, 12, 0)
+    ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+    ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+    info = ctx.amg_setup(rb.default_amg_opts(seed=3, coarse_max=150, smoother=rb.SMOOTH_HYBRID_GS, hgs_seg=seg,
+                                             hgs_block=block))
+    A = disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks)
+    h = amg.setup(A, 0.08, 3, 150, smoother="hgs", grid=(grid.nx, grid.ny, grid.nz), hgs_seg=seg, hgs_block=block)
+    assert info.levels == len(h.levels) >= 3
+    r = np.random.default_rng(2).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), amg.vcycle(h, r)) <= tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("workload,n,steps,prec", [("richards16_fp64", None, 3, 0), ("richards512_mixed", 24, 1, 1)])
+def test_hybrid_gs_newton_steps_match_oracle(workload, n, steps, prec):
+    rb = _rb()
+    w = synth.WORKLOADS[workload]
+    grid, soil, bc, ks, p0, dts = synth.workload_inputs(w, n)
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, seed=w.amg_seed, coarse_max=200, smooth_levels=w.smooth_levels,
+                                  smoother=rb.SMOOTH_HYBRID_GS)
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
+    pd = torch.tensor(p0, device="cuda")
+    prob = newton.Problem(grid, soil, bc, w.kmean, ks)
+    oopt = newton.NewtonOptions(krylov="fcg", amg_seed=w.amg_seed, coarse_max=200, smooth_levels=w.smooth_levels,
+                                smoother="hgs")
+    po = p0
+    for m in range(steps):
+        st = ctx.step(pd, dts[m], opts)
+        po, ost = newton.step(prob, po, dts[m], oopt)
+        assert st.converged and ost.converged
+        if prec == 0:
+            assert st.newton_its == ost.newton_its and abs(st.linear_its - ost.linear_its) <= st.newton_its
+    assert _nrel(pd.cpu().numpy(), po) <= 1e-8
+    ctx.close()

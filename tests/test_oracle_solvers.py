@@ -432,3 +432,105 @@ def test_pins_catch_a_vcycle_without_post_smoothing(monkeypatch):
     monkeypatch.setattr(amg, "vcycle", lambda h, b, nu1=1, nu2=1, level=0: orig(h, b, nu1, 0, level))
     with pytest.raises(AssertionError):
         test_hierarchy_coarsens_and_vcycle_is_symmetric_positive_contraction()
+
+
+# ---------------------------------------------------------------- hybrid Gauss-Seidel smoother (Sec. 5.2, Sec. 6)
+
+def _hgs_loop(A, b, x, block_id, pos, forward):
+    """The definition, one unknown at a time: blocks in any order, inside a block by
+    position, new values inside the block, values from before the sweep outside."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    x0 = np.zeros(n) if x is None else np.array(x, dtype=float)
+    x1 = x0.copy()
+    for blk in np.unique(block_id):
+        members = np.flatnonzero(block_id == blk)
+        members = members[np.argsort(pos[members])]
+        if not forward:
+            members = members[::-1]
+        for i in members:
+            s, d = b[i], 0.0
+            for e in range(A.indptr[i], A.indptr[i + 1]):
+                j, a = A.indices[e], A.data[e]
+                if j == i:
+                    d += a
+                if block_id[j] == block_id[i]:
+                    s -= a * x1[j]
+                else:
+                    s -= a * x0[j]
+                    d += abs(a)
+            x1[i] = x1[i] + s / d
+    return x1
+
+
+def test_hybrid_gs_with_one_block_is_textbook_gauss_seidel():
+    import scipy.sparse.linalg as spla
+    A = _aux(synth.Grid(6, 5, 4))
+    n = A.shape[0]
+    rng = np.random.default_rng(3)
+    b, x = rng.standard_normal(n), rng.standard_normal(n)
+    one = np.zeros(n, dtype=np.int64)
+    pos = np.arange(n)
+    fwd = amg.hybrid_gs_sweep(A, b, x, one, pos, True)
+    L = sp.tril(A, 0, format="csr")
+    np.testing.assert_allclose(fwd, x + spla.spsolve_triangular(L, b - A @ x, lower=True), rtol=1e-12, atol=1e-12)
+    bwd = amg.hybrid_gs_sweep(A, b, x, one, pos, False)
+    U = sp.triu(A, 0, format="csr")
+    np.testing.assert_allclose(bwd, x + spla.spsolve_triangular(U, b - A @ x, lower=False), rtol=1e-12, atol=1e-12)
+
+
+def test_hybrid_gs_with_singleton_blocks_is_l1_jacobi():
+    A = _aux(synth.Grid(5, 5, 5))
+    n = A.shape[0]
+    rng = np.random.default_rng(4)
+    b, x = rng.standard_normal(n), rng.standard_normal(n)
+    y = amg.hybrid_gs_sweep(A, b, x, np.arange(n), np.zeros(n, dtype=np.int64), True)
+    np.testing.assert_allclose(y, x + (b - A @ x) / amg.l1_diagonal(A), rtol=1e-13)
+
+
+@pytest.mark.parametrize("forward", [True, False])
+def test_hybrid_gs_sweep_equals_its_one_unknown_at_a_time_definition(forward):
+    grid = synth.Grid(5, 4, 7)
+    A = _aux(grid)
+    rng = np.random.default_rng(8)
+    b, x = rng.standard_normal(grid.n), rng.standard_normal(grid.n)
+    for level, seg in ((0, 3), (1, 5)):  # column segments of 3 cells; blocks of 5 rows
+        bid, pos = amg.hybrid_blocks(grid.n, level, (grid.nx, grid.ny, grid.nz), seg=seg, block=seg)
+        np.testing.assert_allclose(amg.hybrid_gs_sweep(A, b, x, bid, pos, forward),
+                                   _hgs_loop(A, b, x, bid, pos, forward), rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(amg.hybrid_gs_sweep(A, b, None, bid, pos, forward),
+                                   _hgs_loop(A, b, None, bid, pos, forward), rtol=1e-12, atol=1e-14)
+    # column segments: a block is (i, j) fixed, k in [k0, k0 + seg)
+    bid, pos = amg.hybrid_blocks(grid.n, 0, (grid.nx, grid.ny, grid.nz), seg=3)
+    c = np.arange(grid.n)
+    assert np.all(pos == (c // (grid.nx * grid.ny)) % 3)
+    assert len(np.unique(bid)) == grid.nx * grid.ny * 3
+
+
+def _hgs_hierarchy(grid, A, seg=4, block=6):
+    return amg.setup(A, coarse_max=40, smoother="hgs", grid=(grid.nx, grid.ny, grid.nz), hgs_seg=seg,
+                     hgs_block=block)
+
+
+def test_hybrid_gs_vcycle_is_symmetric_positive_and_beats_l1_jacobi():
+    grid = synth.Grid(14, 12, 16)
+    A = _aux(grid)
+    h = _hgs_hierarchy(grid, A)
+    assert len(h.levels) >= 3
+    n = grid.n
+    rng = np.random.default_rng(1)
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    assert abs(x @ amg.vcycle(h, y) - y @ amg.vcycle(h, x)) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(y) * 10
+    assert y @ amg.vcycle(h, y) > 0
+    b = rng.standard_normal(n)
+    _, its_g, ok_g, _ = krylov.fcg(lambda v: A @ v, lambda v: amg.vcycle(h, v), b, 1e-10, 200)
+    hj = amg.setup(A, coarse_max=40)
+    _, its_j, ok_j, _ = krylov.fcg(lambda v: A @ v, lambda v: amg.vcycle(hj, v), b, 1e-10, 200)
+    assert ok_g and ok_j and its_g < its_j
+
+
+def test_pins_catch_a_forward_pre_smoother(monkeypatch):
+    orig = amg._smooth
+    monkeypatch.setattr(amg, "_smooth", lambda h, level, b, x, forward: orig(h, level, b, x, True))
+    with pytest.raises(AssertionError):
+        test_hybrid_gs_vcycle_is_symmetric_positive_and_beats_l1_jacobi()
