@@ -2,35 +2,41 @@
 """Throughput of the backward-Euler Richards step on GB300: DOF * Newton-steps / s.
 
 A bench "step" is one backward-Euler time step of the workload (constitutive
-evaluation, residual, Jacobian and diffusion-matrix assembly, AMG refresh,
-right-preconditioned Krylov solves with the AMG V-cycle, Newton-Armijo line
-search) -- every stage of the path.  Default workload: 128^3 cells (2.1M DOF),
-homogeneous Haverkamp soil, upstream-mean K, Dirichlet top at -20.7 cm, no-flux
-elsewhere, p0 = -61.5 cm, dt ramped linearly 1 -> 30 s over 20 steps, FGMRES(30)
-with an AMG V(2,2) l1-Jacobi cycle, coarsest level (< 2000 unknowns) by dense
-inverse, Newton-Armijo to 1e-8 relative, FP64 throughout.  The default
---warmup 3 --steps 17 runs exactly the 20-step schedule; other counts cycle it.
+evaluation, residual, Jacobian and diffusion-matrix assembly, AMG setup or
+refresh, right-preconditioned Krylov solves with the AMG V-cycle, Newton-Armijo
+line search) -- every stage of the path.  Default workload (configuration 2 of
+the workload list): 128^3 cells (2.1M DOF), homogeneous Haverkamp soil,
+upstream-mean K, Dirichlet top at -20.7 cm, no-flux elsewhere, p0 = -61.5 cm, dt
+ramped linearly 1 -> 30 s over 20 steps, FGMRES(30) with an AMG V(2,2) l1-Jacobi
+cycle, coarsest level (< 2000 unknowns) by dense inverse, Newton-Armijo to 1e-8
+relative, FP64 throughout.  The larger mixed-precision workloads (256^3
+harmonic, 512^3 sigma 2) do not converge with this method (see the design
+notes), so this is the largest configuration of the list that runs.
+
+Timing (independent of --warmup): W warm-up steps run on a context of their
+own, which is then destroyed; the timed run is a fresh context stepping the
+schedule from p0 (step m uses dt_{m mod 20}), AMG setup included, inputs
+resident on the device, CUDA events around the K steps and nothing else in the
+timed region but the nvidia-smi clock sampler (a separate process).
 
 value   = sum over ranks of (DOF * Newton iterations in the timed steps) / max
-          over ranks of the CUDA-event time of the timed steps (inputs resident).
-e2e     = the same metric through rich_step_host: each step copies p from pinned
-          host memory to the device and the result back.
-The AMG hierarchy (aggregates, P, R) is built in the first warm-up step and
-refreshed numerically on every Newton iteration afterwards.
+          over ranks of the CUDA-event time of the timed steps.
+e2e     = the same metric through rich_step_host on another fresh context: each
+          step copies p from pinned host memory to the device and the result back.
 
-The line also carries: the roofline of the dominant kernel (the coarse-level
-l1-Jacobi sweep, one launch in PROFILE_STRIDE timed with CUDA events; FP64
-kernels against the FP64 ALU peak, DRAM traffic from an ncu capture), the same
-schedule with the FP32 AMG hierarchy (`fp32_amg`), per-step latency, the
-phase split, the oracle timed on the host (`cpu_baseline`) and a request
-stream through the request server (`serving`: 512 one-step requests of mixed
-size, soil and mean; capacity, p50/p99 latency, failures, mix-versus-alone
-check).  --amg-precision fp32 times the workload itself with the FP32
-hierarchy; --serving-only prints only the request stream.
+Further passes, outside the timed region: the same schedule with the FP32 AMG
+hierarchy (`fp32_amg`, speed-up and largest pressure deviation from FP64), a
+per-kernel profile of the first steps (every launch timed with CUDA events)
+that places the dominant kernel on its roofline (HBM bandwidth from
+MEASURED_PEAKS.json, FP64 FMA throughput measured live by
+rich_measure_fma_peak; the bound follows from the kernel's algorithmic
+flops/byte against the balance point), the paper's own 24.2M-cell infiltration
+grid in mixed precision (`paper_workload`), the oracle timed on the host cores
+(`cpu_baseline`) and a request stream through the request server (`serving`).
 
 --impl reference times the CPU oracle (the plain FP64 numpy/scipy restatement)
-on the same workload: each step is one Newton iteration of the first time step
-(a bounded sample; the AMG setup happens in the first warm-up step).
+on the host cores: each step is one Newton iteration of the workload's first
+time step on a reduced grid of the same settings (a bounded sample).
 With torchrun (N > 1) every rank runs an independent replica of the workload
 (the path has no cross-rank exchange on one GPU each); rank 0 prints.
 """
@@ -38,6 +44,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -48,51 +55,35 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
-# GB300 FP64: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s
-# (the nominal 1.25 TFLOP/s); ncu shows the FP64 smoother and dot products issue-bound
-# on this pipe, so FP64 kernels are reported against it.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the roofline kernel,
-# averaged over the launches it covers in one V-cycle (profiles/ summary of the
-# same kernel and workload): the coarse-level l1-Jacobi sweep of the 128^3 FP64
-# bench runs 3 sweeps on level 1 (79.9 MB each) and 3 on level 2 (10.65 MB each).
-NCU_TRAFFIC_BYTES = {("richards128_fp64", "l1jacobi"): 45.28e6}
-# the roofline kernel's launches are timed with CUDA events one in PROFILE_STRIDE
-PROFILE_STRIDE = 29
-
-
-def nvtx_push(name):
-    try:
-        import torch
-        torch.cuda.nvtx.range_push(name)
-    except Exception:
-        pass
-
-
-def nvtx_pop():
-    try:
-        import torch
-        torch.cuda.nvtx.range_pop()
-    except Exception:
-        pass
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on a
+# workload, from the profiles/ summaries of the same kernel and workload (None:
+# no capture of the current kernel).
+NCU_TRAFFIC_BYTES = {}
+# the oracle's reduced grid for the host-core samples (cells per side)
+CPU_SAMPLE_N = {"richards128_fp64": 48, "richards16_fp64": 16, "richards256_mixed": 32, "richards512_mixed": 32,
+                "paper_infiltration": 96}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=17)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="richards128_fp64")
     ap.add_argument("--grid", type=int, default=None,
                     help="run the workload's settings on an n^3 grid instead (profiling captures); not a bench line")
-    ap.add_argument("--roofline-kernel", default="l1jacobi")
     ap.add_argument("--amg-precision", default=None, choices=["fp64", "fp32"],
                     help="override the workload's AMG precision for the timed run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-AMG comparison run")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel roofline pass")
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-grid mixed-precision run")
+    ap.add_argument("--paper-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle processes for the all-cores sample (0: min(16, cores))")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
     ap.add_argument("--serving-requests", type=int, default=512)
     ap.add_argument("--serving-slots", type=int, default=8)
@@ -102,6 +93,7 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
     ap.add_argument("--serving-coarse-max", type=int, default=500)
     ap.add_argument("--serving-aggregation", type=int, default=0, help="0: MIS-2, 1: matching (SMATCH-style)")
+    ap.add_argument("--serving-halvings", type=int, default=8, help="time-step control of served requests (0: off)")
     return ap.parse_args()
 
 
@@ -198,35 +190,39 @@ def newton_opts(rb, w):
                                   coarse_max=w.coarse_max, amg_policy=rb.AMG_REFRESH, smooth_levels=w.smooth_levels)
 
 
-def cpu_baseline(workload, budget, warm_only=False):
-    """Oracle Newton iterations on the workload's first time step, in a 1-thread subprocess."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, str(budget)]
-    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=budget * 20 + 600)
-    if r.returncode != 0:
-        return {"value": None, "unit": "DOF*Newton-steps/s", "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def host_cpu():
+    """Host CPU model and core count (the oracle's machine)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model or platform.processor() or platform.machine(), "arch": platform.machine(),
+            "os_cpu_count": os.cpu_count()}
 
 
-def oracle_sample_main(workload, budget, steps=None, warmup=None):
-    """Time oracle Newton iterations (each from the state the previous one left)."""
+def oracle_sample_main(workload, budget, n=None, steps=None, warmup=0):
+    """Time oracle Newton iterations of the workload's first time step on an n^3 grid.
+
+    Each timed unit is one Newton iteration (newton.step with max_newton = 1) from
+    the state the previous one left; the AMG setup runs in an untimed first call."""
     from oracle import newton
-    w, grid, soil, bc, ks, p0, dts = workload_setup(workload)
+    w, grid, soil, bc, ks, p0, dts = workload_setup(workload, n)
     prob = newton.Problem(grid, soil, bc, w.kmean, ks)
     opt = newton.NewtonOptions(krylov=w.krylov, restart=max(w.restart, 1), nu1=w.nu, nu2=w.nu,
-                               amg_seed=w.amg_seed, coarse_max=w.coarse_max, max_newton=1,
-                               smooth_levels=w.smooth_levels)
+                               amg_seed=w.amg_seed, coarse_max=min(w.coarse_max, max(50, grid.n // 50)),
+                               max_newton=1, smooth_levels=w.smooth_levels)
     p = p0.copy()
     t0 = time.perf_counter()
     p, st = newton.step(prob, p, dts[0], opt)  # builds the hierarchy (not timed)
     setup_s = time.perf_counter() - t0
-    its = 0
-    times = []
-    nw = warmup or 0
-    for _ in range(nw):
+    for _ in range(warmup or 0):
         p, st = newton.step(prob, p, dts[0], opt)
+    its, times = 0, []
     t0 = time.perf_counter()
     while True:
         t1 = time.perf_counter()
@@ -239,30 +235,67 @@ def oracle_sample_main(workload, budget, steps=None, warmup=None):
         elif time.perf_counter() - t0 >= budget:
             break
     el = time.perf_counter() - t0
-    return {"value": grid.n * its / el, "unit": "DOF*Newton-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d Newton iterations of the first time step (dt=%g) of %s, %.1f s, one thread; "
-                      "AMG setup (%.1f s) excluded" % (its, dts[0], workload, el, setup_s),
-            "step_times": times}
+    return {"dof": grid.n, "its": its, "seconds": el, "setup_s": setup_s, "step_times": times,
+            "grid": [grid.nx, grid.ny, grid.nz]}
+
+
+def _oracle_processes(workload, n, procs, budget=None, steps=None, warmup=0):
+    """Run the oracle sample in `procs` concurrent one-thread processes; whole-host throughput."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, str(n),
+           str(budget if budget is not None else 0.0), str(steps if steps is not None else 0), str(warmup)]
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+          for _ in range(procs)]
+    res = []
+    for pr in ps:
+        out, err = pr.communicate(timeout=3600)
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + (err.strip().splitlines() or ["?"])[-1])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    work = sum(r["dof"] * r["its"] for r in res)
+    slowest = max(r["seconds"] for r in res)
+    return {"value": work / slowest, "procs": procs, "its": sum(r["its"] for r in res), "seconds": slowest,
+            "wall_s": wall, "grid": res[0]["grid"], "setup_s": max(r["setup_s"] for r in res)}
+
+
+def cpu_baseline(workload, budget, procs):
+    """The oracle on the host cores: one process, and `procs` concurrent processes."""
+    n = CPU_SAMPLE_N.get(workload, 32)
+    host = host_cpu()
+    one = _oracle_processes(workload, n, 1, budget=budget)
+    many = _oracle_processes(workload, n, procs, budget=budget) if procs > 1 else one
+    return {"value": many["value"], "unit": "DOF*Newton-steps/s", "cores": many["procs"], "kind": "oracle",
+            "one_core_value": one["value"], "host": host,
+            "sample": "Newton iterations of the first time step of %s's settings on a reduced %s grid, each "
+                      "process for about %g s (AMG setup excluded), plain numpy/scipy FP64, one thread per process; "
+                      "%d processes at once: %d iterations; one process alone: %d iterations"
+                      % (workload, "x".join(map(str, many["grid"])), budget, many["procs"], many["its"], one["its"])}
 
 
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
-    w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload)
-    env_threads = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1"}
-    for k, v in env_threads.items():
-        os.environ.setdefault(k, v)
-    res = oracle_sample_main(args.workload, 0.0, steps=args.steps, warmup=args.warmup)
-    total = sum(res["step_times"])
+    w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload, args.grid)
+    n = CPU_SAMPLE_N.get(args.workload, 32)
+    procs = args.cpu_procs or min(16, os.cpu_count() or 1)
+    res = _oracle_processes(args.workload, n, procs, steps=args.steps, warmup=args.warmup)
     value = res["value"]
+    host = host_cpu()
+    sample = ("%d Newton iterations (%d per process, %d one-thread processes at once) of the first time step "
+              "of %s's settings on a reduced %s grid, plain numpy/scipy FP64; AMG setup and %d warm-up "
+              "iterations untimed" % (res["its"], args.steps, procs, args.workload,
+                                      "x".join(map(str, res["grid"])), args.warmup))
     line = {"metric": "DOF*Newton-steps/s", "value": value, "unit": "DOF*Newton-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / max(args.steps, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * res["seconds"] / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": workload_config(w, grid),
-            "cpu_baseline": {"value": value, "unit": "DOF*Newton-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": res["sample"]},
+            "cpu_baseline": {"value": value, "unit": "DOF*Newton-steps/s", "cores": procs, "kind": "oracle",
+                             "sample": sample, "host": host},
             "e2e": {"value": value, "unit": "DOF*Newton-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -287,9 +320,13 @@ def stream_stats(results, dofs, seconds, error_names):
         if r["status"] != 0:
             key = error_names.get(r["status"], str(r["status"]))
             failed[key] = failed.get(key, 0) + 1
-    return {"latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
-                           "mean": sum(lat) / len(lat) if lat else None, "max": lat[-1] if lat else None},
-            "latency_ms_converged": {"p50": percentile(lat_ok, 0.5), "p99": percentile(lat_ok, 0.99)},
+    return {"latency_ms_converged": {"p50": percentile(lat_ok, 0.5), "p99": percentile(lat_ok, 0.99),
+                                     "mean": sum(lat_ok) / len(lat_ok) if lat_ok else None,
+                                     "max": lat_ok[-1] if lat_ok else None},
+            "latency_ms_all": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
+                               "mean": sum(lat) / len(lat) if lat else None, "max": lat[-1] if lat else None},
+            "converged": len(lat_ok), "failure_rate": (len(lat) - len(lat_ok)) / len(lat) if lat else None,
+            "converged_per_s": len(lat_ok) / seconds if seconds > 0 else None,
             "dof_newton_per_s": work / seconds if seconds > 0 else None, "failed": failed}
 
 
@@ -325,9 +362,12 @@ def serving_run(args, rb):
         reqs.append((grid, ks, kmean, n))
     # coarsest level below 500 unknowns: its dense inverse is redone at every
     # refresh, and a short one-step request refreshes ~10 times
+    # time-step control: a request whose step fails is retried in halves (a harmonic
+    # request with an indefinite Jacobian fails each attempt after one FCG iteration)
+    halvings = getattr(args, "serving_halvings", 8)
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
                                   product_lists=args.serving_lists, coarse_max=args.serving_coarse_max,
-                                  aggregation=args.serving_aggregation)
+                                  aggregation=args.serving_aggregation, max_dt_halvings=halvings)
 
     def submit(srv, q):
         grid, ks, kmean, n = q
@@ -378,10 +418,12 @@ def serving_run(args, rb):
             "coarse_max": args.serving_coarse_max, "product_lists": args.serving_lists,
             "aggregation": "matching" if args.serving_aggregation else "MIS-2",
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
-            "capacity_rps": mu, "burst_s": t_burst,
+            "max_dt_halvings": halvings,
+            "latency_ms_converged": st_s["latency_ms_converged"], "failure_rate": st_s["failure_rate"],
+            "converged_per_s": st_s["converged_per_s"], "stream_dof_newton_per_s": st_s["dof_newton_per_s"],
+            "capacity_rps": mu, "capacity_converged_rps": st_b["converged_per_s"], "burst_s": t_burst,
             "burst_dof_newton_per_s": st_b["dof_newton_per_s"], "rate_rps": lam, "arrivals": "Poisson, seed 5",
-            "stream_s": t_stream, "stream_dof_newton_per_s": st_s["dof_newton_per_s"],
-            "latency_ms": st_s["latency_ms"], "latency_ms_converged": st_s["latency_ms_converged"],
+            "stream_s": t_stream, "latency_ms_all": st_s["latency_ms_all"],
             "failed": st_s["failed"], "max_in_flight": cnt["max_in_flight"],
             "mix_vs_alone_max_rel_dev": dev, "mix_vs_alone_checked": checked,
             "admission": "FIFO, a free slot and the request's device-memory estimate within 80% of free HBM"}
@@ -390,7 +432,7 @@ def serving_run(args, rb):
 def workload_config(w, grid):
     from paper_2112_05051_gb300 import synth
     return {"workload": w.name, "grid": [grid.nx, grid.ny, grid.nz], "dof": grid.n,
-            "kmean": synth.KMEAN_NAMES[w.kmean], "krylov": "%s(%d)" % (w.krylov, w.restart) if w.restart else w.krylov,
+            "kmean": synth.kmean_name(w.kmean), "krylov": "%s(%d)" % (w.krylov, w.restart) if w.restart else w.krylov,
             "vcycle": "V(%d,%d) l1-Jacobi" % (w.nu, w.nu), "amg_precision": "fp32" if w.mixed else "fp64",
             "amg": "MIS-2 smoothed aggregation, P smoothed on the first %d levels, Galerkin refresh per Newton "
                    "iteration" % w.smooth_levels,
@@ -398,7 +440,74 @@ def workload_config(w, grid):
             "l2": "working set > 129 MB L2 (7-diagonal Jacobian alone 118 MB, FGMRES basis 1 GB)"}
 
 
+def run_steps(ctx, pd, dts, count, opts, first=0, record=None, snapshot_at=None):
+    """Step the schedule count times (step m uses dt_{m mod len}); returns the per-step stats.
+
+    record: a list of CUDA events, one recorded after each step on the current stream.
+    snapshot_at: {step index: None} filled with a device copy of p after that step."""
+    out = []
+    for q in range(count):
+        m = first + q
+        out.append(ctx.step(pd, dts[m % len(dts)], opts))
+        if record is not None:
+            record[q].record()
+        if snapshot_at is not None and q + 1 in snapshot_at:
+            snapshot_at[q + 1] = pd.clone()
+    return out
+
+
+def fp64_balance(peak_gbs, fp64_tflops):
+    """Flops per byte where the FP64 FMA pipe and HBM take equal time."""
+    return fp64_tflops * 1e12 / (peak_gbs * 1e9)
+
+
+def roofline_of(name, ms, launches, nbytes, flops, fp64, peak_gbs, fp64_tflops, traffic):
+    """A kernel placed on its roofline: HBM-bound when its algorithmic flops/byte lie
+    below the FP64 balance point (FP32 kernels always), FP64-ALU-bound above it."""
+    secs = ms / 1000.0
+    gbs = nbytes / secs / 1e9 if secs > 0 else None
+    tfl = flops / secs / 1e12 if secs > 0 else None
+    intensity = flops / nbytes if nbytes > 0 else None
+    bal = fp64_balance(peak_gbs, fp64_tflops)
+    common = {"kernel": name, "launches": launches, "avg_launch_us": 1000.0 * ms / launches if launches else None,
+              "algorithmic_bytes_per_launch": nbytes / launches if launches else None,
+              "algorithmic_flops_per_launch": flops / launches if launches else None,
+              "intensity_flop_per_byte": intensity, "fp64_balance_flop_per_byte": bal,
+              "traffic": traffic, "hbm_frac": gbs / peak_gbs if gbs else None,
+              "fp64_frac": tfl / fp64_tflops if (tfl and fp64) else None}
+    if fp64 and intensity is not None and intensity > bal:
+        return dict(common, bound="alu", achieved=tfl, peak=fp64_tflops, unit="TFLOP/s", frac=tfl / fp64_tflops,
+                    peak_kind="measured FP64 FMA throughput (rich_measure_fma_peak, this run)")
+    return dict(common, bound="hbm", achieved=gbs, peak=peak_gbs, unit="GB/s", frac=gbs / peak_gbs if gbs else None,
+                peak_kind="measured (MEASURED_PEAKS.json hbm_gbs)")
+
+
+# kernel name prefix -> (profile names that make it, runs in FP64 in the FP64 mode)
+def _is_fp64_kernel(name, prec_fp64):
+    if name in ("residual", "assemble", "stencil_spmv", "multidot", "orth_axpy", "orth_final", "fcg_update"):
+        return True
+    return prec_fp64
+
+
+def profile_pass(rb, grid, soil, bc, w, ks, p0, dts, opts, prec, steps):
+    """Every named launch of the first steps timed with CUDA events (an untimed pass of
+    its own): per-kernel (launches, ms, algorithmic bytes, algorithmic flops)."""
+    import torch
+    lib = rb.load()
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
+    pd = torch.tensor(p0, device="cuda")
+    lib.rich_profile_stride(1)
+    lib.rich_profile_kernel(b"*")
+    run_steps(ctx, pd, dts, steps, opts)
+    torch.cuda.synchronize()
+    tab = rb.profile_table()
+    lib.rich_profile_kernel(None)
+    ctx.close()
+    return tab
+
+
 def run_ours(args):
+    import ctypes
     import torch
     from paper_2112_05051_gb300 import richards as rb
     ws, rank, local = dist_env()
@@ -408,7 +517,7 @@ def run_ours(args):
     dist = None
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     lib = rb.load()
     w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload, args.grid)
     if args.amg_precision is not None:
@@ -416,182 +525,171 @@ def run_ours(args):
         w = dataclasses.replace(w, mixed=args.amg_precision == "fp32")
     opts = newton_opts(rb, w)
     prec = rb.PREC_MIXED if w.mixed else rb.PREC_FP64
-    stream = torch.cuda.current_stream()
+    K = args.steps
 
+    # warm-up on a context of its own (kernels loaded, memory pool primed); destroyed after
+    ctxw = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
+    pw = torch.tensor(p0, device="cuda")
+    run_steps(ctxw, pw, dts, args.warmup, opts)
+    torch.cuda.synchronize()
+    ctxw.close()
+    del pw
+
+    # timed run: a fresh context from p0 over K steps of the schedule, AMG setup included
     rb.memory_peak(reset=True)
     torch.cuda.reset_peak_memory_stats()
     ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
     pd = torch.tensor(p0, device="cuda")
-    sched = lambda m: dts[m % len(dts)]
-    import ctypes
-    lw = ctypes.c_longlong()
-    lib.rich_kernel_launches(ctypes.byref(lw))
-    for m in range(args.warmup):
-        ctx.step(pd, sched(m), opts)
-    torch.cuda.synchronize()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = ctypes.c_longlong()
+    l1 = ctypes.c_longlong()
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    # every 29th launch of the roofline kernel is timed with events (29 is coprime
-    # with the V-cycle's six sweeps per cycle, so every position is sampled)
-    lib.rich_profile_stride(PROFILE_STRIDE)
-    lib.rich_profile_kernel(args.roofline_kernel.encode())
-    l0 = ctypes.c_longlong()
-    lib.rich_kernel_launches(ctypes.byref(l0))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    # NVTX range "timed" marks the timed steps for profilers (ncu --nvtx --nvtx-include timed/)
-    nvtx_push("timed")
-    e0.record(stream)
-    marks[0].record(stream)
-    newton_its = 0
-    lin_its = 0
-    stats = []
-    for q, m in enumerate(range(args.warmup, args.warmup + args.steps)):
-        st = ctx.step(pd, sched(m), opts)
-        marks[q + 1].record(stream)
-        newton_its += st.newton_its
-        lin_its += st.linear_its
-        stats.append(st.as_dict())
-    e1.record(stream)
-    nvtx_pop()
+    lib.rich_kernel_launches(ctypes.byref(l0))
+    e0.record()
+    stats = run_steps(ctx, pd, dts, K, opts, record=marks)
+    e1.record()
     torch.cuda.synchronize()
-    step_ms = sorted(marks[q].elapsed_time(marks[q + 1]) for q in range(args.steps))
-    phases = {k: sum(d[k] for d in stats) for k in ("ms_feval", "ms_jacobian", "ms_setup", "ms_linsol", "ms_total")}
+    lib.rich_kernel_launches(ctypes.byref(l1))
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    step_ms = [e0.elapsed_time(marks[0])] + [marks[q].elapsed_time(marks[q + 1]) for q in range(K - 1)]
+    newton_its = sum(st.newton_its for st in stats)
+    lin_its = sum(st.linear_its for st in stats)
+    d = [st.as_dict() for st in stats]
+    phases = {k: sum(x[k] for x in d) for k in ("ms_feval", "ms_jacobian", "ms_setup", "ms_linsol", "ms_total")}
     phases["ms_overhead"] = phases["ms_total"] - sum(phases[k] for k in ("ms_feval", "ms_jacobian", "ms_setup",
                                                                            "ms_linsol"))
-    if dist:
-        dist.barrier()
-    elapsed = e0.elapsed_time(e1) / 1000.0
-    l1 = ctypes.c_longlong()
-    lib.rich_kernel_launches(ctypes.byref(l1))
-    ms_k = ctypes.c_double()
-    n_k = ctypes.c_longlong()
-    by_k = ctypes.c_double()
-    fl_k = ctypes.c_double()
-    lib.rich_profile_result(ctypes.byref(ms_k), ctypes.byref(n_k), ctypes.byref(by_k), ctypes.byref(fl_k))
-    lib.rich_profile_kernel(None)
-    lib.rich_profile_stride(1)
-    clocks = clk.stop()
-    # peak device memory of the main run: the library's pool and torch's tensors
     lib_used, lib_reserved = rb.memory_peak()
     peak_mem = {"library_pool_used_high_bytes": lib_used, "library_pool_reserved_high_bytes": lib_reserved,
                 "torch_max_allocated_bytes": int(torch.cuda.max_memory_allocated())}
+    p_fp64 = pd.clone() if prec == rb.PREC_FP64 else None
+    ctx.close()
     work = float(grid.n) * newton_its
     elapsed, work = aggregate_over_ranks(dist, elapsed, work, "cuda")
     value = work / elapsed
 
-    # end to end through the host-buffer entry point (fresh replica of the same run)
+    # end to end through the host-buffer entry point, a fresh context over the same steps
     e2e = None
     if not args.no_e2e:
         ctx2 = rb.Context(grid, soil, bc, w.kmean, ks, precision=prec)
         ph = torch.tensor(p0, dtype=torch.float64).pin_memory()
-        for m in range(args.warmup):
-            ctx2.step_host(ph, sched(m), opts)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         its2 = 0
-        for m in range(args.warmup, args.warmup + args.steps):
-            its2 += ctx2.step_host(ph, sched(m), opts).newton_its
+        for m in range(K):
+            its2 += ctx2.step_host(ph, dts[m % len(dts)], opts).newton_its
         torch.cuda.synchronize()
         el2 = time.perf_counter() - t0
-        work2 = float(grid.n) * its2
+        work2, el2 = float(grid.n) * its2, el2
         el2, work2 = aggregate_over_ranks(dist, el2, work2, "cuda")
         e2e = {"value": work2 / el2, "unit": "DOF*Newton-steps/s", "h2d_bytes_per_step": 8 * grid.n,
-               "d2h_bytes_per_step": 8 * grid.n}
+               "d2h_bytes_per_step": 8 * grid.n, "newton_its": its2}
         ctx2.close()
 
-    # the same schedule with the FP32 AMG hierarchy and V-cycle (FP64 residual,
+    # the same steps with the FP32 AMG hierarchy and V-cycle (FP64 residual,
     # Jacobian, line search and outer Krylov): speed and deviation from FP64
     mixed = None
-    if not args.no_mixed and not w.mixed:
+    if not args.no_mixed and prec == rb.PREC_FP64:
         ctx3 = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_MIXED)
         p3 = torch.tensor(p0, device="cuda")
-        for m in range(args.warmup):
-            ctx3.step(p3, sched(m), opts)
-        ref_p = pd  # FP64 state after the same steps
-        torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        its3 = lin3 = 0
-        for m in range(args.warmup, args.warmup + args.steps):
-            st3 = ctx3.step(p3, sched(m), opts)
-            its3 += st3.newton_its
-            lin3 += st3.linear_its
-        f1.record(stream)
+        torch.cuda.synchronize()
+        f0.record()
+        st3 = run_steps(ctx3, p3, dts, K, opts)
+        f1.record()
         torch.cuda.synchronize()
         el3 = f0.elapsed_time(f1) / 1000.0
+        its3 = sum(x.newton_its for x in st3)
         v3 = float(grid.n) * its3 / el3
-        dev_end = float((p3 - ref_p).abs().max() / ref_p.abs().max())
+        dev_end = float((p3 - p_fp64).abs().max() / p_fp64.abs().max())
         ctx3.close()
-        # untimed lockstep replay of the whole schedule: largest deviation of the
-        # MIXED pressure from the FP64 one after any step (the end states can
-        # coincide once both runs reach the same steady state)
+        # untimed lockstep replay: largest deviation of the mixed pressure from the FP64 one after any step
         ca = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_FP64)
         cb = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_MIXED)
         pa = torch.tensor(p0, device="cuda")
         pb = torch.tensor(p0, device="cuda")
         dev = 0.0
-        for m in range(args.warmup + args.steps):
-            ca.step(pa, sched(m), opts)
-            cb.step(pb, sched(m), opts)
+        for m in range(K):
+            ca.step(pa, dts[m % len(dts)], opts)
+            cb.step(pb, dts[m % len(dts)], opts)
             dev = max(dev, float((pb - pa).abs().max() / pa.abs().max()))
         ca.close()
         cb.close()
-        mixed = {"value": v3, "unit": "DOF*Newton-steps/s", "speedup_vs_fp64": v3 / (float(grid.n) * newton_its / elapsed),
-                 "newton_its": its3, "linear_its": lin3, "fp64_newton_its": newton_its, "fp64_linear_its": lin_its,
-                 "max_rel_dev_p_vs_fp64": dev, "rel_dev_p_at_end": dev_end,
-                 "ms_per_step": 1000.0 * el3 / max(args.steps, 1)}
+        mixed = {"value": v3, "unit": "DOF*Newton-steps/s", "speedup_vs_fp64": v3 / value if ws == 1 else None,
+                 "newton_its": its3, "linear_its": sum(x.linear_its for x in st3), "fp64_newton_its": newton_its,
+                 "fp64_linear_its": lin_its, "max_rel_dev_p_vs_fp64": dev, "rel_dev_p_at_end": dev_end,
+                 "ms_per_step": 1000.0 * el3 / max(K, 1)}
 
-    peak, peak_kind = measured_peaks()
-    secs = ms_k.value / 1000.0
-    gbs = (by_k.value / secs / 1e9) if secs > 0 else None
-    tfl = (fl_k.value / secs / 1e12) if secs > 0 else None
-    per_launch_bytes = by_k.value / n_k.value if n_k.value else None
-    traffic = NCU_TRAFFIC_BYTES.get((args.workload, args.roofline_kernel))
-    fp64_kernel = not (w.mixed or args.roofline_kernel.startswith("l1jacobi") and prec == rb.PREC_MIXED)
-    common = {"kernel": args.roofline_kernel, "traffic": traffic, "algorithmic_bytes_per_launch": per_launch_bytes,
-              "algorithmic_flops_per_launch": fl_k.value / n_k.value if n_k.value else None,
-              "launches_timed": n_k.value, "avg_launch_us": 1000.0 * ms_k.value / n_k.value if n_k.value else None,
-              "kernel_share_of_step": PROFILE_STRIDE * secs / elapsed if elapsed > 0 else None,
-              "profile_stride": PROFILE_STRIDE,
-              "hbm": {"achieved": gbs, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                      "frac": gbs / peak if gbs else None}}
-    if fp64_kernel and tfl:
-        roof = dict(common, bound="alu", achieved=tfl, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=tfl / FP64_PEAK_TFLOPS, peak_kind="derived FP64 (unit count x clock)")
-    else:
-        roof = dict(common, bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=gbs / peak if gbs else None,
-                    peak_kind=peak_kind)
+    # per-kernel profile pass and the dominant kernel on its roofline
+    peak_gbs, peak_kind = measured_peaks()
+    fp64_tflops = rb.fma_peak_tflops(fp64=True)
+    fp32_tflops = rb.fma_peak_tflops(fp64=False)
+    roof, kernel_roofs = None, None
+    if not args.no_profile:
+        psteps = min(K, args.profile_steps)
+        tab = profile_pass(rb, grid, soil, bc, w, ks, p0, dts, opts, prec, psteps)
+        total = sum(v[1] for v in tab.values())
+        rows = sorted(tab.items(), key=lambda kv: -kv[1][1])
+        kernel_roofs = []
+        for name, (cnt, kms, kb, kf) in rows[:5]:
+            r = roofline_of(name, kms, cnt, kb, kf, _is_fp64_kernel(name, prec == rb.PREC_FP64), peak_gbs,
+                            fp64_tflops, NCU_TRAFFIC_BYTES.get((w.name, name)))
+            r["share_of_profiled_steps"] = kms / total if total else None
+            r["profiled_steps"] = psteps
+            kernel_roofs.append(r)
+        roof = kernel_roofs[0] if kernel_roofs else None
+        kernel_roofs = [{k: r[k] for k in ("kernel", "share_of_profiled_steps", "bound", "achieved", "peak", "unit",
+                                           "frac", "intensity_flop_per_byte", "hbm_frac", "avg_launch_us")}
+                        for r in kernel_roofs]
+
+    # the paper's own problem (Sec. 6): 798 x 798 x 38 unknowns, mixed precision
+    paper = None
+    if not args.no_paper and ws == 1 and args.grid is None:
+        try:
+            paper = paper_run(rb, args.paper_steps)
+        except Exception as e:
+            paper = {"error": "%s: %s" % (type(e).__name__, e)}
+
     line = {"metric": "DOF*Newton-steps/s", "value": value, "unit": "DOF*Newton-steps/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / max(args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / max(K, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == rb.PREC_FP64 else "f64 outer, f32 AMG",
             "data": "synthetic", "config": workload_config(w, grid), "e2e": e2e,
-            "gpu_launches": int(l1.value - l0.value), "warmup_launches": int(l0.value - lw.value),
-            "clocks": clocks, "roofline": roof,
+            "gpu_launches": int(l1.value - l0.value), "clocks": clocks, "roofline": roof,
+            "kernels_on_their_roofs": kernel_roofs,
+            "measured_peaks": {"hbm_gbs": peak_gbs, "hbm_kind": peak_kind, "fp64_fma_tflops": fp64_tflops,
+                               "fp32_fma_tflops": fp32_tflops,
+                               "fp64_balance_flop_per_byte": fp64_balance(peak_gbs, fp64_tflops)},
             "newton_its": newton_its, "linear_its": lin_its,
-            "latency_ms_per_time_step": {"p50": step_ms[len(step_ms) // 2],
-                                         "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
-                                         "max": step_ms[-1]},
-            "fp32_amg": mixed,
+            "schedule_newton_its": [x.newton_its for x in stats],
+            "latency_ms_per_time_step": {"p50": statistics.median(step_ms), "max": max(step_ms)},
+            "fp32_amg": mixed, "paper_workload": paper,
             "peak_device_memory": peak_mem,
             "phase_ms": {k[3:]: round(v, 3) for k, v in phases.items()},
             "parallelism": "replicas" if ws > 1 else "single"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget,
+                                                args.cpu_procs or min(16, os.cpu_count() or 1))
+        except Exception as e:
+            line["cpu_baseline"] = {"value": None, "error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_serving and ws == 1:
         try:
             line["serving"] = serving_run(args, rb)
         except Exception as e:  # the main measurement stands on its own
             line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
-    ctx.close()
     if rank == 0:
         print(json.dumps(line))
     if dist:
@@ -599,9 +697,34 @@ def run_ours(args):
     return 0
 
 
+def paper_run(rb, steps):
+    """The paper's infiltration problem (Sec. 6) on its 800 x 800 x 40 node grid in mixed precision:
+    DOF * Newton-steps / s over its first steps (CUDA events; setup included)."""
+    import torch
+    w, grid, soil, bc, ks, p0, dts = workload_setup("paper_infiltration")
+    opts = newton_opts(rb, w)
+    ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_MIXED)
+    pd = torch.tensor(p0, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    st = run_steps(ctx, pd, dts, steps, opts)
+    e1.record()
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1000.0
+    its = sum(x.newton_its for x in st)
+    ctx.close()
+    return {"workload": "paper_infiltration", "grid": [grid.nx, grid.ny, grid.nz], "dof": grid.n,
+            "precision": "fp32 AMG, fp64 residual and FGMRES(10)", "steps": steps, "newton_its": its,
+            "linear_its": sum(x.linear_its for x in st), "value": grid.n * its / el, "unit": "DOF*Newton-steps/s",
+            "ms_per_step": 1000.0 * el / steps}
+
+
 def main():
     if len(sys.argv) >= 2 and sys.argv[1] == "--oracle-sample":
-        res = oracle_sample_main(sys.argv[2], float(sys.argv[3]))
+        wl, n, budget, steps, warm = sys.argv[2], int(sys.argv[3]), float(sys.argv[4]), int(sys.argv[5]), int(sys.argv[6])
+        res = oracle_sample_main(wl, budget, n=n, steps=steps or None, warmup=warm)
         res.pop("step_times", None)
         print(json.dumps(res))
         return 0

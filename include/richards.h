@@ -325,6 +325,14 @@ int rich_step_host(rich_ctx* ctx, double* p_host, double dt, const rich_newton_o
                    rich_step_stats* stats_host);
 
 /* ---- instrumentation ----------------------------------------------------- */
+/* Measured arithmetic peak of the current device in TFLOP/s (2 flops per fused
+ * multiply-add): FP64 (fp64 != 0) or FP32 FMA pipes, non-tensor, timed with CUDA
+ * events over launches that keep every SM busy with independent FMA chains (the
+ * best of three after a warm-up launch; about 0.1 s).  Allocates a small buffer
+ * and synchronises the device's legacy default stream.  Used to place FP64
+ * kernels on their roofline. */
+int rich_measure_fma_peak(int fp64, double* tflops);
+
 /* Number of kernels this library has launched since it was loaded. */
 int rich_kernel_launches(long long* out);
 /* Time every launch of the kernel called name (NULL disables) with CUDA events
@@ -344,8 +352,9 @@ int rich_profile_stride(int stride);
  * algorithmic bytes those launches must move and (flops_total may be NULL) their
  * algorithmic floating-point operations (synchronises the events). */
 int rich_profile_result(double* ms_total, long long* launches, double* bytes_total, double* flops_total);
-/* With the target "*": per-kernel totals, one line "name launches ms bytes" each,
- * written into buf (at most cap bytes, NUL-terminated). */
+/* With the target "*": per-kernel totals, one line "name launches ms bytes flops"
+ * each (algorithmic bytes and flops), written into buf (at most cap bytes,
+ * NUL-terminated). */
 int rich_profile_table(char* buf, int cap);
 
 /* Peak device memory of the library on the current device: every allocation it

@@ -69,6 +69,7 @@ static std::string g_prof_target;   // a kernel name, "*" for every named kernel
 static std::vector<cudaEvent_t> g_prof_ev;
 static std::vector<const char*> g_prof_name;
 static std::vector<double> g_prof_b;
+static std::vector<double> g_prof_f;
 static int g_prof_n = 0;          // recorded launch pairs
 static long long g_prof_seen = 0; // launches of the target (recorded or not)
 static long long g_prof_stride = 1;  // record every stride-th launch of the target
@@ -84,6 +85,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(
     for (auto& e : g_prof_ev) cudaEventCreate(&e);
     g_prof_name.resize(kProfEvents / 2);
     g_prof_b.resize(kProfEvents / 2);
+    g_prof_f.resize(kProfEvents / 2);
   }
   on = true;
   g_prof_name[g_prof_n] = name;
@@ -94,6 +96,7 @@ ProfScope::~ProfScope() {
   if (!on) return;
   cudaEventRecord(g_prof_ev[2 * g_prof_n + 1], st);
   g_prof_b[g_prof_n] = bytes;
+  g_prof_f[g_prof_n] = flops;
   g_prof_bytes += bytes;
   g_prof_flops += flops;
   ++g_prof_n;
@@ -270,9 +273,59 @@ int scan_exclusive_ll(rich_ctx* c, const long long* in, long long* out, long lon
   return scan_impl<long long, long long>(c, in, out, n);
 }
 
+// Arithmetic peak probe: every thread runs kChains independent fused multiply-add
+// chains, so the pipe is limited by issue rate, not by the latency of one chain.
+constexpr int kChains = 8;
+template <class T>
+__global__ void k_fma_peak(int iters, T b, T c, T* __restrict__ sink) {
+  T a[kChains];
+#pragma unroll
+  for (int q = 0; q < kChains; ++q) a[q] = T(threadIdx.x + q);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) a[q] = a[q] * b + c;
+  }
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < kChains; ++q) s += a[q];
+  if (s == T(-12345.0)) sink[threadIdx.x] = s;  // keeps the chains live; never true for these inputs
+}
+
+template <class T>
+static int fma_peak(cudaStream_t st, double* tflops) {
+  T* sink = nullptr;
+  RICH_CUDA(cudaMalloc(&sink, kBlock * sizeof(T)));
+  const int blocks = 8 * kNumSM;
+  const int iters = sizeof(T) == 8 ? 4096 : 65536;
+  cudaEvent_t e0, e1;
+  RICH_CUDA(cudaEventCreate(&e0));
+  RICH_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch warms the clocks up
+    RICH_CUDA(cudaEventRecord(e0, st));
+    k_fma_peak<T><<<blocks, kBlock, 0, st>>>(iters, T(0.999999), T(1e-7), sink);
+    RICH_CUDA(cudaEventRecord(e1, st));
+    RICH_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RICH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0 && ms < best) best = ms;
+  }
+  count_launches(4);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  *tflops = 2.0 * kChains * (double)iters * blocks * kBlock / (best * 1e-3) / 1e12;
+  return RICH_OK;
+}
+
 }  // namespace rich
 
 extern "C" {
+
+int rich_measure_fma_peak(int fp64, double* tflops) {
+  if (!tflops) return RICH_EINVAL;
+  return fp64 ? rich::fma_peak<double>(nullptr, tflops) : rich::fma_peak<float>(nullptr, tflops);
+}
 
 int rich_kernel_launches(long long* out) {
   if (!out) return RICH_EINVAL;
@@ -333,7 +386,7 @@ int rich_profile_result(double* ms_total, long long* launches, double* bytes_tot
 // to cap lines "name launches total_ms bytes" into buf (NUL-terminated).
 int rich_profile_table(char* buf, int cap) {
   if (!buf || cap < 1) return RICH_EINVAL;
-  struct Acc { double ms = 0.0; long long n = 0; double bytes = 0.0; };
+  struct Acc { double ms = 0.0; long long n = 0; double bytes = 0.0, flops = 0.0; };
   std::vector<std::pair<std::string, Acc>> tab;
   for (int i = 0; i < rich::g_prof_n; ++i) {
     cudaEventSynchronize(rich::g_prof_ev[2 * i + 1]);
@@ -346,12 +399,13 @@ int rich_profile_table(char* buf, int cap) {
     tab[k].second.ms += t;
     tab[k].second.n += 1;
     tab[k].second.bytes += rich::g_prof_b[i];
+    tab[k].second.flops += rich::g_prof_f[i];
   }
   int off = 0;
   buf[0] = 0;
   for (auto& e : tab) {
-    int w = snprintf(buf + off, cap - off, "%s %lld %.6f %.6e\n", e.first.c_str(), e.second.n, e.second.ms,
-                     e.second.bytes);
+    int w = snprintf(buf + off, cap - off, "%s %lld %.6f %.6e %.6e\n", e.first.c_str(), e.second.n, e.second.ms,
+                     e.second.bytes, e.second.flops);
     if (w < 0 || w >= cap - off) break;
     off += w;
   }

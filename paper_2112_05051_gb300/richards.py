@@ -136,6 +136,7 @@ EXPORTS = {
                                              ctypes.POINTER(BC), _P, _P, ctypes.c_double, _P,
                                              ctypes.POINTER(ctypes.c_double), _P]),
     "rich_kernel_launches": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
+    "rich_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -247,13 +248,13 @@ def residual_noalloc(grid, soil, bc, kmean, p, s_old, dt, F, ks=None, norms=True
 
 
 def profile_table():
-    """Per-kernel totals recorded under the "*" profiling target: {name: (launches, ms, bytes)}."""
+    """Per-kernel totals recorded under the "*" profiling target: {name: (launches, ms, bytes, flops)}."""
     buf = ctypes.create_string_buffer(1 << 16)
     check(load().rich_profile_table(buf, len(buf)), "rich_profile_table")
     out = {}
     for line in buf.value.decode().splitlines():
-        name, n, ms, b = line.split()
-        out[name] = (int(n), float(ms), float(b))
+        name, n, ms, b, f = line.split()
+        out[name] = (int(n), float(ms), float(b), float(f))
     return out
 
 
@@ -475,3 +476,10 @@ def memory_peak(reset=False):
     r = ctypes.c_longlong()
     check(load().rich_memory_peak(ctypes.byref(u), ctypes.byref(r), 1 if reset else 0), "rich_memory_peak")
     return u.value, r.value
+
+
+def fma_peak_tflops(fp64=True):
+    """Measured FP64 (or FP32) FMA peak of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    check(load().rich_measure_fma_peak(1 if fp64 else 0, ctypes.byref(v)), "rich_measure_fma_peak")
+    return v.value

@@ -68,7 +68,8 @@ def test_request_stream_statistics():
     st = bench.stream_stats(res, [1000] * 8, 2.0, {-4: "RICH_ENOTCONV_LIN"})
     assert st["failed"] == {"RICH_ENOTCONV_LIN": 2}
     assert st["dof_newton_per_s"] == 6 * 1000 * 3 / 2.0          # converged work only
-    assert abs(st["latency_ms"]["max"] - 80.0) < 1e-9 and abs(st["latency_ms"]["mean"] - 45.0) < 1e-9
+    assert abs(st["latency_ms_all"]["max"] - 80.0) < 1e-9 and abs(st["latency_ms_all"]["mean"] - 45.0) < 1e-9
+    assert st["converged"] == 6 and st["failure_rate"] == 0.25 and st["converged_per_s"] == 3.0
     assert abs(st["latency_ms_converged"]["p50"] - 40.0) < 1e-9  # 20,30,40,60,70,80 -> nearest rank 3
 
 
@@ -108,6 +109,7 @@ def test_serving_run_end_to_end_against_a_fake_server(monkeypatch):
                                  serving_aggregation=0)
     out = bench.serving_run(args, fake)
     assert out["requests"] == 12 and out["max_in_flight"] == 3
-    assert out["capacity_rps"] > 0 and out["latency_ms"]["p50"] == pytest.approx(5.0, abs=1e-6)
+    assert out["capacity_rps"] > 0 and out["latency_ms_converged"]["p50"] == pytest.approx(5.0, abs=1e-6)
+    assert 0.0 < out["failure_rate"] < 1.0
     assert set(out["failed"]) <= {"RICH_ENOTCONV_LIN"}
     assert out["mix_vs_alone_max_rel_dev"] == 0.0

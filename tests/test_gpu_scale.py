@@ -72,18 +72,22 @@ def test_bench_scale_hierarchy_vcycle_and_fgmres_128():
 
 
 def test_mixed_step_of_the_512_workload_at_48_matches_fp64_oracle():
+    # sigma 2 spans ~14 decades of K_s here, so J is ill conditioned: two iterates that
+    # both meet rtol = 1e-8 can differ by ~1e-7 relative.  Both sides are therefore
+    # driven to rtol = 1e-12 (or the evaluation floor), where the discrete solution
+    # is pinned to better than 1e-8.
     rb = _rb()
     w = synth.WORKLOADS["richards512_mixed"]
     grid, soil, bc, ks, p0, dts = synth.workload_inputs(w, 48)
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=w.nu, nu2=w.nu, seed=w.amg_seed, coarse_max=w.coarse_max,
-                                  smooth_levels=w.smooth_levels)
+                                  smooth_levels=w.smooth_levels, rtol=1e-12)
     ctx = rb.Context(grid, soil, bc, w.kmean, ks, precision=rb.PREC_MIXED)
     pd = torch.tensor(p0, device="cuda")
     st = ctx.step(pd, dts[0], opts)
     prob = newton.Problem(grid, soil, bc, w.kmean, ks)
     po, ost = newton.step(prob, p0, dts[0], newton.NewtonOptions(krylov="fcg", nu1=w.nu, nu2=w.nu,
                                                                   amg_seed=w.amg_seed, coarse_max=w.coarse_max,
-                                                                  smooth_levels=w.smooth_levels))
+                                                                  smooth_levels=w.smooth_levels, rtol=1e-12))
     assert st.converged and ost.converged
     assert _nrel(pd.cpu().numpy(), po) <= 1e-8
     # the FP32 hierarchy costs at most a few Krylov iterations over the FP64 one
