@@ -367,7 +367,8 @@ def serving_run(args, rb):
     halvings = getattr(args, "serving_halvings", 8)
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
                                   product_lists=args.serving_lists, coarse_max=args.serving_coarse_max,
-                                  aggregation=args.serving_aggregation, max_dt_halvings=halvings)
+                                  aggregation=args.serving_aggregation, max_dt_halvings=halvings,
+                                  max_newton=20 if halvings else 50)
 
     def submit(srv, q):
         grid, ks, kmean, n = q
@@ -418,7 +419,7 @@ def serving_run(args, rb):
             "coarse_max": args.serving_coarse_max, "product_lists": args.serving_lists,
             "aggregation": "matching" if args.serving_aggregation else "MIS-2",
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
-            "max_dt_halvings": halvings,
+            "max_dt_halvings": halvings, "max_newton_per_attempt": 20 if halvings else 50,
             "latency_ms_converged": st_s["latency_ms_converged"], "failure_rate": st_s["failure_rate"],
             "converged_per_s": st_s["converged_per_s"], "stream_dof_newton_per_s": st_s["dof_newton_per_s"],
             "capacity_rps": mu, "capacity_converged_rps": st_b["converged_per_s"], "burst_s": t_burst,
@@ -672,6 +673,7 @@ def run_ours(args):
             "measured_peaks": {"hbm_gbs": peak_gbs, "hbm_kind": peak_kind, "fp64_fma_tflops": fp64_tflops,
                                "fp32_fma_tflops": fp32_tflops,
                                "fp64_balance_flop_per_byte": fp64_balance(peak_gbs, fp64_tflops)},
+            "autotuned_shapes": len(rb.autotune_table()),
             "newton_its": newton_its, "linear_its": lin_its,
             "schedule_newton_its": [x.newton_its for x in stats],
             "latency_ms_per_time_step": {"p50": statistics.median(step_ms), "max": max(step_ms)},

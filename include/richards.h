@@ -158,6 +158,11 @@ typedef struct {
   int hgs_seg;             /* hybrid Gauss-Seidel blocks on the finest grid: segments of this many cells of
                               one vertical column (16) */
   int hgs_block;           /* hybrid Gauss-Seidel blocks on coarser levels: this many consecutive rows (16) */
+  int autotune;            /* 1 (default): the first time a CSR row operation of the V-cycle (sweep,
+                              residual, restriction, prolongation) meets a matrix shape, every lane-group
+                              width (1..32 lanes per row) is timed on it and the fastest is kept for the
+                              process (rich_autotune_table lists the choices); 0: a fixed rule by the
+                              average row length */
   int isolated_join;       /* MIS-2 pass 3 (1, default): a node without strong neighbours whose row is not
                               diagonally dominant (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
                               aggregated neighbour j with the largest (fp32 |a_ij|, key(j)); dominant rows
@@ -190,8 +195,10 @@ typedef struct {
   int fcg_fallback_restart;/* FGMRES(m) retry after an FCG failure (30) */
   int max_dt_halvings;     /* time-step control (0 = off, default).  H > 0: rich_step covers dt with
                               backward-Euler steps of length dt / 2^k: an attempt that fails with
-                              RICH_ENOTCONV_LIN, RICH_ENOTCONV_NEWTON or RICH_ELINESEARCH is discarded
-                              (p restored) and retried with half its length, down to dt / 2^H; after an
+                              RICH_ENOTCONV_NEWTON, RICH_ELINESEARCH or, when FCG met (p, J p) <= 0,
+                              RICH_ENOTCONV_LIN is discarded (p restored) and retried with half its
+                              length, down to dt / 2^H (a Krylov solve that only ran out of iterations
+                              ends the step: a shorter step does not mend the preconditioner); after an
                               accepted substep the length doubles back whenever the time reached is a
                               multiple of the doubled length, so the substeps end exactly at dt.  Under
                               control an FCG solve that meets (p, J p) <= 0 fails the attempt at once
@@ -314,7 +321,7 @@ int krylov_solve(rich_ctx* ctx, const double* b_dev, double* x_dev, const rich_k
 /* ---- Sec. 3: one backward-Euler step ------------------------------------ */
 /* p_dev holds p^{l-1} on entry and p^l on return (or the last accepted
  * Newton iterate on error; under time-step control, the pressure at the start
- * of the substep that failed at the shortest length).  opts NULL = defaults.
+ * of the substep that failed).  opts NULL = defaults.
  * The first call of a context builds the AMG hierarchy.  Counts in stats_host
  * cover every attempt, discarded ones included. */
 int rich_step(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_opts* opts,
@@ -332,6 +339,11 @@ int rich_step_host(rich_ctx* ctx, double* p_host, double dt, const rich_newton_o
  * and synchronises the device's legacy default stream.  Used to place FP64
  * kernels on their roofline. */
 int rich_measure_fma_peak(int fp64, double* tflops);
+
+/* The autotuner's choices so far, one line "mode value_bytes rows nonzeros lanes
+ * best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep, 3 residual), written
+ * into buf (at most cap bytes, NUL-terminated). */
+int rich_autotune_table(char* buf, int cap);
 
 /* Number of kernels this library has launched since it was loaded. */
 int rich_kernel_launches(long long* out);

@@ -88,6 +88,7 @@ class StepStats:
     lin_its: list = dataclasses.field(default_factory=list)
     res_hist: list = dataclasses.field(default_factory=list)
     line_searches: list = dataclasses.field(default_factory=list)  # (f0, slope, [(lam, f(lam)), ...]) per iteration
+    indefinite: bool = False      # the last attempt ended on (p, J p) <= 0 in FCG
     substeps: int = 1             # backward-Euler steps taken to cover dt (advance)
     dt_min: float = 0.0           # smallest of them
     dt_failures: int = 0          # attempts that failed and were retried with half the step
@@ -159,6 +160,7 @@ def linear_solve(J, h, rhs, opt, stats):
         if opt.max_dt_halvings > 0 and info.get("reason") == "curvature":
             # under time-step control a Jacobian that is not positive definite along
             # a preconditioned direction ends the attempt: the step is retried shorter
+            stats.indefinite = True
             return d, its, False
         stats.fallbacks += 1
     d, its, ok, _ = krylov.fgmres(mv, prec, rhs, opt.eta, opt.maxit, opt.restart)
@@ -238,8 +240,11 @@ def advance(prob, p, dt, opt):
     The paper fixes dt per step (Sec. 6) and gives no control; this is the usual
     host-side remedy when Newton fails at a steep wetting front.  With
     opt.max_dt_halvings = H > 0 the step is tried whole; an attempt that fails
-    (Krylov, line search or Newton non-convergence) is discarded and retried
-    with half its length, down to dt / 2^H; after each accepted substep the
+    in the line search, in Newton, or in FCG on a Jacobian that is not positive
+    definite along a preconditioned direction is discarded and retried with half
+    its length, down to dt / 2^H (a Krylov solve that merely runs out of
+    iterations ends the step: a shorter step does not mend the preconditioner,
+    and retrying it would multiply the cost); after each accepted substep the
     length doubles again whenever the time reached is a multiple of the doubled
     length, so the substeps land exactly on dt.  Lengths are dt / 2^k (exact in
     binary floating point).  Returns (p_new, stats) with the Newton and Krylov
@@ -264,6 +269,8 @@ def advance(prob, p, dt, opt):
             err = None if ok else NewtonError("Newton did not converge")
         except (LinearSolveError, LineSearchError) as e:
             st, ok, err = getattr(e, "stats", None), False, e
+            if isinstance(e, LinearSolveError) and not (st is not None and st.indefinite):
+                raise
         if st is not None:
             acc.newton_its += st.newton_its
             acc.linear_its += st.linear_its

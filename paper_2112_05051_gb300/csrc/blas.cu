@@ -76,6 +76,8 @@ static long long g_prof_stride = 1;  // record every stride-th launch of the tar
 static double g_prof_bytes = 0.0;
 static double g_prof_flops = 0.0;
 
+bool profiling_active() { return !g_prof_target.empty(); }
+
 ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(false), st(s), bytes(b), flops(f) {
   if (g_prof_target.empty() || (g_prof_target != "*" && g_prof_target != name)) return;
   if (g_prof_seen++ % g_prof_stride != 0) return;  // only every stride-th launch is timed
@@ -321,6 +323,11 @@ static int fma_peak(cudaStream_t st, double* tflops) {
 }  // namespace rich
 
 extern "C" {
+
+int rich_autotune_table(char* buf, int cap) {
+  if (!buf || cap < 1) return RICH_EINVAL;
+  return rich::autotune_table(buf, cap);
+}
 
 int rich_measure_fma_peak(int fp64, double* tflops) {
   if (!tflops) return RICH_EINVAL;

@@ -29,9 +29,9 @@ void set_cuda_error(cudaError_t e, const char* where);
     }                                                                \
   } while (0)
 
-#define RICH_CHECK(expr)                 \
+#define RICH_CHECK(...)                  \
   do {                                   \
-    int s_ = (expr);                     \
+    int s_ = (__VA_ARGS__);              \
     if (s_ != RICH_OK) return s_;        \
   } while (0)
 
@@ -427,7 +427,11 @@ int amg_refresh(rich_ctx* c);
 int amg_update_fine(rich_ctx* c);
 void amg_free(rich_ctx* c);
 
+// blas.cu: whether a profiling target is set (the autotuner then stays off)
+bool profiling_active();
+
 // solve.cu
+int autotune_table(char* buf, int cap);
 int vcycle_apply(rich_ctx* c, const double* r, double* z);
 int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st);
 

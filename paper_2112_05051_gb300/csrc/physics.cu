@@ -350,6 +350,7 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->smoother = RICH_SMOOTH_L1JACOBI;
   o->hgs_seg = 16;
   o->hgs_block = 16;
+  o->autotune = 1;
   o->isolated_join = 1;
 }
 

@@ -11,6 +11,8 @@
 // Krylov scalars live in device memory; each iteration reads one small block
 // of them back for the convergence test.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -79,13 +81,104 @@ __global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restri
 }
 
 template <class T, int MODE>
-static void csr_op(cudaStream_t st, int n, long long nnz, const int* rp, const int* col, const T* val, const T* dinv,
-                   const T* b, const T* x, T* y) {
-  double avg = n > 0 ? (double)nnz / n : 0.0;
-  if (avg > 96) k_csr_grp<T, MODE, 32><<<grid_for((long long)n * 32), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else if (avg > 64) k_csr_grp<T, MODE, 16><<<grid_for((long long)n * 16), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else if (avg > 40) k_csr_grp<T, MODE, 8><<<grid_for((long long)n * 8), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
-  else k_csr_grp<T, MODE, 4><<<grid_for((long long)n * 4), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y);
+static void csr_launch(cudaStream_t st, int G, int n, const int* rp, const int* col, const T* val, const T* dinv,
+                       const T* b, const T* x, T* y) {
+  long long thr = (long long)n * G;
+  switch (G) {
+    case 1: k_csr_grp<T, MODE, 1><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 2: k_csr_grp<T, MODE, 2><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 4: k_csr_grp<T, MODE, 4><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 8: k_csr_grp<T, MODE, 8><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 16: k_csr_grp<T, MODE, 16><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    default: k_csr_grp<T, MODE, 32><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+  }
+}
+
+// Lanes per row when nothing has been measured: one thread per short row, wider
+// groups as rows grow.
+static int default_lanes(double avg) {
+  if (avg <= 6) return 1;
+  if (avg > 96) return 32;
+  if (avg > 64) return 16;
+  if (avg > 40) return 8;
+  return 4;
+}
+
+// Autotuner of the CSR row operations: the first time an operation meets a matrix
+// shape (mode, value type, rows, nonzeros), every lane-group width is timed on the
+// actual operands (output to a scratch vector, one warm-up and three timed launches
+// each, CUDA events) and the fastest is kept for the rest of the process.  The
+// table is shared by all contexts (under a mutex, held while tuning, so concurrent
+// requests of one shape agree); a given shape therefore always runs the same
+// kernel, and its results do not depend on what else is in flight.
+struct TuneKey {
+  int mode, tsize, n;
+  long long nnz;
+  bool operator<(const TuneKey& o) const {
+    if (mode != o.mode) return mode < o.mode;
+    if (tsize != o.tsize) return tsize < o.tsize;
+    if (n != o.n) return n < o.n;
+    return nnz < o.nnz;
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, float>> g_tune;  // -> (lanes, best us)
+
+template <class T, int MODE>
+static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* col, const T* val, const T* dinv,
+                  const T* b, const T* x, T* y) {
+  if (n <= 0) return RICH_OK;
+  int G = default_lanes((double)nnz / n);
+  if (c->H.opts.autotune && !profiling_active()) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneKey key{MODE, (int)sizeof(T), n, nnz};
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      G = it->second.first;
+    } else {
+      T* scratch = nullptr;
+      RICH_CHECK(dalloc(&scratch, n));
+      RICH_CUDA(cudaMemsetAsync(scratch, 0, sizeof(T) * (size_t)n, c->st));
+      cudaEvent_t e0, e1;
+      RICH_CUDA(cudaEventCreate(&e0));
+      RICH_CUDA(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int g : {1, 2, 4, 8, 16, 32}) {
+        csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch);
+        RICH_CUDA(cudaEventRecord(e0, c->st));
+        for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch);
+        RICH_CUDA(cudaEventRecord(e1, c->st));
+        RICH_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        RICH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        count_launches(4);
+        if (ms < best) {
+          best = ms;
+          G = g;
+        }
+      }
+      RICH_CUDA(cudaGetLastError());
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      dfree(scratch);
+      g_tune[key] = {G, best * 1000.f / 3.f};
+    }
+  }
+  csr_launch<T, MODE>(c->st, G, n, rp, col, val, dinv, b, x, y);
+  return RICH_OK;
+}
+
+int autotune_table(char* buf, int cap) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int off = 0;
+  buf[0] = 0;
+  for (auto& e : g_tune) {
+    int w = snprintf(buf + off, cap - off, "%d %d %d %lld %d %.3f\n", e.first.mode, e.first.tsize, e.first.n,
+                     e.first.nnz, e.second.first, e.second.second);
+    if (w < 0 || w >= cap - off) break;
+    off += w;
+  }
+  return RICH_OK;
 }
 
 // x = M b for a dense row-major n x n matrix; one warp per row.
@@ -136,6 +229,39 @@ __global__ void __launch_bounds__(kLineThreads) k_st_smooth(GridP g, Stencil4<T>
   if (k < g.nz - 1) ax -= wzp * x[c + sxy];
   if (MODE == 2) xo[c] = b[c] - ax;
   else xo[c] = xc + A.dinv[c] * (b[c] - ax);
+}
+
+// The first l1-Jacobi sweep from zero, y = D_l1^-1 b, folded into the next stencil
+// pass on the finest level: y is recomputed from b and the l1 scaling wherever the
+// next pass reads it (own cell and the six neighbours, all cache hits), so it is
+// never written and read back.  MODE 1: out = y + D_l1^-1 (b - A y), the second
+// sweep; MODE 2: x1 = y and out = b - A y, the residual after a single sweep.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kLineThreads) k_st_first(GridP g, Stencil4<T> A, const T* __restrict__ b,
+                                                           T* __restrict__ x1, T* __restrict__ out) {
+  int i = blockIdx.y * kLineThreads + threadIdx.x;
+  if (i >= g.nx) return;
+  int r = blockIdx.x;
+  int j = r % g.ny;
+  int k = r / g.ny;
+  int nx = g.nx;
+  int sxy = g.nx * g.ny;
+  int c = r * nx + i;
+  T bc = b[c];
+  T yc = A.dinv[c] * bc;
+  T ay = A.diag[c] * yc;
+  if (i > 0) ay -= A.wx[c - 1] * (A.dinv[c - 1] * b[c - 1]);
+  if (i < nx - 1) ay -= A.wx[c] * (A.dinv[c + 1] * b[c + 1]);
+  if (j > 0) ay -= A.wy[c - nx] * (A.dinv[c - nx] * b[c - nx]);
+  if (j < g.ny - 1) ay -= A.wy[c] * (A.dinv[c + nx] * b[c + nx]);
+  if (k > 0) ay -= A.wz[c - sxy] * (A.dinv[c - sxy] * b[c - sxy]);
+  if (k < g.nz - 1) ay -= A.wz[c] * (A.dinv[c + sxy] * b[c + sxy]);
+  if (MODE == 2) {
+    x1[c] = yc;
+    out[c] = bc - ay;
+  } else {
+    out[c] = yc + A.dinv[c] * (bc - ay);
+  }
 }
 
 // Hybrid Gauss-Seidel (the paper's smoother, Sec. 5.2 / Sec. 6): Gauss-Seidel inside
@@ -326,28 +452,21 @@ static int vcycle_level_hgs(rich_ctx* c, int l, const T* b, T** xres) {
     ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st,
                  st0 ? (double)n * 7.0 * es : (double)n * (4.0 + 3.0 * es) + (double)L.A.nnz * (4.0 + es));
     if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-    else if (L.A.nnz > 6LL * n) csr_op<T, 3>(c->st, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r);
-    else k_resid<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, b, x, (T*)L.r);
+    else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r));
   }
   RICH_LAUNCH_CHECK();
   Level& C = H.lv[l + 1];
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
-    if (L.R.nnz > 6LL * C.n)
-      csr_op<T, 0>(c->st, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr, (const T*)L.r,
-                   (T*)C.b);
-    else
-      k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
+    RICH_CHECK(csr_op<T, 0>(c, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr,
+                            (const T*)L.r, (T*)C.b));
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    if (L.P.nnz > 6LL * n)
-      csr_op<T, 1>(c->st, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x);
-    else
-      k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
+    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x));
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < H.opts.nu2; ++s) {
@@ -384,8 +503,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
       RICH_LAUNCH_CHECK();
       for (int s = 1; s < kCoarseSweeps; ++s) {
-        if (L.A.nnz > 6LL * n) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
-        else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+        RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t));
         RICH_LAUNCH_CHECK();
         std::swap(x, t);
       }
@@ -398,20 +516,31 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   const bool st0 = (l == 0);
   if (H.opts.smoother == RICH_SMOOTH_HYBRID_GS) return vcycle_level_hgs<T>(c, l, b, xres);
   // warp-per-row CSR kernels where rows are long
-  const bool wA = L.A.nnz > 6LL * n;
   const double st_bytes = (double)n * 8.0 * es;  // diag, 3 face weights, dinv, b, x in; x out
-  if (nu1 > 0) {
-    // first sweep from x = 0: x = D_l1^-1 b, elementwise on every level (on the
-    // finest level the stencil copy's 1/l1 array)
-    k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, st0 ? fine<T>(c).dinv : v.dinv, b, x);
+  if (st0 && nu1 == 1) {
+    // finest level, one pre-sweep: the sweep from zero and the residual in one pass
+    ProfScope ps("resid_l0", c->st, (double)n * 8.0 * es, 17.0 * n);
+    k_st_first<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
     RICH_LAUNCH_CHECK();
-    for (int s = 1; s < nu1; ++s) {
+  } else if (nu1 > 0) {
+    int s0 = 1;
+    if (st0) {
+      // finest level: the first two sweeps from zero in one pass
+      ProfScope ps("l1jacobi_l0", c->st, (double)n * 7.0 * es, 20.0 * n);
+      k_st_first<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, nullptr, x);
+      RICH_LAUNCH_CHECK();
+      s0 = 2;
+    } else {
+      // first sweep from x = 0: x = D_l1^-1 b, elementwise
+      k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
+      RICH_LAUNCH_CHECK();
+    }
+    for (int s = s0; s < nu1; ++s) {
       {
         ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
                      st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
         if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-        else if (wA) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
-        else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+        else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t));
       }
       RICH_LAUNCH_CHECK();
       std::swap(x, t);
@@ -419,8 +548,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     {
       ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st, st0 ? st_bytes : sweep_bytes - (double)n * es);
       if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-      else if (wA) csr_op<T, 3>(c->st, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r);
-      else k_resid<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, b, x, (T*)L.r);
+      else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r));
     }
     RICH_LAUNCH_CHECK();
   } else {
@@ -430,21 +558,15 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   Level& C = H.lv[l + 1];
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
-    if (L.R.nnz > 6LL * C.n)
-      csr_op<T, 0>(c->st, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr, (const T*)L.r,
-                   (T*)C.b);
-    else
-      k_spmv<T><<<grid_for(C.n), kBlock, 0, c->st>>>(C.n, v.rrp, v.rcol, v.rval, (const T*)L.r, (T*)C.b, 0);
+    RICH_CHECK(csr_op<T, 0>(c, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr,
+                            (const T*)L.r, (T*)C.b));
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    if (L.P.nnz > 6LL * n)
-      csr_op<T, 1>(c->st, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x);
-    else
-      k_spmv<T><<<g, kBlock, 0, c->st>>>(n, v.prp, v.pcol, v.pval, xc, x, 1);
+    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x));
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < nu2; ++s) {
@@ -452,8 +574,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
                    st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
       if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-      else if (wA) csr_op<T, 2>(c->st, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t);
-      else k_jacobi<T><<<g, kBlock, 0, c->st>>>(n, v.rp, v.col, v.val, v.dinv, b, x, t);
+      else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t));
     }
     RICH_LAUNCH_CHECK();
     std::swap(x, t);
@@ -849,6 +970,7 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
 
 int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
   if (o->maxit < 1 || !(o->eta > 0)) return RICH_EINVAL;
+  c->kw.fail_reason = 0;
   if (o->kind == RICH_KRYLOV_FGMRES) {
     if (o->restart < 1 || o->restart > 63) return RICH_EINVAL;
     RICH_CHECK(ensure_krylov(c, o->restart));
@@ -1041,8 +1163,12 @@ static int step_body(rich_ctx* c, double* p, double dt, const rich_newton_opts* 
 // its length, down to dt / 2^H; after an accepted substep the length doubles back
 // whenever the time reached (counted in units of dt / 2^H) is a multiple of the
 // doubled length, so the substeps end exactly at dt.
-static bool retryable(int s) {
-  return s == RICH_ENOTCONV_LIN || s == RICH_ENOTCONV_NEWTON || s == RICH_ELINESEARCH;
+// A Krylov solve that merely ran out of iterations ends the step: a shorter step
+// does not mend the preconditioner, and retrying would multiply the cost.  FCG's
+// (p, J p) <= 0 on an indefinite Jacobian is retried.
+static bool retryable(rich_ctx* c, int s) {
+  if (s == RICH_ENOTCONV_NEWTON || s == RICH_ELINESEARCH) return true;
+  return s == RICH_ENOTCONV_LIN && c->kw.fail_reason == 2;
 }
 
 static int advance_impl(rich_ctx* c, double* p, double dt, const rich_newton_opts* o, rich_step_stats* st) {
@@ -1078,9 +1204,10 @@ static int advance_impl(rich_ctx* c, double* p, double dt, const rich_newton_opt
     first = false;
     st->res = sub.res;
     if (s != RICH_OK) {
-      if (!retryable(s)) return s;
+      if (s != RICH_ECUDA)  // the substep's start is the last accepted state
+        RICH_CUDA(cudaMemcpyAsync(p, c->psave, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+      if (!retryable(c, s)) return s;
       st->dt_failures++;
-      RICH_CUDA(cudaMemcpyAsync(p, c->psave, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
       if (k == H) return s;
       ++k;
       continue;

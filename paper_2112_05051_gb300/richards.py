@@ -67,7 +67,7 @@ class AmgOpts(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int), ("aggregation", ctypes.c_int),
                 ("max_agg_size", ctypes.c_int), ("smoother", ctypes.c_int), ("hgs_seg", ctypes.c_int),
-                ("hgs_block", ctypes.c_int), ("isolated_join", ctypes.c_int)]
+                ("hgs_block", ctypes.c_int), ("autotune", ctypes.c_int), ("isolated_join", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -137,6 +137,7 @@ EXPORTS = {
                                              ctypes.POINTER(ctypes.c_double), _P]),
     "rich_kernel_launches": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
     "rich_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "rich_autotune_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -215,7 +216,8 @@ def default_newton_opts(**kw):
         if k in ("kind", "restart", "eta", "maxit"):
             setattr(o.krylov, k, v)
         elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
-                   "aggregation", "max_agg_size", "isolated_join", "smoother", "hgs_seg", "hgs_block"):
+                   "aggregation", "max_agg_size", "isolated_join", "smoother", "hgs_seg", "hgs_block",
+                   "autotune"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)
@@ -483,3 +485,14 @@ def fma_peak_tflops(fp64=True):
     v = ctypes.c_double()
     check(load().rich_measure_fma_peak(1 if fp64 else 0, ctypes.byref(v)), "rich_measure_fma_peak")
     return v.value
+
+
+def autotune_table():
+    """The CSR autotuner's choices: [(mode, value_bytes, rows, nnz, lanes, best_us)]."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(load().rich_autotune_table(buf, len(buf)), "rich_autotune_table")
+    out = []
+    for line in buf.value.decode().splitlines():
+        m, t, n, z, g, us = line.split()
+        out.append((int(m), int(t), int(n), int(z), int(g), float(us)))
+    return out

@@ -326,7 +326,7 @@ def test_substep_schedule_halves_on_failure_and_grows_back(monkeypatch):
         calls.append(h)
         st = newton.StepStats(newton_its=1, converged=True, res0=1.0, res=0.0)
         if h > 0.25 and len(calls) < 4:  # the first attempts above a quarter of the step fail
-            raise newton.LinearSolveError("forced")
+            raise newton.LineSearchError("forced")
         return p + h, st
 
     monkeypatch.setattr(newton, "step", fake_step)
@@ -336,6 +336,21 @@ def test_substep_schedule_halves_on_failure_and_grows_back(monkeypatch):
     assert calls == [1.0, 0.5, 0.25, 0.25, 0.5]
     assert st.substeps == 3 and st.dt_failures == 2 and st.dt_min == 0.25
     np.testing.assert_array_equal(p, np.ones(3))
+
+
+def test_krylov_running_out_of_iterations_is_not_retried(monkeypatch):
+    calls = []
+
+    def fake_step(prob, p, h, opt):
+        calls.append(h)
+        e = newton.LinearSolveError("forced")
+        e.stats = newton.StepStats()  # not an indefinite Jacobian: maxit
+        raise e
+
+    monkeypatch.setattr(newton, "step", fake_step)
+    with pytest.raises(newton.LinearSolveError):
+        newton.advance(None, np.zeros(2), 1.0, newton.NewtonOptions(max_dt_halvings=3))
+    assert calls == [1.0]
 
 
 def test_substep_schedule_gives_up_at_the_smallest_step(monkeypatch):
