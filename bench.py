@@ -93,7 +93,9 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
     ap.add_argument("--serving-coarse-max", type=int, default=500)
     ap.add_argument("--serving-aggregation", type=int, default=0, help="0: MIS-2, 1: matching (SMATCH-style)")
-    ap.add_argument("--serving-halvings", type=int, default=8, help="time-step control of served requests (0: off)")
+    ap.add_argument("--serving-halvings", type=int, default=0,
+                    help="time-step control of served requests (0: off; retries multiply the device time of the "
+                         "failing requests, measured 3-10x on this stream)")
     return ap.parse_args()
 
 
@@ -362,9 +364,8 @@ def serving_run(args, rb):
         reqs.append((grid, ks, kmean, n))
     # coarsest level below 500 unknowns: its dense inverse is redone at every
     # refresh, and a short one-step request refreshes ~10 times
-    # time-step control: a request whose step fails is retried in halves (a harmonic
-    # request with an indefinite Jacobian fails each attempt after one FCG iteration)
-    halvings = getattr(args, "serving_halvings", 8)
+    # optional time-step control: a request whose step fails is retried in halves
+    halvings = getattr(args, "serving_halvings", 0)
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
                                   product_lists=args.serving_lists, coarse_max=args.serving_coarse_max,
                                   aggregation=args.serving_aggregation, max_dt_halvings=halvings,
@@ -441,19 +442,26 @@ def workload_config(w, grid):
             "l2": "working set > 129 MB L2 (7-diagonal Jacobian alone 118 MB, FGMRES basis 1 GB)"}
 
 
-def run_steps(ctx, pd, dts, count, opts, first=0, record=None, snapshot_at=None):
+class StepFailure(RuntimeError):
+    def __init__(self, step, status, stats, done):
+        super().__init__("step %d failed with status %d" % (step, status))
+        self.step, self.status, self.stats, self.done = step, status, stats, done
+
+
+def run_steps(ctx, pd, dts, count, opts, first=0, record=None):
     """Step the schedule count times (step m uses dt_{m mod len}); returns the per-step stats.
 
     record: a list of CUDA events, one recorded after each step on the current stream.
-    snapshot_at: {step index: None} filled with a device copy of p after that step."""
+    A failing step raises StepFailure carrying its statistics and the steps done."""
     out = []
     for q in range(count):
         m = first + q
-        out.append(ctx.step(pd, dts[m % len(dts)], opts))
+        s, st = ctx.step(pd, dts[m % len(dts)], opts, check_status=False)
         if record is not None:
             record[q].record()
-        if snapshot_at is not None and q + 1 in snapshot_at:
-            snapshot_at[q + 1] = pd.clone()
+        if s != 0:
+            raise StepFailure(m, s, st, out)
+        out.append(st)
     return out
 
 
@@ -554,9 +562,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     lib.rich_kernel_launches(ctypes.byref(l0))
     e0.record()
-    stats = run_steps(ctx, pd, dts, K, opts, record=marks)
+    failure = None
+    try:
+        stats = run_steps(ctx, pd, dts, K, opts, record=marks)
+    except StepFailure as f:  # a workload the method cannot solve: report where it stopped
+        stats = f.done
+        failure = {"step": f.step, "status": rb.ERRORS.get(f.status, str(f.status)),
+                   "stats": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in f.stats.as_dict().items()},
+                   "p_range": [float(pd.min()), float(pd.max())]}
     e1.record()
     torch.cuda.synchronize()
+    if failure is not None:
+        clk.stop()
+        lib_used, _ = rb.memory_peak()
+        ctx.close()
+        print(json.dumps({"metric": "DOF*Newton-steps/s", "value": None, "unit": "DOF*Newton-steps/s",
+                          "config": workload_config(w, grid), "failed": failure,
+                          "steps_done": [x.newton_its for x in stats], "peak_device_memory_bytes": lib_used,
+                          "amg_precision": "fp32" if prec == rb.PREC_MIXED else "fp64"}))
+        return 1
+    K = len(stats)
     lib.rich_kernel_launches(ctypes.byref(l1))
     if dist:
         dist.barrier()

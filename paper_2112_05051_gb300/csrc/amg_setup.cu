@@ -342,24 +342,26 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t* keys, int M, int lan
   }
 }
 
-constexpr int kEscWarps = 2;     // warps per block of the shared-memory ESC kernel
-constexpr int kEscCap = 1024;    // products per warp held in shared memory
+constexpr int kEscCap = 1024;    // most products per row the shared-memory ESC kernel takes
 
 // mode 0: cnt[row] = number of distinct columns; mode 1: write the compressed row at crp[row].
-// Rows whose product count exceeds kEscCap are left to k_spgemm_hash.
+// Each warp owns `cap` key/value slots of shared memory (cap = the launch's largest
+// product count rounded up to a power of two, at most kEscCap), so short rows
+// (the 7-point level: tens of products) run many warps per SM.  Rows whose product
+// count exceeds kEscCap are left to k_spgemm_hash.
 __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* __restrict__ acol,
                              const double* __restrict__ aval, const int* __restrict__ brp,
                              const int* __restrict__ bcol, const double* __restrict__ bval,
                              const int* __restrict__ u, int mode, const int* __restrict__ crp,
-                             int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt) {
+                             int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt, int cap) {
   extern __shared__ unsigned char smem[];
   int wpb = blockDim.x >> 5;
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint64_t* skeys = reinterpret_cast<uint64_t*>(smem) + (size_t)w * kEscCap;
-  double* svals = reinterpret_cast<double*>(smem + (size_t)wpb * kEscCap * sizeof(uint64_t)) + (size_t)w * kEscCap;
+  uint64_t* skeys = reinterpret_cast<uint64_t*>(smem) + (size_t)w * cap;
+  double* svals = reinterpret_cast<double*>(smem + (size_t)wpb * cap * sizeof(uint64_t)) + (size_t)w * cap;
   for (int row = blockIdx.x * wpb + w; row < nrows; row += gridDim.x * wpb) {
     int ur = u[row];
-    if (ur > kEscCap) continue;
+    if (ur > cap) continue;
     uint64_t* keys = skeys;
     double* vals = svals;
     int M = 1;
@@ -1095,8 +1097,12 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
   int umax = 0;
   RICH_CHECK(spgemm_upper(c, A, B, u, &umax));
   if (umax >= (1 << 30)) return RICH_ELIMIT;
-  size_t smem = (size_t)kEscWarps * kEscCap * (sizeof(uint64_t) + sizeof(double));
-  int nblk = (n + kEscWarps - 1) / kEscWarps;
+  // shared memory per warp sized by the largest row of this product
+  int cap = 32;
+  while (cap < umax && cap < kEscCap) cap <<= 1;
+  const int esc_warps = cap <= 128 ? 8 : (cap <= 512 ? 4 : 2);
+  size_t smem = (size_t)esc_warps * cap * (sizeof(uint64_t) + sizeof(double));
+  int nblk = (n + esc_warps - 1) / esc_warps;
   if (nblk > 65535 * 4) nblk = 65535 * 4;
   bool big = umax > kEscCap;
   size_t hsmem = (size_t)kHashSlots * (sizeof(int) + sizeof(double) + sizeof(uint64_t));
@@ -1122,8 +1128,8 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
       RICH_CHECK(dalloc(&C.col, nnz));
       RICH_CHECK(dalloc(&C.val, nnz));
     }
-    k_spgemm_esc<<<nblk, 32 * kEscWarps, smem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
-                                                       C.rowptr, C.col, C.val, cnt);
+    k_spgemm_esc<<<nblk, 32 * esc_warps, smem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
+                                                       C.rowptr, C.col, C.val, cnt, cap);
     RICH_LAUNCH_CHECK();
     if (big) {
       int hb = n < 8 * kNumSM ? n : 8 * kNumSM;

@@ -352,10 +352,14 @@ class Context:
             check(s, "krylov_solve")
         return s, st
 
-    def step(self, p, dt, opts=None):
+    def step(self, p, dt, opts=None, check_status=True):
+        """One backward-Euler step; returns the step statistics (and, with
+        check_status=False, the status code first instead of raising on failure)."""
         st = StepStats()
-        check(load().rich_step(self.h, _ptr(p), dt, ctypes.byref(opts) if opts is not None else None,
-                               ctypes.byref(st)), "rich_step")
+        s = load().rich_step(self.h, _ptr(p), dt, ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+        if not check_status:
+            return s, st
+        check(s, "rich_step")
         return st
 
     def step_host(self, p_host, dt, opts=None):
