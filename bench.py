@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="print only the request-stream measurement")
     ap.add_argument("--serving-coarse-max", type=int, default=500)
     ap.add_argument("--serving-aggregation", type=int, default=0, help="0: MIS-2, 1: matching (SMATCH-style)")
+    ap.add_argument("--serving-batch", type=int, default=8,
+                    help="largest packed batch of same-shape requests (1: one request per slot)")
     ap.add_argument("--serving-halvings", type=int, default=0,
                     help="time-step control of served requests (0: off; retries multiply the device time of the "
                          "failing requests, measured 3-10x on this stream)")
@@ -375,7 +377,9 @@ def serving_run(args, rb):
         grid, ks, kmean, n = q
         return srv.submit(grid, soil, bc, kmean, 1.0, p0=p0s[n], ks=ks, precision=rb.PREC_MIXED, opts=opts)
 
-    srv = rb.Server(slots=args.serving_slots)
+    batch_max = getattr(args, "serving_batch", 1)
+    srv = rb.Server(slots=args.serving_slots, batch_max=batch_max) if batch_max > 1 else rb.Server(
+        slots=args.serving_slots)
     # warm-up: one request of each size (library kernels loaded, memory pool primed)
     for n in sizes:
         k = next((j for j, q in enumerate(reqs) if q[3] == n), None)
@@ -426,7 +430,9 @@ def serving_run(args, rb):
             "capacity_rps": mu, "capacity_converged_rps": st_b["converged_per_s"], "burst_s": t_burst,
             "burst_dof_newton_per_s": st_b["dof_newton_per_s"], "rate_rps": lam, "arrivals": "Poisson, seed 5",
             "stream_s": t_stream, "latency_ms_all": st_s["latency_ms_all"],
-            "failed": st_s["failed"], "max_in_flight": cnt["max_in_flight"],
+            "failed": st_s["failed"], "max_in_flight": cnt["max_in_flight"], "batch_max": batch_max,
+            "batched_requests": sum(1 for r in stream if r.get("batch_size", 1) > 1),
+            "batch_reruns": sum(1 for r in stream if r.get("batch_rerun", 0)),
             "mix_vs_alone_max_rel_dev": dev, "mix_vs_alone_checked": checked,
             "admission": "FIFO, a free slot and the request's device-memory estimate within 80% of free HBM"}
 

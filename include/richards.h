@@ -331,6 +331,31 @@ int rich_step(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_opts* o
 int rich_step_host(rich_ctx* ctx, double* p_host, double dt, const rich_newton_opts* opts,
                    rich_step_stats* stats_host);
 
+/* ---- batched steps (several small problems, one launch per operation) ----- */
+/* A context holding nbatch (1..32) independent problems of one grid shape,
+ * stacked along z: problem b owns cells [b n, (b+1) n) (n = nx ny nz of `grid`),
+ * the stacked grid keeps the problems' spacing, and the faces between two stacked
+ * problems are their own bottom and top faces (bc applies to each).  soil->ks_field_dev,
+ * if not NULL, holds nbatch * n values; per-cell Dirichlet values are accepted on the
+ * z faces only (the same for every problem).  The paper has no batched form; this is
+ * how the request server packs small requests: every kernel launch (constitutive
+ * law, residual, Jacobian, stencil SpMV, each V-cycle level operation) covers all
+ * problems, while the Newton iteration, its line search and FCG keep their scalars,
+ * convergence tests and statistics per problem. */
+int rich_create_batch(const rich_grid* grid, int nbatch, const rich_soil* soil, int kmean, const rich_bc* bc,
+                      int precision, void* stream, rich_ctx** out);
+/* One backward-Euler step (Sec. 3) of every problem of a batch context: p_dev holds
+ * nbatch * n values; stats_host and status_host receive one entry per problem
+ * (status as rich_step's; a problem that fails is left at its last accepted Newton
+ * iterate and does not hold the others back).  opts must use FCG without time-step
+ * control (RICH_EINVAL otherwise); there is no FGMRES fallback in a batch, so a
+ * problem whose FCG fails reports RICH_ENOTCONV_LIN.  The AMG hierarchy is built on
+ * the block-diagonal diffusion matrix of all problems (aggregates never cross
+ * problems) at the first call and refreshed afterwards.  Returns RICH_OK when the
+ * batch ran (whatever the per-problem statuses), an error code otherwise. */
+int rich_step_batch(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_opts* opts,
+                    rich_step_stats* stats_host, int* status_host);
+
 /* ---- instrumentation ----------------------------------------------------- */
 /* Measured arithmetic peak of the current device in TFLOP/s (2 flops per fused
  * multiply-add): FP64 (fp64 != 0) or FP32 FMA pipes, non-tensor, timed with CUDA
@@ -397,6 +422,14 @@ typedef struct {
   int slots;               /* requests in flight at once (8) */
   double mem_budget_bytes; /* device bytes requests and sessions may hold; <= 0: 80 % of the free memory at creation */
   int max_sessions;        /* resident sessions kept at most (64) */
+  int batch_max;           /* 1 (default): one request per slot.  B > 1: a worker that takes a one-off
+                              request also takes up to B-1 more queued one-off requests of the same grid,
+                              soil parameters, mean, boundary values, precision, dt and options (FCG,
+                              no time-step control) and steps them together as one batch
+                              (rich_create_batch / rich_step_batch); a member whose step fails in the
+                              batch is rerun alone, so every result is the lone path's wherever the
+                              batch cannot match it */
+  int batch_min_cells;     /* only requests of at most this many cells are batched (300000) */
 } rich_server_opts;
 
 typedef struct {
@@ -424,6 +457,8 @@ typedef struct {
   int slot;                    /* worker slot that ran it */
   double mem_estimate;         /* device bytes reserved for it at admission */
   double mem_in_flight;        /* bytes reserved by all admitted requests and sessions, itself included */
+  int batch_size;              /* requests stepped together with this one (1: alone) */
+  int batch_rerun;             /* 1 if its step failed in a batch and was rerun alone */
 } rich_request_result;
 
 void rich_default_server_opts(rich_server_opts* o);

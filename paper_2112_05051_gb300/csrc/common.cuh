@@ -73,6 +73,7 @@ struct SoilP {
 
 struct GridP {
   int nx, ny, nz;
+  int nzs;           // layers per stacked problem (nz unless a batch stacks several problems along z)
   long long n;
   double inv_h[3];   // 1/h_d
   double inv_h2[3];  // 1/h_d^2
@@ -236,6 +237,7 @@ struct rich_ctx {
   double* rhs = nullptr;
   double* pbuf = nullptr;      // device p for rich_step_host
   double* psave = nullptr;     // p at the start of a substep (time-step control)
+  int nbatch = 1;              // problems stacked along z (rich_create_batch)
   double* bc_fields[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // owned per-cell BC values
   bool amg_ever = false;
 };
@@ -415,8 +417,10 @@ void dfree(T*& p) {
 int constit_eval(rich_ctx* c, const double* p);
 // constit_current: the context's K, K', s, s' already hold the values of this p
 // (the last constitutive evaluation was at the same pressure), so they are reused.
+// nseg > 1: the grid stacks nseg problems along z and the norms are summed per problem
+// (dsc[q * nseg + s] for quantity q of problem s).
 int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms,
-                  bool constit_current = false);
+                  bool constit_current = false, int nseg = 1);
 int jacobian_eval(rich_ctx* c, const double* p, double dt, bool constit_current = false);
 int stencil_apply(rich_ctx* c, const double* A7, const double* x, double* y);
 int refresh_a0_values(rich_ctx* c);

@@ -161,6 +161,7 @@ extern "C" int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soi
   g.nx = grid->nx;
   g.ny = grid->ny;
   g.nz = grid->nz;
+  g.nzs = grid->nz;
   g.n = n;
   double h[3] = {grid->lx / (grid->nx + 1), grid->ly / (grid->ny + 1), grid->lz / (grid->nz + 1)};
   for (int d = 0; d < 3; ++d) {

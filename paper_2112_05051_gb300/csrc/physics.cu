@@ -56,8 +56,9 @@ __device__ __forceinline__ bool face_neighbour(const GridP& g, const BCP& bc, co
                                                double ksc, FaceNb& nb) {
   int axis = f >> 1;
   int side = (f & 1) ? 1 : -1;
-  int coord = axis == 0 ? i : (axis == 1 ? j : k);
-  int extent = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+  // a batch stacks problems along z: their top and bottom layers are boundaries
+  int coord = axis == 0 ? i : (axis == 1 ? j : (g.nzs == g.nz ? k : k % g.nzs));
+  int extent = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nzs);
   bool bnd = side > 0 ? (coord == extent - 1) : (coord == 0);
   if (bnd) {
     if (bc.kind[f] == RICH_BC_NOFLUX) return false;
@@ -83,7 +84,10 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
   double acc[2] = {0.0, 0.0};
   double amax = 0.0;
   const double rdt = so.rho_phi / dt;  // one division per thread, not per cell
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.n;
+  // gridDim.y problems stacked along z: block row y sums the cells of problem y
+  const long long ns = g.n / gridDim.y;
+  const long long c0 = (long long)blockIdx.y * ns, c1 = c0 + ns;
+  for (long long c = c0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < c1;
        c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % g.nx);
     long long r = c / g.nx;
@@ -120,10 +124,11 @@ __global__ void k_residual(GridP g, SoilP so, BCP bc, int kmean, const double* _
   }
   block_sum<2>(acc);
   double m = block_max(amax);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = acc[0];
-    partials[gridDim.x + blockIdx.x] = m;
-    partials[2 * gridDim.x + blockIdx.x] = acc[1];
+  if (threadIdx.x == 0) {  // partials[(q * nseg + seg) * gridDim.x + block]
+    const long long S = gridDim.y, b = blockIdx.y * (long long)gridDim.x + blockIdx.x;
+    partials[b] = acc[0];
+    partials[S * gridDim.x + b] = m;
+    partials[2 * S * gridDim.x + b] = acc[1];
   }
 }
 
@@ -245,19 +250,21 @@ int constit_eval(rich_ctx* c, const double* p) {
 }
 
 int residual_eval(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, bool want_norms,
-                  bool constit_current) {
+                  bool constit_current, int nseg) {
   if (!constit_current) RICH_CHECK(constit_eval(c, p));
-  int nb = red_grid(c->g.n);
+  int nb = red_grid(c->g.n / nseg);
+  if ((long long)nb * nseg * 3 > (long long)kRedBlocks * 64) return RICH_ELIMIT;  // partials buffer
   {
     ProfScope ps("residual", c->st, (double)c->g.n * (32.0 + (c->ks ? 8.0 : 0.0)));
-    k_residual<<<nb, kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->S, s_old, c->ks, dt, F,
-                                         c->partials);
+    k_residual<<<dim3(nb, nseg), kBlock, 0, c->st>>>(c->g, c->soil, c->bc, c->kmean, p, c->K, c->S, s_old, c->ks, dt,
+                                                     F, c->partials);
   }
   RICH_LAUNCH_CHECK();
-  if (want_norms) {  // dsc[0] = ||F||^2, dsc[1] = ||F||_inf, dsc[2] = ||term magnitudes||^2
-    RICH_CHECK(finish_sums(c, c->partials, nb, 1, c->dsc + 0));
-    RICH_CHECK(finish_max(c, c->partials + nb, nb, c->dsc + 1));
-    RICH_CHECK(finish_sums(c, c->partials + 2 * nb, nb, 1, c->dsc + 2));
+  if (want_norms) {  // dsc[q * nseg + s]: q = 0 ||F||^2, 1 ||F||_inf, 2 ||term magnitudes||^2
+    const long long S = nseg;
+    RICH_CHECK(finish_sums(c, c->partials, nb, nseg, c->dsc + 0));
+    for (int s = 0; s < nseg; ++s) RICH_CHECK(finish_max(c, c->partials + (S + s) * nb, nb, c->dsc + S + s));
+    RICH_CHECK(finish_sums(c, c->partials + 2 * S * nb, nb, nseg, c->dsc + 2 * S));
   }
   return RICH_OK;
 }
@@ -391,6 +398,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   c->g.nx = grid->nx;
   c->g.ny = grid->ny;
   c->g.nz = grid->nz;
+  c->g.nzs = grid->nz;
   c->g.n = n;
   double h[3] = {grid->lx / (grid->nx + 1), grid->ly / (grid->ny + 1), grid->lz / (grid->nz + 1)};
   for (int d = 0; d < 3; ++d) {

@@ -159,6 +159,83 @@ static SrvRequest* srv_pick(rich_server* s, std::vector<SrvSession*>* evict) {
   return nullptr;
 }
 
+// Whether request b may be stepped in one batch with request a (rich_step_batch).
+static bool srv_batchable(const rich_server* s, const rich_request& a, const rich_request& b) {
+  if (a.session || b.session || !a.p0_host || !b.p0_host) return false;
+  if ((long long)a.grid.nx * a.grid.ny * a.grid.nz > s->o.batch_min_cells) return false;
+  if (!srv_same_shape(a, b) || a.dt != b.dt) return false;
+  if ((a.ks_field_host == nullptr) != (b.ks_field_host == nullptr)) return false;
+  if (a.opts.krylov.kind != RICH_KRYLOV_FCG || a.opts.max_dt_halvings != 0) return false;
+  return memcmp(&a.opts, &b.opts, sizeof(a.opts)) == 0;
+}
+
+// Under s->mu: queued one-off requests that can join q's batch and fit the budget.
+static void srv_pick_mates(rich_server* s, SrvRequest* q, std::vector<SrvRequest*>* mates) {
+  if (s->o.batch_max <= 1) return;
+  for (auto it = s->queue.begin(); it != s->queue.end() && (int)mates->size() + 1 < s->o.batch_max;) {
+    SrvRequest* m = *it;
+    if (srv_batchable(s, q->r, m->r) && s->reserved + m->est <= s->budget) {
+      s->reserved += m->est;
+      mates->push_back(m);
+      it = s->queue.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+static void srv_run(SrvRequest* q, SrvSession* se, cudaStream_t st);
+
+// Steps q and its mates as one batch; a member whose step fails is rerun alone.
+static void srv_run_batch(std::vector<SrvRequest*>& qs, cudaStream_t st) {
+  const rich_request& r0 = qs[0]->r;
+  const int B = (int)qs.size();
+  const long long n = (long long)r0.grid.nx * r0.grid.ny * r0.grid.nz;
+  int status = RICH_OK;
+  {
+    AllocStream guard(st);
+    double* ks = nullptr;
+    double* p = nullptr;
+    rich_ctx* c = nullptr;
+    if (r0.ks_field_host) {
+      status = dalloc(&ks, n * B);
+      for (int b = 0; b < B && !status; ++b)
+        if (cudaMemcpyAsync(ks + b * n, qs[b]->r.ks_field_host, sizeof(double) * n, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+          status = RICH_ECUDA;
+    }
+    rich_soil so = r0.soil;
+    so.ks_field_dev = ks;
+    if (!status) status = rich_create_batch(&r0.grid, B, &so, r0.kmean, &r0.bc, r0.precision, st, &c);
+    dfree(ks);
+    if (!status) status = dalloc(&p, n * B);
+    for (int b = 0; b < B && !status; ++b)
+      if (cudaMemcpyAsync(p + b * n, qs[b]->r.p0_host, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        status = RICH_ECUDA;
+    std::vector<rich_step_stats> stats(B);
+    std::vector<int> stb(B, RICH_ECUDA);
+    if (!status) status = rich_step_batch(c, p, r0.dt, &r0.opts, stats.data(), stb.data());
+    for (int b = 0; b < B; ++b) {
+      qs[b]->res.batch_size = B;
+      qs[b]->res.batch_rerun = 0;
+      if (status || stb[b] != RICH_OK) continue;
+      if (qs[b]->r.p_out_host &&
+          cudaMemcpyAsync(qs[b]->r.p_out_host, p + b * n, sizeof(double) * n, cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess)
+        stb[b] = RICH_ECUDA;
+      qs[b]->res.status = stb[b];
+      qs[b]->res.stats = stats[b];
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && !status) status = RICH_ECUDA;
+    dfree(p);
+    if (c) rich_destroy(c);
+    for (int b = 0; b < B; ++b)
+      if (status || stb[b] != RICH_OK) qs[b]->res.batch_rerun = 1;
+  }
+  for (int b = 0; b < B; ++b)
+    if (qs[b]->res.batch_rerun) srv_run(qs[b], nullptr, st);  // the lone path decides its result
+}
+
 static void srv_run(SrvRequest* q, SrvSession* se, cudaStream_t st) {
   const rich_request& r = q->r;
   AllocStream guard(st);
@@ -223,6 +300,7 @@ static void srv_worker(rich_server* s, int slot) {
     SrvRequest* q = nullptr;
     SrvSession* se = nullptr;
     std::vector<SrvSession*> evict;
+    std::vector<SrvRequest*> group;
     {
       std::unique_lock<std::mutex> lock(s->mu);
       for (;;) {
@@ -232,13 +310,19 @@ static void srv_worker(rich_server* s, int slot) {
       }
       if (q) {
         if (q->r.session) se = s->sessions[q->r.session];
-        ++s->in_flight;
-        ++s->admitted;
+        group.push_back(q);
+        if (!se) srv_pick_mates(s, q, &group);
+        const double t_admit = srv_now(s);
+        for (SrvRequest* m : group) {
+          ++s->in_flight;
+          ++s->admitted;
+          m->res.t_admit = t_admit;
+          m->res.slot = slot;
+          m->res.mem_estimate = m->est;
+          m->res.mem_in_flight = s->reserved;
+          m->res.batch_size = 1;
+        }
         if (s->in_flight > s->max_in_flight) s->max_in_flight = s->in_flight;
-        q->res.t_admit = srv_now(s);
-        q->res.slot = slot;
-        q->res.mem_estimate = q->est;
-        q->res.mem_in_flight = s->reserved;
       }
     }
     for (SrvSession* v : evict) srv_free_session(v, st);
@@ -247,11 +331,13 @@ static void srv_worker(rich_server* s, int slot) {
       if (s->stop && s->queue.empty()) break;
       continue;
     }
-    srv_run(q, se, st);
+    if (group.size() > 1) srv_run_batch(group, st);
+    else srv_run(q, se, st);
     SrvSession* dead = nullptr;
     {
       std::lock_guard<std::mutex> lock(s->mu);
-      if (!q->r.session) s->reserved -= q->est;
+      for (SrvRequest* m : group)
+        if (!m->r.session) s->reserved -= m->est;
       if (se && !se->ctx) {  // the session's first request failed before creating its state
         s->sessions.erase(se->id);
         s->reserved -= se->est;
@@ -259,9 +345,12 @@ static void srv_worker(rich_server* s, int slot) {
         se = nullptr;
       }
       if (se) se->busy = false;
-      --s->in_flight;
-      q->res.t_done = srv_now(s);
-      q->done = true;
+      const double t_done = srv_now(s);
+      for (SrvRequest* m : group) {
+        --s->in_flight;
+        m->res.t_done = t_done;
+        m->done = true;
+      }
     }
     delete dead;
     s->cv_done.notify_all();
@@ -281,6 +370,8 @@ void rich_default_server_opts(rich_server_opts* o) {
   o->slots = 8;
   o->mem_budget_bytes = 0.0;
   o->max_sessions = 64;
+  o->batch_max = 1;
+  o->batch_min_cells = 300000;
 }
 
 int rich_server_create(const rich_server_opts* opts, rich_server** out) {
@@ -288,7 +379,7 @@ int rich_server_create(const rich_server_opts* opts, rich_server** out) {
   *out = nullptr;
   rich_server_opts o;
   if (opts) o = *opts; else rich_default_server_opts(&o);
-  if (o.slots < 1 || o.slots > 256 || o.max_sessions < 0) return RICH_EINVAL;
+  if (o.slots < 1 || o.slots > 256 || o.max_sessions < 0 || o.batch_max < 1 || o.batch_max > 32) return RICH_EINVAL;
   rich_server* s = new rich_server();
   s->o = o;
   s->t0 = std::chrono::steady_clock::now();

@@ -100,7 +100,8 @@ class StepStats(ctypes.Structure):
 
 
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double), ("max_sessions", ctypes.c_int)]
+    _fields_ = [("slots", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double), ("max_sessions", ctypes.c_int),
+                ("batch_max", ctypes.c_int), ("batch_min_cells", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -112,7 +113,8 @@ class Request(ctypes.Structure):
 class RequestResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("stats", StepStats), ("t_submit", ctypes.c_double),
                 ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("slot", ctypes.c_int),
-                ("mem_estimate", ctypes.c_double), ("mem_in_flight", ctypes.c_double)]
+                ("mem_estimate", ctypes.c_double), ("mem_in_flight", ctypes.c_double), ("batch_size", ctypes.c_int),
+                ("batch_rerun", ctypes.c_int)]
 
 
 class AmgInfo(ctypes.Structure):
@@ -156,6 +158,10 @@ EXPORTS = {
     "rich_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(NewtonOpts), ctypes.POINTER(StepStats)]),
     "rich_step_host": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(NewtonOpts),
                                       ctypes.POINTER(StepStats)]),
+    "rich_create_batch": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Soil), ctypes.c_int,
+                                         ctypes.POINTER(BC), ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "rich_step_batch": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(NewtonOpts), ctypes.POINTER(StepStats),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "rich_default_newton_opts": (None, [ctypes.POINTER(NewtonOpts)]),
     "rich_default_amg_opts": (None, [ctypes.POINTER(AmgOpts)]),
     "rich_default_server_opts": (None, [ctypes.POINTER(ServerOpts)]),
@@ -374,6 +380,40 @@ class Context:
         return st
 
 
+class BatchContext(Context):
+    """nbatch problems of one grid stacked along z (rich_create_batch / rich_step_batch).
+
+    ks: None or an (nbatch * n) array of K_s values, problem b at [b n, (b+1) n)."""
+
+    def __init__(self, grid: synth.Grid, nbatch: int, soil: synth.Soil, bc: synth.BC, kmean: int, ks=None,
+                 precision=PREC_MIXED):
+        import torch
+        lib = load()
+        g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        self._ks = None
+        if ks is not None:
+            self._ks = torch.as_tensor(ks, dtype=torch.float64).reshape(-1).cuda().contiguous()
+        s = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
+                 _ptr(self._ks) if self._ks is not None else None)
+        self._bc_keep = []
+        b = _bc_struct(bc, self._bc_keep)
+        h = ctypes.c_void_p()
+        check(lib.rich_create_batch(ctypes.byref(g), nbatch, ctypes.byref(s), kmean, ctypes.byref(b), precision,
+                                    _stream(), ctypes.byref(h)), "rich_create_batch")
+        self.h = h
+        self.nbatch = nbatch
+        self.n = grid.n * nbatch
+        self.grid = grid
+
+    def step_batch(self, p, dt, opts=None):
+        """Returns ([status per problem], [StepStats per problem])."""
+        st = (StepStats * self.nbatch)()
+        status = (ctypes.c_int * self.nbatch)()
+        check(load().rich_step_batch(self.h, _ptr(p), dt, ctypes.byref(opts) if opts is not None else None, st,
+                                     status), "rich_step_batch")
+        return list(status), list(st)
+
+
 def default_server_opts(**kw):
     o = ServerOpts()
     load().rich_default_server_opts(ctypes.byref(o))
@@ -392,10 +432,11 @@ class Server:
     Newton iterate).
     """
 
-    def __init__(self, slots=8, mem_budget_bytes=0.0, max_sessions=64):
+    def __init__(self, slots=8, mem_budget_bytes=0.0, max_sessions=64, batch_max=1):
         self._lib = load()
         self.h = ctypes.c_void_p()
-        o = default_server_opts(slots=slots, mem_budget_bytes=float(mem_budget_bytes), max_sessions=max_sessions)
+        o = default_server_opts(slots=slots, mem_budget_bytes=float(mem_budget_bytes), max_sessions=max_sessions,
+                                batch_max=batch_max)
         check(self._lib.rich_server_create(ctypes.byref(o), ctypes.byref(self.h)), "rich_server_create")
         self._keep = {}
 
@@ -437,7 +478,8 @@ class Server:
         keep, out = self._keep.pop(rid)
         return {"status": res.status, "stats": res.stats.as_dict(), "t_submit": res.t_submit,
                 "t_admit": res.t_admit, "t_done": res.t_done, "slot": res.slot, "mem_estimate": res.mem_estimate,
-                "mem_in_flight": res.mem_in_flight, "p": out}
+                "mem_in_flight": res.mem_in_flight, "batch_size": res.batch_size, "batch_rerun": res.batch_rerun,
+                "p": out}
 
     def wait(self, rid):
         res = RequestResult()
