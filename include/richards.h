@@ -64,6 +64,17 @@ extern "C" {
 #define RICH_SMOOTH_L1JACOBI   0
 #define RICH_SMOOTH_HYBRID_GS  1
 
+/* Preconditioner of the Krylov solves.  AMG: the V-cycle above.  AS: the paper's
+ * one-level additive Schwarz preconditioner (Sec. 5.2, eq. (AS); Sec. 6 overlaps the
+ * subdomains by one layer and applies ILU(0) to each), M^-1 = sum_t R_t^T M_t^-1 R_t
+ * over subdomains that are boxes of as_block cells per side grown by as_overlap
+ * layers; M_t is the principal submatrix of the diffusion matrix A_aux and M_t^-1
+ * its ILU(0) solve in the box's lexicographic order (for the 7-point matrix:
+ * L = I + L_A D^-1, U = D + U_A, D_c = m_cc - sum over lower neighbours of
+ * m_ck^2 / D_k); the contributions covering a cell are summed in a fixed order. */
+#define RICH_PRECOND_AMG       0
+#define RICH_PRECOND_AS        1
+
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
  * (eq. (upstream_mean)) K_U if p_U - p_L >= 0 else K_L with U the +d cell;
@@ -158,6 +169,9 @@ typedef struct {
   int hgs_seg;             /* hybrid Gauss-Seidel blocks on the finest grid: segments of this many cells of
                               one vertical column (16) */
   int hgs_block;           /* hybrid Gauss-Seidel blocks on coarser levels: this many consecutive rows (16) */
+  int precond;             /* RICH_PRECOND_AMG (default) or RICH_PRECOND_AS */
+  int as_block;            /* AS subdomain box: cells per side (8) */
+  int as_overlap;          /* AS overlap in layers (1, as in the paper's runs); as_block + 2 as_overlap <= 24 */
   int autotune;            /* 1 (default): the first time a CSR row operation of the V-cycle (sweep,
                               residual, restriction, prolongation) meets a matrix shape, every lane-group
                               width (1..32 lanes per row) is timed on it and the fastest is kept for the

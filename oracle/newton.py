@@ -40,6 +40,7 @@ import scipy.sparse.linalg as spla
 
 from . import amg
 from . import constitutive as cst
+from . import schwarz
 from . import discretization as disc
 from . import krylov
 
@@ -70,6 +71,9 @@ class NewtonOptions:
     lambda_min: float = 1e-10
     isolated_join: bool = True    # pass 3 of the MIS-2 aggregation (amg module docstring)
     smoother: str = "l1jacobi"    # or "hgs": hybrid backward/forward Gauss-Seidel (amg module)
+    precond: str = "amg"          # or "as": one-level additive Schwarz with ILU(0) (schwarz module)
+    as_block: int = 8
+    as_overlap: int = 1
     hgs_seg: int = 16
     hgs_block: int = 16
     max_dt_halvings: int = 0      # time-step control (advance); 0 = off
@@ -149,7 +153,10 @@ def armijo_backtrack(merit, f0, slope, c, lambda_min):
 def linear_solve(J, h, rhs, opt, stats):
     if opt.krylov == "direct":  # exact correction (tests: separates Newton from the preconditioner)
         return spla.spsolve(sp.csc_matrix(J), rhs), 0, True
-    prec = lambda v: amg.vcycle(h, v, opt.nu1, opt.nu2)
+    if isinstance(h, schwarz.AS):
+        prec = h.apply
+    else:
+        prec = lambda v: amg.vcycle(h, v, opt.nu1, opt.nu2)
     mv = lambda v: J @ v
     if opt.krylov == "fcg":
         info = {}
@@ -198,7 +205,9 @@ def _step(prob, p, dt, opt, st):
             break
         J = prob.jacobian(p, dt)
         A = prob.aux(p, dt)
-        if prob.hierarchy is None or (opt.amg_policy == "rebuild_step" and r == 0):
+        if opt.precond == "as":  # subdomain factors of the current A_aux
+            prob.hierarchy = schwarz.AS(A, (prob.grid.nx, prob.grid.ny, prob.grid.nz), opt.as_block, opt.as_overlap)
+        elif prob.hierarchy is None or (opt.amg_policy == "rebuild_step" and r == 0):
             prob.hierarchy = amg.setup(A, opt.theta, opt.amg_seed, opt.coarse_max, opt.max_levels,
                                        smooth_levels=opt.smooth_levels, aggregation=opt.aggregation,
                                        max_agg_size=opt.max_agg_size, isolated_join=opt.isolated_join,

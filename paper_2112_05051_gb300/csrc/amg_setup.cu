@@ -1501,6 +1501,7 @@ void amg_free(rich_ctx* c) {
   if (H.gj_exec) cudaGraphExecDestroy(H.gj_exec);
   H.gj_exec = nullptr;
   H.gj_nodes = 0;
+  as_free(c);
   H.built = false;
 }
 
@@ -1786,6 +1787,13 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
     return RICH_EINVAL;
   if (H.opts.aggregation == RICH_AGG_MATCHING && (H.opts.max_agg_size < 2 || H.opts.max_agg_size > 1024))
     return RICH_EINVAL;
+  if (H.opts.precond != RICH_PRECOND_AMG && H.opts.precond != RICH_PRECOND_AS) return RICH_EINVAL;
+  if (H.opts.precond == RICH_PRECOND_AS) {  // one level: the subdomain factors of A_aux
+    RICH_CHECK(fine_stencil(c));
+    RICH_CHECK(as_setup(c));
+    H.built = true;
+    return RICH_OK;
+  }
   RICH_CHECK(refresh_a0_values(c));
   Level L0;
   L0.n = (int)c->g.n;
@@ -1823,6 +1831,10 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
 int amg_refresh(rich_ctx* c) {
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
+  if (H.opts.precond == RICH_PRECOND_AS) {
+    RICH_CHECK(fine_stencil(c));
+    return as_setup(c);
+  }
   RICH_CHECK(refresh_a0_values(c));
   H.lv[0].A = c->A0;
   for (int l = 0; l + 1 < H.nlev; ++l) {
@@ -1861,6 +1873,10 @@ int amg_refresh(rich_ctx* c) {
 int amg_update_fine(rich_ctx* c) {
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
+  if (H.opts.precond == RICH_PRECOND_AS) {
+    RICH_CHECK(fine_stencil(c));
+    return as_setup(c);
+  }
   RICH_CHECK(refresh_a0_values(c));
   H.lv[0].A = c->A0;
   RICH_CHECK(level_diag_data(c, H.lv[0]));

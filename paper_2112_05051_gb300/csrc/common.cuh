@@ -176,6 +176,12 @@ struct Hierarchy {
   bool dense = true;              // coarsest level by dense inverse (else kCoarseSweeps l1-Jacobi sweeps)
   cudaGraphExec_t gj_exec = nullptr;  // the coarsest inverse (one launch per pivot) as one graph
   long long gj_nodes = 0;
+  // one-level additive Schwarz (precond = RICH_PRECOND_AS): ILU(0) diagonals and
+  // subdomain solutions (hierarchy precision), FP32 staging of r and z in MIXED
+  void* asD = nullptr;
+  void* asZ = nullptr;
+  float* asR32 = nullptr;
+  float* asZ32 = nullptr;
 };
 
 constexpr int kMaxCoarseDense = 8192;  // largest coarsest level inverted densely
@@ -433,6 +439,11 @@ void amg_free(rich_ctx* c);
 
 // blas.cu: whether a profiling target is set (the autotuner then stays off)
 bool profiling_active();
+
+// schwarz.cu
+int as_setup(rich_ctx* c);   // allocate (first call) and factor every subdomain of the current A_aux
+int as_apply(rich_ctx* c, const double* r, double* z);
+void as_free(rich_ctx* c);
 
 // solve.cu
 int autotune_table(char* buf, int cap);

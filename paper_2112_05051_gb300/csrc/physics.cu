@@ -357,6 +357,9 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->smoother = RICH_SMOOTH_L1JACOBI;
   o->hgs_seg = 16;
   o->hgs_block = 16;
+  o->precond = RICH_PRECOND_AMG;
+  o->as_block = 8;
+  o->as_overlap = 1;
   o->autotune = 1;
   o->isolated_join = 1;
 }

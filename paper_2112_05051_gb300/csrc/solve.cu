@@ -517,22 +517,28 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   if (H.opts.smoother == RICH_SMOOTH_HYBRID_GS) return vcycle_level_hgs<T>(c, l, b, xres);
   // warp-per-row CSR kernels where rows are long
   const double st_bytes = (double)n * 8.0 * es;  // diag, 3 face weights, dinv, b, x in; x out
-  if (st0 && nu1 == 1) {
+  // In FP32 the first sweep from zero is folded into the next stencil pass (one pass
+  // over the finest level less); in FP64 the fold's extra products (D^-1 b at the six
+  // neighbours) cost more on GB300's narrow FP64 pipe than the pass it saves (ncu:
+  // 88-91 % FP64-pipe utilisation in these sweeps), so FP64 keeps separate passes.
+  constexpr bool kFold = sizeof(T) == 4;
+  if (kFold && st0 && nu1 == 1) {
     // finest level, one pre-sweep: the sweep from zero and the residual in one pass
     ProfScope ps("resid_l0", c->st, (double)n * 8.0 * es, 17.0 * n);
     k_st_first<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
     RICH_LAUNCH_CHECK();
   } else if (nu1 > 0) {
     int s0 = 1;
-    if (st0) {
+    if (kFold && st0) {
       // finest level: the first two sweeps from zero in one pass
       ProfScope ps("l1jacobi_l0", c->st, (double)n * 7.0 * es, 20.0 * n);
       k_st_first<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, nullptr, x);
       RICH_LAUNCH_CHECK();
       s0 = 2;
     } else {
-      // first sweep from x = 0: x = D_l1^-1 b, elementwise
-      k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
+      // first sweep from x = 0: x = D_l1^-1 b, elementwise (on the finest level the
+      // stencil copy's 1/l1 array)
+      k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, st0 ? fine<T>(c).dinv : v.dinv, b, x);
       RICH_LAUNCH_CHECK();
     }
     for (int s = s0; s < nu1; ++s) {
@@ -591,6 +597,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
 int vcycle_apply(rich_ctx* c, const double* r, double* z) {
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
+  if (H.opts.precond == RICH_PRECOND_AS) return as_apply(c, r, z);
   long long n = c->g.n;
   if (c->prec == RICH_PREC_MIXED) {
     Level& L0 = H.lv[0];

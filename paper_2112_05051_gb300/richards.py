@@ -18,6 +18,7 @@ AMG_REFRESH, AMG_SETUP_ONCE, AMG_REBUILD_STEP = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 AGG_MIS2, AGG_MATCHING = 0, 1
 SMOOTH_L1JACOBI, SMOOTH_HYBRID_GS = 0, 1
+PRECOND_AMG, PRECOND_AS = 0, 1
 
 ERRORS = {-1: "RICH_EINVAL", -2: "RICH_ENOMEM", -3: "RICH_ECUDA", -4: "RICH_ENOTCONV_LIN",
           -5: "RICH_ENOTCONV_NEWTON", -6: "RICH_ELINESEARCH", -7: "RICH_ENONFINITE", -8: "RICH_ESTATE",
@@ -67,7 +68,8 @@ class AmgOpts(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int), ("aggregation", ctypes.c_int),
                 ("max_agg_size", ctypes.c_int), ("smoother", ctypes.c_int), ("hgs_seg", ctypes.c_int),
-                ("hgs_block", ctypes.c_int), ("autotune", ctypes.c_int), ("isolated_join", ctypes.c_int)]
+                ("hgs_block", ctypes.c_int), ("precond", ctypes.c_int), ("as_block", ctypes.c_int),
+                ("as_overlap", ctypes.c_int), ("autotune", ctypes.c_int), ("isolated_join", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -223,7 +225,7 @@ def default_newton_opts(**kw):
             setattr(o.krylov, k, v)
         elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
                    "aggregation", "max_agg_size", "isolated_join", "smoother", "hgs_seg", "hgs_block",
-                   "autotune"):
+                   "autotune", "precond", "as_block", "as_overlap"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)

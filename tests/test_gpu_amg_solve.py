@@ -384,3 +384,42 @@ def test_hybrid_gs_newton_steps_match_oracle(workload, n, steps, prec):
             assert st.newton_its == ost.newton_its and abs(st.linear_its - ost.linear_its) <= st.newton_its
     assert _nrel(pd.cpu().numpy(), po) <= 1e-8
     ctx.close()
+
+
+# ---------------------------------------------------------------- additive Schwarz / ILU(0)
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("dims,block,overlap", [((18, 16, 20), 8, 1), ((33, 17, 9), 4, 1), ((7, 5, 11), 3, 2),
+                                                ((12, 12, 12), 12, 0)])
+def test_additive_schwarz_apply_parity(prec, tol, dims, block, overlap):
+    from oracle import schwarz
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem(dims, 13, 1)
+    ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+    ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+    ctx.amg_setup(rb.default_amg_opts(precond=rb.PRECOND_AS, as_block=block, as_overlap=overlap))
+    A = disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks)
+    pre = schwarz.AS(A, (grid.nx, grid.ny, grid.nz), block, overlap)
+    r = np.random.default_rng(4).standard_normal(grid.n)
+    z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    ctx.vcycle(torch.tensor(r, device="cuda"), z)
+    assert _nrel(z.cpu().numpy(), pre.apply(r)) <= tol
+    ctx.close()
+
+
+def test_additive_schwarz_newton_step_matches_oracle():
+    rb = _rb()
+    grid = synth.Grid(10, 9, 8)
+    ks = synth.ks_field(grid, 3, 1.0, (4.0, 4.0, 2.0))
+    bc = synth.infiltration_bc()
+    p0 = np.full(grid.n, synth.P_INITIAL)
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FGMRES, restart=30, precond=rb.PRECOND_AS, as_block=4)
+    ctx = rb.Context(grid, SOIL, bc, synth.KMEAN_UPSTREAM, ks)
+    pd = torch.tensor(p0, device="cuda")
+    st = ctx.step(pd, 1.0, opts)
+    po, ost = newton.step(newton.Problem(grid, SOIL, bc, synth.KMEAN_UPSTREAM, ks), p0, 1.0,
+                          newton.NewtonOptions(krylov="fgmres", precond="as", as_block=4))
+    assert st.converged and ost.converged and st.newton_its == ost.newton_its
+    assert abs(st.linear_its - ost.linear_its) <= st.newton_its
+    assert _nrel(pd.cpu().numpy(), po) <= 1e-8
+    ctx.close()
