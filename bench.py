@@ -58,7 +58,7 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on a
 # workload, from the profiles/ summaries of the same kernel and workload (None:
 # no capture of the current kernel).
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {("richards128_fp64", "l1jacobi_l0"): 125.615616e6}
 # the oracle's reduced grid for the host-core samples (cells per side)
 CPU_SAMPLE_N = {"richards128_fp64": 48, "richards16_fp64": 16, "richards256_mixed": 32, "richards512_mixed": 32,
                 "paper_infiltration": 96}
