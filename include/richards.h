@@ -173,10 +173,11 @@ typedef struct {
   int as_block;            /* AS subdomain box: cells per side (8) */
   int as_overlap;          /* AS overlap in layers (1, as in the paper's runs); as_block + 2 as_overlap <= 24 */
   int autotune;            /* 1 (default): the first time a CSR row operation of the V-cycle (sweep,
-                              residual, restriction, prolongation) meets a matrix shape, every lane-group
-                              width (1..32 lanes per row) is timed on it and the fastest is kept for the
-                              process (rich_autotune_table lists the choices); 0: a fixed rule by the
-                              average row length */
+                              residual, restriction, prolongation) meets a shape class (rows in
+                              quarter-octave bins, mean row length), every lane-group width (1..32 lanes
+                              per row) is timed on it and the fastest is kept for the process
+                              (rich_autotune_table lists the choices); 0: a fixed rule by the mean row
+                              length */
   int isolated_join;       /* MIS-2 pass 3 (1, default): a node without strong neighbours whose row is not
                               diagonally dominant (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
                               aggregated neighbour j with the largest (fp32 |a_ij|, key(j)); dominant rows
@@ -379,9 +380,9 @@ int rich_step_batch(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_o
  * kernels on their roofline. */
 int rich_measure_fma_peak(int fp64, double* tflops);
 
-/* The autotuner's choices so far, one line "mode value_bytes rows nonzeros lanes
- * best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep, 3 residual), written
- * into buf (at most cap bytes, NUL-terminated). */
+/* The autotuner's choices so far, one line "mode value_bytes rows_bin mean_row_length
+ * lanes best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep, 3 residual;
+ * rows_bin = floor(4 log2 rows)), written into buf (at most cap bytes, NUL-terminated). */
 int rich_autotune_table(char* buf, int cap);
 
 /* Number of kernels this library has launched since it was loaded. */

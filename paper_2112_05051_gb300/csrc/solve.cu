@@ -104,16 +104,18 @@ static int default_lanes(double avg) {
   return 4;
 }
 
-// Autotuner of the CSR row operations: the first time an operation meets a matrix
-// shape (mode, value type, rows, nonzeros), every lane-group width is timed on the
-// actual operands (output to a scratch vector, one warm-up and three timed launches
-// each, CUDA events) and the fastest is kept for the rest of the process.  The
-// table is shared by all contexts (under a mutex, held while tuning, so concurrent
-// requests of one shape agree); a given shape therefore always runs the same
-// kernel, and its results do not depend on what else is in flight.
+// Autotuner of the CSR row operations: the first time an operation meets a shape
+// class (mode, value type, rows in quarter-octave bins, mean row length rounded to
+// an integer), every lane-group width is timed on the actual operands (output to a
+// scratch vector, one warm-up and three timed launches each, CUDA events) and the
+// fastest is kept for the rest of the process.  Classes, not exact shapes, so that
+// a stream of requests of similar size (whose coarse levels differ by a few rows)
+// tunes once.  The table is shared by all contexts (under a mutex, held while
+// tuning, so concurrent requests of one class agree); a class therefore always runs
+// the same kernel, and results do not depend on what else is in flight.
 struct TuneKey {
-  int mode, tsize, n;
-  long long nnz;
+  int mode, tsize, n;   // n: quarter-octave bin of the row count
+  long long nnz;        // rounded mean row length
   bool operator<(const TuneKey& o) const {
     if (mode != o.mode) return mode < o.mode;
     if (tsize != o.tsize) return tsize < o.tsize;
@@ -131,7 +133,8 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
   int G = default_lanes((double)nnz / n);
   if (c->H.opts.autotune && !profiling_active()) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneKey key{MODE, (int)sizeof(T), n, nnz};
+    TuneKey key{MODE, (int)sizeof(T), (int)std::floor(4.0 * std::log2((double)n)),
+                (long long)std::llround((double)nnz / n)};
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       G = it->second.first;
