@@ -175,7 +175,8 @@ typedef struct {
   int autotune;            /* 1 (default): the first time a CSR row operation of the V-cycle (sweep,
                               residual, restriction, prolongation) meets a shape class (rows in
                               quarter-octave bins, mean row length), every lane-group width (1..32 lanes
-                              per row) is timed on it and the fastest is kept for the process
+                              per row, and 1..8 with four-way unrolled rows) is timed on it and the
+                              fastest is kept for the process
                               (rich_autotune_table lists the choices); 0: a fixed rule by the mean row
                               length */
   int isolated_join;       /* MIS-2 pass 3 (1, default): a node without strong neighbours whose row is not

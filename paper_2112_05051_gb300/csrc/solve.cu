@@ -59,7 +59,9 @@ __global__ void k_spmv(int n, const int* __restrict__ rp, const int* __restrict_
 // CSR row operation with G lanes per row (G = 4..32), for levels whose rows are
 // long (coarse Galerkin operators carry tens to hundreds of entries per row).
 // MODE 0: y = A x; 1: y += A x; 2: y = x + dinv (b - A x); 3: y = b - A x.
-template <class T, int MODE, int G>
+// U = 4: each lane keeps four partial sums over entries e, e+G, e+2G, e+3G, so four
+// independent gathers of x are in flight (the coarse levels are gather-latency bound).
+template <class T, int MODE, int G, int U = 1>
 __global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
                           const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
                           T* __restrict__ y) {
@@ -68,7 +70,21 @@ __global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restri
   int rows_per_grid = (gridDim.x * blockDim.x) / G;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) / G; row < n; row += rows_per_grid) {
     T s = 0;
-    for (int e = rp[row] + lane; e < rp[row + 1]; e += G) s += val[e] * x[col[e]];
+    int e = rp[row] + lane;
+    const int end = rp[row + 1];
+    if (U == 4) {
+      T s1 = 0, s2 = 0, s3 = 0;
+      for (; e + 3 * G < end; e += 4 * G) {
+        const int c0 = col[e], c1 = col[e + G], c2 = col[e + 2 * G], c3 = col[e + 3 * G];
+        const T v0 = val[e], v1 = val[e + G], v2 = val[e + 2 * G], v3 = val[e + 3 * G];
+        s += v0 * x[c0];
+        s1 += v1 * x[c1];
+        s2 += v2 * x[c2];
+        s3 += v3 * x[c3];
+      }
+      s = (s + s1) + (s2 + s3);
+    }
+    for (; e < end; e += G) s += val[e] * x[col[e]];
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(mask, s, o, G);
     if (lane == 0) {
@@ -80,17 +96,31 @@ __global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restri
   }
 }
 
+// Variant v of the CSR row kernel: lanes per row G = v & 0xff, four-way unrolled
+// rows when v & kUnroll.
+constexpr int kUnroll = 0x100;
 template <class T, int MODE>
-static void csr_launch(cudaStream_t st, int G, int n, const int* rp, const int* col, const T* val, const T* dinv,
+static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* col, const T* val, const T* dinv,
                        const T* b, const T* x, T* y) {
+  const int G = v & 0xff;
   long long thr = (long long)n * G;
+  const dim3 gr(grid_for(thr));
+  if (v & kUnroll) {
+    switch (G) {
+      case 1: k_csr_grp<T, MODE, 1, 4><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+      case 2: k_csr_grp<T, MODE, 2, 4><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+      case 4: k_csr_grp<T, MODE, 4, 4><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+      default: k_csr_grp<T, MODE, 8, 4><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    }
+    return;
+  }
   switch (G) {
-    case 1: k_csr_grp<T, MODE, 1><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
-    case 2: k_csr_grp<T, MODE, 2><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
-    case 4: k_csr_grp<T, MODE, 4><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
-    case 8: k_csr_grp<T, MODE, 8><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
-    case 16: k_csr_grp<T, MODE, 16><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
-    default: k_csr_grp<T, MODE, 32><<<grid_for(thr), kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 1: k_csr_grp<T, MODE, 1><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 2: k_csr_grp<T, MODE, 2><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 4: k_csr_grp<T, MODE, 4><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 8: k_csr_grp<T, MODE, 8><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    case 16: k_csr_grp<T, MODE, 16><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
+    default: k_csr_grp<T, MODE, 32><<<gr, kBlock, 0, st>>>(n, rp, col, val, dinv, b, x, y); break;
   }
 }
 
@@ -146,7 +176,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       RICH_CUDA(cudaEventCreate(&e0));
       RICH_CUDA(cudaEventCreate(&e1));
       float best = 1e30f;
-      for (int g : {1, 2, 4, 8, 16, 32}) {
+      for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll}) {
         csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch);
         RICH_CUDA(cudaEventRecord(e0, c->st));
         for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch);
