@@ -685,6 +685,15 @@ def run_ours(args):
         kernel_roofs = [{k: r[k] for k in ("kernel", "share_of_profiled_steps", "bound", "achieved", "peak", "unit",
                                            "frac", "intensity_flop_per_byte", "hbm_frac", "avg_launch_us")}
                         for r in kernel_roofs]
+        if mixed is not None:  # the same pass on the FP32-AMG arm: its V-cycle kernels are FP32
+            tab3 = profile_pass(rb, grid, soil, bc, w, ks, p0, dts, opts, rb.PREC_MIXED, psteps)
+            tot3 = sum(v[1] for v in tab3.values())
+            mixed["kernels_on_their_roofs"] = []
+            for name, (cnt, kms, kb, kf) in sorted(tab3.items(), key=lambda kv: -kv[1][1])[:5]:
+                r = roofline_of(name, kms, cnt, kb, kf, _is_fp64_kernel(name, False), peak_gbs, fp64_tflops, None)
+                mixed["kernels_on_their_roofs"].append(
+                    {"kernel": name, "share_of_profiled_steps": kms / tot3 if tot3 else None, "bound": r["bound"],
+                     "frac": r["frac"], "hbm_frac": r["hbm_frac"], "avg_launch_us": r["avg_launch_us"]})
 
     # the paper's own problem (Sec. 6): 798 x 798 x 38 unknowns, mixed precision
     paper = None

@@ -249,7 +249,7 @@ typedef struct {
   int mis_rounds[16];      /* MIS-2 rounds used to coarsen level l */
   double omega[16];        /* prolongator damping 4/(3 rho) of level l */
   double operator_complexity; /* sum nnz(A_l) / nnz(A_0) */
-} rich_amg_info;
+} rich_amg_info;               /* all zero with the AS preconditioner (one level, no hierarchy) */
 
 typedef struct rich_ctx rich_ctx;
 
@@ -318,7 +318,8 @@ int amg_update(rich_ctx* ctx, int policy);
 /* z_dev = B r_dev: one V-cycle with zero initial guess (FP64 in and out; in
  * MIXED mode the cycle itself runs in FP32). */
 int amg_vcycle(rich_ctx* ctx, const double* r_dev, double* z_dev);
-/* Export level l for inspection (host buffers sized from rich_amg_info):
+/* Export level l for inspection (host buffers sized from rich_amg_info;
+ * RICH_EINVAL for a level the hierarchy does not have, e.g. any with AS):
  * aggregate index per node of level l (n[l] ints, level < levels-1), and the
  * CSR of A_l (rowptr n[l]+1, col nnz, val nnz).  Any pointer may be NULL.
  * In MIXED precision, levels below the finest return the FP32 values the
@@ -364,7 +365,8 @@ int rich_create_batch(const rich_grid* grid, int nbatch, const rich_soil* soil, 
  * nbatch * n values; stats_host and status_host receive one entry per problem
  * (status as rich_step's; a problem that fails is left at its last accepted Newton
  * iterate and does not hold the others back).  opts must use FCG without time-step
- * control (RICH_EINVAL otherwise); there is no FGMRES fallback in a batch, so a
+ * control (RICH_EINVAL otherwise); RICH_ELIMIT where 3 x nbatch x the per-problem
+ * reduction grid exceeds the context's partial-sum buffer (only above 21 problems); there is no FGMRES fallback in a batch, so a
  * problem whose FCG fails reports RICH_ENOTCONV_LIN.  The AMG hierarchy is built on
  * the block-diagonal diffusion matrix of all problems (aggregates never cross
  * problems) at the first call and refreshed afterwards.  Returns RICH_OK when the

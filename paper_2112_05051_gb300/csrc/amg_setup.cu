@@ -1898,6 +1898,7 @@ int amg_setup(rich_ctx* c, const rich_amg_opts* o, rich_amg_info* info) {
   if (info) {
     Hierarchy& H = c->H;
     memset(info, 0, sizeof(*info));
+    if (H.opts.precond == RICH_PRECOND_AS || H.nlev == 0) return RICH_OK;  // no hierarchy: all zero
     info->levels = H.nlev;
     long long tot = 0;
     for (int l = 0; l < H.nlev && l < 16; ++l) {

@@ -446,6 +446,8 @@ int rich_step_batch(rich_ctx* c, double* p, double dt, const rich_newton_opts* o
   if (o->krylov.kind != RICH_KRYLOV_FCG || o->max_dt_halvings != 0) return RICH_EINVAL;
   const int S = c->nbatch;
   if (S < 1 || c->g.n % S) return RICH_EINVAL;
+  // every segmented reduction writes at most 3 quantities x S problems x its blocks of partials
+  if (3LL * S * red_grid(c->g.n / S) > (long long)kRedBlocks * 64) return RICH_ELIMIT;
   BatchWork w;
   int rc = batch_work(c, w, S);
   if (rc == RICH_OK) rc = batch_step(c, w, S, p, dt, o, stats, status);

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kLineThreads) k_as_gather(GridP g, int bs, int
         if (li < 0 || lj < 0 || lk < 0 || li >= b.ex || lj >= b.ey || lk >= b.ez) continue;
         s += zpart[(long long)t * E * E * E + li + b.ex * (lj + b.ey * lk)];
       }
-  z[r * g.nx + i] = s;
+  z[(long long)r * g.nx + i] = s;
 }
 
 static long long as_tiles(const GridP& g, int bs) {
@@ -174,7 +174,12 @@ int as_setup(rich_ctx* c) {
       RICH_CHECK(dalloc(&H.asR32, c->g.n));
       RICH_CHECK(dalloc(&H.asZ32, c->g.n));
     }
-    size_t smem2 = 2 * es * (size_t)E * E * E;
+    // dynamic shared memory above 48 KB needs the opt-in (E = 24 in FP64: 108 KB and 216 KB)
+    const size_t smem1 = es * (size_t)E * E * E, smem2 = 2 * smem1;
+    if (smem1 > 48 * 1024) {
+      if (mp) RICH_CUDA(cudaFuncSetAttribute(k_as_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+      else RICH_CUDA(cudaFuncSetAttribute(k_as_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+    }
     if (smem2 > 48 * 1024) {
       if (mp) RICH_CUDA(cudaFuncSetAttribute(k_as_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
       else RICH_CUDA(cudaFuncSetAttribute(k_as_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
