@@ -75,6 +75,11 @@ extern "C" {
 #define RICH_PRECOND_AMG       0
 #define RICH_PRECOND_AS        1
 
+/* Storage of the coarse-level matrices for the V-cycle's row operations */
+#define RICH_LAYOUT_AUTO       0
+#define RICH_LAYOUT_CSR        1
+#define RICH_LAYOUT_SELL       2
+
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
  * (eq. (upstream_mean)) K_U if p_U - p_L >= 0 else K_L with U the +d cell;
@@ -183,6 +188,12 @@ typedef struct {
                               diagonally dominant (a_ii < 2 sum_{j!=i} |a_ij|) joins the aggregate of its
                               aggregated neighbour j with the largest (fp32 |a_ij|, key(j)); dominant rows
                               (e.g. under a Dirichlet face) stay out.  0: every such node stays out */
+  int csr_layout;          /* the V-cycle's sparse row operations below the finest level (sweep, residual,
+                              restriction, prolongation).  RICH_LAYOUT_AUTO (default): a SELL-C-sigma copy
+                              (slices of 32 rows sorted by length within windows of 1024 rows, one thread
+                              per row) of every coarse A and every P and R with >= 2048 rows is built,
+                              and the autotuner times it beside the CSR variants; RICH_LAYOUT_CSR: CSR
+                              only, no copy; RICH_LAYOUT_SELL: the SELL copy wherever one is built */
 } rich_amg_opts;
 
 typedef struct {
@@ -384,8 +395,10 @@ int rich_step_batch(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_o
 int rich_measure_fma_peak(int fp64, double* tflops);
 
 /* The autotuner's choices so far, one line "mode value_bytes rows_bin mean_row_length
- * lanes best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep, 3 residual;
- * rows_bin = floor(4 log2 rows)), written into buf (at most cap bytes, NUL-terminated). */
+ * sell_offered variant best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep,
+ * 3 residual; rows_bin = floor(4 log2 rows); sell_offered 1 where a SELL copy was a
+ * candidate; variant = lanes per row, + 256 for four-way unrolled rows, 512 for the
+ * SELL copy), written into buf (at most cap bytes, NUL-terminated). */
 int rich_autotune_table(char* buf, int cap);
 
 /* Number of kernels this library has launched since it was loaded. */

@@ -104,6 +104,26 @@ struct Csr {
   T* val = nullptr;
 };
 
+// SELL-C-sigma copy of a CSR matrix for the coarse-level row operations: rows are
+// sorted by decreasing length within windows of kSellSigma rows and cut into slices
+// of kSellC = 32 (one warp, one thread per row); slice s is stored column by column,
+// slot sptr[s] + 32 j + t holding the j-th entry of row perm[32 s + t] (value and
+// column), or a zero with column 0 past the end of that row.  Loads of a slice are
+// coalesced and a row needs no cross-lane reduction.
+constexpr int kSellC = 32;
+constexpr int kSellSigma = 1024;
+constexpr int kSellMinRows = 2048;
+struct Sell {
+  int nrows = 0, nslice = 0;
+  long long slots = 0;
+  int* sptr = nullptr;      // nslice + 1 slot offsets
+  int* perm = nullptr;      // 32 nslice rows, -1 past nrows
+  int* col = nullptr;       // slots
+  double* val = nullptr;    // values for an FP64 hierarchy
+  float* val32 = nullptr;   // values for an FP32 hierarchy (MIXED)
+  bool built() const { return sptr != nullptr; }
+};
+
 // One level of the AMG hierarchy.  Level 0 holds the diffusion matrix of the
 // finest grid; levels 1.. hold Galerkin products.  FP32 copies exist in MIXED mode.
 // Galerkin refresh by product lists: entry q of C = A B is the sum over
@@ -133,6 +153,7 @@ struct Level {
   float* R32 = nullptr;
   float* AP32 = nullptr;           // values of A P in FP32 (MIXED-precision refresh)
   ProdList pl_ap, pl_rap;          // product lists of A P and R (A P), built at the first refresh
+  Sell sA, sP, sR;                 // SELL-C-sigma copies (levels with >= kSellMinRows rows)
   bool pl_tried = false;
   int mis_rounds = 0;
   double omega = 0.0;
@@ -444,6 +465,12 @@ bool profiling_active();
 int as_setup(rich_ctx* c);   // allocate (first call) and factor every subdomain of the current A_aux
 int as_apply(rich_ctx* c, const double* r, double* z);
 void as_free(rich_ctx* c);
+
+// sell.cu: SELL-C-sigma copies of the coarse-level matrices
+int sell_build(rich_ctx* c, const Csr<double>& M, Sell& S);  // pattern; nothing below kSellMinRows rows
+int sell_fill(rich_ctx* c, const Csr<double>& M, const double* val, Sell& S);  // values, M's entry order
+int sell_fill(rich_ctx* c, const Csr<double>& M, const float* val, Sell& S);
+void sell_free(Sell& S);
 
 // solve.cu
 int autotune_table(char* buf, int cap);

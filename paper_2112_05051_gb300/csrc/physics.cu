@@ -362,6 +362,7 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->as_overlap = 1;
   o->autotune = 1;
   o->isolated_join = 1;
+  o->csr_layout = RICH_LAYOUT_AUTO;
 }
 
 void rich_default_newton_opts(rich_newton_opts* o) {

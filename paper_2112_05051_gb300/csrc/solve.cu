@@ -96,12 +96,56 @@ __global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restri
   }
 }
 
+// The same row operations on the SELL-C-sigma copy: one warp per slice of 32 rows,
+// one thread per row, slot loads coalesced across the warp, four gathers of x in
+// flight per thread, no cross-lane reduction (on GB300's narrow FP64 pipe the
+// shuffle-add reductions and the idle lanes of ragged rows cost as much as the
+// products themselves).  Past a row's end the slots hold zeros.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_sell(int nslice, const int* __restrict__ sptr,
+                                                 const int* __restrict__ perm, const int* __restrict__ col,
+                                                 const T* __restrict__ val, const T* __restrict__ dinv,
+                                                 const T* __restrict__ b, const T* __restrict__ x,
+                                                 T* __restrict__ y) {
+  const int lane = threadIdx.x & (kSellC - 1);
+  const int warps = (gridDim.x * blockDim.x) / kSellC;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) / kSellC; s < nslice; s += warps) {
+    const int row = perm[s * kSellC + lane];
+    const int end = sptr[s + 1];
+    int e = sptr[s] + lane;
+    T s0 = 0, s1 = 0;
+    for (; e + 3 * kSellC < end; e += 4 * kSellC) {  // warp-uniform: the slice's columns are full
+      const int c0 = col[e], c1 = col[e + kSellC], c2 = col[e + 2 * kSellC], c3 = col[e + 3 * kSellC];
+      const T v0 = val[e], v1 = val[e + kSellC], v2 = val[e + 2 * kSellC], v3 = val[e + 3 * kSellC];
+      const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+      s0 += v0 * x0;
+      s1 += v1 * x1;
+      s0 += v2 * x2;
+      s1 += v3 * x3;
+    }
+    for (; e < end; e += kSellC) s0 += val[e] * x[col[e]];
+    const T a = s0 + s1;
+    if (row >= 0) {
+      if (MODE == 0) y[row] = a;
+      else if (MODE == 1) y[row] += a;
+      else if (MODE == 2) y[row] = x[row] + dinv[row] * (b[row] - a);
+      else y[row] = b[row] - a;
+    }
+  }
+}
+
 // Variant v of the CSR row kernel: lanes per row G = v & 0xff, four-way unrolled
-// rows when v & kUnroll.
+// rows when v & kUnroll; v == kSellVariant runs the SELL copy (sl, sval) instead.
 constexpr int kUnroll = 0x100;
+constexpr int kSellVariant = 0x200;
 template <class T, int MODE>
 static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* col, const T* val, const T* dinv,
-                       const T* b, const T* x, T* y) {
+                       const T* b, const T* x, T* y, const Sell* sl = nullptr, const T* sval = nullptr) {
+  if (v == kSellVariant) {
+    k_sell<T, MODE><<<grid_for((long long)sl->nslice * kSellC), kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm,
+                                                                                 sl->col, sval, dinv, b, x, y);
+    return;
+  }
   const int G = v & 0xff;
   long long thr = (long long)n * G;
   const dim3 gr(grid_for(thr));
@@ -146,25 +190,31 @@ static int default_lanes(double avg) {
 struct TuneKey {
   int mode, tsize, n;   // n: quarter-octave bin of the row count
   long long nnz;        // rounded mean row length
+  int sell;             // 1: the SELL copy is among the candidates
   bool operator<(const TuneKey& o) const {
     if (mode != o.mode) return mode < o.mode;
     if (tsize != o.tsize) return tsize < o.tsize;
     if (n != o.n) return n < o.n;
-    return nnz < o.nnz;
+    if (nnz != o.nnz) return nnz < o.nnz;
+    return sell < o.sell;
   }
 };
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, float>> g_tune;  // -> (lanes, best us)
+static std::map<TuneKey, std::pair<int, float>> g_tune;  // -> (variant, best us)
 
+// sl/sval: the matrix's SELL copy and its values in T (nullptr where none is built).
 template <class T, int MODE>
 static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* col, const T* val, const T* dinv,
-                  const T* b, const T* x, T* y) {
+                  const T* b, const T* x, T* y, const Sell* sl = nullptr, const T* sval = nullptr) {
   if (n <= 0) return RICH_OK;
+  const bool has_sell = sl && sl->built() && sl->nrows == n && sval && c->H.opts.csr_layout != RICH_LAYOUT_CSR;
   int G = default_lanes((double)nnz / n);
-  if (c->H.opts.autotune && !profiling_active()) {
+  if (has_sell && c->H.opts.csr_layout == RICH_LAYOUT_SELL) {
+    G = kSellVariant;
+  } else if (c->H.opts.autotune && !profiling_active()) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneKey key{MODE, (int)sizeof(T), (int)std::floor(4.0 * std::log2((double)n)),
-                (long long)std::llround((double)nnz / n)};
+                (long long)std::llround((double)nnz / n), has_sell ? 1 : 0};
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       G = it->second.first;
@@ -176,10 +226,11 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       RICH_CUDA(cudaEventCreate(&e0));
       RICH_CUDA(cudaEventCreate(&e1));
       float best = 1e30f;
-      for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll}) {
-        csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch);
+      for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll, kSellVariant}) {
+        if (g == kSellVariant && !has_sell) continue;
+        csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
         RICH_CUDA(cudaEventRecord(e0, c->st));
-        for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch);
+        for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
         RICH_CUDA(cudaEventRecord(e1, c->st));
         RICH_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -197,7 +248,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       g_tune[key] = {G, best * 1000.f / 3.f};
     }
   }
-  csr_launch<T, MODE>(c->st, G, n, rp, col, val, dinv, b, x, y);
+  csr_launch<T, MODE>(c->st, G, n, rp, col, val, dinv, b, x, y, sl, sval);
   return RICH_OK;
 }
 
@@ -206,8 +257,8 @@ int autotune_table(char* buf, int cap) {
   int off = 0;
   buf[0] = 0;
   for (auto& e : g_tune) {
-    int w = snprintf(buf + off, cap - off, "%d %d %d %lld %d %.3f\n", e.first.mode, e.first.tsize, e.first.n,
-                     e.first.nnz, e.second.first, e.second.second);
+    int w = snprintf(buf + off, cap - off, "%d %d %d %lld %d %d %.3f\n", e.first.mode, e.first.tsize, e.first.n,
+                     e.first.nnz, e.first.sell, e.second.first, e.second.second);
     if (w < 0 || w >= cap - off) break;
     off += w;
   }
@@ -412,6 +463,8 @@ struct LevelView {
   const T* dinv;
   const int *prp, *pcol, *rrp, *rcol;
   const T *pval, *rval;
+  const Sell *sa, *sp, *sr;  // SELL copies of A, P, R and their values in T
+  const T *sav, *spv, *srv;
 };
 
 template <class T>
@@ -420,14 +473,16 @@ static LevelView<T> view(rich_ctx* c, int l);
 template <>
 LevelView<double> view<double>(rich_ctx* c, int l) {
   Level& L = c->H.lv[l];
-  return LevelView<double>{L.n, L.A.rowptr, L.A.col, L.A.val, L.dinv, L.P.rowptr, L.P.col, L.R.rowptr, L.R.col,
-                           L.P.val, L.R.val};
+  return LevelView<double>{L.n,       L.A.rowptr, L.A.col,  L.A.val,  L.dinv,   L.P.rowptr, L.P.col,
+                           L.R.rowptr, L.R.col,    L.P.val,  L.R.val,  &L.sA,    &L.sP,      &L.sR,
+                           L.sA.val,   L.sP.val,   L.sR.val};
 }
 template <>
 LevelView<float> view<float>(rich_ctx* c, int l) {
   Level& L = c->H.lv[l];
-  return LevelView<float>{L.n, L.A.rowptr, L.A.col, L.A32, L.dinv32, L.P.rowptr, L.P.col, L.R.rowptr, L.R.col,
-                          L.P32, L.R32};
+  return LevelView<float>{L.n,        L.A.rowptr, L.A.col,    L.A32, L.dinv32, L.P.rowptr, L.P.col,
+                          L.R.rowptr, L.R.col,    L.P32,      L.R32, &L.sA,    &L.sP,      &L.sR,
+                          L.sA.val32, L.sP.val32, L.sR.val32};
 }
 
 template <class T>
@@ -485,21 +540,23 @@ static int vcycle_level_hgs(rich_ctx* c, int l, const T* b, T** xres) {
     ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st,
                  st0 ? (double)n * 7.0 * es : (double)n * (4.0 + 3.0 * es) + (double)L.A.nnz * (4.0 + es));
     if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-    else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r));
+    else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r, v.sa,
+                                 v.sav));
   }
   RICH_LAUNCH_CHECK();
   Level& C = H.lv[l + 1];
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
     RICH_CHECK(csr_op<T, 0>(c, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr,
-                            (const T*)L.r, (T*)C.b));
+                            (const T*)L.r, (T*)C.b, v.sr, v.srv));
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x));
+    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x, v.sp,
+                            v.spv));
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < H.opts.nu2; ++s) {
@@ -536,7 +593,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
       RICH_LAUNCH_CHECK();
       for (int s = 1; s < kCoarseSweeps; ++s) {
-        RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t));
+        RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, v.sa, v.sav));
         RICH_LAUNCH_CHECK();
         std::swap(x, t);
       }
@@ -579,7 +636,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
         ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
                      st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
         if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-        else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t));
+        else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, v.sa, v.sav));
       }
       RICH_LAUNCH_CHECK();
       std::swap(x, t);
@@ -587,7 +644,8 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     {
       ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st, st0 ? st_bytes : sweep_bytes - (double)n * es);
       if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-      else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r));
+      else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r, v.sa,
+                                 v.sav));
     }
     RICH_LAUNCH_CHECK();
   } else {
@@ -598,14 +656,15 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
     RICH_CHECK(csr_op<T, 0>(c, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr,
-                            (const T*)L.r, (T*)C.b));
+                            (const T*)L.r, (T*)C.b, v.sr, v.srv));
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x));
+    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x, v.sp,
+                            v.spv));
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < nu2; ++s) {
@@ -613,7 +672,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
                    st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
       if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-      else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t));
+      else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, v.sa, v.sav));
     }
     RICH_LAUNCH_CHECK();
     std::swap(x, t);

@@ -19,6 +19,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 AGG_MIS2, AGG_MATCHING = 0, 1
 SMOOTH_L1JACOBI, SMOOTH_HYBRID_GS = 0, 1
 PRECOND_AMG, PRECOND_AS = 0, 1
+LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_SELL = 0, 1, 2
+UNROLL, SELL_VARIANT = 0x100, 0x200
 
 ERRORS = {-1: "RICH_EINVAL", -2: "RICH_ENOMEM", -3: "RICH_ECUDA", -4: "RICH_ENOTCONV_LIN",
           -5: "RICH_ENOTCONV_NEWTON", -6: "RICH_ELINESEARCH", -7: "RICH_ENONFINITE", -8: "RICH_ESTATE",
@@ -69,7 +71,8 @@ class AmgOpts(ctypes.Structure):
                 ("smooth_levels", ctypes.c_int), ("product_lists", ctypes.c_int), ("aggregation", ctypes.c_int),
                 ("max_agg_size", ctypes.c_int), ("smoother", ctypes.c_int), ("hgs_seg", ctypes.c_int),
                 ("hgs_block", ctypes.c_int), ("precond", ctypes.c_int), ("as_block", ctypes.c_int),
-                ("as_overlap", ctypes.c_int), ("autotune", ctypes.c_int), ("isolated_join", ctypes.c_int)]
+                ("as_overlap", ctypes.c_int), ("autotune", ctypes.c_int), ("isolated_join", ctypes.c_int),
+                ("csr_layout", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -225,7 +228,7 @@ def default_newton_opts(**kw):
             setattr(o.krylov, k, v)
         elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
                    "aggregation", "max_agg_size", "isolated_join", "smoother", "hgs_seg", "hgs_block",
-                   "autotune", "precond", "as_block", "as_overlap"):
+                   "autotune", "precond", "as_block", "as_overlap", "csr_layout"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)
@@ -536,11 +539,13 @@ def fma_peak_tflops(fp64=True):
 
 
 def autotune_table():
-    """The CSR autotuner's choices: [(mode, value_bytes, rows, nnz, lanes, best_us)]."""
+    """The row-operation autotuner's choices:
+    [(mode, value_bytes, rows_bin, mean_row_length, sell_offered, variant, best_us)],
+    variant = lanes per row (+ UNROLL for four-way unrolled rows) or SELL_VARIANT."""
     buf = ctypes.create_string_buffer(1 << 16)
     check(load().rich_autotune_table(buf, len(buf)), "rich_autotune_table")
     out = []
     for line in buf.value.decode().splitlines():
-        m, t, n, z, g, us = line.split()
-        out.append((int(m), int(t), int(n), int(z), int(g), float(us)))
+        m, t, n, z, so, g, us = line.split()
+        out.append((int(m), int(t), int(n), int(z), int(so), int(g), float(us)))
     return out

@@ -161,6 +161,38 @@ def test_vcycle_parity_fp64_and_mixed(nu):
         ctx.close()
 
 
+@pytest.mark.parametrize("layout", ["csr", "sell", "auto"])
+def test_vcycle_parity_per_row_layout_after_refresh(layout):
+    """The coarse-level row operations on CSR, on the SELL-C-sigma copies (P_0 with
+    84k rows, R_0 and A_1 with a few thousand; ragged last slices and windows), and
+    as the autotuner picks: one V-cycle after the setup and after a Galerkin refresh
+    (the copies of A are refilled), FP64 and MIXED, against the oracle."""
+    rb = _rb()
+    lay = {"csr": rb.LAYOUT_CSR, "sell": rb.LAYOUT_SELL, "auto": rb.LAYOUT_AUTO}[layout]
+    grid, p, ks, bc, dt, kmean = _problem((48, 44, 40), 9, 1)
+    p2 = p + np.random.default_rng(6).uniform(0, 10, grid.n)
+    r = np.random.default_rng(3).standard_normal(grid.n)
+    h = amg.setup(disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks), 0.08, 5, 100)
+    z1 = amg.vcycle(h, r, 2, 2)
+    amg.refresh(h, disc.aux_matrix(grid, SOIL, bc, kmean, p2, dt, ks))
+    z2 = amg.vcycle(h, r, 2, 2)
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+        ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+        info = ctx.amg_setup(rb.default_amg_opts(seed=5, coarse_max=100, nu1=2, nu2=2, csr_layout=lay))
+        assert info.levels >= 3 and info.n[1] >= 2048  # A_1 has a SELL copy
+        z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+        ctx.vcycle(torch.tensor(r, device="cuda"), z)
+        assert _nrel(z.cpu().numpy(), z1) <= tol
+        ctx.jacobian(torch.tensor(p2, device="cuda"), dt)
+        ctx.amg_update(rb.AMG_REFRESH)
+        ctx.vcycle(torch.tensor(r, device="cuda"), z)
+        assert _nrel(z.cpu().numpy(), z2) <= tol
+        ctx.close()
+    if layout == "auto":  # SELL copies were offered to the tuner
+        assert any(e[4] == 1 for e in rb.autotune_table())
+
+
 @pytest.mark.parametrize("lists", [1, 0])
 @pytest.mark.parametrize("dims,coarse_max", [((18, 16, 14), 150), ((40, 36, 32), 2000)])
 def test_refresh_matches_oracle_galerkin_refresh(dims, coarse_max, lists):
