@@ -32,7 +32,8 @@ MEASURED_PEAKS.json, FP64 FMA throughput measured live by
 rich_measure_fma_peak; the bound follows from the kernel's algorithmic
 flops/byte against the balance point), the paper's own 24.2M-cell infiltration
 grid in mixed precision (`paper_workload`), the oracle timed on the host cores
-(`cpu_baseline`) and a request stream through the request server (`serving`).
+(`cpu_baseline`), a request stream through the request server (`serving`) and a
+burst of same-shape requests served with and without batching (`serving_uniform`).
 
 --impl reference times the CPU oracle (the plain FP64 numpy/scipy restatement)
 on the host cores: each step is one Newton iteration of the workload's first
@@ -437,6 +438,48 @@ def serving_run(args, rb):
             "admission": "FIFO, a free slot and the request's device-memory estimate within 80% of free HBM"}
 
 
+def serving_uniform(args, rb, n_req=256, n=32):
+    """Where batching applies: a burst of same-shape requests (n^3 columns, sigma 0.5
+    log-normal K_s fields, upstream mean, dt = 0.25 s, FP32 AMG, FCG) on which FCG
+    needs no fallback, through the server with batch_max 1 and 8.  Capacity of the
+    burst, failures, and the largest deviation of a batched result from the same
+    request served alone."""
+    import numpy as np
+    from paper_2112_05051_gb300 import synth
+    soil = synth.Soil()
+    bc = synth.infiltration_bc(synth.P_TOP)
+    grid = synth.Grid(n, n, n)
+    p0 = np.full(grid.n, synth.P_INITIAL)
+    fields = [synth.ks_field(grid, 5000 + i, 0.5, (4.0, 4.0, 2.0)) for i in range(n_req)]
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
+                                  coarse_max=args.serving_coarse_max)
+    out = {"requests": n_req, "grid": [n, n, n], "sigma": 0.5, "kmean": "upstream", "dt": 0.25,
+           "slots": args.serving_slots}
+    results = {}
+    for bm in (1, 8):
+        srv = rb.Server(slots=args.serving_slots, batch_max=bm)
+        srv.wait(srv.submit(grid, soil, bc, synth.KMEAN_UPSTREAM, 0.25, p0=p0, ks=fields[0], precision=rb.PREC_MIXED,
+                            opts=opts))  # warm-up
+        t0 = time.perf_counter()
+        ids = [srv.submit(grid, soil, bc, synth.KMEAN_UPSTREAM, 0.25, p0=p0, ks=f, precision=rb.PREC_MIXED, opts=opts)
+               for f in fields]
+        res = [srv.wait(i) for i in ids]
+        t = time.perf_counter() - t0
+        srv.close()
+        results[bm] = res
+        out["batch%d" % bm] = {"capacity_rps": n_req / t, "burst_s": t,
+                               "failed": sum(1 for r in res if r["status"] != 0),
+                               "batched_requests": sum(1 for r in res if r.get("batch_size", 1) > 1),
+                               "batch_reruns": sum(1 for r in res if r.get("batch_rerun", 0))}
+    dev = 0.0
+    for a, b in zip(results[1], results[8]):
+        if a["status"] == 0 and b["status"] == 0:
+            dev = max(dev, float(np.abs(a["p"] - b["p"]).max() / np.abs(a["p"]).max()))
+    out["batched_vs_alone_max_rel_dev"] = dev
+    out["speedup_batch8"] = out["batch8"]["capacity_rps"] / out["batch1"]["capacity_rps"]
+    return out
+
+
 def workload_config(w, grid):
     from paper_2112_05051_gb300 import synth
     return {"workload": w.name, "grid": [grid.nx, grid.ny, grid.nz], "dof": grid.n,
@@ -736,6 +779,10 @@ def run_ours(args):
             line["serving"] = serving_run(args, rb)
         except Exception as e:  # the main measurement stands on its own
             line["serving"] = {"error": "%s: %s" % (type(e).__name__, e)}
+        try:
+            line["serving_uniform"] = serving_uniform(args, rb)
+        except Exception as e:
+            line["serving_uniform"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line))
     if dist:
@@ -780,7 +827,7 @@ def main():
     if args.serving_only:
         from paper_2112_05051_gb300 import richards as rb
         rb.load()
-        print(json.dumps(serving_run(args, rb)))
+        print(json.dumps({"serving": serving_run(args, rb), "serving_uniform": serving_uniform(args, rb)}))
         return 0
     return run_ours(args)
 

@@ -48,45 +48,34 @@ def _lone(rb, grid, kmean, ks, p0, dt, prec, dt2=None):
 
 @pytest.mark.parametrize("kmean,prec", [(synth.KMEAN_ARITH, 0), (synth.KMEAN_UPSTREAM, 1)])
 def test_batch_equals_lone_steps_and_the_oracle(kmean, prec):
+    # Fields (sigma 0.5) and steps (dt 0.25, twice) on which the oracle's FCG needs
+    # no FGMRES fallback for any of the three problems: a batch has no fallback, and
+    # its hierarchy (built on all problems at once) differs from a lone one, so on
+    # inputs where FCG is near breakdown the two could part ways.
     rb = _rb()
     grid = synth.Grid(14, 13, 12)
-    fields = [synth.ks_field(grid, 40 + b, 1.0, (4.0, 4.0, 2.0)) for b in range(3)]
+    fields = [synth.ks_field(grid, 40 + b, 0.5, (4.0, 4.0, 2.0)) for b in range(3)]
     p0 = np.full(grid.n, synth.P_INITIAL)
+    dt = 0.25
     bctx = rb.BatchContext(grid, 3, SOIL, synth.infiltration_bc(), kmean, np.concatenate(fields), precision=prec)
     pb = torch.tensor(np.tile(p0, 3), device="cuda")
-    status, stats = bctx.step_batch(pb, 1.0, _opts(rb))
+    status, stats = bctx.step_batch(pb, dt, _opts(rb))
     assert status == [0, 0, 0]
-    pbh = pb.cpu().numpy().reshape(3, grid.n)
-    lone = []
-    for b in range(3):
-        lone.append(_lone(rb, grid, kmean, fields[b], p0, 1.0, prec, dt2=0.5))
-        s, st, pl = lone[b][0]
-        assert s == 0
-        assert _rel(pbh[b], pl) <= 1e-8
-        assert abs(stats[b].newton_its - st.newton_its) <= 1 and stats[b].converged
-        po, ost = newton.step(newton.Problem(grid, SOIL, synth.infiltration_bc(), kmean, fields[b]), p0, 1.0,
-                              newton.NewtonOptions(krylov="fcg", amg_seed=3, coarse_max=100, smooth_levels=2))
-        assert _rel(pbh[b], po) <= 1e-8
-    # A second step of the batch reuses its hierarchy (numeric refresh).  FCG may
-    # break down on the nonsymmetric J of a later step; a lone step then falls back
-    # to FGMRES while a batch member reports RICH_ENOTCONV_LIN (the server reruns
-    # it alone).  Where the lone step needed no fallback the batch converges too,
-    # to the same pressure.
-    status, stats = bctx.step_batch(pb, 0.5, _opts(rb))
-    assert all(s.amg_setups == 0 for s in stats)
-    lin = {name: code for code, name in rb.ERRORS.items()}["RICH_ENOTCONV_LIN"]
-    assert all(s in (0, lin) for s in status)
-    pbh = pb.cpu().numpy().reshape(3, grid.n)
-    compared = 0
-    for b in range(3):
-        s2, st2, pl2 = lone[b][1]
-        if s2 == 0 and st2.fallbacks == 0:
-            assert status[b] == 0
-            assert _rel(pbh[b], pl2) <= 1e-8
-            compared += 1
-    if kmean == synth.KMEAN_ARITH:
-        assert compared >= 1
+    step1 = pb.cpu().numpy().reshape(3, grid.n)
+    # a second step of the batch reuses its hierarchy (numeric refresh)
+    status2, stats2 = bctx.step_batch(pb, dt, _opts(rb))
+    assert status2 == [0, 0, 0] and all(s.amg_setups == 0 for s in stats2)
+    step2 = pb.cpu().numpy().reshape(3, grid.n)
     bctx.close()
+    for b in range(3):
+        (s, st, pl), (s2, st2, pl2) = _lone(rb, grid, kmean, fields[b], p0, dt, prec, dt2=dt)
+        assert s == 0 and s2 == 0
+        assert _rel(step1[b], pl) <= 1e-8 and _rel(step2[b], pl2) <= 1e-8
+        assert abs(stats[b].newton_its - st.newton_its) <= 1 and stats[b].converged
+        po, ost = newton.step(newton.Problem(grid, SOIL, synth.infiltration_bc(), kmean, fields[b]), p0, dt,
+                              newton.NewtonOptions(krylov="fcg", amg_seed=3, coarse_max=100, smooth_levels=2))
+        assert ost.fallbacks == 0
+        assert _rel(step1[b], po) <= 1e-8
 
 
 def test_a_failing_problem_does_not_hold_the_batch_back():
