@@ -189,11 +189,13 @@ typedef struct {
                               aggregated neighbour j with the largest (fp32 |a_ij|, key(j)); dominant rows
                               (e.g. under a Dirichlet face) stay out.  0: every such node stays out */
   int csr_layout;          /* the V-cycle's sparse row operations below the finest level (sweep, residual,
-                              restriction, prolongation).  RICH_LAYOUT_AUTO (default): a SELL-C-sigma copy
-                              (slices of 32 rows sorted by length within windows of 1024 rows, one thread
-                              per row) of every coarse A and every P and R with >= 2048 rows is built,
-                              and the autotuner times it beside the CSR variants; RICH_LAYOUT_CSR: CSR
-                              only, no copy; RICH_LAYOUT_SELL: the SELL copy wherever one is built */
+                              restriction, prolongation).  RICH_LAYOUT_AUTO (default): a coarse A, P or R
+                              with >= 2048 rows may get a SELL-C-sigma copy (slices of 32 rows sorted by
+                              length within windows of 1024 rows, one thread per row): the autotuner
+                              times it beside the CSR variants when it first meets the matrix's shape
+                              class, and keeps it only if it wins; a matrix whose class chose it gets
+                              its copy on first use.  RICH_LAYOUT_CSR: CSR only, no copy.
+                              RICH_LAYOUT_SELL: the SELL copy for every such matrix (no timing) */
 } rich_amg_opts;
 
 typedef struct {

@@ -1447,38 +1447,11 @@ static int level_diag_data(rich_ctx* c, Level& L) {
   return RICH_OK;
 }
 
-// Values of level L's SELL copy of A from the values the V-cycle uses (FP32 in MIXED).
+// Values of level L's SELL copy of A (if the V-cycle has laid one out) from the
+// values the V-cycle uses (FP32 in MIXED).
 static int sell_fill_a(rich_ctx* c, Level& L) {
   if (c->prec == RICH_PREC_MIXED) return sell_fill(c, L.A, L.A32, L.sA);
   return sell_fill(c, L.A, L.A.val, L.sA);
-}
-
-// SELL copies of the coarse-level operators (A below the finest level, unless the
-// coarsest is inverted densely) and of every P and R, for the CSR row operations
-// of the V-cycle.  P and R keep their setup values; A is refilled at every refresh.
-static int sell_setup(rich_ctx* c) {
-  Hierarchy& H = c->H;
-  if (H.opts.csr_layout == RICH_LAYOUT_CSR) return RICH_OK;
-  const bool mp = c->prec == RICH_PREC_MIXED;
-  for (int l = 0; l < H.nlev; ++l) {
-    Level& L = H.lv[l];
-    if (l > 0 && !(l == H.nlev - 1 && H.dense)) {
-      RICH_CHECK(sell_build(c, L.A, L.sA));
-      RICH_CHECK(sell_fill_a(c, L));
-    }
-    if (l + 1 < H.nlev) {
-      RICH_CHECK(sell_build(c, L.P, L.sP));
-      RICH_CHECK(sell_build(c, L.R, L.sR));
-      if (mp) {
-        RICH_CHECK(sell_fill(c, L.P, L.P32, L.sP));
-        RICH_CHECK(sell_fill(c, L.R, L.R32, L.sR));
-      } else {
-        RICH_CHECK(sell_fill(c, L.P, L.P.val, L.sP));
-        RICH_CHECK(sell_fill(c, L.R, L.R.val, L.sR));
-      }
-    }
-  }
-  return RICH_OK;
 }
 
 static int level_alloc_vectors(rich_ctx* c, Level& L) {
@@ -1852,7 +1825,6 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
     RICH_CHECK(level_alloc_vectors(c, H.lv[l]));
     RICH_CHECK(level_diag_data(c, H.lv[l]));
   }
-  RICH_CHECK(sell_setup(c));
   RICH_CHECK(fine_stencil(c));
   if (H.dense) {
     RICH_CHECK(dalloc(&H.cdense, (long long)H.cn * H.cn));

@@ -75,8 +75,13 @@ static long long g_prof_seen = 0; // launches of the target (recorded or not)
 static long long g_prof_stride = 1;  // record every stride-th launch of the target
 static double g_prof_bytes = 0.0;
 static double g_prof_flops = 0.0;
+static int g_prof_open = -1;         // the pair whose end is still to be recorded
 
 bool profiling_active() { return !g_prof_target.empty(); }
+
+void prof_restart(cudaStream_t st) {
+  if (g_prof_open >= 0) cudaEventRecord(g_prof_ev[2 * g_prof_open], st);
+}
 
 ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(false), st(s), bytes(b), flops(f) {
   if (g_prof_target.empty() || (g_prof_target != "*" && g_prof_target != name)) return;
@@ -91,6 +96,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(
   }
   on = true;
   g_prof_name[g_prof_n] = name;
+  g_prof_open = g_prof_n;
   cudaEventRecord(g_prof_ev[2 * g_prof_n], st);
 }
 
@@ -101,6 +107,7 @@ ProfScope::~ProfScope() {
   g_prof_f[g_prof_n] = flops;
   g_prof_bytes += bytes;
   g_prof_flops += flops;
+  g_prof_open = -1;
   ++g_prof_n;
 }
 
@@ -344,6 +351,7 @@ int rich_profile_kernel(const char* name) {
   rich::g_prof_target = name ? name : "";
   rich::g_prof_n = 0;
   rich::g_prof_seen = 0;
+  rich::g_prof_open = -1;
   rich::g_prof_bytes = 0.0;
   rich::g_prof_flops = 0.0;
   return RICH_OK;

@@ -46,6 +46,9 @@ void count_launches(long long k);  // k may be negative (launches recorded into 
 
 // Optional live timing of one named kernel: when its name matches the profiling
 // target, CUDA events are recorded around its launches on the launching stream.
+// Moves the start of the open timed launch to now (work done on the stream since
+// it opened, e.g. a one-time layout, is not charged to the launch).
+void prof_restart(cudaStream_t st);
 struct ProfScope {
   bool on;
   cudaStream_t st;

@@ -190,7 +190,7 @@ static int default_lanes(double avg) {
 struct TuneKey {
   int mode, tsize, n;   // n: quarter-octave bin of the row count
   long long nnz;        // rounded mean row length
-  int sell;             // 1: the SELL copy is among the candidates
+  int sell;             // 1: a SELL copy is among the candidates
   bool operator<(const TuneKey& o) const {
     if (mode != o.mode) return mode < o.mode;
     if (tsize != o.tsize) return tsize < o.tsize;
@@ -199,35 +199,74 @@ struct TuneKey {
     return sell < o.sell;
   }
 };
+struct TuneVal {
+  int variant;   // fastest candidate
+  float us;      // its time per launch
+  int best_csr;  // fastest CSR candidate (used where a matrix of the class has no SELL copy)
+};
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, float>> g_tune;  // -> (variant, best us)
+static std::map<TuneKey, TuneVal> g_tune;
 
-// sl/sval: the matrix's SELL copy and its values in T (nullptr where none is built).
+// Where a row operation's matrix can get a SELL copy: the copy, the CSR it is laid
+// out from and the values in the hierarchy precision.
+template <class T>
+struct SellSrc {
+  Sell* s;
+  const Csr<double>* M;
+  const T* vals;
+};
+
+// Lays out the SELL copy on first use (the row operations of a class that chose it,
+// or a class being tuned): matrices whose class keeps CSR never get one.
+template <class T>
+static int sell_ensure(rich_ctx* c, const SellSrc<T>& src, bool* ok) {
+  if (!src.s->built()) {
+    RICH_CHECK(sell_build(c, *src.M, *src.s));
+    if (src.s->built()) RICH_CHECK(sell_fill(c, *src.M, src.vals, *src.s));
+    prof_restart(c->st);
+  }
+  *ok = src.s->built();
+  return RICH_OK;
+}
+
+// src: the matrix's SELL source (nullptr: CSR only).
 template <class T, int MODE>
 static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* col, const T* val, const T* dinv,
-                  const T* b, const T* x, T* y, const Sell* sl = nullptr, const T* sval = nullptr) {
+                  const T* b, const T* x, T* y, const SellSrc<T>* src = nullptr) {
   if (n <= 0) return RICH_OK;
-  const bool has_sell = sl && sl->built() && sl->nrows == n && sval && c->H.opts.csr_layout != RICH_LAYOUT_CSR;
-  int G = default_lanes((double)nnz / n);
-  if (has_sell && c->H.opts.csr_layout == RICH_LAYOUT_SELL) {
-    G = kSellVariant;
-  } else if (c->H.opts.autotune && !profiling_active()) {
+  const int layout = c->H.opts.csr_layout;
+  const bool offer = src && src->s && n >= kSellMinRows && layout != RICH_LAYOUT_CSR;
+  int v = default_lanes((double)nnz / n);
+  bool sell_ok = false;
+  if (offer && layout == RICH_LAYOUT_SELL) {
+    RICH_CHECK(sell_ensure(c, *src, &sell_ok));
+    if (sell_ok) v = kSellVariant;
+  } else if (c->H.opts.autotune) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneKey key{MODE, (int)sizeof(T), (int)std::floor(4.0 * std::log2((double)n)),
-                (long long)std::llround((double)nnz / n), has_sell ? 1 : 0};
+                (long long)std::llround((double)nnz / n), offer ? 1 : 0};
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      G = it->second.first;
-    } else {
+      v = it->second.variant;
+      if (v == kSellVariant) {
+        RICH_CHECK(sell_ensure(c, *src, &sell_ok));
+        if (!sell_ok) v = it->second.best_csr;
+      }
+    } else if (!profiling_active()) {  // a profiled pass runs what is tuned, and tunes nothing
+      const bool had_copy = offer && src->s->built();
+      if (offer) RICH_CHECK(sell_ensure(c, *src, &sell_ok));
       T* scratch = nullptr;
       RICH_CHECK(dalloc(&scratch, n));
       RICH_CUDA(cudaMemsetAsync(scratch, 0, sizeof(T) * (size_t)n, c->st));
       cudaEvent_t e0, e1;
       RICH_CUDA(cudaEventCreate(&e0));
       RICH_CUDA(cudaEventCreate(&e1));
-      float best = 1e30f;
+      float best = 1e30f, best_csr_us = 1e30f;
+      int best_csr = v;
+      const Sell* sl = sell_ok ? src->s : nullptr;
+      const T* sval = sell_ok ? (sizeof(T) == 8 ? (const T*)sl->val : (const T*)sl->val32) : nullptr;
       for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll, kSellVariant}) {
-        if (g == kSellVariant && !has_sell) continue;
+        if (g == kSellVariant && !sell_ok) continue;
         csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
         RICH_CUDA(cudaEventRecord(e0, c->st));
         for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
@@ -238,17 +277,31 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
         count_launches(4);
         if (ms < best) {
           best = ms;
-          G = g;
+          v = g;
+        }
+        if (g != kSellVariant && ms < best_csr_us) {
+          best_csr_us = ms;
+          best_csr = g;
         }
       }
       RICH_CUDA(cudaGetLastError());
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       dfree(scratch);
-      g_tune[key] = {G, best * 1000.f / 3.f};
+      g_tune[key] = {v, best * 1000.f / 3.f, best_csr};
+      if (sell_ok && v != kSellVariant && !had_copy) {  // the copy lost: not kept, not refreshed
+        sell_free(*src->s);
+        sell_ok = false;
+      }
     }
   }
-  csr_launch<T, MODE>(c->st, G, n, rp, col, val, dinv, b, x, y, sl, sval);
+  const Sell* sl = nullptr;
+  const T* sval = nullptr;
+  if (v == kSellVariant) {
+    sl = src->s;
+    sval = sizeof(T) == 8 ? (const T*)sl->val : (const T*)sl->val32;
+  }
+  csr_launch<T, MODE>(c->st, v, n, rp, col, val, dinv, b, x, y, sl, sval);
   return RICH_OK;
 }
 
@@ -258,7 +311,7 @@ int autotune_table(char* buf, int cap) {
   buf[0] = 0;
   for (auto& e : g_tune) {
     int w = snprintf(buf + off, cap - off, "%d %d %d %lld %d %d %.3f\n", e.first.mode, e.first.tsize, e.first.n,
-                     e.first.nnz, e.first.sell, e.second.first, e.second.second);
+                     e.first.nnz, e.first.sell, e.second.variant, e.second.us);
     if (w < 0 || w >= cap - off) break;
     off += w;
   }
@@ -463,8 +516,7 @@ struct LevelView {
   const T* dinv;
   const int *prp, *pcol, *rrp, *rcol;
   const T *pval, *rval;
-  const Sell *sa, *sp, *sr;  // SELL copies of A, P, R and their values in T
-  const T *sav, *spv, *srv;
+  SellSrc<T> sa, sp, sr;  // SELL sources of A, P, R
 };
 
 template <class T>
@@ -473,16 +525,18 @@ static LevelView<T> view(rich_ctx* c, int l);
 template <>
 LevelView<double> view<double>(rich_ctx* c, int l) {
   Level& L = c->H.lv[l];
-  return LevelView<double>{L.n,       L.A.rowptr, L.A.col,  L.A.val,  L.dinv,   L.P.rowptr, L.P.col,
-                           L.R.rowptr, L.R.col,    L.P.val,  L.R.val,  &L.sA,    &L.sP,      &L.sR,
-                           L.sA.val,   L.sP.val,   L.sR.val};
+  return LevelView<double>{L.n,     L.A.rowptr, L.A.col, L.A.val,
+                           L.dinv,  L.P.rowptr, L.P.col, L.R.rowptr,
+                           L.R.col, L.P.val,    L.R.val, {&L.sA, &L.A, L.A.val},
+                           {&L.sP, &L.P, L.P.val}, {&L.sR, &L.R, L.R.val}};
 }
 template <>
 LevelView<float> view<float>(rich_ctx* c, int l) {
   Level& L = c->H.lv[l];
-  return LevelView<float>{L.n,        L.A.rowptr, L.A.col,    L.A32, L.dinv32, L.P.rowptr, L.P.col,
-                          L.R.rowptr, L.R.col,    L.P32,      L.R32, &L.sA,    &L.sP,      &L.sR,
-                          L.sA.val32, L.sP.val32, L.sR.val32};
+  return LevelView<float>{L.n,       L.A.rowptr, L.A.col, L.A32,
+                          L.dinv32,  L.P.rowptr, L.P.col, L.R.rowptr,
+                          L.R.col,   L.P32,      L.R32,   {&L.sA, &L.A, L.A32},
+                          {&L.sP, &L.P, L.P32},  {&L.sR, &L.R, L.R32}};
 }
 
 template <class T>
@@ -540,23 +594,22 @@ static int vcycle_level_hgs(rich_ctx* c, int l, const T* b, T** xres) {
     ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st,
                  st0 ? (double)n * 7.0 * es : (double)n * (4.0 + 3.0 * es) + (double)L.A.nnz * (4.0 + es));
     if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-    else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r, v.sa,
-                                 v.sav));
+    else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r, &v.sa));
   }
   RICH_LAUNCH_CHECK();
   Level& C = H.lv[l + 1];
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
     RICH_CHECK(csr_op<T, 0>(c, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr,
-                            (const T*)L.r, (T*)C.b, v.sr, v.srv));
+                            (const T*)L.r, (T*)C.b, &v.sr));
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x, v.sp,
-                            v.spv));
+    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x,
+                            &v.sp));
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < H.opts.nu2; ++s) {
@@ -593,7 +646,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       k_jacobi0<T><<<g, kBlock, 0, c->st>>>(n, v.dinv, b, x);
       RICH_LAUNCH_CHECK();
       for (int s = 1; s < kCoarseSweeps; ++s) {
-        RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, v.sa, v.sav));
+        RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, &v.sa));
         RICH_LAUNCH_CHECK();
         std::swap(x, t);
       }
@@ -636,7 +689,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
         ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
                      st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
         if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-        else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, v.sa, v.sav));
+        else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, &v.sa));
       }
       RICH_LAUNCH_CHECK();
       std::swap(x, t);
@@ -644,8 +697,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
     {
       ProfScope ps(st0 ? "resid_l0" : "csr_resid", c->st, st0 ? st_bytes : sweep_bytes - (double)n * es);
       if (st0) k_st_smooth<T, 2><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, (T*)L.r);
-      else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r, v.sa,
-                                 v.sav));
+      else RICH_CHECK(csr_op<T, 3>(c, n, L.A.nnz, v.rp, v.col, v.val, (const T*)nullptr, b, x, (T*)L.r, &v.sa));
     }
     RICH_LAUNCH_CHECK();
   } else {
@@ -656,15 +708,15 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   {
     ProfScope ps("restrict", c->st, (double)C.n * (4.0 + es) + (double)L.R.nnz * (4.0 + es) + (double)n * es);
     RICH_CHECK(csr_op<T, 0>(c, C.n, L.R.nnz, v.rrp, v.rcol, v.rval, (const T*)nullptr, (const T*)nullptr,
-                            (const T*)L.r, (T*)C.b, v.sr, v.srv));
+                            (const T*)L.r, (T*)C.b, &v.sr));
   }
   RICH_LAUNCH_CHECK();
   T* xc = nullptr;
   RICH_CHECK(vcycle_level<T>(c, l + 1, (const T*)C.b, &xc));
   {
     ProfScope ps("prolong", c->st, (double)n * (4.0 + 2.0 * es) + (double)L.P.nnz * (4.0 + es) + (double)C.n * es);
-    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x, v.sp,
-                            v.spv));
+    RICH_CHECK(csr_op<T, 1>(c, n, L.P.nnz, v.prp, v.pcol, v.pval, (const T*)nullptr, (const T*)nullptr, xc, x,
+                            &v.sp));
   }
   RICH_LAUNCH_CHECK();
   for (int s = 0; s < nu2; ++s) {
@@ -672,7 +724,7 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
       ProfScope ps(l == 0 ? "l1jacobi_l0" : "l1jacobi", c->st, st0 ? st_bytes : sweep_bytes,
                    st0 ? 16.0 * n : 2.0 * L.A.nnz + 3.0 * n);
       if (st0) k_st_smooth<T, 1><<<line_grid(c->g), kLineThreads, 0, c->st>>>(c->g, fine<T>(c), b, x, t);
-      else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, v.sa, v.sav));
+      else RICH_CHECK(csr_op<T, 2>(c, n, L.A.nnz, v.rp, v.col, v.val, v.dinv, b, x, t, &v.sa));
     }
     RICH_LAUNCH_CHECK();
     std::swap(x, t);
