@@ -79,8 +79,22 @@ static int g_prof_open = -1;         // the pair whose end is still to be record
 
 bool profiling_active() { return !g_prof_target.empty(); }
 
+// Keeps the stream busy for a fixed number of clock cycles (the loop ends by itself):
+// queued ahead of a timed launch's start event, it lets the host enqueue the event
+// and the launch before the GPU reaches them, so the pair measures the kernel and not
+// the host's submission gap (the Krylov loops synchronise every iteration, leaving the
+// GPU idle between launches).
+__global__ void k_prof_delay(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+constexpr long long kProfDelayCycles = 40000;  // ~20 us at 2 GHz
+
 void prof_restart(cudaStream_t st) {
-  if (g_prof_open >= 0) cudaEventRecord(g_prof_ev[2 * g_prof_open], st);
+  if (g_prof_open < 0) return;
+  k_prof_delay<<<1, 32, 0, st>>>(kProfDelayCycles);
+  cudaEventRecord(g_prof_ev[2 * g_prof_open], st);
 }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(false), st(s), bytes(b), flops(f) {
@@ -97,6 +111,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t s, double b, double f) : on(
   on = true;
   g_prof_name[g_prof_n] = name;
   g_prof_open = g_prof_n;
+  k_prof_delay<<<1, 32, 0, st>>>(kProfDelayCycles);
   cudaEventRecord(g_prof_ev[2 * g_prof_n], st);
 }
 
