@@ -399,8 +399,9 @@ int rich_measure_fma_peak(int fp64, double* tflops);
 /* The autotuner's choices so far, one line "mode value_bytes rows_bin mean_row_length
  * sell_offered variant best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep,
  * 3 residual; rows_bin = floor(4 log2 rows); sell_offered 1 where a SELL copy was a
- * candidate; variant = lanes per row, + 256 for four-way unrolled rows, 512 for the
- * SELL copy), written into buf (at most cap bytes, NUL-terminated). */
+ * candidate; variant = lanes per row, + 256 for four-way unrolled rows, 512 / 513 for
+ * the SELL copy with 4 / 8 gathers in flight per row), written into buf (at most cap
+ * bytes, NUL-terminated). */
 int rich_autotune_table(char* buf, int cap);
 
 /* Number of kernels this library has launched since it was loaded. */

@@ -97,11 +97,11 @@ __global__ void k_csr_grp(int n, const int* __restrict__ rp, const int* __restri
 }
 
 // The same row operations on the SELL-C-sigma copy: one warp per slice of 32 rows,
-// one thread per row, slot loads coalesced across the warp, four gathers of x in
-// flight per thread, no cross-lane reduction (on GB300's narrow FP64 pipe the
+// one thread per row, slot loads coalesced across the warp, U gathers of x in flight
+// per thread (U = 4 or 8), no cross-lane reduction (on GB300's narrow FP64 pipe the
 // shuffle-add reductions and the idle lanes of ragged rows cost as much as the
 // products themselves).  Past a row's end the slots hold zeros.
-template <class T, int MODE>
+template <class T, int MODE, int U>
 __global__ void __launch_bounds__(kBlock) k_sell(int nslice, const int* __restrict__ sptr,
                                                  const int* __restrict__ perm, const int* __restrict__ col,
                                                  const T* __restrict__ val, const T* __restrict__ dinv,
@@ -114,14 +114,20 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslice, const int* __restri
     const int end = sptr[s + 1];
     int e = sptr[s] + lane;
     T s0 = 0, s1 = 0;
-    for (; e + 3 * kSellC < end; e += 4 * kSellC) {  // warp-uniform: the slice's columns are full
-      const int c0 = col[e], c1 = col[e + kSellC], c2 = col[e + 2 * kSellC], c3 = col[e + 3 * kSellC];
-      const T v0 = val[e], v1 = val[e + kSellC], v2 = val[e + 2 * kSellC], v3 = val[e + 3 * kSellC];
-      const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-      s0 += v0 * x0;
-      s1 += v1 * x1;
-      s0 += v2 * x2;
-      s1 += v3 * x3;
+    for (; e + (U - 1) * kSellC < end; e += U * kSellC) {  // warp-uniform: the slice's columns are full
+      int cc[U];
+      T vv[U], xx[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) cc[u] = col[e + u * kSellC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) vv[u] = val[e + u * kSellC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) xx[u] = x[cc[u]];
+#pragma unroll
+      for (int u = 0; u < U; u += 2) {
+        s0 += vv[u] * xx[u];
+        s1 += vv[u + 1] * xx[u + 1];
+      }
     }
     for (; e < end; e += kSellC) s0 += val[e] * x[col[e]];
     const T a = s0 + s1;
@@ -135,15 +141,21 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslice, const int* __restri
 }
 
 // Variant v of the CSR row kernel: lanes per row G = v & 0xff, four-way unrolled
-// rows when v & kUnroll; v == kSellVariant runs the SELL copy (sl, sval) instead.
+// rows when v & kUnroll; v == kSellVariant (4 gathers in flight) or kSellVariant8
+// (8) runs the SELL copy (sl, sval) instead.
 constexpr int kUnroll = 0x100;
 constexpr int kSellVariant = 0x200;
+constexpr int kSellVariant8 = 0x201;
+inline bool is_sell(int v) { return (v & kSellVariant) != 0; }
 template <class T, int MODE>
 static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* col, const T* val, const T* dinv,
                        const T* b, const T* x, T* y, const Sell* sl = nullptr, const T* sval = nullptr) {
-  if (v == kSellVariant) {
-    k_sell<T, MODE><<<grid_for((long long)sl->nslice * kSellC), kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm,
-                                                                                 sl->col, sval, dinv, b, x, y);
+  if (is_sell(v)) {
+    const int g = grid_for((long long)sl->nslice * kSellC);
+    if (v == kSellVariant8)
+      k_sell<T, MODE, 8><<<g, kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm, sl->col, sval, dinv, b, x, y);
+    else
+      k_sell<T, MODE, 4><<<g, kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm, sl->col, sval, dinv, b, x, y);
     return;
   }
   const int G = v & 0xff;
@@ -248,7 +260,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       v = it->second.variant;
-      if (v == kSellVariant) {
+      if (is_sell(v)) {
         RICH_CHECK(sell_ensure(c, *src, &sell_ok));
         if (!sell_ok) v = it->second.best_csr;
       }
@@ -265,8 +277,9 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       int best_csr = v;
       const Sell* sl = sell_ok ? src->s : nullptr;
       const T* sval = sell_ok ? (sizeof(T) == 8 ? (const T*)sl->val : (const T*)sl->val32) : nullptr;
-      for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll, kSellVariant}) {
-        if (g == kSellVariant && !sell_ok) continue;
+      for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll, kSellVariant,
+                    kSellVariant8}) {
+        if (is_sell(g) && !sell_ok) continue;
         csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
         RICH_CUDA(cudaEventRecord(e0, c->st));
         for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
@@ -279,7 +292,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
           best = ms;
           v = g;
         }
-        if (g != kSellVariant && ms < best_csr_us) {
+        if (!is_sell(g) && ms < best_csr_us) {
           best_csr_us = ms;
           best_csr = g;
         }
@@ -289,7 +302,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       cudaEventDestroy(e1);
       dfree(scratch);
       g_tune[key] = {v, best * 1000.f / 3.f, best_csr};
-      if (sell_ok && v != kSellVariant && !had_copy) {  // the copy lost: not kept, not refreshed
+      if (sell_ok && !is_sell(v) && !had_copy) {  // the copy lost: not kept, not refreshed
         sell_free(*src->s);
         sell_ok = false;
       }
@@ -297,7 +310,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
   }
   const Sell* sl = nullptr;
   const T* sval = nullptr;
-  if (v == kSellVariant) {
+  if (is_sell(v)) {
     sl = src->s;
     sval = sizeof(T) == 8 ? (const T*)sl->val : (const T*)sl->val32;
   }
