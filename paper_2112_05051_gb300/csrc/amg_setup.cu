@@ -344,7 +344,9 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t* keys, int M, int lan
 
 constexpr int kEscCap = 1024;    // most products per row the shared-memory ESC kernel takes
 
-// mode 0: cnt[row] = number of distinct columns; mode 1: write the compressed row at crp[row].
+// mode 0: cnt[row] = number of distinct columns; mode 1: write the compressed row at crp[row];
+// mode 2 (single pass): write it at the row's product offset uoff[row] of a temporary
+// and set cnt[row].
 // Each warp owns `cap` key/value slots of shared memory (cap = the launch's largest
 // product count rounded up to a power of two, at most kEscCap), so short rows
 // (the 7-point level: tens of products) run many warps per SM.  Rows whose product
@@ -353,7 +355,8 @@ __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* 
                              const double* __restrict__ aval, const int* __restrict__ brp,
                              const int* __restrict__ bcol, const double* __restrict__ bval,
                              const int* __restrict__ u, int mode, const int* __restrict__ crp,
-                             int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt, int cap) {
+                             const long long* __restrict__ uoff, int* __restrict__ ccol, double* __restrict__ cval,
+                             int* __restrict__ cnt, int cap) {
   extern __shared__ unsigned char smem[];
   int wpb = blockDim.x >> 5;
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -383,7 +386,7 @@ __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* 
     __syncwarp();
     warp_bitonic_sort(keys, M, lane);
     // segment heads
-    int base = (mode == 1) ? crp[row] : 0;
+    const long long base = mode == 1 ? (long long)crp[row] : (mode == 2 ? uoff[row] : 0);
     int running = 0;
     for (int t0s = 0; t0s < ur; t0s += 32) {
       int t = t0s + lane;
@@ -394,8 +397,8 @@ __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* 
         head = (t == 0) || ((uint32_t)(keys[t - 1] >> 32) != c);
       }
       unsigned mask = __ballot_sync(0xffffffffu, head);
-      if (mode == 1 && head) {
-        int pos = base + running + __popc(mask & ((1u << lane) - 1));
+      if (mode != 0 && head) {
+        const long long pos = base + running + __popc(mask & ((1u << lane) - 1));
         double s = 0.0;
         for (int q = t; q < ur && (uint32_t)(keys[q] >> 32) == c; ++q) s += vals[(uint32_t)(keys[q] & kLow32)];
         ccol[pos] = (int)c;
@@ -403,7 +406,7 @@ __global__ void k_spgemm_esc(int nrows, const int* __restrict__ arp, const int* 
       }
       running += __popc(mask);
     }
-    if (mode == 0 && lane == 0) cnt[row] = running;
+    if (mode != 1 && lane == 0) cnt[row] = running;
     __syncwarp();
   }
 }
@@ -418,8 +421,8 @@ constexpr int kHashThreads = 256;
 __global__ void __launch_bounds__(kHashThreads) k_spgemm_hash(
     int nrows, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
     const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
-    const int* __restrict__ u, int mode, const int* __restrict__ crp, int* __restrict__ ccol,
-    double* __restrict__ cval, int* __restrict__ cnt, int* __restrict__ overflow) {
+    const int* __restrict__ u, int mode, const int* __restrict__ crp, const long long* __restrict__ uoff,
+    int* __restrict__ ccol, double* __restrict__ cval, int* __restrict__ cnt, int* __restrict__ overflow) {
   extern __shared__ unsigned char smem[];
   int* hkey = reinterpret_cast<int*>(smem);
   double* hval = reinterpret_cast<double*>(smem + kHashSlots * sizeof(int));
@@ -500,10 +503,9 @@ __global__ void __launch_bounds__(kHashThreads) k_spgemm_hash(
         __syncthreads();
       }
     }
-    if (mode == 0) {
-      if (threadIdx.x == 0) cnt[row] = L;
-    } else {
-      int base = crp[row];
+    if (mode != 1 && threadIdx.x == 0) cnt[row] = L;
+    if (mode != 0) {
+      const long long base = mode == 1 ? (long long)crp[row] : uoff[row];
       for (int t = threadIdx.x; t < L; t += blockDim.x) {
         ccol[base + t] = (int)(keys[t] >> 32);
         cval[base + t] = hval[(uint32_t)(keys[t] & kLow32)];
@@ -1055,6 +1057,23 @@ __global__ void k_iota(int n, int* __restrict__ a) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
 
+// Single-pass SpGEMM: row r's cnt[r] compressed entries move from the temporary at
+// its product offset uoff[r] to crp[r]; one warp per row.
+__global__ void k_compact_rows(int n, const long long* __restrict__ uoff, const int* __restrict__ cnt,
+                               const int* __restrict__ crp, const int* __restrict__ tcol,
+                               const double* __restrict__ tval, int* __restrict__ ccol, double* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long src = uoff[row];
+    const int dst = crp[row], m = cnt[row];
+    for (int t = lane; t < m; t += 32) {
+      ccol[dst + t] = tcol[src + t];
+      cval[dst + t] = tval[src + t];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host side
 
 // One int from the device, on the context's stream only (a plain cudaMemcpy would
@@ -1109,8 +1128,27 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
   if (big) RICH_CUDA(cudaFuncSetAttribute(k_spgemm_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
   int* ovf = c->iflag + 1;
   RICH_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c->st));
-  for (int mode = 0; mode < 2; ++mode) {
-    if (mode == 1) {
+  // One pass when a temporary of every product's slot fits in a quarter of the free
+  // memory: each row is expanded, sorted and compressed once, at its product offset,
+  // then compacted.  Otherwise two passes (count, then write at the final offsets).
+  long long* uoff = nullptr;
+  RICH_CHECK(dalloc(&uoff, (long long)n + 1));
+  RICH_CHECK(scan_exclusive_int_ll(c, u, uoff, n));
+  long long nprod = 0;
+  RICH_CUDA(cudaMemcpyAsync(&nprod, uoff + n, sizeof(long long), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  size_t mfree = 0, mtotal = 0;
+  RICH_CUDA(cudaMemGetInfo(&mfree, &mtotal));
+  const bool one_pass = (double)nprod * (sizeof(int) + sizeof(double)) <= 0.25 * (double)mfree;
+  int* tcol = nullptr;
+  double* tval = nullptr;
+  if (one_pass) {
+    RICH_CHECK(dalloc(&tcol, nprod));
+    RICH_CHECK(dalloc(&tval, nprod));
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    const int mode = one_pass ? 2 : pass;
+    if (pass == 1) {
       // the row offsets are 32-bit: check the total in 64 bits before the scan
       unsigned long long* dsum = reinterpret_cast<unsigned long long*>(c->iflag + 4);  // slots 4-5
       RICH_CUDA(cudaMemsetAsync(dsum, 0, sizeof(unsigned long long), c->st));
@@ -1127,20 +1165,30 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
       C.nnz = nnz;
       RICH_CHECK(dalloc(&C.col, nnz));
       RICH_CHECK(dalloc(&C.val, nnz));
+      if (one_pass) {
+        k_compact_rows<<<grid_for(32LL * n), kBlock, 0, c->st>>>(n, uoff, cnt, C.rowptr, tcol, tval, C.col, C.val);
+        RICH_LAUNCH_CHECK();
+        break;
+      }
     }
+    int* ocol = mode == 2 ? tcol : C.col;
+    double* oval = mode == 2 ? tval : C.val;
     k_spgemm_esc<<<nblk, 32 * esc_warps, smem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
-                                                       C.rowptr, C.col, C.val, cnt, cap);
+                                                       C.rowptr, uoff, ocol, oval, cnt, cap);
     RICH_LAUNCH_CHECK();
     if (big) {
       int hb = n < 8 * kNumSM ? n : 8 * kNumSM;
       k_spgemm_hash<<<hb, kHashThreads, hsmem, c->st>>>(n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, u, mode,
-                                                        C.rowptr, C.col, C.val, cnt, ovf);
+                                                        C.rowptr, uoff, ocol, oval, cnt, ovf);
       RICH_LAUNCH_CHECK();
       RICH_CUDA(cudaMemcpyAsync(c->hflag + 1, ovf, sizeof(int), cudaMemcpyDeviceToHost, c->st));
       RICH_CUDA(cudaStreamSynchronize(c->st));
       if (c->hflag[1]) return RICH_ELIMIT;  // a row has more distinct columns than the hash table holds
     }
   }
+  dfree(tcol);
+  dfree(tval);
+  dfree(uoff);
   RICH_CUDA(cudaStreamSynchronize(c->st));
   if (u_keep) *u_keep = u; else dfree(u);
   dfree(cnt);
