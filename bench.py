@@ -440,6 +440,7 @@ def serving_run(args, rb):
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
             "max_dt_halvings": halvings, "max_newton_per_attempt": 20 if halvings else 50,
             "latency_ms_converged": st_s["latency_ms_converged"], "failure_rate": st_s["failure_rate"],
+            "device_ms_burst": st_b["device_ms"],
             "converged_per_s": st_s["converged_per_s"], "stream_dof_newton_per_s": st_s["dof_newton_per_s"],
             "capacity_rps": mu, "capacity_converged_rps": st_b["converged_per_s"], "burst_s": t_burst,
             "burst_dof_newton_per_s": st_b["dof_newton_per_s"], "rate_rps": lam, "arrivals": "Poisson, seed 5",

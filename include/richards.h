@@ -462,7 +462,9 @@ typedef struct {
                               no time-step control) and steps them together as one batch
                               (rich_create_batch / rich_step_batch); a member whose step fails in the
                               batch is rerun alone, so every result is the lone path's wherever the
-                              batch cannot match it */
+                              batch cannot match it.  A class (grid, mean, precision) of which more than
+                              a quarter of the batched members failed, once 16 were recorded, is served
+                              alone from then on */
   int batch_min_cells;     /* only requests of at most this many cells are batched (300000) */
 } rich_server_opts;
 

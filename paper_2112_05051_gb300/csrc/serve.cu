@@ -25,7 +25,9 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <thread>
 #include <unordered_map>
 
@@ -68,6 +70,10 @@ struct rich_server {
   bool stop = false;
   std::vector<std::thread> workers;
   std::chrono::steady_clock::time_point t0;
+  // batched members and their failures per class (grid, mean, precision): a class
+  // whose members fail often is served alone (a failed member costs its batch
+  // attempt and a lone rerun)
+  std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> batch_record;
 };
 
 namespace rich {
@@ -160,9 +166,20 @@ static SrvRequest* srv_pick(rich_server* s, std::vector<SrvSession*>* evict) {
 }
 
 // Whether request b may be stepped in one batch with request a (rich_step_batch).
+constexpr int kBatchRecordMin = 16;        // members recorded before a class can be taken out of batching
+constexpr double kBatchFailMax = 0.25;     // failure fraction above which it is
+
+static std::tuple<int, int, int, int, int> srv_class(const rich_request& r) {
+  return std::make_tuple(r.grid.nx, r.grid.ny, r.grid.nz, r.kmean, r.precision);
+}
+
 static bool srv_batchable(const rich_server* s, const rich_request& a, const rich_request& b) {
   if (a.session || b.session || !a.p0_host || !b.p0_host) return false;
   if ((long long)a.grid.nx * a.grid.ny * a.grid.nz > s->o.batch_min_cells) return false;
+  auto rec = s->batch_record.find(srv_class(a));
+  if (rec != s->batch_record.end() && rec->second.first >= kBatchRecordMin &&
+      rec->second.second > kBatchFailMax * rec->second.first)
+    return false;
   if (!srv_same_shape(a, b) || a.dt != b.dt) return false;
   if ((a.ks_field_host == nullptr) != (b.ks_field_host == nullptr)) return false;
   if (a.opts.krylov.kind != RICH_KRYLOV_FCG || a.opts.max_dt_halvings != 0) return false;
@@ -187,7 +204,7 @@ static void srv_pick_mates(rich_server* s, SrvRequest* q, std::vector<SrvRequest
 static void srv_run(SrvRequest* q, SrvSession* se, cudaStream_t st);
 
 // Steps q and its mates as one batch; a member whose step fails is rerun alone.
-static void srv_run_batch(std::vector<SrvRequest*>& qs, cudaStream_t st) {
+static void srv_run_batch(rich_server* s, std::vector<SrvRequest*>& qs, cudaStream_t st) {
   const rich_request& r0 = qs[0]->r;
   const int B = (int)qs.size();
   const long long n = (long long)r0.grid.nx * r0.grid.ny * r0.grid.nz;
@@ -229,8 +246,16 @@ static void srv_run_batch(std::vector<SrvRequest*>& qs, cudaStream_t st) {
     if (cudaStreamSynchronize(st) != cudaSuccess && !status) status = RICH_ECUDA;
     dfree(p);
     if (c) rich_destroy(c);
+    int failed = 0;
     for (int b = 0; b < B; ++b)
-      if (status || stb[b] != RICH_OK) qs[b]->res.batch_rerun = 1;
+      if (status || stb[b] != RICH_OK) {
+        qs[b]->res.batch_rerun = 1;
+        ++failed;
+      }
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto& rec = s->batch_record[srv_class(r0)];
+    rec.first += B;
+    rec.second += failed;
   }
   for (int b = 0; b < B; ++b)
     if (qs[b]->res.batch_rerun) srv_run(qs[b], nullptr, st);  // the lone path decides its result
@@ -331,7 +356,7 @@ static void srv_worker(rich_server* s, int slot) {
       if (s->stop && s->queue.empty()) break;
       continue;
     }
-    if (group.size() > 1) srv_run_batch(group, st);
+    if (group.size() > 1) srv_run_batch(s, group, st);
     else srv_run(q, se, st);
     SrvSession* dead = nullptr;
     {
