@@ -200,7 +200,7 @@ typedef struct {
 
 typedef struct {
   int kind;                /* RICH_KRYLOV_* */
-  int restart;             /* m of FGMRES(m), <= 64 */
+  int restart;             /* m of FGMRES(m), <= 63 */
   double eta;              /* stop when ||b - J x||_2 <= eta ||b||_2 */
   int maxit;               /* iteration limit */
 } rich_krylov_opts;

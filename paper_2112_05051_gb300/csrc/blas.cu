@@ -3,6 +3,8 @@
 // partials in block order, so FP64 results reproduce bit for bit run to run.
 #include <mutex>
 
+#include <cstring>
+
 #include "common.cuh"
 
 #include <atomic>
@@ -90,6 +92,14 @@ __global__ void k_prof_delay(long long cycles) {
   }
 }
 constexpr long long kProfDelayCycles = 40000;  // ~20 us at 2 GHz
+
+void prof_adjust_last(const char* name, double bytes, double flops) {
+  if (g_prof_n < 1 || g_prof_open >= 0 || strcmp(g_prof_name[g_prof_n - 1], name) != 0) return;
+  g_prof_bytes += bytes - g_prof_b[g_prof_n - 1];
+  g_prof_flops += flops - g_prof_f[g_prof_n - 1];
+  g_prof_b[g_prof_n - 1] = bytes;
+  g_prof_f[g_prof_n - 1] = flops;
+}
 
 void prof_restart(cudaStream_t st) {
   if (g_prof_open < 0) return;

@@ -49,6 +49,9 @@ void count_launches(long long k);  // k may be negative (launches recorded into 
 // Moves the start of the open timed launch to now (work done on the stream since
 // it opened, e.g. a one-time layout, is not charged to the launch).
 void prof_restart(cudaStream_t st);
+// Corrects the algorithmic bytes and flops of the last timed launch if it was `name`
+// (for launches whose work a device-side decision settled after they were queued).
+void prof_adjust_last(const char* name, double bytes, double flops);
 struct ProfScope {
   bool on;
   cudaStream_t st;
@@ -254,7 +257,7 @@ struct rich_ctx {
   rich::KrylovWork kw;
   // reductions: partial sums per block and device scalars
   double* partials = nullptr;  // kRedBlocks * 64
-  double* dsc = nullptr;       // device scalars (128)
+  double* dsc = nullptr;       // device scalars (256)
   double* hsc = nullptr;       // pinned host mirror (128)
   int* iflag = nullptr;        // device int flags (16)
   int* hflag = nullptr;        // pinned host (16)

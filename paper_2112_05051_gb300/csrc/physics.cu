@@ -428,7 +428,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   };
   if ((s = dalloc(&c->K, n)) || (s = dalloc(&c->dK, n)) || (s = dalloc(&c->S, n)) || (s = dalloc(&c->dS, n)) ||
       (s = dalloc(&c->J7, 7 * n)) || (s = dalloc(&c->A7, 7 * n)) || (s = dalloc(&c->partials, (long long)kRedBlocks * 64)) ||
-      (s = dalloc(&c->dsc, 128)) || (s = dalloc(&c->iflag, 16)))
+      (s = dalloc(&c->dsc, 256)) || (s = dalloc(&c->iflag, 16)))
     return fail(s);
   {
     // 128 doubles then 16 ints of pinned host memory from the process-wide pool

@@ -850,9 +850,18 @@ __global__ void k_orth_axpy(long long n, int nv, const double* __restrict__ V, c
   }
 }
 
+// Device scalars of an FGMRES iteration (restart <= 63, so j <= 62): h1 in [0, j],
+// h2 in [64, 64 + j]; ||w'||^2 and the DGKS decision in the slots neither reaches
+// (both come back with the one 128-double read-back); ||w||^2, read on the device
+// only, past the read-back.
+constexpr int kSlotW1 = 63, kSlotRun = 127, kSlotW = 130;
+
 // DGKS decision on the device: run the second pass when ||w'||^2 < ||w||^2 / 2
-__global__ void k_dgks(const double* __restrict__ s, int i_w, int i_wp, int* __restrict__ run) {
-  *run = s[i_wp] < 0.5 * s[i_w] ? 1 : 0;
+// (also left in s[i_out] as 1.0 / 0.0 for the host's read-back of the scalars)
+__global__ void k_dgks(double* __restrict__ s, int i_w, int i_wp, int i_out, int* __restrict__ run) {
+  const int r = s[i_wp] < 0.5 * s[i_w] ? 1 : 0;
+  *run = r;
+  s[i_out] = r;
 }
 
 // out = f * (w - sum_q h2[q] V[q]); without a second pass (run == 0) out = f * w
@@ -1042,7 +1051,7 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       //   V[j+1] = (w' - V h2) / hn, hn^2 = ||w'||^2 - ||h2||^2 (V orthonormal).
       // The decision stays on the device; one read-back per iteration.
       int* run = c->iflag + 2;
-      RICH_CHECK(nrm2sq(c, k.w, n, s + 120));
+      RICH_CHECK(nrm2sq(c, k.w, n, s + kSlotW));
       {
         ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2), 2.0 * n * (j + 1));
         launch_multidot(nb, c->st, n, j + 1, k.V, k.w, c->partials);
@@ -1050,12 +1059,13 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       RICH_LAUNCH_CHECK();
       RICH_CHECK(finish_sums(c, c->partials, kBdotBlocks, j + 1, s));
       {
-        ProfScope ps("orth_axpy", c->st, (double)n * 8.0 * (j + 3));  // w -= V h1 (w read and written)
+        // w -= V h1 (w read and written; j + 1 FMAs per cell)
+        ProfScope ps("orth_axpy", c->st, (double)n * 8.0 * (j + 3), 2.0 * n * (j + 1));
         k_orth_axpy<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s, k.w);
       }
       RICH_LAUNCH_CHECK();
-      RICH_CHECK(nrm2sq(c, k.w, n, s + 121));
-      k_dgks<<<1, 1, 0, c->st>>>(s, 120, 121, run);
+      RICH_CHECK(nrm2sq(c, k.w, n, s + kSlotW1));
+      k_dgks<<<1, 1, 0, c->st>>>(s, kSlotW, kSlotW1, kSlotRun, run);
       RICH_LAUNCH_CHECK();
       {
         ProfScope ps("multidot", c->st, (double)n * 8.0 * (j + 2), 2.0 * n * (j + 1));
@@ -1065,17 +1075,21 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
       RICH_CHECK(finish_sums(c, c->partials, kBdotBlocks, j + 1, s + 64));
       RICH_CUDA(cudaMemcpyAsync(c->hsc, s, 128 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       RICH_CUDA(cudaStreamSynchronize(c->st));
+      const bool second = c->hsc[kSlotRun] != 0.0;
+      if (!second) prof_adjust_last("multidot", 0.0, 0.0);  // the skipped pass only zeroed its partials
       double h2sq = 0.0;
       for (int i = 0; i <= j; ++i) {
         Hij(i, j) = c->hsc[i] + c->hsc[64 + i];
         h2sq += c->hsc[64 + i] * c->hsc[64 + i];
       }
-      double wsq = c->hsc[121] - h2sq;
+      double wsq = c->hsc[kSlotW1] - h2sq;
       double hn = wsq > 0 ? sqrt(wsq) : 0.0;
       if (!std::isfinite(hn)) return RICH_ENONFINITE;
       Hij(j + 1, j) = hn;
       {
-        ProfScope ps("orth_final", c->st, (double)n * 8.0 * (j + 3));
+        // with the second pass: w' - V h2, scaled (j + 3 vectors); without: w' scaled (2 vectors)
+        ProfScope ps("orth_final", c->st, second ? (double)n * 8.0 * (j + 3) : 16.0 * n,
+                     second ? 2.0 * n * (j + 1) + n : (double)n);
         k_orth_final<<<g, kBlock, 0, c->st>>>(n, j + 1, k.V, s + 64, k.w, hn > 0 ? 1.0 / hn : 0.0,
                                              k.V + (long long)(j + 1) * n, run);
       }

@@ -264,6 +264,31 @@ def test_krylov_solution_parity(kind):
     ctx.close()
 
 
+def test_fgmres_long_restart_cycle_matches_oracle():
+    """FGMRES(63), the largest restart, with a weak preconditioner (one 9600-unknown
+    level: eight l1-Jacobi sweeps), so that a cycle runs past j = 57 where the
+    Hessenberg columns h1 and h2 fill the device scalar slots up to 62 and 126."""
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((24, 20, 20), 9, 0)
+    ctx = rb.Context(grid, SOIL, bc, kmean, ks)
+    ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+    ctx.amg_setup(rb.default_amg_opts(seed=2, max_levels=1))
+    h = amg.setup(disc.aux_matrix(grid, SOIL, bc, kmean, p, dt, ks), 0.08, 2, 2000, max_levels=1)
+    b = np.random.default_rng(5).standard_normal(grid.n)
+    x = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+    s, st = ctx.krylov_solve(torch.tensor(b, device="cuda"), x, kind=rb.KRYLOV_FGMRES, restart=63, eta=1e-12,
+                             maxit=300)
+    J = disc.jacobian(grid, SOIL, bc, kmean, p, dt, ks)
+    from oracle import krylov
+    xr, its, ok, _ = krylov.fgmres(lambda v: J @ v, lambda v: amg.vcycle(h, v), b, 1e-12, 300, 63)
+    assert ok and st.converged and its >= 60  # the first cycle reaches j >= 59
+    assert abs(st.iterations - its) <= 1
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(J @ xg - b) <= 1e-12 * np.linalg.norm(b) * 1.0001
+    assert _nrel(xg, xr) <= 1e-8
+    ctx.close()
+
+
 def _run_steps(workload, n, steps, prec=0, policy=0, opts_kw=None):
     rb = _rb()
     w = synth.WORKLOADS[workload]
