@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel roofline pass")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-grid mixed-precision run")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotuner table: loaded at start if the file exists, written at the end (a profiled run "
+                         "then runs the variants a plain run chose)")
     ap.add_argument("--paper-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -591,6 +594,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     lib = rb.load()
+    if args.tune_file and os.path.exists(args.tune_file):
+        rb.autotune_load(open(args.tune_file).read())
     w, grid, soil, bc, ks, p0, dts = workload_setup(args.workload, args.grid)
     if args.amg_precision is not None:
         import dataclasses
@@ -801,6 +806,9 @@ def run_ours(args):
             line["serving_uniform"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line))
+        if args.tune_file:
+            with open(args.tune_file, "w") as f:
+                f.write(rb.autotune_text())
     if dist:
         dist.destroy_process_group()
     return 0

@@ -397,12 +397,18 @@ int rich_step_batch(rich_ctx* ctx, double* p_dev, double dt, const rich_newton_o
 int rich_measure_fma_peak(int fp64, double* tflops);
 
 /* The autotuner's choices so far, one line "mode value_bytes rows_bin mean_row_length
- * sell_offered variant best_us" each (mode 0 y = A x, 1 y += A x, 2 l1-Jacobi sweep,
- * 3 residual; rows_bin = floor(4 log2 rows); sell_offered 1 where a SELL copy was a
- * candidate; variant = lanes per row, + 256 for four-way unrolled rows, 512 / 513 for
- * the SELL copy with 4 / 8 gathers in flight per row), written into buf (at most cap
- * bytes, NUL-terminated). */
+ * sell_offered variant best_us best_csr_variant" each (mode 0 y = A x, 1 y += A x,
+ * 2 l1-Jacobi sweep, 3 residual; rows_bin = floor(4 log2 rows); sell_offered 1 where a
+ * SELL copy was a candidate; variant = lanes per row, + 256 for four-way unrolled rows,
+ * 512 / 513 for the SELL copy with 4 / 8 gathers in flight per row; best_csr_variant
+ * the fastest CSR candidate), written into buf (at most cap bytes, NUL-terminated). */
 int rich_autotune_table(char* buf, int cap);
+/* Adds the entries of a saved table (rich_autotune_table's text) to the process's
+ * autotuner, so that a later process runs the same variants without timing them
+ * (e.g. under a profiler, whose serialised launches would skew the timings).
+ * Classes already tuned keep their choice.  RICH_EINVAL (nothing added) on a
+ * malformed line or an unknown variant. */
+int rich_autotune_load(const char* text);
 
 /* Number of kernels this library has launched since it was loaded. */
 int rich_kernel_launches(long long* out);

@@ -361,6 +361,11 @@ int rich_autotune_table(char* buf, int cap) {
   return rich::autotune_table(buf, cap);
 }
 
+int rich_autotune_load(const char* text) {
+  if (!text) return RICH_EINVAL;
+  return rich::autotune_load(text);
+}
+
 int rich_measure_fma_peak(int fp64, double* tflops) {
   if (!tflops) return RICH_EINVAL;
   return fp64 ? rich::fma_peak<double>(nullptr, tflops) : rich::fma_peak<float>(nullptr, tflops);

@@ -480,6 +480,7 @@ void sell_free(Sell& S);
 
 // solve.cu
 int autotune_table(char* buf, int cap);
+int autotune_load(const char* text);
 int vcycle_apply(rich_ctx* c, const double* r, double* z);
 int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st);
 

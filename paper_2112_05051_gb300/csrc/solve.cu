@@ -11,8 +11,10 @@
 // Krylov scalars live in device memory; each iteration reads one small block
 // of them back for the convergence test.
 #include <algorithm>
+#include <cstdio>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -323,11 +325,42 @@ int autotune_table(char* buf, int cap) {
   int off = 0;
   buf[0] = 0;
   for (auto& e : g_tune) {
-    int w = snprintf(buf + off, cap - off, "%d %d %d %lld %d %d %.3f\n", e.first.mode, e.first.tsize, e.first.n,
-                     e.first.nnz, e.first.sell, e.second.variant, e.second.us);
+    int w = snprintf(buf + off, cap - off, "%d %d %d %lld %d %d %.3f %d\n", e.first.mode, e.first.tsize,
+                     e.first.n, e.first.nnz, e.first.sell, e.second.variant, e.second.us, e.second.best_csr);
     if (w < 0 || w >= cap - off) break;
     off += w;
   }
+  return RICH_OK;
+}
+
+// Entries in autotune_table's format (a saved table): classes already present keep
+// their choice.  A variant that is not one of the candidates is rejected.
+int autotune_load(const char* text) {
+  auto valid = [](int v) {
+    if (v == kSellVariant || v == kSellVariant8) return true;
+    const int g = v & 0xff, u = v & ~0xff;
+    if (u != 0 && u != kUnroll) return false;
+    if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return false;
+    return u == 0 || g <= 8;
+  };
+  std::vector<std::pair<TuneKey, TuneVal>> rows;
+  const char* p = text;
+  while (*p) {
+    int mode, tsize, n, sell, variant, best_csr, used = 0;
+    long long nnz;
+    float us;
+    if (sscanf(p, "%d %d %d %lld %d %d %f %d%n", &mode, &tsize, &n, &nnz, &sell, &variant, &us, &best_csr, &used) !=
+        8)
+      return RICH_EINVAL;
+    if (mode < 0 || mode > 3 || (tsize != 4 && tsize != 8) || (sell != 0 && sell != 1) || !valid(variant) ||
+        !valid(best_csr) || best_csr >= kSellVariant || (!sell && variant >= kSellVariant))
+      return RICH_EINVAL;
+    rows.push_back({TuneKey{mode, tsize, n, nnz, sell}, TuneVal{variant, us, best_csr}});
+    p += used;
+    while (*p == '\n' || *p == ' ' || *p == '\r') ++p;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& r : rows) g_tune.insert(r);
   return RICH_OK;
 }
 

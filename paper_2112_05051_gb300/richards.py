@@ -145,6 +145,7 @@ EXPORTS = {
     "rich_kernel_launches": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
     "rich_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rich_autotune_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
+    "rich_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -542,10 +543,20 @@ def autotune_table():
     """The row-operation autotuner's choices:
     [(mode, value_bytes, rows_bin, mean_row_length, sell_offered, variant, best_us)],
     variant = lanes per row (+ UNROLL for four-way unrolled rows) or SELL_VARIANT."""
-    buf = ctypes.create_string_buffer(1 << 16)
-    check(load().rich_autotune_table(buf, len(buf)), "rich_autotune_table")
     out = []
-    for line in buf.value.decode().splitlines():
-        m, t, n, z, so, g, us = line.split()
+    for line in autotune_text().splitlines():
+        m, t, n, z, so, g, us, _ = line.split()
         out.append((int(m), int(t), int(n), int(z), int(so), int(g), float(us)))
     return out
+
+
+def autotune_text():
+    """The autotuner's table as text (rich_autotune_table), for saving."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(load().rich_autotune_table(buf, len(buf)), "rich_autotune_table")
+    return buf.value.decode()
+
+
+def autotune_load(text):
+    """Adds a saved table (autotune_text) to the process's autotuner."""
+    check(load().rich_autotune_load(text.encode()), "rich_autotune_load")

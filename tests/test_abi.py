@@ -63,3 +63,32 @@ def test_server_options_and_argument_checks_without_a_gpu(lib):
     assert lib.rich_server_submit(None, None, None) == -1
     assert lib.rich_server_poll(None, 1, None) == -1
     assert lib.rich_server_destroy(None) == 0
+
+
+def test_autotune_table_round_trip_without_a_gpu(lib):
+    """A saved tuner table loads back (host-only: no device work) and reads out the
+    same; a malformed line or an unknown variant is rejected whole."""
+    from paper_2112_05051_gb300 import richards as rb
+    rb.load()
+    before = rb.autotune_text()
+    rows = ("2 8 70 32 1 513 21.376 4\n"     # l1-Jacobi sweep, FP64, SELL x8 chosen, 4 lanes the best CSR
+            "0 4 90 19 1 512 213.195 8\n"    # restriction, FP32, SELL x4
+            "1 8 84 3 1 1 35.509 1\n"        # prolongation, 1 lane
+            "3 4 52 101 0 260 6.315 260\n")  # residual, 4 lanes x4, no SELL offered
+    rb.autotune_load(rows)
+    table = rb.autotune_text()
+    for line in rows.splitlines():
+        assert line in table.splitlines()
+    again = rb.autotune_text()
+    rb.autotune_load("2 8 70 32 1 2 1.0 2\n")  # an existing class keeps its choice
+    assert rb.autotune_text() == again
+    for bad in ("2 8 70 32 1 513 21.3\n",          # a field missing
+                "2 8 71 32 1 3 1.0 2\n",           # 3 lanes is not a candidate
+                "2 8 71 32 0 512 1.0 2\n",         # SELL without a SELL candidate
+                "2 8 71 32 1 512 1.0 512\n",       # best CSR variant that is SELL
+                "5 8 71 32 1 1 1.0 1\n",           # no such mode
+                "2 2 71 32 1 1 1.0 1\n"):          # no such value size
+        with pytest.raises(rb.RichError):
+            rb.autotune_load(bad)
+    assert rb.autotune_text() == again
+    assert set(before.splitlines()) <= set(again.splitlines())
