@@ -99,6 +99,9 @@ def parse():
     ap.add_argument("--serving-aggregation", type=int, default=0, help="0: MIS-2, 1: matching (SMATCH-style)")
     ap.add_argument("--serving-batch", type=int, default=8,
                     help="largest packed batch of same-shape requests (1: one request per slot)")
+    ap.add_argument("--serving-stall", type=float, default=0.1,
+                    help="serving requests' FGMRES gives up after a restart cycle that reduced the residual by less "
+                         "than this fraction (0: off)")
     ap.add_argument("--serving-halvings", type=int, default=0,
                     help="time-step control of served requests (0: off; retries multiply the device time of the "
                          "failing requests, measured 3-10x on this stream)")
@@ -388,7 +391,7 @@ def serving_run(args, rb):
     opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, nu1=1, nu2=1, seed=3, smooth_levels=2,
                                   product_lists=args.serving_lists, coarse_max=args.serving_coarse_max,
                                   aggregation=args.serving_aggregation, max_dt_halvings=halvings,
-                                  max_newton=20 if halvings else 50)
+                                  max_newton=20 if halvings else 50, stall=getattr(args, "serving_stall", 0.0))
 
     def submit(srv, q):
         grid, ks, kmean, n = q
@@ -442,6 +445,7 @@ def serving_run(args, rb):
             "aggregation": "matching" if args.serving_aggregation else "MIS-2",
             "kmeans": ["arithmetic", "upstream", "harmonic"], "precision": "fp32 AMG, fp64 residual and FCG",
             "max_dt_halvings": halvings, "max_newton_per_attempt": 20 if halvings else 50,
+            "fgmres_stall": getattr(args, "serving_stall", 0.0),
             "latency_ms_converged": st_s["latency_ms_converged"], "failure_rate": st_s["failure_rate"],
             "device_ms_burst": st_b["device_ms"],
             "converged_per_s": st_s["converged_per_s"], "stream_dof_newton_per_s": st_s["dof_newton_per_s"],

@@ -17,7 +17,10 @@ flexible variants, which keep the preconditioned directions:
 Both start from x0 = 0 and stop when ||b - J x||_2 <= eta ||b||_2.  FCG
 reports failure (converged=False) when it reaches maxit, when (p, q) <= 0, or
 when its residual norm grows above 10x the smallest seen; the Newton driver
-then retries the solve with FGMRES(30).
+then retries the solve with FGMRES(30).  FGMRES with stall > 0 (an option of
+this implementation, not the paper's; off by default) also gives up after a
+restart cycle that reduced the true residual norm by less than the fraction
+stall of its value at the cycle's start.
 """
 import numpy as np
 
@@ -65,7 +68,7 @@ def fcg(matvec, prec, b, eta, maxit, info=None):
     return x, maxit, False, hist
 
 
-def fgmres(matvec, prec, b, eta, maxit, m):
+def fgmres(matvec, prec, b, eta, maxit, m, stall=0.0):
     b = np.asarray(b, dtype=np.float64)
     n = b.shape[0]
     bnorm = np.linalg.norm(b)
@@ -129,6 +132,9 @@ def fgmres(matvec, prec, b, eta, maxit, m):
         if converged or its >= maxit:
             return x, its, converged, hist
         r = b - matvec(x)
-        beta = np.linalg.norm(r)
+        beta_cycle, beta = beta, np.linalg.norm(r)
         if beta <= target:
             return x, its, True, hist
+        if stall > 0.0 and beta > (1.0 - stall) * beta_cycle:
+            # the restart cycle reduced the true residual by less than the fraction stall
+            return x, its, False, hist

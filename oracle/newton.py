@@ -54,6 +54,7 @@ class NewtonOptions:
     restart: int = 30
     eta: float = 1e-7
     maxit: int = 200
+    stall: float = 0.0            # FGMRES: give up after a restart cycle reducing the residual by less
     nu1: int = 1
     nu2: int = 1
     rtol: float = 1e-8
@@ -170,7 +171,7 @@ def linear_solve(J, h, rhs, opt, stats):
             stats.indefinite = True
             return d, its, False
         stats.fallbacks += 1
-    d, its, ok, _ = krylov.fgmres(mv, prec, rhs, opt.eta, opt.maxit, opt.restart)
+    d, its, ok, _ = krylov.fgmres(mv, prec, rhs, opt.eta, opt.maxit, opt.restart, opt.stall)
     stats.linear_its += its
     return d, its, ok
 

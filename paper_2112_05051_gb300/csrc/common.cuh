@@ -227,7 +227,8 @@ struct KrylovWork {
   double* z = nullptr;
   double* w = nullptr;
   double* hcoef = nullptr;  // device coefficients (m+1)
-  int fail_reason = 0;      // last FCG failure: 0 none, 1 maxit, 2 (p, J p) <= 0, 3 residual growth
+  int fail_reason = 0;      // last failure: 0 none, FCG 1 maxit, 2 (p, J p) <= 0, 3 residual growth;
+                            // FGMRES 4 a stagnated restart cycle
 };
 
 }  // namespace rich

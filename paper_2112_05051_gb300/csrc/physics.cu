@@ -370,6 +370,7 @@ void rich_default_newton_opts(rich_newton_opts* o) {
   o->krylov.restart = 30;
   o->krylov.eta = 1e-7;
   o->krylov.maxit = 200;
+  o->krylov.stall = 0.0;
   rich_default_amg_opts(&o->amg);
   o->amg_policy = RICH_AMG_REFRESH;
   o->rtol = 1e-8;

@@ -1169,18 +1169,23 @@ static int fgmres(rich_ctx* c, const double* b, double* x, const rich_krylov_opt
     RICH_LAUNCH_CHECK();
     RICH_CHECK(nrm2sq(c, k.r, n, s));
     RICH_CHECK(fetch_scalars(c, s, 1, h0));
+    const double beta_cycle = beta;
     beta = sqrt(h0[0]);
     st->res = beta;
     if (beta <= target) {
       st->converged = 1;
       return RICH_OK;
     }
+    if (o->stall > 0 && beta > (1.0 - o->stall) * beta_cycle) {  // the cycle stagnated
+      c->kw.fail_reason = 4;
+      return RICH_ENOTCONV_LIN;
+    }
     r0 = k.r;
   }
 }
 
 int krylov_run(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
-  if (o->maxit < 1 || !(o->eta > 0)) return RICH_EINVAL;
+  if (o->maxit < 1 || !(o->eta > 0) || !(o->stall >= 0.0 && o->stall < 1.0)) return RICH_EINVAL;
   c->kw.fail_reason = 0;
   if (o->kind == RICH_KRYLOV_FGMRES) {
     if (o->restart < 1 || o->restart > 63) return RICH_EINVAL;

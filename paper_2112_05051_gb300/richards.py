@@ -77,7 +77,7 @@ class AmgOpts(ctypes.Structure):
 
 class KrylovOpts(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("restart", ctypes.c_int), ("eta", ctypes.c_double),
-                ("maxit", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("stall", ctypes.c_double)]
 
 
 class KrylovStats(ctypes.Structure):
@@ -225,7 +225,7 @@ def default_newton_opts(**kw):
     o = NewtonOpts()
     load().rich_default_newton_opts(ctypes.byref(o))
     for k, v in kw.items():
-        if k in ("kind", "restart", "eta", "maxit"):
+        if k in ("kind", "restart", "eta", "maxit", "stall"):
             setattr(o.krylov, k, v)
         elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
                    "aggregation", "max_agg_size", "isolated_join", "smoother", "hgs_seg", "hgs_block",
@@ -356,8 +356,8 @@ class Context:
               "amg_export_prolongator")
         return rp, col, val
 
-    def krylov_solve(self, b, x, kind=KRYLOV_FCG, restart=30, eta=1e-7, maxit=200, check_status=True):
-        o = KrylovOpts(kind, restart, eta, maxit)
+    def krylov_solve(self, b, x, kind=KRYLOV_FCG, restart=30, eta=1e-7, maxit=200, check_status=True, stall=0.0):
+        o = KrylovOpts(kind, restart, eta, maxit, stall)
         st = KrylovStats()
         s = load().krylov_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
         if check_status:

@@ -264,6 +264,32 @@ def test_krylov_solution_parity(kind):
     ctx.close()
 
 
+def test_fgmres_stall_option_matches_oracle():
+    """krylov.stall: a fraction the first restart cycle cannot meet ends the solve
+    after that cycle (RICH_ENOTCONV_LIN) with the oracle's iterate; a small one
+    changes nothing."""
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((16, 14, 12), 11, 1)
+    ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, 100)
+    b = np.random.default_rng(3).standard_normal(grid.n)
+    J = disc.jacobian(grid, SOIL, bc, kmean, p, dt, ks)
+    from oracle import krylov
+    prec = lambda v: amg.vcycle(h, v)
+    lin = {name: code for code, name in rb.ERRORS.items()}["RICH_ENOTCONV_LIN"]
+    for stall, ok_expected in ((0.999999, False), (0.01, True)):
+        x = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+        s, st = ctx.krylov_solve(torch.tensor(b, device="cuda"), x, kind=rb.KRYLOV_FGMRES, restart=4, eta=1e-11,
+                                 maxit=400, check_status=False, stall=stall)
+        xr, its, ok, _ = krylov.fgmres(lambda v: J @ v, prec, b, 1e-11, 400, 4, stall=stall)
+        assert ok == ok_expected and (s == 0) == ok and bool(st.converged) == ok
+        if not ok:
+            assert s == lin and st.iterations == its == 4
+        else:
+            assert abs(st.iterations - its) <= 1
+        assert _nrel(x.cpu().numpy(), xr) <= 1e-8
+    ctx.close()
+
+
 def test_fgmres_long_restart_cycle_matches_oracle():
     """FGMRES(63), the largest restart, with a weak preconditioner (one 9600-unknown
     level: eight l1-Jacobi sweeps), so that a cycle runs past j = 57 where the

@@ -224,6 +224,33 @@ def test_fgmres_full_space_is_exact_solve_and_monotone():
     assert ok and np.linalg.norm(M @ x - b) <= 1e-10 * np.linalg.norm(b) * 1.01
 
 
+def test_fgmres_stall_stops_a_stagnating_restart_cycle():
+    # The cyclic shift S e_i = e_{i+1 mod n} with b = e_1: the Krylov space K_m(S, b)
+    # is spanned by e_2..e_{m+1} after the first vector, all orthogonal to b, so
+    # restarted GMRES(m) with m < n makes no progress at all (complete stagnation):
+    # the residual stays ||b|| and x stays 0.
+    n, m = 8, 3
+    S = np.roll(np.eye(n), 1, axis=0)
+    b = np.zeros(n)
+    b[0] = 1.0
+    x, its, ok, hist = krylov.fgmres(lambda v: S @ v, lambda v: v, b, 1e-10, 30, m)
+    assert not ok and its == 30 and np.abs(x).max() < 1e-14
+    np.testing.assert_allclose(hist, 1.0, atol=1e-14)
+    x, its, ok, _ = krylov.fgmres(lambda v: S @ v, lambda v: v, b, 1e-10, 30, m, stall=0.01)
+    assert not ok and its == m and np.abs(x).max() < 1e-14  # one cycle, then it gives up
+    # a cycle that does reduce the residual by more than the fraction keeps going
+    rng = np.random.default_rng(9)
+    M = np.eye(30) * 4 + rng.standard_normal((30, 30)) * 0.5
+    c = rng.standard_normal(30)
+    ref = krylov.fgmres(lambda v: M @ v, lambda v: v, c, 1e-10, 300, 5)
+    got = krylov.fgmres(lambda v: M @ v, lambda v: v, c, 1e-10, 300, 5, stall=0.05)
+    assert ref[2] and got[2] and ref[1] == got[1]
+    np.testing.assert_array_equal(ref[0], got[0])
+    # a stall fraction the cycles cannot meet: stops after the first restart
+    got = krylov.fgmres(lambda v: M @ v, lambda v: v, c, 1e-10, 300, 5, stall=0.999999)
+    assert not got[2] and got[1] == 5
+
+
 def test_fcg_unpreconditioned_iterates_minimise_energy_error_on_krylov_space():
     # With B = I on an SPD matrix, FCG is CG: x_k minimises the A-norm error over K_k(A, b).
     rng = np.random.default_rng(4)
