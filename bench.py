@@ -743,14 +743,15 @@ def run_ours(args):
         total = sum(v[1] for v in tab.values())
         rows = sorted(tab.items(), key=lambda kv: -kv[1][1])
         kernel_roofs = []
-        for name, (cnt, kms, kb, kf) in rows[:5]:
+        for name, (cnt, kms, kb, kf) in rows[:12]:
             r = roofline_of(name, kms, cnt, kb, kf, _is_fp64_kernel(name, prec == rb.PREC_FP64), peak_gbs,
                             fp64_tflops, NCU_TRAFFIC_BYTES.get((w.name, name)))
             r["share_of_profiled_steps"] = kms / total if total else None
             r["profiled_steps"] = psteps
             kernel_roofs.append(r)
         roof = kernel_roofs[0] if kernel_roofs else None
-        kernel_roofs = [{k: r[k] for k in ("kernel", "share_of_profiled_steps", "bound", "achieved", "peak", "unit",
+        kernel_roofs = [{k: r[k] for k in ("kernel", "launches", "share_of_profiled_steps", "bound", "achieved",
+                                           "peak", "unit",
                                            "frac", "intensity_flop_per_byte", "hbm_frac", "avg_launch_us")}
                         for r in kernel_roofs]
         if mixed is not None:  # the same pass on the FP32-AMG arm: its V-cycle kernels are FP32
