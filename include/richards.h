@@ -203,9 +203,9 @@ typedef struct {
   int restart;             /* m of FGMRES(m), <= 63 */
   double eta;              /* stop when ||b - J x||_2 <= eta ||b||_2 */
   int maxit;               /* iteration limit */
-  double stall;            /* FGMRES: give up (RICH_ENOTCONV_LIN) after a restart cycle that reduced
-                              ||b - J x||_2 by less than this fraction of its value at the cycle's start;
-                              0 (default): off.  In [0, 1) */
+  double stall;            /* give up (RICH_ENOTCONV_LIN) after an FGMRES restart cycle, or a window of 30
+                              FCG iterations, that reduced ||b - J x||_2 by less than this fraction of
+                              its value at the cycle's (window's) start; 0 (default): off.  In [0, 1) */
 } rich_krylov_opts;
 
 typedef struct {

@@ -17,17 +17,23 @@ flexible variants, which keep the preconditioned directions:
 Both start from x0 = 0 and stop when ||b - J x||_2 <= eta ||b||_2.  FCG
 reports failure (converged=False) when it reaches maxit, when (p, q) <= 0, or
 when its residual norm grows above 10x the smallest seen; the Newton driver
-then retries the solve with FGMRES(30).  FGMRES with stall > 0 (an option of
-this implementation, not the paper's; off by default) also gives up after a
+then retries the solve with FGMRES(30).  With stall > 0 (an option of this
+implementation, not the paper's; off by default) FGMRES also gives up after a
 restart cycle that reduced the true residual norm by less than the fraction
-stall of its value at the cycle's start.
+stall of its value at the cycle's start, and FCG after a window of 30
+iterations that did the same.
 """
 import numpy as np
 
 
-def fcg(matvec, prec, b, eta, maxit, info=None):
+STALL_WINDOW = 30  # FCG iterations per stagnation test
+
+
+def fcg(matvec, prec, b, eta, maxit, info=None, stall=0.0):
     """Returns (x, iterations, converged, residual history); info, if a dict, receives
-    the reason of a failure: "maxit", "curvature" ((p, q) <= 0) or "growth"."""
+    the reason of a failure: "maxit", "curvature" ((p, q) <= 0), "growth", or "stall"
+    (stall > 0: after every STALL_WINDOW iterations, the residual norm is above
+    (1 - stall) times its value STALL_WINDOW iterations earlier)."""
     if info is None:
         info = {}
     b = np.asarray(b, dtype=np.float64)
@@ -61,6 +67,9 @@ def fcg(matvec, prec, b, eta, maxit, info=None):
             return x, k, True, hist
         if rn > 10.0 * best:
             info["reason"] = "growth"
+            return x, k, False, hist
+        if stall > 0.0 and k % STALL_WINDOW == 0 and rn > (1.0 - stall) * hist[k - STALL_WINDOW]:
+            info["reason"] = "stall"
             return x, k, False, hist
         best = min(best, rn)
         p_prev, q_prev, pq_prev = p, q, pq

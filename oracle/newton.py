@@ -54,7 +54,7 @@ class NewtonOptions:
     restart: int = 30
     eta: float = 1e-7
     maxit: int = 200
-    stall: float = 0.0            # FGMRES: give up after a restart cycle reducing the residual by less
+    stall: float = 0.0            # give up after an FGMRES cycle / 30 FCG iterations reducing the residual by less
     nu1: int = 1
     nu2: int = 1
     rtol: float = 1e-8
@@ -161,7 +161,7 @@ def linear_solve(J, h, rhs, opt, stats):
     mv = lambda v: J @ v
     if opt.krylov == "fcg":
         info = {}
-        d, its, ok, _ = krylov.fcg(mv, prec, rhs, opt.eta, opt.maxit, info=info)
+        d, its, ok, _ = krylov.fcg(mv, prec, rhs, opt.eta, opt.maxit, info=info, stall=opt.stall)
         stats.linear_its += its
         if ok:
             return d, its, True

@@ -157,7 +157,8 @@ static int upload_flags(rich_ctx* c, BatchWork& w, const std::vector<int>& a) {
 
 // Segmented FCG (Notay, truncation 1) for J x = b with x0 = 0.  Problems with
 // active[s] == 0 on entry keep x_s = 0.  On return fail[s] = 1 where FCG stopped
-// on (p, q) <= 0, on residual growth or at maxit; its[s] counts the iterations.
+// on (p, q) <= 0, on residual growth, on stagnation (krylov.stall) or at maxit;
+// its[s] counts the iterations.
 static int batch_fcg(rich_ctx* c, BatchWork& w, int S, const double* b, double* x, const rich_krylov_opts* o,
                      std::vector<int> active, std::vector<int>& fail, std::vector<int>& its) {
   KrylovWork& k = c->kw;
@@ -172,13 +173,14 @@ static int batch_fcg(rich_ctx* c, BatchWork& w, int S, const double* b, double* 
   k_seg_dot2<<<grid, kBlock, 0, c->st>>>(ns, b, b, nullptr, nullptr, c->partials);
   RICH_LAUNCH_CHECK();
   RICH_CHECK(seg_finish(c, c->partials, nb, 1, S, sc, w.hsc));
-  std::vector<double> target(S), best(S);
+  std::vector<double> target(S), best(S), window_start(S);
   for (int s = 0; s < S; ++s) {
     double bn = sqrt(w.hsc[s]);
     if (!std::isfinite(bn)) return RICH_ENONFINITE;
     if (!(bn > 0)) active[s] = 0;
     target[s] = o->eta * bn;
     best[s] = bn;
+    window_start[s] = bn;
   }
   double* q = k.q;
   double* qprev = k.qprev;
@@ -218,6 +220,14 @@ static int batch_fcg(rich_ctx* c, BatchWork& w, int S, const double* b, double* 
       if (rn <= target[s]) {
         active[s] = 0;
         continue;
+      }
+      if (it % kStallWindow == 0) {  // stagnation over the last window (krylov.stall)
+        if (o->stall > 0 && rn > (1.0 - o->stall) * window_start[s]) {
+          fail[s] = 1;
+          active[s] = 0;
+          continue;
+        }
+        window_start[s] = rn;
       }
       best[s] = std::min(best[s], rn);
     }

@@ -211,6 +211,7 @@ struct Hierarchy {
   float* asZ32 = nullptr;
 };
 
+constexpr int kStallWindow = 30;        // FCG iterations per stagnation test (krylov.stall)
 constexpr int kMaxCoarseDense = 8192;  // largest coarsest level inverted densely
 constexpr int kCoarseSweeps = 8;       // l1-Jacobi sweeps on a stalled (larger) coarsest level
 
@@ -228,7 +229,7 @@ struct KrylovWork {
   double* w = nullptr;
   double* hcoef = nullptr;  // device coefficients (m+1)
   int fail_reason = 0;      // last failure: 0 none, FCG 1 maxit, 2 (p, J p) <= 0, 3 residual growth;
-                            // FGMRES 4 a stagnated restart cycle
+                            // 4 stagnation (an FCG window or an FGMRES restart cycle, krylov.stall)
 };
 
 }  // namespace rich

@@ -969,6 +969,8 @@ static int ensure_krylov(rich_ctx* c, int m) {
 
 // Flexible CG (Notay, truncation 1).  Returns RICH_ENOTCONV_LIN on maxit, on
 // (p, q) <= 0, or when ||r|| exceeds 10x the smallest seen.
+// Notay's flexible CG (truncation 1).  With o->stall > 0 it gives up when a window
+// of kStallWindow iterations reduced the residual by less than that fraction.
 static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
   KrylovWork& k = c->kw;
   long long n = c->g.n;
@@ -991,7 +993,7 @@ static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* 
   }
   if (!std::isfinite(bn)) return RICH_ENONFINITE;
   RICH_CUDA(cudaMemcpyAsync(k.r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
-  double target = o->eta * bn, best = bn;
+  double target = o->eta * bn, best = bn, window_start = bn;
   double* q = k.q;
   double* qprev = k.qprev;
   for (int it = 1; it <= o->maxit; ++it) {
@@ -1031,6 +1033,13 @@ static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* 
     if (rn > 10.0 * best) {
       k.fail_reason = 3;
       return RICH_ENOTCONV_LIN;
+    }
+    if (it % kStallWindow == 0) {  // stagnation over the last window
+      if (o->stall > 0 && rn > (1.0 - o->stall) * window_start) {
+        k.fail_reason = 4;
+        return RICH_ENOTCONV_LIN;
+      }
+      window_start = rn;
     }
     best = std::min(best, rn);
     std::swap(q, qprev);

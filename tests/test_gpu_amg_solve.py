@@ -264,10 +264,11 @@ def test_krylov_solution_parity(kind):
     ctx.close()
 
 
-def test_fgmres_stall_option_matches_oracle():
-    """krylov.stall: a fraction the first restart cycle cannot meet ends the solve
-    after that cycle (RICH_ENOTCONV_LIN) with the oracle's iterate; a small one
-    changes nothing."""
+@pytest.mark.parametrize("kind", ["fgmres", "fcg"])
+def test_krylov_stall_option_matches_oracle(kind):
+    """krylov.stall: a fraction that an FGMRES(4) restart cycle, or a window of 30
+    FCG iterations, cannot meet ends the solve there (RICH_ENOTCONV_LIN) with the
+    oracle's iterate and count; a small fraction changes nothing."""
     rb = _rb()
     grid, p, ks, bc, dt, kmean = _problem((16, 14, 12), 11, 1)
     ctx, info, h = _setup_both(grid, p, ks, bc, dt, kmean, 100)
@@ -276,14 +277,19 @@ def test_fgmres_stall_option_matches_oracle():
     from oracle import krylov
     prec = lambda v: amg.vcycle(h, v)
     lin = {name: code for code, name in rb.ERRORS.items()}["RICH_ENOTCONV_LIN"]
+    eta = 1e-11 if kind == "fgmres" else 1e-13
+    k = rb.KRYLOV_FGMRES if kind == "fgmres" else rb.KRYLOV_FCG
     for stall, ok_expected in ((0.999999, False), (0.01, True)):
         x = torch.empty(grid.n, dtype=torch.float64, device="cuda")
-        s, st = ctx.krylov_solve(torch.tensor(b, device="cuda"), x, kind=rb.KRYLOV_FGMRES, restart=4, eta=1e-11,
-                                 maxit=400, check_status=False, stall=stall)
-        xr, its, ok, _ = krylov.fgmres(lambda v: J @ v, prec, b, 1e-11, 400, 4, stall=stall)
+        s, st = ctx.krylov_solve(torch.tensor(b, device="cuda"), x, kind=k, restart=4, eta=eta, maxit=400,
+                                 check_status=False, stall=stall)
+        if kind == "fgmres":
+            xr, its, ok, _ = krylov.fgmres(lambda v: J @ v, prec, b, eta, 400, 4, stall=stall)
+        else:
+            xr, its, ok, _ = krylov.fcg(lambda v: J @ v, prec, b, eta, 400, stall=stall)
         assert ok == ok_expected and (s == 0) == ok and bool(st.converged) == ok
-        if not ok:
-            assert s == lin and st.iterations == its == 4
+        if not ok:  # stopped at the end of a cycle (FGMRES(4)) or a 30-iteration window (FCG)
+            assert s == lin and st.iterations == its and its % (4 if kind == "fgmres" else 30) == 0
         else:
             assert abs(st.iterations - its) <= 1
         assert _nrel(x.cpu().numpy(), xr) <= 1e-8

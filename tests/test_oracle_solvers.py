@@ -561,3 +561,23 @@ def test_pins_catch_a_forward_pre_smoother(monkeypatch):
     monkeypatch.setattr(amg, "_smooth", lambda h, level, b, x, forward: orig(h, level, b, x, True))
     with pytest.raises(AssertionError):
         test_hybrid_gs_vcycle_is_symmetric_positive_and_beats_l1_jacobi()
+
+
+def test_fcg_stall_window():
+    # CG on an SPD matrix with eigenvalues spread over [1, 1e4] and no preconditioner
+    # reduces the residual slowly; a stall fraction a 30-iteration window cannot meet
+    # stops it at iteration 30 with reason "stall", and the iterate is the plain
+    # run's iterate 30 (the test only ends the loop).
+    rng = np.random.default_rng(12)
+    n = 200
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = (Q * np.logspace(0, 4, n)) @ Q.T
+    b = rng.standard_normal(n)
+    ref30 = krylov.fcg(lambda v: M @ v, lambda v: v, b, 1e-14, 30)
+    info = {}
+    x, its, ok, hist = krylov.fcg(lambda v: M @ v, lambda v: v, b, 1e-14, 500, info=info, stall=0.999)
+    assert not ok and its == 30 and info["reason"] == "stall" and hist[30] > 1e-3 * hist[0]
+    np.testing.assert_array_equal(x, ref30[0])
+    info = {}
+    x2, its2, ok2, _ = krylov.fcg(lambda v: M @ v, lambda v: v, b, 1e-14, 500, info=info, stall=0.0)
+    assert its2 > 30
