@@ -78,7 +78,9 @@ extern "C" {
 /* Storage of the coarse-level matrices for the V-cycle's row operations */
 #define RICH_LAYOUT_AUTO       0
 #define RICH_LAYOUT_CSR        1
-#define RICH_LAYOUT_SELL       2
+#define RICH_LAYOUT_SELL       2   /* SELL kernel: four gathers in flight per row */
+#define RICH_LAYOUT_SELL8      3   /* eight gathers in flight per row */
+#define RICH_LAYOUT_SELL2      4   /* two lanes per row */
 
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
@@ -195,7 +197,8 @@ typedef struct {
                               times it beside the CSR variants when it first meets the matrix's shape
                               class, and keeps it only if it wins; a matrix whose class chose it gets
                               its copy on first use.  RICH_LAYOUT_CSR: CSR only, no copy.
-                              RICH_LAYOUT_SELL: the SELL copy for every such matrix (no timing) */
+                              RICH_LAYOUT_SELL / _SELL8 / _SELL2: the SELL copy for every such matrix,
+                              with that SELL kernel (no timing) */
 } rich_amg_opts;
 
 typedef struct {
@@ -403,7 +406,8 @@ int rich_measure_fma_peak(int fp64, double* tflops);
  * sell_offered variant best_us best_csr_variant" each (mode 0 y = A x, 1 y += A x,
  * 2 l1-Jacobi sweep, 3 residual; rows_bin = floor(4 log2 rows); sell_offered 1 where a
  * SELL copy was a candidate; variant = lanes per row, + 256 for four-way unrolled rows,
- * 512 / 513 for the SELL copy with 4 / 8 gathers in flight per row; best_csr_variant
+ * 512 / 513 for the SELL copy with 4 / 8 gathers in flight per row, 514 for the SELL
+ * copy with two lanes per row; best_csr_variant
  * the fastest CSR candidate), written into buf (at most cap bytes, NUL-terminated). */
 int rich_autotune_table(char* buf, int cap);
 /* Adds the entries of a saved table (rich_autotune_table's text) to the process's

@@ -142,12 +142,56 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslice, const int* __restri
   }
 }
 
+// SELL with two lanes per row: one warp per half-slice (16 rows); lane t + 16 ph
+// takes the row's columns j = ph, ph + 2, ... (each load instruction reads two
+// contiguous 128-byte runs), and one shuffle-add joins the two partial sums.  Twice
+// the warps of k_sell for the same slices: more loads in flight on levels whose
+// slices alone fill only part of the GPU.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_sell2(int nslice, const int* __restrict__ sptr,
+                                                  const int* __restrict__ perm, const int* __restrict__ col,
+                                                  const T* __restrict__ val, const T* __restrict__ dinv,
+                                                  const T* __restrict__ b, const T* __restrict__ x,
+                                                  T* __restrict__ y) {
+  const int lane = threadIdx.x & 31, ph = lane >> 4;
+  const int warps = (gridDim.x * blockDim.x) / 32;
+  for (int hs = (blockIdx.x * blockDim.x + threadIdx.x) / 32; hs < 2 * nslice; hs += warps) {
+    const int s = hs >> 1, r = (hs & 1) * 16 + (lane & 15);
+    const int row = perm[s * kSellC + r];
+    const int base = sptr[s] + r, w = (sptr[s + 1] - sptr[s]) / kSellC;
+    T s0 = 0, s1 = 0;
+    int j = ph;
+    for (; j + 6 < w; j += 8) {  // columns j, j + 2, j + 4, j + 6 of this lane
+      const int c0 = col[base + j * kSellC], c1 = col[base + (j + 2) * kSellC];
+      const int c2 = col[base + (j + 4) * kSellC], c3 = col[base + (j + 6) * kSellC];
+      const T v0 = val[base + j * kSellC], v1 = val[base + (j + 2) * kSellC];
+      const T v2 = val[base + (j + 4) * kSellC], v3 = val[base + (j + 6) * kSellC];
+      const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+      s0 += v0 * x0;
+      s1 += v1 * x1;
+      s0 += v2 * x2;
+      s1 += v3 * x3;
+    }
+    for (; j < w; j += 2) s0 += val[base + j * kSellC] * x[col[base + j * kSellC]];
+    T a = s0 + s1;
+    a += __shfl_xor_sync(0xffffffffu, a, 16);
+    if (ph == 0 && row >= 0) {
+      if (MODE == 0) y[row] = a;
+      else if (MODE == 1) y[row] += a;
+      else if (MODE == 2) y[row] = x[row] + dinv[row] * (b[row] - a);
+      else y[row] = b[row] - a;
+    }
+  }
+}
+
 // Variant v of the CSR row kernel: lanes per row G = v & 0xff, four-way unrolled
-// rows when v & kUnroll; v == kSellVariant (4 gathers in flight) or kSellVariant8
-// (8) runs the SELL copy (sl, sval) instead.
+// rows when v & kUnroll; v == kSellVariant (4 gathers in flight per thread),
+// kSellVariant8 (8) or kSellVariant2 (two lanes per row) runs the SELL copy
+// (sl, sval) instead.
 constexpr int kUnroll = 0x100;
 constexpr int kSellVariant = 0x200;
 constexpr int kSellVariant8 = 0x201;
+constexpr int kSellVariant2 = 0x202;
 inline bool is_sell(int v) { return (v & kSellVariant) != 0; }
 template <class T, int MODE>
 static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* col, const T* val, const T* dinv,
@@ -156,6 +200,9 @@ static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* 
     const int g = grid_for((long long)sl->nslice * kSellC);
     if (v == kSellVariant8)
       k_sell<T, MODE, 8><<<g, kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm, sl->col, sval, dinv, b, x, y);
+    else if (v == kSellVariant2)
+      k_sell2<T, MODE><<<grid_for(2LL * sl->nslice * kSellC), kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm,
+                                                                               sl->col, sval, dinv, b, x, y);
     else
       k_sell<T, MODE, 4><<<g, kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm, sl->col, sval, dinv, b, x, y);
     return;
@@ -252,9 +299,10 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
   const bool offer = src && src->s && n >= kSellMinRows && layout != RICH_LAYOUT_CSR;
   int v = default_lanes((double)nnz / n);
   bool sell_ok = false;
-  if (offer && layout == RICH_LAYOUT_SELL) {
+  if (offer && layout >= RICH_LAYOUT_SELL) {  // a SELL kernel named by the option
     RICH_CHECK(sell_ensure(c, *src, &sell_ok));
-    if (sell_ok) v = kSellVariant;
+    if (sell_ok)
+      v = layout == RICH_LAYOUT_SELL8 ? kSellVariant8 : (layout == RICH_LAYOUT_SELL2 ? kSellVariant2 : kSellVariant);
   } else if (c->H.opts.autotune) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneKey key{MODE, (int)sizeof(T), (int)std::floor(4.0 * std::log2((double)n)),
@@ -280,7 +328,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       const Sell* sl = sell_ok ? src->s : nullptr;
       const T* sval = sell_ok ? (sizeof(T) == 8 ? (const T*)sl->val : (const T*)sl->val32) : nullptr;
       for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll, kSellVariant,
-                    kSellVariant8}) {
+                    kSellVariant8, kSellVariant2}) {
         if (is_sell(g) && !sell_ok) continue;
         csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
         RICH_CUDA(cudaEventRecord(e0, c->st));
@@ -337,7 +385,7 @@ int autotune_table(char* buf, int cap) {
 // their choice.  A variant that is not one of the candidates is rejected.
 int autotune_load(const char* text) {
   auto valid = [](int v) {
-    if (v == kSellVariant || v == kSellVariant8) return true;
+    if (v == kSellVariant || v == kSellVariant8 || v == kSellVariant2) return true;
     const int g = v & 0xff, u = v & ~0xff;
     if (u != 0 && u != kUnroll) return false;
     if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return false;
