@@ -59,7 +59,11 @@ FALLBACK_HBM_GBS = 6800.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on a
 # workload, from the profiles/ summaries of the same kernel and workload (None:
 # no capture of the current kernel).
-NCU_TRAFFIC_BYTES = {("richards128_fp64", "l1jacobi_l0"): 125.615616e6}
+# DRAM bytes per launch from ncu captures of the same workload: the finest FP64
+# sweep measured whole; the batched dots measured over their first 60 launches
+# (DRAM / algorithmic = 1.037) and scaled to the profile pass's 241.2 MB per launch
+NCU_TRAFFIC_BYTES = {("richards128_fp64", "l1jacobi_l0"): 125.615616e6,
+                     ("richards128_fp64", "multidot"): 1.037 * 241.2e6}
 # the oracle's reduced grid for the host-core samples (cells per side)
 CPU_SAMPLE_N = {"richards128_fp64": 48, "richards16_fp64": 16, "richards256_mixed": 32, "richards512_mixed": 32,
                 "paper_infiltration": 96}
@@ -99,7 +103,7 @@ def parse():
     ap.add_argument("--serving-aggregation", type=int, default=0, help="0: MIS-2, 1: matching (SMATCH-style)")
     ap.add_argument("--serving-batch", type=int, default=8,
                     help="largest packed batch of same-shape requests (1: one request per slot)")
-    ap.add_argument("--serving-stall", type=float, default=0.1,
+    ap.add_argument("--serving-stall", type=float, default=0.5,
                     help="serving requests' FGMRES gives up after a restart cycle that reduced the residual by less "
                          "than this fraction (0: off)")
     ap.add_argument("--serving-halvings", type=int, default=0,
