@@ -788,7 +788,8 @@ def run_ours(args):
                                "fp64_balance_flop_per_byte": fp64_balance(peak_gbs, fp64_tflops)},
             "autotuned_shapes": len(rb.autotune_table()),
             "autotune": [{"mode": m, "value_bytes": t, "rows_bin": nb, "mean_row": z, "sell_offered": so,
-                          "choice": {rb.SELL_VARIANT8: "sell x8", rb.SELL_VARIANT2: "sell 2 lanes"}.get(g, "sell")
+                          "choice": {rb.SELL_VARIANT8: "sell x8", rb.SELL_VARIANT2: "sell 2 lanes",
+                                     rb.SELL_VARIANTP: "sell pipelined"}.get(g, "sell")
                           if g & rb.SELL_VARIANT else
                           ("%d lanes%s" % (g & 0xff, " x4" if g & rb.UNROLL else "")),
                           "us": us} for m, t, nb, z, so, g, us in rb.autotune_table()],

@@ -81,6 +81,7 @@ extern "C" {
 #define RICH_LAYOUT_SELL       2   /* SELL kernel: four gathers in flight per row */
 #define RICH_LAYOUT_SELL8      3   /* eight gathers in flight per row */
 #define RICH_LAYOUT_SELL2      4   /* two lanes per row */
+#define RICH_LAYOUT_SELLP      5   /* slot loads of the next four columns in flight during the gathers */
 
 /* ---- enumerations ------------------------------------------------------- */
 /* Face conductivity K_av (Sec. 2.1): arithmetic (K_L+K_U)/2; upstream
@@ -197,8 +198,8 @@ typedef struct {
                               times it beside the CSR variants when it first meets the matrix's shape
                               class, and keeps it only if it wins; a matrix whose class chose it gets
                               its copy on first use.  RICH_LAYOUT_CSR: CSR only, no copy.
-                              RICH_LAYOUT_SELL / _SELL8 / _SELL2: the SELL copy for every such matrix,
-                              with that SELL kernel (no timing) */
+                              RICH_LAYOUT_SELL / _SELL8 / _SELL2 / _SELLP: the SELL copy for every such
+                              matrix, with that SELL kernel (no timing) */
 } rich_amg_opts;
 
 typedef struct {
@@ -407,7 +408,7 @@ int rich_measure_fma_peak(int fp64, double* tflops);
  * 2 l1-Jacobi sweep, 3 residual; rows_bin = floor(4 log2 rows); sell_offered 1 where a
  * SELL copy was a candidate; variant = lanes per row, + 256 for four-way unrolled rows,
  * 512 / 513 for the SELL copy with 4 / 8 gathers in flight per row, 514 for the SELL
- * copy with two lanes per row; best_csr_variant
+ * copy with two lanes per row, 515 for the software-pipelined one; best_csr_variant
  * the fastest CSR candidate), written into buf (at most cap bytes, NUL-terminated). */
 int rich_autotune_table(char* buf, int cap);
 /* Adds the entries of a saved table (rich_autotune_table's text) to the process's

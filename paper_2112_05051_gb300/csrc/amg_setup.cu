@@ -1846,7 +1846,7 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
   if (H.opts.aggregation == RICH_AGG_MATCHING && (H.opts.max_agg_size < 2 || H.opts.max_agg_size > 1024))
     return RICH_EINVAL;
   if (H.opts.precond != RICH_PRECOND_AMG && H.opts.precond != RICH_PRECOND_AS) return RICH_EINVAL;
-  if (H.opts.csr_layout < RICH_LAYOUT_AUTO || H.opts.csr_layout > RICH_LAYOUT_SELL2) return RICH_EINVAL;
+  if (H.opts.csr_layout < RICH_LAYOUT_AUTO || H.opts.csr_layout > RICH_LAYOUT_SELLP) return RICH_EINVAL;
   if (H.opts.precond == RICH_PRECOND_AS) {  // one level: the subdomain factors of A_aux
     RICH_CHECK(fine_stencil(c));
     RICH_CHECK(as_setup(c));

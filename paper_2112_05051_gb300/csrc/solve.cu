@@ -142,6 +142,78 @@ __global__ void __launch_bounds__(kBlock) k_sell(int nslice, const int* __restri
   }
 }
 
+// SELL, software-pipelined: while the gathers of x for four columns and their
+// products run, the slot loads (column and value) of the next four are already in
+// flight, so the DRAM latency of the copy overlaps the L2 latency of the gathers
+// instead of adding to it.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_sellp(int nslice, const int* __restrict__ sptr,
+                                                  const int* __restrict__ perm, const int* __restrict__ col,
+                                                  const T* __restrict__ val, const T* __restrict__ dinv,
+                                                  const T* __restrict__ b, const T* __restrict__ x,
+                                                  T* __restrict__ y) {
+  const int lane = threadIdx.x & (kSellC - 1);
+  const int warps = (gridDim.x * blockDim.x) / kSellC;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) / kSellC; s < nslice; s += warps) {
+    const int row = perm[s * kSellC + lane];
+    const int end = sptr[s + 1];
+    int e = sptr[s] + lane;
+    T s0 = 0, s1 = 0;
+    bool have = e + 3 * kSellC < end;  // warp-uniform, as every test below
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    T v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if (have) {
+      c0 = col[e];
+      c1 = col[e + kSellC];
+      c2 = col[e + 2 * kSellC];
+      c3 = col[e + 3 * kSellC];
+      v0 = val[e];
+      v1 = val[e + kSellC];
+      v2 = val[e + 2 * kSellC];
+      v3 = val[e + 3 * kSellC];
+    }
+    while (have) {
+      const int en = e + 4 * kSellC;
+      const bool next = en + 3 * kSellC < end;
+      int d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+      T w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+      if (next) {
+        d0 = col[en];
+        d1 = col[en + kSellC];
+        d2 = col[en + 2 * kSellC];
+        d3 = col[en + 3 * kSellC];
+        w0 = val[en];
+        w1 = val[en + kSellC];
+        w2 = val[en + 2 * kSellC];
+        w3 = val[en + 3 * kSellC];
+      }
+      const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+      s0 += v0 * x0;
+      s1 += v1 * x1;
+      s0 += v2 * x2;
+      s1 += v3 * x3;
+      c0 = d0;
+      c1 = d1;
+      c2 = d2;
+      c3 = d3;
+      v0 = w0;
+      v1 = w1;
+      v2 = w2;
+      v3 = w3;
+      e = en;
+      have = next;
+    }
+    for (; e < end; e += kSellC) s0 += val[e] * x[col[e]];
+    const T a = s0 + s1;
+    if (row >= 0) {
+      if (MODE == 0) y[row] = a;
+      else if (MODE == 1) y[row] += a;
+      else if (MODE == 2) y[row] = x[row] + dinv[row] * (b[row] - a);
+      else y[row] = b[row] - a;
+    }
+  }
+}
+
 // SELL with two lanes per row: one warp per half-slice (16 rows); lane t + 16 ph
 // takes the row's columns j = ph, ph + 2, ... (each load instruction reads two
 // contiguous 128-byte runs), and one shuffle-add joins the two partial sums.  Twice
@@ -186,12 +258,13 @@ __global__ void __launch_bounds__(kBlock) k_sell2(int nslice, const int* __restr
 
 // Variant v of the CSR row kernel: lanes per row G = v & 0xff, four-way unrolled
 // rows when v & kUnroll; v == kSellVariant (4 gathers in flight per thread),
-// kSellVariant8 (8) or kSellVariant2 (two lanes per row) runs the SELL copy
-// (sl, sval) instead.
+// kSellVariant8 (8), kSellVariant2 (two lanes per row) or kSellVariantP
+// (software-pipelined) runs the SELL copy (sl, sval) instead.
 constexpr int kUnroll = 0x100;
 constexpr int kSellVariant = 0x200;
 constexpr int kSellVariant8 = 0x201;
 constexpr int kSellVariant2 = 0x202;
+constexpr int kSellVariantP = 0x203;
 inline bool is_sell(int v) { return (v & kSellVariant) != 0; }
 template <class T, int MODE>
 static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* col, const T* val, const T* dinv,
@@ -203,6 +276,8 @@ static void csr_launch(cudaStream_t st, int v, int n, const int* rp, const int* 
     else if (v == kSellVariant2)
       k_sell2<T, MODE><<<grid_for(2LL * sl->nslice * kSellC), kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm,
                                                                                sl->col, sval, dinv, b, x, y);
+    else if (v == kSellVariantP)
+      k_sellp<T, MODE><<<g, kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm, sl->col, sval, dinv, b, x, y);
     else
       k_sell<T, MODE, 4><<<g, kBlock, 0, st>>>(sl->nslice, sl->sptr, sl->perm, sl->col, sval, dinv, b, x, y);
     return;
@@ -303,7 +378,10 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
   if (offer && layout >= RICH_LAYOUT_SELL) {  // a SELL kernel named by the option
     RICH_CHECK(sell_ensure(c, *src, &sell_ok));
     if (sell_ok)
-      v = layout == RICH_LAYOUT_SELL8 ? kSellVariant8 : (layout == RICH_LAYOUT_SELL2 ? kSellVariant2 : kSellVariant);
+      v = layout == RICH_LAYOUT_SELL8   ? kSellVariant8
+          : layout == RICH_LAYOUT_SELL2 ? kSellVariant2
+          : layout == RICH_LAYOUT_SELLP ? kSellVariantP
+                                        : kSellVariant;
   } else if (c->H.opts.autotune) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneKey key{MODE, (int)sizeof(T), (int)std::floor(4.0 * std::log2((double)n)),
@@ -337,7 +415,7 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       const Sell* sl = sell_ok ? src->s : nullptr;
       const T* sval = sell_ok ? (sizeof(T) == 8 ? (const T*)sl->val : (const T*)sl->val32) : nullptr;
       for (int g : {1, 2, 4, 8, 16, 32, 1 | kUnroll, 2 | kUnroll, 4 | kUnroll, 8 | kUnroll, kSellVariant,
-                    kSellVariant8, kSellVariant2}) {
+                    kSellVariant8, kSellVariant2, kSellVariantP}) {
         if (is_sell(g) && !sell_ok) continue;
         csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
         float ms = 0.f;
@@ -400,7 +478,7 @@ int autotune_table(char* buf, int cap) {
 // their choice.  A variant that is not one of the candidates is rejected.
 int autotune_load(const char* text) {
   auto valid = [](int v) {
-    if (v == kSellVariant || v == kSellVariant8 || v == kSellVariant2) return true;
+    if (v == kSellVariant || v == kSellVariant8 || v == kSellVariant2 || v == kSellVariantP) return true;
     const int g = v & 0xff, u = v & ~0xff;
     if (u != 0 && u != kUnroll) return false;
     if (g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return false;

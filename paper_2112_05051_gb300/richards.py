@@ -19,8 +19,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 AGG_MIS2, AGG_MATCHING = 0, 1
 SMOOTH_L1JACOBI, SMOOTH_HYBRID_GS = 0, 1
 PRECOND_AMG, PRECOND_AS = 0, 1
-LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_SELL, LAYOUT_SELL8, LAYOUT_SELL2 = 0, 1, 2, 3, 4
-UNROLL, SELL_VARIANT, SELL_VARIANT8, SELL_VARIANT2 = 0x100, 0x200, 0x201, 0x202
+LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_SELL, LAYOUT_SELL8, LAYOUT_SELL2, LAYOUT_SELLP = 0, 1, 2, 3, 4, 5
+UNROLL, SELL_VARIANT, SELL_VARIANT8, SELL_VARIANT2, SELL_VARIANTP = 0x100, 0x200, 0x201, 0x202, 0x203
 
 ERRORS = {-1: "RICH_EINVAL", -2: "RICH_ENOMEM", -3: "RICH_ECUDA", -4: "RICH_ENOTCONV_LIN",
           -5: "RICH_ENOTCONV_NEWTON", -6: "RICH_ELINESEARCH", -7: "RICH_ENONFINITE", -8: "RICH_ESTATE",

@@ -161,7 +161,7 @@ def test_vcycle_parity_fp64_and_mixed(nu):
         ctx.close()
 
 
-@pytest.mark.parametrize("layout", ["csr", "sell", "sell8", "sell2", "auto"])
+@pytest.mark.parametrize("layout", ["csr", "sell", "sell8", "sell2", "sellp", "auto"])
 def test_vcycle_parity_per_row_layout_after_refresh(layout):
     """The coarse-level row operations on CSR, on the SELL-C-sigma copies (P_0 with
     84k rows, R_0 and A_1 with a few thousand; ragged last slices and windows), and
@@ -169,7 +169,7 @@ def test_vcycle_parity_per_row_layout_after_refresh(layout):
     (the copies of A are refilled), FP64 and MIXED, against the oracle."""
     rb = _rb()
     lay = {"csr": rb.LAYOUT_CSR, "sell": rb.LAYOUT_SELL, "sell8": rb.LAYOUT_SELL8, "sell2": rb.LAYOUT_SELL2,
-           "auto": rb.LAYOUT_AUTO}[layout]
+           "sellp": rb.LAYOUT_SELLP, "auto": rb.LAYOUT_AUTO}[layout]
     grid, p, ks, bc, dt, kmean = _problem((48, 44, 40), 9, 1)
     p2 = p + np.random.default_rng(6).uniform(0, 10, grid.n)
     r = np.random.default_rng(3).standard_normal(grid.n)
