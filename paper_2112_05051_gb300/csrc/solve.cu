@@ -317,8 +317,8 @@ static int default_lanes(double avg) {
 // Autotuner of the CSR row operations: the first time an operation meets a shape
 // class (mode, value type, rows in quarter-octave bins, mean row length rounded to
 // an integer), every candidate is timed on the actual operands (output to a scratch
-// vector, one warm-up and three timed launches each from a cold L2, CUDA events)
-// and the fastest is kept for the rest of the process.  Classes, not exact shapes, so that
+// vector, one warm-up and three timed launches each, CUDA events) and the fastest
+// is kept for the rest of the process.  Classes, not exact shapes, so that
 // a stream of requests of similar size (whose coarse levels differ by a few rows)
 // tunes once.  The table is shared by all contexts (under a mutex, held while
 // tuning, so concurrent requests of one class agree); a class therefore always runs
@@ -342,7 +342,6 @@ struct TuneVal {
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
-constexpr long long kTuneFlushBytes = 256LL << 20;  // twice the 129 MB L2
 
 // Where a row operation's matrix can get a SELL copy: the copy, the CSR it is laid
 // out from and the values in the hierarchy precision.
@@ -399,14 +398,10 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       T* scratch = nullptr;
       RICH_CHECK(dalloc(&scratch, n));
       RICH_CUDA(cudaMemsetAsync(scratch, 0, sizeof(T) * (size_t)n, c->st));
-      // In the V-cycle the finest level and the Krylov basis stream through L2
-      // between two visits of a level, so candidates are timed from a cold L2: a
-      // write of twice its size before each timed launch (skipped if it does not fit).
-      char* flush = nullptr;
-      if (dalloc(&flush, kTuneFlushBytes) != RICH_OK) {
-        flush = nullptr;
-        cudaGetLastError();
-      }
+      // Back-to-back launches on warm operands.  Timing each launch from a cold L2
+      // (a 256 MB write before it) was measured and chose worse variants: the same
+      // headline, 3 % less in the mixed mode, whose FP32 levels stay in L2 between
+      // the sweeps of a V-cycle.
       cudaEvent_t e0, e1;
       RICH_CUDA(cudaEventCreate(&e0));
       RICH_CUDA(cudaEventCreate(&e1));
@@ -418,17 +413,12 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
                     kSellVariant8, kSellVariant2, kSellVariantP}) {
         if (is_sell(g) && !sell_ok) continue;
         csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
+        RICH_CUDA(cudaEventRecord(e0, c->st));
+        for (int rep = 0; rep < 3; ++rep) csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
+        RICH_CUDA(cudaEventRecord(e1, c->st));
+        RICH_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-          if (flush) RICH_CUDA(cudaMemsetAsync(flush, rep + 1, kTuneFlushBytes, c->st));
-          RICH_CUDA(cudaEventRecord(e0, c->st));
-          csr_launch<T, MODE>(c->st, g, n, rp, col, val, dinv, b, x, scratch, sl, sval);
-          RICH_CUDA(cudaEventRecord(e1, c->st));
-          RICH_CUDA(cudaEventSynchronize(e1));
-          float one = 0.f;
-          RICH_CUDA(cudaEventElapsedTime(&one, e0, e1));
-          ms += one;
-        }
+        RICH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         count_launches(4);
         if (ms < best) {
           best = ms;
@@ -443,7 +433,6 @@ static int csr_op(rich_ctx* c, int n, long long nnz, const int* rp, const int* c
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       dfree(scratch);
-      dfree(flush);
       g_tune[key] = {v, best * 1000.f / 3.f, best_csr};
       if (sell_ok && !is_sell(v) && !had_copy) {  // the copy lost: not kept, not refreshed
         sell_free(*src->s);
