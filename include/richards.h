@@ -417,6 +417,15 @@ int rich_autotune_table(char* buf, int cap);
  * Classes already tuned keep their choice.  RICH_EINVAL (nothing added) on a
  * malformed line or an unknown variant. */
 int rich_autotune_load(const char* text);
+/* The SELL-C-sigma layout (csr_layout) the library gives a CSR matrix of n rows,
+ * computed on the host from its row pointer (rowptr_host, n + 1 entries,
+ * non-decreasing): rows sorted by decreasing length (ties in row order) within
+ * each window of 1024 rows, cut into slices of 32.  perm_host receives
+ * 32 * ceil(n / 32) row indices (-1 past n), sptr_host the ceil(n / 32) + 1 slot
+ * offsets of the slices (slice s spans 32 x its first row's length slots), and
+ * *slots their total.  Host memory only; RICH_EINVAL on a bad argument or a
+ * decreasing row pointer, RICH_ELIMIT when the slots exceed 32-bit offsets. */
+int rich_sell_layout(const int* rowptr_host, int n, int* perm_host, int* sptr_host, long long* slots);
 
 /* Number of kernels this library has launched since it was loaded. */
 int rich_kernel_launches(long long* out);

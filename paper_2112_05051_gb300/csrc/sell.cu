@@ -37,15 +37,13 @@ __global__ void k_sell_vals(int nslice, const int* __restrict__ sptr, const int*
   }
 }
 
-int sell_build(rich_ctx* c, const Csr<double>& M, Sell& S) {
-  sell_free(S);
-  const int n = M.nrows;
-  if (n < kSellMinRows) return RICH_OK;
-  std::vector<int> rp(n + 1);
-  RICH_CUDA(cudaMemcpyAsync(rp.data(), M.rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, c->st));
-  RICH_CUDA(cudaStreamSynchronize(c->st));
+// The layout of a SELL copy from the row pointer alone (host): perm (32 ns entries,
+// -1 past n) and sptr (ns + 1 slot offsets).  Returns the slot count, or -1 when it
+// exceeds 32-bit offsets.
+long long sell_layout(const int* rp, int n, int* perm, int* sptr) {
   const int ns = (n + kSellC - 1) / kSellC;
-  std::vector<int> perm((size_t)ns * kSellC, -1), sptr(ns + 1, 0), cnt;
+  for (long long t = 0; t < (long long)ns * kSellC; ++t) perm[t] = -1;
+  std::vector<int> cnt;
   for (int w0 = 0; w0 < n; w0 += kSellSigma) {
     const int w1 = std::min(n, w0 + kSellSigma);
     int lmax = 0;
@@ -60,9 +58,23 @@ int sell_build(rich_ctx* c, const Csr<double>& M, Sell& S) {
     sptr[s] = (int)slots;
     const int r0 = perm[(size_t)s * kSellC];
     slots += (long long)kSellC * (rp[r0 + 1] - rp[r0]);
-    if (slots > 2147483647LL) return RICH_OK;  // too large for 32-bit slot offsets: CSR only
+    if (slots > 2147483647LL) return -1;
   }
   sptr[ns] = (int)slots;
+  return slots;
+}
+
+int sell_build(rich_ctx* c, const Csr<double>& M, Sell& S) {
+  sell_free(S);
+  const int n = M.nrows;
+  if (n < kSellMinRows) return RICH_OK;
+  std::vector<int> rp(n + 1);
+  RICH_CUDA(cudaMemcpyAsync(rp.data(), M.rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, c->st));
+  RICH_CUDA(cudaStreamSynchronize(c->st));
+  const int ns = (n + kSellC - 1) / kSellC;
+  std::vector<int> perm((size_t)ns * kSellC), sptr(ns + 1);
+  const long long slots = sell_layout(rp.data(), n, perm.data(), sptr.data());
+  if (slots < 0) return RICH_OK;  // too large for 32-bit slot offsets: CSR only
   RICH_CHECK(dalloc(&S.sptr, ns + 1));
   RICH_CHECK(dalloc(&S.perm, (long long)ns * kSellC));
   RICH_CHECK(dalloc(&S.col, slots));
@@ -107,3 +119,14 @@ void sell_free(Sell& S) {
 }
 
 }  // namespace rich
+
+extern "C" int rich_sell_layout(const int* rowptr_host, int n, int* perm_host, int* sptr_host,
+                                long long* slots) {
+  if (!rowptr_host || n < 1 || !perm_host || !sptr_host || !slots) return RICH_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (rowptr_host[i + 1] < rowptr_host[i]) return RICH_EINVAL;
+  const long long s = rich::sell_layout(rowptr_host, n, perm_host, sptr_host);
+  if (s < 0) return RICH_ELIMIT;
+  *slots = s;
+  return RICH_OK;
+}

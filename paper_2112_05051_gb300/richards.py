@@ -146,6 +146,7 @@ EXPORTS = {
     "rich_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rich_autotune_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "rich_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "rich_sell_layout": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -548,6 +549,20 @@ def autotune_table():
         m, t, n, z, so, g, us, _ = line.split()
         out.append((int(m), int(t), int(n), int(z), int(so), int(g), float(us)))
     return out
+
+
+def sell_layout(rowptr):
+    """The SELL-C-sigma layout of a CSR row pointer (host): (perm, sptr, slots)."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    n = len(rp) - 1
+    ns = (n + 31) // 32
+    perm = np.empty(32 * ns, dtype=np.int32)
+    sptr = np.empty(ns + 1, dtype=np.int32)
+    slots = ctypes.c_longlong()
+    cp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    check(load().rich_sell_layout(cp(rp), n, cp(perm), cp(sptr), ctypes.byref(slots)), "rich_sell_layout")
+    return perm, sptr, slots.value
 
 
 def autotune_text():

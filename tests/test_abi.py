@@ -92,3 +92,32 @@ def test_autotune_table_round_trip_without_a_gpu(lib):
             rb.autotune_load(bad)
     assert rb.autotune_text() == again
     assert set(before.splitlines()) <= set(again.splitlines())
+
+
+def test_sell_layout_host_logic_without_a_gpu(lib):
+    """The SELL-C-sigma layout: within each 1024-row window a stable sort by
+    decreasing row length, slices of 32 whose width is their first row's length,
+    ragged last slice and window padded with -1, slot offsets their running sum."""
+    import numpy as np
+    from paper_2112_05051_gb300 import richards as rb
+    rb.load()
+    rng = np.random.default_rng(7)
+    for n in (2048, 2500, 1, 31, 33, 1025, 3000):
+        lens = rng.integers(0, 60, n)
+        lens[rng.integers(0, n, max(1, n // 50))] = 0  # empty rows
+        rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+        perm, sptr, slots = rb.sell_layout(rp)
+        ns = (n + 31) // 32
+        assert perm.shape == (32 * ns,) and sptr.shape == (ns + 1,)
+        assert np.all(perm[n:] == -1) and sorted(perm[:n]) == list(range(n))
+        for w0 in range(0, n, 1024):  # each window is a permutation of its own rows ...
+            w = perm[w0:min(n, w0 + 1024)]
+            assert sorted(w) == list(range(w0, min(n, w0 + 1024)))
+            key = [(-lens[r], r) for r in w]  # ... longest first, ties in row order
+            assert key == sorted(key)
+        width = [lens[perm[32 * s]] for s in range(ns)]
+        assert all(lens[r] <= width[i // 32] for i, r in enumerate(perm[:n]))
+        np.testing.assert_array_equal(sptr, np.concatenate([[0], np.cumsum(32 * np.array(width))]))
+        assert slots == sptr[-1] >= rp[-1]
+    with pytest.raises(rb.RichError):
+        rb.sell_layout(np.array([0, 3, 2], dtype=np.int32))  # decreasing row pointer
