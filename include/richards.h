@@ -100,6 +100,12 @@ extern "C" {
 
 #define RICH_BC_NOFLUX     0  /* the whole face flux (diffusion + gravity) is zero */
 #define RICH_BC_DIRICHLET  1  /* ghost node at p = value, K from the adjacent cell's K_s */
+#define RICH_BC_INTERFACE  2  /* the face between two subdomains of a split grid (Sec. 5.1): the ghost is
+                                 the neighbouring subdomain's cell, its pressure per cell in
+                                 value_field_dev[f] (required; refreshed by rich_set_face_values) and its
+                                 K_s in ghost_ks_dev[f] (NULL: the soil's ks_const).  The residual and the
+                                 Jacobian rows of the face cells are those of the unsplit grid: J and
+                                 A_aux keep the coupling to the ghost in their plane of face f */
 
 /* Precision of the AMG preconditioner.  The Newton residual, the Jacobian,
  * line-search norms and the outer Krylov vectors and dot products are FP64
@@ -152,6 +158,9 @@ typedef struct {
    * infiltration problem (Sec. 6): p = 0 on a centred square of the top face,
    * h_r elsewhere. */
   const double* value_field_dev[6];
+  /* RICH_BC_INTERFACE faces: per-cell K_s of the ghost cells (device, same indexing), or
+   * NULL for the soil's ks_const; copied at create.  Ignored on other faces. */
+  const double* ghost_ks_dev[6];
 } rich_bc;
 
 typedef struct {
@@ -284,6 +293,18 @@ int rich_destroy(rich_ctx* ctx);
 const char* rich_strerror(int status);
 const char* rich_last_cuda_error(void);
 int rich_num_cells(const rich_ctx* ctx, long long* n_out);
+
+/* Replaces the per-cell values of face f (Dirichlet pressures, or the ghost
+ * pressures of a RICH_BC_INTERFACE face after a halo exchange) with values_dev
+ * (device, the face's cell count, indexing of rich_bc.value_field_dev), copied on
+ * the context's stream.  RICH_ESTATE if the face was created without a per-cell
+ * field, RICH_EINVAL on a bad face or pointer. */
+int rich_set_face_values(rich_ctx* ctx, int face, const double* values_dev);
+/* out_dev[t] = field_dev[the cell next to face f with face index t]: packs the cells
+ * a neighbouring subdomain needs as its ghosts (the send side of a halo exchange),
+ * in the layout of the per-cell face arrays.  Device pointers; the context's
+ * stream; out_dev holds the face's cell count. */
+int rich_pack_face(rich_ctx* ctx, int face, const double* field_dev, double* out_dev);
 
 /* ---- Sec. 2: constitutive law and residual ----------------------------- */
 /* s_dev[c] = s(p_dev[c]) (eq. (s(p))).  Used for s(p^{l-1}) of a step. */

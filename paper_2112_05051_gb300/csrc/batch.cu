@@ -431,6 +431,8 @@ int rich_create_batch(const rich_grid* grid, int nbatch, const rich_soil* soil, 
   if (grid->nz < 1) return RICH_EINVAL;
   for (int f = 0; f < 4; ++f)  // per-cell values on x and y faces are indexed by layer: one problem only
     if (bc->value_field_dev[f]) return RICH_EINVAL;
+  for (int f = 0; f < 6; ++f)  // stacked problems are whole grids, not subdomains
+    if (bc->kind[f] == RICH_BC_INTERFACE) return RICH_EINVAL;
   rich_grid g = *grid;
   const double hz = grid->lz / (grid->nz + 1);
   g.nz = grid->nz * nbatch;

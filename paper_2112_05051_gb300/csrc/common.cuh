@@ -88,17 +88,22 @@ struct GridP {
 struct BCP {
   int kind[6];
   double value[6];
-  const double* field[6];  // per-cell Dirichlet values of the face, or nullptr
+  const double* field[6];  // per-cell Dirichlet values (ghost pressures of an interface face), or nullptr
+  const double* gks[6];    // interface faces: per-cell K_s of the ghost cells, or nullptr (soil ks)
 };
+
+// Index of the boundary cell (i, j, k) in the per-cell arrays of face f.
+__device__ __forceinline__ long long face_index(int f, int i, int j, int k, int nx, int ny) {
+  int axis = f >> 1;
+  return axis == 2 ? (long long)i + (long long)nx * j
+                   : (axis == 1 ? (long long)i + (long long)nx * k : (long long)j + (long long)ny * k);
+}
 
 // Dirichlet value of face f at the boundary cell (i, j, k).
 __device__ __forceinline__ double bc_value(const BCP& bc, int f, int i, int j, int k, int nx, int ny) {
   const double* fv = bc.field[f];
   if (!fv) return bc.value[f];
-  int axis = f >> 1;
-  long long idx = axis == 2 ? (long long)i + (long long)nx * j : (axis == 1 ? (long long)i + (long long)nx * k
-                                                                          : (long long)j + (long long)ny * k);
-  return fv[idx];
+  return fv[face_index(f, i, j, k, nx, ny)];
 }
 
 template <class T>
@@ -274,6 +279,7 @@ struct rich_ctx {
   double* psave = nullptr;     // p at the start of a substep (time-step control)
   int nbatch = 1;              // problems stacked along z (rich_create_batch)
   double* bc_fields[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // owned per-cell BC values
+  double* bc_gks[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};     // owned ghost K_s (interfaces)
   bool amg_ever = false;
 };
 

@@ -175,6 +175,7 @@ extern "C" int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soi
     b.kind[f] = bc->kind[f];
     b.value[f] = bc->value[f];
     b.field[f] = bc->value_field_dev[f];
+    b.gks[f] = nullptr;
   }
   cudaStream_t st = (cudaStream_t)stream;
   k_residual_noalloc<<<(int)nb, kNoAllocThreads, 0, st>>>(g, so, b, kmean, p_dev, s_old_dev, soil->ks_field_dev, dt,

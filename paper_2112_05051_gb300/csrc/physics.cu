@@ -35,6 +35,31 @@ __global__ void k_constit(long long n, SoilP so, const double* __restrict__ p, c
   }
 }
 
+// out[t] = field[cell next to face f whose face index is t] (the layout of the
+// per-cell face arrays: i + nx j on z faces, i + nx k on y faces, j + ny k on x faces).
+__global__ void k_pack_face(GridP g, int f, long long m, const double* __restrict__ field,
+                            double* __restrict__ out) {
+  const int axis = f >> 1;
+  const bool hi = f & 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m; t += (long long)gridDim.x * blockDim.x) {
+    long long i, j, k;
+    if (axis == 0) {
+      j = t % g.ny;
+      k = t / g.ny;
+      i = hi ? g.nx - 1 : 0;
+    } else if (axis == 1) {
+      i = t % g.nx;
+      k = t / g.nx;
+      j = hi ? g.ny - 1 : 0;
+    } else {
+      i = t % g.nx;
+      j = t / g.nx;
+      k = hi ? g.nz - 1 : 0;
+    }
+    out[t] = field[i + (long long)g.nx * (j + (long long)g.ny * k)];
+  }
+}
+
 __global__ void k_saturation(long long n, SoilP so, const double* __restrict__ p, double* __restrict__ s) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
@@ -47,8 +72,9 @@ __global__ void k_saturation(long long n, SoilP so, const double* __restrict__ p
 // Neighbour data of face f of cell (i,j,k).  Returns false for a no-flux boundary face.
 struct FaceNb {
   double p, K, dK;
-  long long idx;   // -1 for a Dirichlet ghost
+  long long idx;   // -1 for a Dirichlet ghost, kInterfaceGhost for a neighbouring subdomain's cell
 };
+constexpr long long kInterfaceGhost = -2;
 
 __device__ __forceinline__ bool face_neighbour(const GridP& g, const BCP& bc, const SoilP& so, int f, int i, int j,
                                                int k, long long c, const double* __restrict__ p,
@@ -63,6 +89,14 @@ __device__ __forceinline__ bool face_neighbour(const GridP& g, const BCP& bc, co
   if (bnd) {
     if (bc.kind[f] == RICH_BC_NOFLUX) return false;
     nb.p = bc_value(bc, f, i, j, k, g.nx, g.ny);
+    if (bc.kind[f] == RICH_BC_INTERFACE) {  // a cell of the neighbouring subdomain, with its own K_s
+      const double* gk = bc.gks[f];
+      double s_, ds_;
+      constit(nb.p, gk ? gk[face_index(f, i, j, k, g.nx, g.ny)] : so.ks, so, s_, ds_, nb.K, nb.dK);
+      if (!dK) nb.dK = 0.0;
+      nb.idx = kInterfaceGhost;
+      return true;
+    }
     nb.K = conductivity_only(nb.p, ksc, so);
     nb.dK = 0.0;
     nb.idx = -1;
@@ -169,7 +203,7 @@ __global__ void k_assemble(GridP g, SoilP so, BCP bc, int kmean, const double* _
         }
         dj += dd;
         da += w;
-        if (nb.idx >= 0) {
+        if (nb.idx >= 0 || nb.idx == kInterfaceGhost) {  // a Dirichlet ghost is no unknown
           offj = off;
           offa = -w;
         }
@@ -397,8 +431,11 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   if (!kmean_valid(kmean) || (precision != RICH_PREC_FP64 && precision != RICH_PREC_MIXED)) return RICH_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   if (n > 2147483647LL / 8) return RICH_ELIMIT;  // 32-bit CSR indices of the 7-point pattern
-  for (int f = 0; f < 6; ++f)
-    if (bc->kind[f] != RICH_BC_NOFLUX && bc->kind[f] != RICH_BC_DIRICHLET) return RICH_EINVAL;
+  for (int f = 0; f < 6; ++f) {
+    if (bc->kind[f] != RICH_BC_NOFLUX && bc->kind[f] != RICH_BC_DIRICHLET && bc->kind[f] != RICH_BC_INTERFACE)
+      return RICH_EINVAL;
+    if (bc->kind[f] == RICH_BC_INTERFACE && !bc->value_field_dev[f]) return RICH_EINVAL;  // ghost pressures
+  }
   rich_ctx* c = new rich_ctx();
   c->g.nx = grid->nx;
   c->g.ny = grid->ny;
@@ -416,6 +453,7 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
     c->bc.kind[f] = bc->kind[f];
     c->bc.value[f] = bc->value[f];
     c->bc.field[f] = nullptr;
+    c->bc.gks[f] = nullptr;
   }
   c->kmean = kmean;
   c->prec = precision;
@@ -456,6 +494,14 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
     if (cudaMemcpyAsync(dst, bc->value_field_dev[f], m * sizeof(double), cudaMemcpyDeviceToDevice, c->st) !=
         cudaSuccess)
       return fail(RICH_ECUDA);
+    if (bc->kind[f] != RICH_BC_INTERFACE || !bc->ghost_ks_dev[f]) continue;
+    double* gk = nullptr;
+    if ((s = dalloc(&gk, m))) return fail(s);
+    c->bc_gks[f] = gk;
+    c->bc.gks[f] = gk;
+    if (cudaMemcpyAsync(gk, bc->ghost_ks_dev[f], m * sizeof(double), cudaMemcpyDeviceToDevice, c->st) !=
+        cudaSuccess)
+      return fail(RICH_ECUDA);
   }
   if ((s = build_a0_pattern(c))) return fail(s);
   *out = c;
@@ -488,7 +534,10 @@ int rich_destroy(rich_ctx* c) {
   dfree(c->rhs);
   dfree(c->pbuf);
   dfree(c->psave);
-  for (int f = 0; f < 6; ++f) dfree(c->bc_fields[f]);
+  for (int f = 0; f < 6; ++f) {
+    dfree(c->bc_fields[f]);
+    dfree(c->bc_gks[f]);
+  }
   KrylovWork& k = c->kw;
   dfree(k.V);
   dfree(k.Z);
@@ -502,6 +551,26 @@ int rich_destroy(rich_ctx* c) {
   dfree(k.hcoef);
   pinned_put(c->hsc);
   delete c;
+  return RICH_OK;
+}
+
+int rich_pack_face(rich_ctx* c, int face, const double* field, double* out) {
+  if (!c || face < 0 || face > 5 || !field || !out) return RICH_EINVAL;
+  const int axis = face >> 1;
+  const long long m = axis == 2 ? (long long)c->g.nx * c->g.ny
+                                : (axis == 1 ? (long long)c->g.nx * c->g.nz : (long long)c->g.ny * c->g.nz);
+  k_pack_face<<<grid_for(m), kBlock, 0, c->st>>>(c->g, face, m, field, out);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+int rich_set_face_values(rich_ctx* c, int face, const double* values) {
+  if (!c || face < 0 || face > 5 || !values) return RICH_EINVAL;
+  if (!c->bc_fields[face]) return RICH_ESTATE;
+  const int axis = face >> 1;
+  const long long m = axis == 2 ? (long long)c->g.nx * c->g.ny
+                                : (axis == 1 ? (long long)c->g.nx * c->g.nz : (long long)c->g.ny * c->g.nz);
+  RICH_CUDA(cudaMemcpyAsync(c->bc_fields[face], values, m * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   return RICH_OK;
 }
 

@@ -19,6 +19,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 AGG_MIS2, AGG_MATCHING = 0, 1
 SMOOTH_L1JACOBI, SMOOTH_HYBRID_GS = 0, 1
 PRECOND_AMG, PRECOND_AS = 0, 1
+BC_NOFLUX, BC_DIRICHLET, BC_INTERFACE = 0, 1, 2
 LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_SELL, LAYOUT_SELL8, LAYOUT_SELL2, LAYOUT_SELLP = 0, 1, 2, 3, 4, 5
 UNROLL, SELL_VARIANT, SELL_VARIANT8, SELL_VARIANT2, SELL_VARIANTP = 0x100, 0x200, 0x201, 0x202, 0x203
 
@@ -47,22 +48,26 @@ class Soil(ctypes.Structure):
 
 
 class BC(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int * 6), ("value", ctypes.c_double * 6), ("value_field_dev", ctypes.c_void_p * 6)]
+    _fields_ = [("kind", ctypes.c_int * 6), ("value", ctypes.c_double * 6), ("value_field_dev", ctypes.c_void_p * 6),
+                ("ghost_ks_dev", ctypes.c_void_p * 6)]
 
 
 def _bc_struct(bc, keep):
-    """ctypes BC; per-face value arrays are uploaded to device tensors kept in `keep`."""
+    """ctypes BC; per-face value arrays (and the ghost K_s of interface faces) are
+    uploaded to device tensors kept in `keep`."""
     import torch
-    ptrs = []
-    for f in range(6):
-        fld = bc.field(f) if hasattr(bc, "field") else None
-        if fld is None:
-            ptrs.append(None)
-        else:
-            t = torch.as_tensor(fld, dtype=torch.float64).reshape(-1).cuda().contiguous()
-            keep.append(t)
-            ptrs.append(t.data_ptr())
-    return BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value), (ctypes.c_void_p * 6)(*ptrs))
+
+    def upload(arr):
+        if arr is None:
+            return None
+        t = torch.as_tensor(arr, dtype=torch.float64).reshape(-1).cuda().contiguous()
+        keep.append(t)
+        return t.data_ptr()
+
+    ptrs = [upload(bc.field(f) if hasattr(bc, "field") else None) for f in range(6)]
+    gks = [upload(bc.ghost_ks_field(f) if hasattr(bc, "ghost_ks_field") else None) for f in range(6)]
+    return BC((ctypes.c_int * 6)(*bc.kind), (ctypes.c_double * 6)(*bc.value), (ctypes.c_void_p * 6)(*ptrs),
+              (ctypes.c_void_p * 6)(*gks))
 
 
 class AmgOpts(ctypes.Structure):
@@ -146,6 +151,8 @@ EXPORTS = {
     "rich_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rich_autotune_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "rich_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "rich_set_face_values": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "rich_pack_face": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "rich_sell_layout": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -308,6 +315,15 @@ class Context:
 
     def saturation(self, p, s):
         check(load().rich_saturation(self.h, _ptr(p), _ptr(s)), "rich_saturation")
+
+    def pack_face(self, face, field, out):
+        """out = the cells of `field` next to face `face`, in the face layout (device)."""
+        check(load().rich_pack_face(self.h, face, _ptr(field), _ptr(out)), "rich_pack_face")
+
+    def set_face_values(self, face, values):
+        """Per-cell values of a face created with a field (Dirichlet values, or the
+        ghost pressures of an interface face), from a float64 CUDA tensor."""
+        check(load().rich_set_face_values(self.h, face, _ptr(values)), "rich_set_face_values")
 
     def residual(self, p, s_old, dt, F, norms=True):
         arr = (ctypes.c_double * 2)() if norms else None
