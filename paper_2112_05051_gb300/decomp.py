@@ -1,0 +1,249 @@
+"""Slab decomposition of the grid (Sec. 5.1): 2D x-y blocks with full z-columns.
+
+The paper distributes the domain over processes by a block decomposition in
+the horizontal plane, every process owning whole vertical columns, and
+exchanges a one-cell halo before each residual evaluation.  Here each block is a
+grid of its own (`rich_create`), with the spacing of the whole grid, whose faces
+towards a neighbouring block are `RICH_BC_INTERFACE` faces: the ghost behind
+such a face is the neighbour's boundary cell, with the neighbour's K_s (known
+from the input) and the neighbour's current pressure (refreshed by a halo
+exchange before every residual).  Faces on the boundary of the whole grid keep
+its boundary condition, per-cell values sliced to the block.  With that, a
+block's residual and its rows of J and A_aux are those of the whole grid.
+
+The exchange packs the cells next to each interface face with the library's
+face-pack kernel and hands them to the neighbour: between ranks through
+`torch.distributed` point-to-point messages (one rank per block), or, for
+blocks held by one process, by copies between their buffers.
+"""
+import dataclasses
+from typing import List, Tuple
+
+FACES = 6  # x-, x+, y-, y+, z-, z+
+
+
+@dataclasses.dataclass(frozen=True)
+class Block:
+    rank: int
+    i0: int  # cells [i0, i1) x [j0, j1) x all k of the whole grid
+    i1: int
+    j0: int
+    j1: int
+    nbr: Tuple[int, int, int, int, int, int]  # neighbour rank behind each face, -1 on the grid boundary
+
+
+def _split(n, parts):
+    base, extra = divmod(n, parts)
+    edges = [0]
+    for q in range(parts):
+        edges.append(edges[-1] + base + (1 if q < extra else 0))
+    return edges
+
+
+def partition(grid, px, py) -> List[Block]:
+    """px x py blocks of nearly equal size (the first n % p parts one cell wider);
+    rank = bx + px * by."""
+    if px < 1 or py < 1 or px > grid.nx or py > grid.ny:
+        raise ValueError("a %d x %d split of a %d x %d grid" % (px, py, grid.nx, grid.ny))
+    ex, ey = _split(grid.nx, px), _split(grid.ny, py)
+    out = []
+    for by in range(py):
+        for bx in range(px):
+            r = bx + px * by
+            nbr = (r - 1 if bx > 0 else -1, r + 1 if bx < px - 1 else -1,
+                   r - px if by > 0 else -1, r + px if by < py - 1 else -1, -1, -1)
+            out.append(Block(r, ex[bx], ex[bx + 1], ey[by], ey[by + 1], nbr))
+    return out
+
+
+def sub_grid(grid, b):
+    """The block as a grid of its own with the whole grid's spacing (h = L / (n + 1))."""
+    from paper_2112_05051_gb300 import synth
+    hx, hy, hz = grid.h
+    nx, ny = b.i1 - b.i0, b.j1 - b.j0
+    return synth.Grid(nx, ny, grid.nz, hx * (nx + 1), hy * (ny + 1), grid.lz)
+
+
+def face_cells(grid, f):
+    """Cells of face f of a grid: ny nz on x faces, nx nz on y faces, nx ny on z faces."""
+    axis = f >> 1
+    return grid.ny * grid.nz if axis == 0 else (grid.nx * grid.nz if axis == 1 else grid.nx * grid.ny)
+
+
+def cell_block(a3, b):
+    """The block's cells of a whole-grid array of shape (nz, ny, nx)."""
+    return a3[:, b.j0:b.j1, b.i0:b.i1]
+
+
+def _face_slice(a2, f, b):
+    """The block's part of a whole-grid per-cell face array (flat face layout)."""
+    axis = f >> 1
+    return a2[:, b.j0:b.j1] if axis == 0 else (a2[:, b.i0:b.i1] if axis == 1 else a2[b.j0:b.j1, b.i0:b.i1])
+
+
+def ghost_plane(a3, b, f):
+    """The whole-grid cells behind interface face f of block b, in the face layout
+    (x faces: j + ny k, y faces: i + nx k): the ghosts of that face."""
+    if f == 0:
+        return a3[:, b.j0:b.j1, b.i0 - 1]
+    if f == 1:
+        return a3[:, b.j0:b.j1, b.i1]
+    if f == 2:
+        return a3[:, b.j0 - 1, b.i0:b.i1]
+    if f == 3:
+        return a3[:, b.j1, b.i0:b.i1]
+    raise ValueError("blocks have no interface on the z faces")
+
+
+@dataclasses.dataclass(frozen=True)
+class BlockBC:
+    """Boundary conditions of a block: the whole grid's on its outer faces (per-cell
+    values sliced), interface faces towards its neighbours."""
+    kind: Tuple[int, int, int, int, int, int]
+    value: Tuple[float, float, float, float, float, float]
+    fields: Tuple
+    ghost_ks: Tuple
+
+    def field(self, f):
+        return self.fields[f]
+
+    def ghost_ks_field(self, f):
+        return self.ghost_ks[f]
+
+
+def block_bc(grid, bc, b, ks=None):
+    """BlockBC of block b: whole-grid bc on the outer faces; on interface faces a
+    placeholder ghost pressure (set by the first exchange) and the ghost K_s
+    (ks: whole-grid K_s, flat in cell order, or None for a constant K_s)."""
+    import numpy as np
+    from paper_2112_05051_gb300 import richards as rb
+    sg = sub_grid(grid, b)
+    k3 = None if ks is None else np.asarray(ks, dtype=np.float64).reshape(grid.shape)
+    shapes = [(grid.nz, grid.ny), (grid.nz, grid.ny), (grid.nz, grid.nx), (grid.nz, grid.nx),
+              (grid.ny, grid.nx), (grid.ny, grid.nx)]
+    kind, value, fields, gks = [], [], [], []
+    for f in range(FACES):
+        if b.nbr[f] >= 0:
+            kind.append(rb.BC_INTERFACE)
+            value.append(0.0)
+            fields.append(np.zeros(face_cells(sg, f)))
+            gks.append(None if k3 is None else np.ascontiguousarray(ghost_plane(k3, b, f)).ravel())
+        else:
+            kind.append(bc.kind[f])
+            value.append(bc.value[f])
+            fld = bc.field(f) if hasattr(bc, "field") else None
+            if fld is not None:
+                fld = np.ascontiguousarray(_face_slice(np.asarray(fld).reshape(shapes[f]), f, b)).ravel()
+            fields.append(fld)
+            gks.append(None)
+    return BlockBC(tuple(kind), tuple(value), tuple(fields), tuple(gks))
+
+
+class Halo:
+    """Halo exchange of one cell field between the blocks of a partition.
+
+    ``pack(f, out)`` must write the cells of the local field next to face f into
+    ``out`` (the face layout); ``apply(f, ghosts)`` receives the neighbour's cells
+    behind face f.  The neighbour behind face f packs its opposite face f ^ 1, and
+    the two index their face arrays the same way (a tensor-product partition: the
+    blocks on either side of an x interface share their j range, of a y interface
+    their i range).
+    """
+
+    def __init__(self, blocks, rank):
+        self.blocks = blocks
+        self.block = blocks[rank]
+
+    def exchange(self, dist, pack, apply, buffers):
+        """Point-to-point exchange with the neighbour ranks (torch.distributed):
+        buffers[f] = (send, recv) tensors of face f's size on the backend's device."""
+        reqs = []
+        for f in range(FACES):
+            r = self.block.nbr[f]
+            if r < 0:
+                continue
+            send, recv = buffers[f]
+            pack(f, send)
+            reqs.append(dist.isend(send, r, tag=f))       # my face f is the neighbour's face f ^ 1
+            reqs.append(dist.irecv(recv, r, tag=f ^ 1))
+        for q in reqs:
+            q.wait()
+        for f in range(FACES):
+            if self.block.nbr[f] >= 0:
+                apply(f, buffers[f][1])
+
+
+def exchange_local(blocks, packs, applies, buffers):
+    """The same exchange for blocks held by one process: packs[r](f, out) and
+    applies[r](f, ghosts) of every block, buffers[r][f] = (send, recv)."""
+    for b in blocks:
+        for f in range(FACES):
+            if b.nbr[f] >= 0:
+                packs[b.rank](f, buffers[b.rank][f][0])
+    for b in blocks:
+        for f in range(FACES):
+            r = b.nbr[f]
+            if r >= 0:
+                recv = buffers[b.rank][f][1]
+                recv.copy_(buffers[r][f ^ 1][0])
+                applies[b.rank](f, recv)
+
+
+class BlockProblem:
+    """One block of a partition as a context of its own, with the halo exchange of
+    its pressure before each residual.
+
+    grid, soil, bc, kmean, ks: the whole problem (ks flat in cell order or None);
+    blocks, rank: the partition and this block.  Cell arrays of the block are in
+    its own order (i fastest over its nx, then j over its ny, then k).
+    """
+
+    def __init__(self, grid, soil, bc, kmean, ks, blocks, rank, precision=0):
+        import numpy as np
+        import torch
+        from paper_2112_05051_gb300 import richards as rb
+        self.block = blocks[rank]
+        self.grid = sub_grid(grid, self.block)
+        ks_b = None
+        if ks is not None:
+            ks_b = np.ascontiguousarray(cell_block(np.asarray(ks).reshape(grid.shape), self.block)).ravel()
+        self.ctx = rb.Context(self.grid, soil, block_bc(grid, bc, self.block, ks), kmean, ks_b, precision=precision)
+        self.halo = Halo(blocks, rank)
+        self.buffers = {}
+        for f in range(FACES):
+            if self.block.nbr[f] >= 0:
+                m = face_cells(self.grid, f)
+                self.buffers[f] = (torch.empty(m, dtype=torch.float64, device="cuda"),
+                                   torch.empty(m, dtype=torch.float64, device="cuda"))
+
+    def pack(self, field):
+        return lambda f, out: self.ctx.pack_face(f, field, out)
+
+    def apply(self, f, ghosts):
+        self.ctx.set_face_values(f, ghosts)
+
+    def exchange(self, dist, p):
+        """Ghost pressures from the neighbour ranks (one rank per block)."""
+        self.halo.exchange(dist, self.pack(p), self.apply, self.buffers)
+
+    def residual(self, p, s_old, dt, F):
+        """Phi of the block (after an exchange); returns (sum of Phi^2, max |Phi|),
+        the pieces of the whole grid's norms."""
+        n2, ninf = self.ctx.residual(p, s_old, dt, F)
+        return n2 * n2, ninf
+
+    def close(self):
+        self.ctx.close()
+
+
+def exchange_blocks(problems, fields):
+    """Halo exchange of one field among blocks held by this process
+    (problems[r], fields[r]: block r and its cell field)."""
+    exchange_local([q.block for q in problems], [q.pack(x) for q, x in zip(problems, fields)],
+                   [q.apply for q in problems], [q.buffers for q in problems])
+
+
+def combine_norms(parts):
+    """(||Phi||_2, ||Phi||_inf) of the whole grid from the blocks' (sum of squares, max)."""
+    import math
+    return math.sqrt(sum(p[0] for p in parts)), max(p[1] for p in parts)

@@ -1,0 +1,123 @@
+"""Slab decomposition on the GPU (Sec. 5.1): the blocks of a split grid, each a
+context of its own with interface faces, run one after another on one device
+(no kernel waits on another block: the host exchanges the halos between the
+launches), reproduce the whole grid.
+
+* the face-pack kernel writes the cells next to a face in the face layout;
+* after a halo exchange of p, the blocks' residuals put together are the whole
+  grid's residual bit for bit (the interface ghost's conductivity is evaluated
+  by the same constitutive code as an interior neighbour's), and the oracle's
+  within 1e-12; the whole grid's norms follow from the blocks' pieces;
+* the blocks' J and A_aux (7 planes each) are the whole grid's rows, the
+  couplings across an interface kept in the plane of that face.
+"""
+import numpy as np
+import pytest
+
+from oracle import constitutive as cst, discretization as disc
+from paper_2112_05051_gb300 import decomp, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SOIL = synth.Soil()
+
+
+def _rb():
+    from paper_2112_05051_gb300 import richards as rb
+    rb.load()
+    return rb
+
+
+def _state(grid, seed):
+    rng = np.random.default_rng(seed)
+    z = (np.arange(grid.nz) + 1.0) / (grid.nz + 1)
+    front = -61.5 + 40.8 * np.exp(-(1.0 - z) / 0.2)
+    p = np.broadcast_to(front[:, None, None], grid.shape).ravel() + rng.uniform(-0.5, 0.5, grid.n)
+    return p
+
+
+def _blocks_of(a, grid, blocks):
+    a3 = np.asarray(a).reshape(grid.shape)
+    return [np.ascontiguousarray(decomp.cell_block(a3, b)).ravel() for b in blocks]
+
+
+def _whole(parts, grid, blocks, planes=1):
+    out = np.empty((planes,) + grid.shape)
+    for b, x in zip(blocks, parts):
+        out[:, :, b.j0:b.j1, b.i0:b.i1] = x.reshape((planes, grid.nz, b.j1 - b.j0, b.i1 - b.i0))
+    return out.reshape(planes, -1) if planes > 1 else out.ravel()
+
+
+def test_pack_face_kernel_layout():
+    rb = _rb()
+    grid = synth.Grid(7, 5, 4)
+    ctx = rb.Context(grid, SOIL, synth.infiltration_bc(), 0, None)
+    a3 = np.arange(grid.n, dtype=np.float64).reshape(grid.shape)
+    x = torch.tensor(a3.ravel(), device="cuda")
+    want = [a3[:, :, 0], a3[:, :, -1], a3[:, 0, :], a3[:, -1, :], a3[0], a3[-1]]
+    for f in range(6):
+        out = torch.empty(decomp.face_cells(grid, f), dtype=torch.float64, device="cuda")
+        ctx.pack_face(f, x, out)
+        np.testing.assert_array_equal(out.cpu().numpy(), want[f].ravel())
+    ctx.close()
+
+
+@pytest.mark.parametrize("px,py,kmean,paper_bc", [(2, 2, synth.KMEAN_UPSTREAM, False), (3, 1, synth.KMEAN_ARITH, True),
+                                                  (2, 3, synth.KMEAN_HARMONIC, False)])
+def test_blocks_reproduce_the_whole_grid(px, py, kmean, paper_bc):
+    rb = _rb()
+    grid = synth.Grid(24, 20, 12)
+    bc = synth.paper_infiltration_bc(grid, -30.0) if paper_bc else synth.infiltration_bc()
+    ks = synth.ks_field(grid, 8, 1.0, (3.0, 3.0, 2.0))
+    p = _state(grid, 5)
+    s_old = cst.saturation(p - 1.0, SOIL)
+    dt = 0.7
+    # the whole grid on the GPU and in the oracle
+    whole = rb.Context(grid, SOIL, bc, kmean, ks)
+    pd = torch.tensor(p, device="cuda")
+    F = torch.empty_like(pd)
+    n2, ninf = whole.residual(pd, torch.tensor(s_old, device="cuda"), dt, F)
+    Fw = F.cpu().numpy()
+    J7 = torch.empty(7 * grid.n, dtype=torch.float64, device="cuda")
+    A7 = torch.empty_like(J7)
+    whole.jacobian(pd, dt, J7, A7)
+    J7w, A7w = J7.cpu().numpy().reshape(7, -1), A7.cpu().numpy().reshape(7, -1)
+    whole.close()
+    ref = disc.residual(grid, SOIL, bc, kmean, p, s_old, dt, ks)
+    # the blocks, one context each, on this device
+    blocks = decomp.partition(grid, px, py)
+    probs = [decomp.BlockProblem(grid, SOIL, bc, kmean, ks, blocks, r) for r in range(len(blocks))]
+    pb = [torch.tensor(x, device="cuda") for x in _blocks_of(p, grid, blocks)]
+    sb = [torch.tensor(x, device="cuda") for x in _blocks_of(s_old, grid, blocks)]
+    decomp.exchange_blocks(probs, pb)
+    Fb, parts, Jb, Ab = [], [], [], []
+    for q, x, so in zip(probs, pb, sb):
+        f = torch.empty_like(x)
+        parts.append(q.residual(x, so, dt, f))
+        Fb.append(f.cpu().numpy())
+        jb = torch.empty(7 * x.numel(), dtype=torch.float64, device="cuda")
+        ab = torch.empty_like(jb)
+        q.ctx.jacobian(x, dt, jb, ab)
+        Jb.append(jb.cpu().numpy())
+        Ab.append(ab.cpu().numpy())
+        q.close()
+    Fs = _whole(Fb, grid, blocks)
+    np.testing.assert_array_equal(Fs, Fw)  # bit for bit
+    assert np.abs(Fs - ref).max() <= 1e-12 * np.abs(ref).max()
+    n2s, ninfs = decomp.combine_norms(parts)
+    assert abs(n2s - n2) <= 1e-13 * n2 and ninfs == ninf
+    np.testing.assert_array_equal(_whole(Jb, grid, blocks, 7), J7w)
+    np.testing.assert_array_equal(_whole(Ab, grid, blocks, 7), A7w)
+
+
+def test_interface_faces_need_their_ghost_pressures():
+    rb = _rb()
+    grid = synth.Grid(6, 6, 4)
+    bad = synth.BC(kind=(rb.BC_INTERFACE, 0, 0, 0, 0, 1), value=(0.0,) * 5 + (-20.0,))  # no per-cell field
+    with pytest.raises(rb.RichError):
+        rb.Context(grid, SOIL, bad, 0, None)
+    ctx = rb.Context(grid, SOIL, synth.infiltration_bc(), 0, None)
+    with pytest.raises(rb.RichError):  # the face was created without per-cell values
+        ctx.set_face_values(0, torch.zeros(grid.ny * grid.nz, dtype=torch.float64, device="cuda"))
+    ctx.close()
