@@ -135,6 +135,9 @@ extern "C" {
 typedef struct {
   int nx, ny, nz;          /* unknown cells per direction, each >= 1 */
   double lx, ly, lz;       /* box size (cm) */
+  double h[3];             /* cell spacing per axis (cm); 0 (the usual): l / (n + 1).  A block of a split
+                              grid gives its whole grid's spacing here, which l / (n + 1) of its own box
+                              cannot always reproduce to the last bit */
 } rich_grid;
 
 /* Celia/Haverkamp laws, eqs. (s(p)) and (K(p)) of Sec. 2:

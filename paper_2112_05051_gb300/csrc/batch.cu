@@ -434,7 +434,9 @@ int rich_create_batch(const rich_grid* grid, int nbatch, const rich_soil* soil, 
   for (int f = 0; f < 6; ++f)  // stacked problems are whole grids, not subdomains
     if (bc->kind[f] == RICH_BC_INTERFACE) return RICH_EINVAL;
   rich_grid g = *grid;
-  const double hz = grid->lz / (grid->nz + 1);
+  double hs[3];
+  grid_spacing(grid, hs);
+  const double hz = hs[2];
   g.nz = grid->nz * nbatch;
   g.lz = hz * (g.nz + 1);  // the stacked grid keeps the problems' spacing
   int s = rich_create(&g, soil, kmean, bc, precision, stream, out);

@@ -92,6 +92,13 @@ struct BCP {
   const double* gks[6];    // interface faces: per-cell K_s of the ghost cells, or nullptr (soil ks)
 };
 
+// Cell spacing of a grid: the explicit h[d] where given, else l / (n + 1).
+inline void grid_spacing(const rich_grid* g, double h[3]) {
+  h[0] = g->h[0] > 0 ? g->h[0] : g->lx / (g->nx + 1);
+  h[1] = g->h[1] > 0 ? g->h[1] : g->ly / (g->ny + 1);
+  h[2] = g->h[2] > 0 ? g->h[2] : g->lz / (g->nz + 1);
+}
+
 // Index of the boundary cell (i, j, k) in the per-cell arrays of face f.
 __device__ __forceinline__ long long face_index(int f, int i, int j, int k, int nx, int ny) {
   int axis = f >> 1;

@@ -147,7 +147,8 @@ extern "C" int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soi
                                      const double* p_dev, const double* s_old_dev, double dt, double* F_dev,
                                      double* norms_host, void* stream) {
   if (!grid || !soil || !bc || !p_dev || !s_old_dev || !F_dev || !(dt > 0)) return RICH_EINVAL;
-  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0 && grid->ly > 0 && grid->lz > 0))
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0 && grid->ly > 0 && grid->lz > 0) ||
+      !(grid->h[0] >= 0.0 && grid->h[1] >= 0.0 && grid->h[2] >= 0.0))
     return RICH_EINVAL;
   if (!kmean_valid(kmean)) return RICH_EINVAL;
   for (int f = 0; f < 6; ++f)
@@ -163,7 +164,8 @@ extern "C" int rich_residual_noalloc(const rich_grid* grid, const rich_soil* soi
   g.nz = grid->nz;
   g.nzs = grid->nz;
   g.n = n;
-  double h[3] = {grid->lx / (grid->nx + 1), grid->ly / (grid->ny + 1), grid->lz / (grid->nz + 1)};
+  double h[3];
+  grid_spacing(grid, h);
   for (int d = 0; d < 3; ++d) {
     g.inv_h[d] = 1.0 / h[d];
     g.inv_h2[d] = 1.0 / (h[d] * h[d]);

@@ -428,6 +428,8 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   *out = nullptr;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return RICH_EINVAL;
   if (!(grid->lx > 0 && grid->ly > 0 && grid->lz > 0)) return RICH_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!(grid->h[d] >= 0.0) || !std::isfinite(grid->h[d])) return RICH_EINVAL;
   if (!kmean_valid(kmean) || (precision != RICH_PREC_FP64 && precision != RICH_PREC_MIXED)) return RICH_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   if (n > 2147483647LL / 8) return RICH_ELIMIT;  // 32-bit CSR indices of the 7-point pattern
@@ -442,7 +444,8 @@ int rich_create(const rich_grid* grid, const rich_soil* soil, int kmean, const r
   c->g.nz = grid->nz;
   c->g.nzs = grid->nz;
   c->g.n = n;
-  double h[3] = {grid->lx / (grid->nx + 1), grid->ly / (grid->ny + 1), grid->lz / (grid->nz + 1)};
+  double h[3];
+  grid_spacing(grid, h);
   for (int d = 0; d < 3; ++d) {
     c->g.inv_h[d] = 1.0 / h[d];
     c->g.inv_h2[d] = 1.0 / (h[d] * h[d]);

@@ -97,6 +97,7 @@ static double srv_estimate(const rich_request& r) {
 static bool srv_same_shape(const rich_request& a, const rich_request& b) {
   if (a.grid.nx != b.grid.nx || a.grid.ny != b.grid.ny || a.grid.nz != b.grid.nz) return false;
   if (a.grid.lx != b.grid.lx || a.grid.ly != b.grid.ly || a.grid.lz != b.grid.lz) return false;
+  if (a.grid.h[0] != b.grid.h[0] || a.grid.h[1] != b.grid.h[1] || a.grid.h[2] != b.grid.h[2]) return false;
   if (a.kmean != b.kmean || a.precision != b.precision) return false;
   if (memcmp(a.bc.kind, b.bc.kind, sizeof(a.bc.kind)) || memcmp(a.bc.value, b.bc.value, sizeof(a.bc.value)))
     return false;

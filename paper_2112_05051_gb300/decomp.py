@@ -57,11 +57,12 @@ def partition(grid, px, py) -> List[Block]:
 
 
 def sub_grid(grid, b):
-    """The block as a grid of its own with the whole grid's spacing (h = L / (n + 1))."""
+    """The block as a grid of its own, carrying the whole grid's spacing explicitly
+    (its own box's l / (n + 1) need not reproduce h to the last bit)."""
     from paper_2112_05051_gb300 import synth
     hx, hy, hz = grid.h
     nx, ny = b.i1 - b.i0, b.j1 - b.j0
-    return synth.Grid(nx, ny, grid.nz, hx * (nx + 1), hy * (ny + 1), grid.lz)
+    return synth.Grid(nx, ny, grid.nz, hx * (nx + 1), hy * (ny + 1), grid.lz, spacing=(hx, hy, hz))
 
 
 def face_cells(grid, f):

@@ -38,7 +38,14 @@ class RichError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("h", ctypes.c_double * 3)]
+
+
+def _grid_struct(grid):
+    """ctypes Grid of a synth.Grid (its explicit spacing, if it has one)."""
+    sp = getattr(grid, "spacing", None)
+    return Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz, (ctypes.c_double * 3)(*(sp or (0.0, 0.0, 0.0))))
 
 
 class Soil(ctypes.Structure):
@@ -258,7 +265,7 @@ def residual_noalloc(grid, soil, bc, kmean, p, s_old, dt, F, ks=None, norms=True
     ks, if given, must be a contiguous float64 CUDA tensor of n cells (read in place).
     Returns the status code and (||Phi||_2, ||Phi||_inf) or None.
     """
-    g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+    g = _grid_struct(grid)
     s = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
              _ptr(ks) if ks is not None else None)
     keep = []
@@ -287,7 +294,7 @@ class Context:
                  precision=PREC_FP64):
         import torch
         lib = load()
-        g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        g = _grid_struct(grid)
         self._ks = None
         if ks is not None:
             self._ks = torch.as_tensor(ks, dtype=torch.float64).reshape(-1).cuda().contiguous()
@@ -412,7 +419,7 @@ class BatchContext(Context):
                  precision=PREC_MIXED):
         import torch
         lib = load()
-        g = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        g = _grid_struct(grid)
         self._ks = None
         if ks is not None:
             self._ks = torch.as_tensor(ks, dtype=torch.float64).reshape(-1).cuda().contiguous()
@@ -469,7 +476,7 @@ class Server:
         if any(bc.field(f) is not None for f in range(6)):
             raise ValueError("the request server takes constant boundary values only")
         r = Request()
-        r.grid = Grid(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        r.grid = _grid_struct(grid)
         r.soil = Soil(soil.alpha, soil.beta, soil.theta_s, soil.theta_r, soil.a, soil.gamma, soil.ks, soil.rho_phi,
                       None)
         keep = []

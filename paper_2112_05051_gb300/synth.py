@@ -86,6 +86,7 @@ class Grid:
     lx: float = 1.0
     ly: float = 1.0
     lz: float = 1.0
+    spacing: Optional[Tuple[float, float, float]] = None  # explicit (h_x, h_y, h_z), e.g. a block of a split grid
 
     @property
     def n(self) -> int:
@@ -98,6 +99,8 @@ class Grid:
 
     @property
     def h(self) -> Tuple[float, float, float]:
+        if self.spacing is not None:
+            return tuple(self.spacing)
         return (self.lx / (self.nx + 1), self.ly / (self.ny + 1), self.lz / (self.nz + 1))
 
 

@@ -45,12 +45,17 @@ def test_partition_covers_the_grid_once_with_symmetric_neighbours():
         decomp.partition(grid, 24, 1)
 
 
-def test_sub_grid_keeps_the_spacing():
-    grid = synth.Grid(23, 17, 5, 3.0, 2.0, 1.5)
-    for b in decomp.partition(grid, 3, 2):
-        sg = decomp.sub_grid(grid, b)
-        assert (sg.nx, sg.ny, sg.nz) == (b.i1 - b.i0, b.j1 - b.j0, grid.nz)
-        np.testing.assert_allclose(sg.h, grid.h, rtol=1e-15)
+def test_sub_grid_keeps_the_spacing_bit_for_bit():
+    # the library derives h = L / (n + 1); a block's h must be the whole grid's exactly,
+    # or every flux of the block rounds differently
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        grid = synth.Grid(int(rng.integers(3, 300)), int(rng.integers(3, 300)), 5, float(rng.uniform(0.1, 1e3)),
+                          float(rng.uniform(0.1, 1e3)), 1.5)
+        for b in decomp.partition(grid, min(3, grid.nx), min(2, grid.ny)):
+            sg = decomp.sub_grid(grid, b)
+            assert (sg.nx, sg.ny, sg.nz) == (b.i1 - b.i0, b.j1 - b.j0, grid.nz)
+            assert sg.h == grid.h  # carried explicitly: l / (n + 1) of the block's box need not give it
 
 
 def _pack(l3, f):
