@@ -308,6 +308,13 @@ int rich_set_face_values(rich_ctx* ctx, int face, const double* values_dev);
  * in the layout of the per-cell face arrays.  Device pointers; the context's
  * stream; out_dev holds the face's cell count. */
 int rich_pack_face(rich_ctx* ctx, int face, const double* field_dev, double* out_dev);
+/* y_dev[c] += M[c, ghost t] ghost_dev[t] over the cells c next to interface face f:
+ * the coupling to the neighbouring subdomain's cells that the context's current J
+ * (which = 0) or A_aux (which = 1) keeps in the plane of face f.  After
+ * rich_jacobian_apply on the subdomain's own cells, one call per interface face
+ * with the neighbour's x (a halo exchange of x) gives the split grid's J x.
+ * RICH_EINVAL unless face is an interface face; RICH_ESTATE before rich_jacobian. */
+int rich_face_apply(rich_ctx* ctx, int face, int which, const double* ghost_dev, double* y_dev);
 
 /* ---- Sec. 2: constitutive law and residual ----------------------------- */
 /* s_dev[c] = s(p_dev[c]) (eq. (s(p))).  Used for s(p^{l-1}) of a step. */

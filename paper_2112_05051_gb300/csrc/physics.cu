@@ -60,6 +60,33 @@ __global__ void k_pack_face(GridP g, int f, long long m, const double* __restric
   }
 }
 
+// y[c] += M_f[c] ghost[t] for the cells c next to face f (t their face index): the
+// coupling of a subdomain's face cells to its neighbour's cells, kept in plane f of
+// the 7-plane stencil M.
+__global__ void k_face_apply(GridP g, int f, long long m, const double* __restrict__ M,
+                             const double* __restrict__ ghost, double* __restrict__ y) {
+  const int axis = f >> 1;
+  const bool hi = f & 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m; t += (long long)gridDim.x * blockDim.x) {
+    long long i, j, k;
+    if (axis == 0) {
+      j = t % g.ny;
+      k = t / g.ny;
+      i = hi ? g.nx - 1 : 0;
+    } else if (axis == 1) {
+      i = t % g.nx;
+      k = t / g.nx;
+      j = hi ? g.ny - 1 : 0;
+    } else {
+      i = t % g.nx;
+      j = t / g.nx;
+      k = hi ? g.nz - 1 : 0;
+    }
+    const long long c = i + (long long)g.nx * (j + (long long)g.ny * k);
+    y[c] += M[(1 + f) * g.n + c] * ghost[t];
+  }
+}
+
 __global__ void k_saturation(long long n, SoilP so, const double* __restrict__ p, double* __restrict__ s) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
@@ -563,6 +590,18 @@ int rich_pack_face(rich_ctx* c, int face, const double* field, double* out) {
   const long long m = axis == 2 ? (long long)c->g.nx * c->g.ny
                                 : (axis == 1 ? (long long)c->g.nx * c->g.nz : (long long)c->g.ny * c->g.nz);
   k_pack_face<<<grid_for(m), kBlock, 0, c->st>>>(c->g, face, m, field, out);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
+
+int rich_face_apply(rich_ctx* c, int face, int which, const double* ghost, double* y) {
+  if (!c || face < 0 || face > 5 || (which != 0 && which != 1) || !ghost || !y) return RICH_EINVAL;
+  if (c->bc.kind[face] != RICH_BC_INTERFACE) return RICH_EINVAL;
+  if (!c->have_jac) return RICH_ESTATE;
+  const int axis = face >> 1;
+  const long long m = axis == 2 ? (long long)c->g.nx * c->g.ny
+                                : (axis == 1 ? (long long)c->g.nx * c->g.nz : (long long)c->g.ny * c->g.nz);
+  k_face_apply<<<grid_for(m), kBlock, 0, c->st>>>(c->g, face, m, which ? c->A7 : c->J7, ghost, y);
   RICH_LAUNCH_CHECK();
   return RICH_OK;
 }

@@ -227,6 +227,16 @@ class BlockProblem:
         """Ghost pressures from the neighbour ranks (one rank per block)."""
         self.halo.exchange(dist, self.pack(p), self.apply, self.buffers)
 
+    def couple(self, which, y):
+        """The apply of a halo exchange of x that adds the block's interface couplings
+        in J (which = 0) or A_aux (which = 1) times the neighbour's x to y."""
+        return lambda f, ghosts: self.ctx.face_apply(f, which, ghosts, y)
+
+    def apply_J(self, dist, x, y):
+        """y = J x of the split grid, this block's rows (one rank per block)."""
+        self.ctx.jacobian_apply(x, y)
+        self.halo.exchange(dist, self.pack(x), self.couple(0, y), self.buffers)
+
     def residual(self, p, s_old, dt, F):
         """Phi of the block (after an exchange); returns (sum of Phi^2, max |Phi|),
         the pieces of the whole grid's norms."""
@@ -237,11 +247,20 @@ class BlockProblem:
         self.ctx.close()
 
 
-def exchange_blocks(problems, fields):
+def exchange_blocks(problems, fields, applies=None):
     """Halo exchange of one field among blocks held by this process
-    (problems[r], fields[r]: block r and its cell field)."""
+    (problems[r], fields[r]: block r and its cell field; applies[r](f, ghosts):
+    what block r does with the neighbour's cells behind face f, by default they
+    become the ghost pressures of its interface faces)."""
     exchange_local([q.block for q in problems], [q.pack(x) for q, x in zip(problems, fields)],
-                   [q.apply for q in problems], [q.buffers for q in problems])
+                   applies or [q.apply for q in problems], [q.buffers for q in problems])
+
+
+def apply_J_blocks(problems, xs, ys):
+    """ys[r] = J x of the split grid on block r, for blocks held by this process."""
+    for q, x, y in zip(problems, xs, ys):
+        q.ctx.jacobian_apply(x, y)
+    exchange_blocks(problems, xs, [q.couple(0, y) for q, y in zip(problems, ys)])
 
 
 def combine_norms(parts):

@@ -160,6 +160,7 @@ EXPORTS = {
     "rich_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_set_face_values": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "rich_pack_face": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "rich_face_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "rich_sell_layout": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -326,6 +327,10 @@ class Context:
     def pack_face(self, face, field, out):
         """out = the cells of `field` next to face `face`, in the face layout (device)."""
         check(load().rich_pack_face(self.h, face, _ptr(field), _ptr(out)), "rich_pack_face")
+
+    def face_apply(self, face, which, ghost, y):
+        """y += (J if which == 0 else A_aux) coupling of interface face `face` times ghost."""
+        check(load().rich_face_apply(self.h, face, which, _ptr(ghost), _ptr(y)), "rich_face_apply")
 
     def set_face_values(self, face, values):
         """Per-cell values of a face created with a field (Dirichlet values, or the

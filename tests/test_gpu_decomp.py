@@ -9,7 +9,10 @@ launches), reproduce the whole grid.
   by the same constitutive code as an interior neighbour's), and the oracle's
   within 1e-12; the whole grid's norms follow from the blocks' pieces;
 * the blocks' J and A_aux (7 planes each) are the whole grid's rows, the
-  couplings across an interface kept in the plane of that face.
+  couplings across an interface kept in the plane of that face;
+* J x of the split grid (each block's stencil SpMV plus its interface couplings
+  times the neighbours' x after a halo exchange of x) is the whole grid's J x
+  within 1e-14 (the terms are summed in another order).
 """
 import numpy as np
 import pytest
@@ -83,6 +86,10 @@ def test_blocks_reproduce_the_whole_grid(px, py, kmean, paper_bc):
     A7 = torch.empty_like(J7)
     whole.jacobian(pd, dt, J7, A7)
     J7w, A7w = J7.cpu().numpy().reshape(7, -1), A7.cpu().numpy().reshape(7, -1)
+    x = np.random.default_rng(11).standard_normal(grid.n)
+    yw = torch.empty_like(pd)
+    whole.jacobian_apply(torch.tensor(x, device="cuda"), yw)
+    yw = yw.cpu().numpy()
     whole.close()
     ref = disc.residual(grid, SOIL, bc, kmean, p, s_old, dt, ks)
     # the blocks, one context each, on this device
@@ -92,15 +99,36 @@ def test_blocks_reproduce_the_whole_grid(px, py, kmean, paper_bc):
     sb = [torch.tensor(x, device="cuda") for x in _blocks_of(s_old, grid, blocks)]
     decomp.exchange_blocks(probs, pb)
     Fb, parts, Jb, Ab = [], [], [], []
-    for q, x, so in zip(probs, pb, sb):
-        f = torch.empty_like(x)
-        parts.append(q.residual(x, so, dt, f))
+    for q, pq, so in zip(probs, pb, sb):
+        f = torch.empty_like(pq)
+        parts.append(q.residual(pq, so, dt, f))
         Fb.append(f.cpu().numpy())
-        jb = torch.empty(7 * x.numel(), dtype=torch.float64, device="cuda")
+        jb = torch.empty(7 * pq.numel(), dtype=torch.float64, device="cuda")
         ab = torch.empty_like(jb)
-        q.ctx.jacobian(x, dt, jb, ab)
+        q.ctx.jacobian(pq, dt, jb, ab)
         Jb.append(jb.cpu().numpy())
         Ab.append(ab.cpu().numpy())
+    # J x of the split grid: local stencil SpMV, then the interface couplings times
+    # the neighbours' x after a halo exchange of x
+    xb = [torch.tensor(v, device="cuda") for v in _blocks_of(x, grid, blocks)]
+    yb = [torch.empty_like(v) for v in xb]
+    decomp.apply_J_blocks(probs, xb, yb)
+    ys = _whole([y.cpu().numpy() for y in yb], grid, blocks)
+    assert np.abs(ys - yw).max() <= 1e-14 * np.abs(yw).max()
+    # the A_aux coupling of one interface face alone: plane f of A_aux times the ghosts
+    q, b = probs[0], blocks[0]
+    f = next(f for f in range(4) if b.nbr[f] >= 0)
+    ghost = torch.tensor(np.ascontiguousarray(decomp.ghost_plane(x.reshape(grid.shape), b, f)).ravel(), device="cuda")
+    y0 = torch.zeros_like(xb[0])
+    q.ctx.face_apply(f, 1, ghost, y0)
+    sg = q.grid
+    a3 = Ab[0].reshape(7, sg.nz, sg.ny, sg.nx)[1 + f]
+    face = [a3[:, :, 0], a3[:, :, -1], a3[:, 0, :], a3[:, -1, :]][f].ravel() * ghost.cpu().numpy()
+    y03 = y0.cpu().numpy().reshape(sg.nz, sg.ny, sg.nx)
+    got = [y03[:, :, 0], y03[:, :, -1], y03[:, 0, :], y03[:, -1, :]][f].ravel()
+    np.testing.assert_array_equal(got, face)
+    assert np.count_nonzero(y03) == np.count_nonzero(got)  # nothing but the face cells
+    for q in probs:
         q.close()
     Fs = _whole(Fb, grid, blocks)
     np.testing.assert_array_equal(Fs, Fw)  # bit for bit
