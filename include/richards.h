@@ -315,6 +315,12 @@ int rich_pack_face(rich_ctx* ctx, int face, const double* field_dev, double* out
  * with the neighbour's x (a halo exchange of x) gives the split grid's J x.
  * RICH_EINVAL unless face is an interface face; RICH_ESTATE before rich_jacobian. */
 int rich_face_apply(rich_ctx* ctx, int face, int which, const double* ghost_dev, double* y_dev);
+/* Vector operations on the context's cells, for drivers above the library (the
+ * split grid's Krylov method): *out_host = x . y (device vectors of n doubles,
+ * the library's fixed-order reduction; synchronises), and y = a x + b y (y = a x
+ * when b == 0).  On the context's stream. */
+int rich_vec_dot(rich_ctx* ctx, const double* x_dev, const double* y_dev, double* out_host);
+int rich_vec_axpby(rich_ctx* ctx, double a, const double* x_dev, double b, double* y_dev);
 
 /* ---- Sec. 2: constitutive law and residual ----------------------------- */
 /* s_dev[c] = s(p_dev[c]) (eq. (s(p))).  Used for s(p^{l-1}) of a step. */

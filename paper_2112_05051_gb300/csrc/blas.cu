@@ -194,6 +194,12 @@ int dot(rich_ctx* c, const double* x, const double* y, long long n, double* dst)
 
 int nrm2sq(rich_ctx* c, const double* x, long long n, double* dst) { return dot(c, x, x, n, dst); }
 
+// y = a x + b y (y = a x when b == 0, whatever y held)
+__global__ void k_vec_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
+}
+
 // ---------------------------------------------------------------- exclusive scan (3 phases)
 
 constexpr int kScanItems = 8;
@@ -355,6 +361,21 @@ static int fma_peak(cudaStream_t st, double* tflops) {
 }  // namespace rich
 
 extern "C" {
+
+int rich_vec_dot(rich_ctx* c, const double* x, const double* y, double* out) {
+  if (!c || !x || !y || !out) return RICH_EINVAL;
+  rich::AllocStream guard(c->st);
+  double* d = c->dsc + 200;  // a slot no solver uses
+  RICH_CHECK(rich::dot(c, x, y, c->g.n, d));
+  return rich::fetch_scalars(c, d, 1, out);
+}
+
+int rich_vec_axpby(rich_ctx* c, double a, const double* x, double b, double* y) {
+  if (!c || !x || !y) return RICH_EINVAL;
+  rich::k_vec_axpby<<<rich::grid_for(c->g.n), rich::kBlock, 0, c->st>>>(c->g.n, a, x, b, y);
+  RICH_LAUNCH_CHECK();
+  return RICH_OK;
+}
 
 int rich_autotune_table(char* buf, int cap) {
   if (!buf || cap < 1) return RICH_EINVAL;

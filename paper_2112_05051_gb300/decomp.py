@@ -267,3 +267,174 @@ def combine_norms(parts):
     """(||Phi||_2, ||Phi||_inf) of the whole grid from the blocks' (sum of squares, max)."""
     import math
     return math.sqrt(sum(p[0] for p in parts)), max(p[1] for p in parts)
+
+
+# ---------------------------------------------------------------- the split grid's solve
+
+class LocalComm:
+    """All blocks of the split grid in this process (one device): halo exchanges
+    are copies, sums run over the blocks in rank order."""
+
+    def __init__(self, problems):
+        self.problems = problems
+
+    def exchange(self, fields, applies=None):
+        exchange_blocks(self.problems, fields, applies)
+
+    def sum(self, values):
+        return float(sum(values))
+
+    def max(self, values):
+        return float(max(values))
+
+
+class DistComm:
+    """One block per rank (torch.distributed, a device per rank): halo exchanges are
+    point-to-point messages, sums gather every rank's value and add them in rank
+    order (the same result on every rank, whatever the backend's reduction order)."""
+
+    def __init__(self, dist, problem, device):
+        self.dist, self.problems, self.device = dist, [problem], device
+
+    def exchange(self, fields, applies=None):
+        q = self.problems[0]
+        q.halo.exchange(self.dist, q.pack(fields[0]), (applies or [q.apply])[0], q.buffers)
+
+    def _gather(self, v):
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.device)
+        out = [torch.empty_like(t) for _ in range(self.dist.get_world_size())]
+        self.dist.all_gather(out, t)
+        return [float(o.item()) for o in out]
+
+    def sum(self, values):
+        return float(sum(self._gather(values[0])))
+
+    def max(self, values):
+        return float(max(self._gather(values[0])))
+
+
+def dot(problems, comm, xs, ys):
+    return comm.sum([q.ctx.dot(x, y) for q, x, y in zip(problems, xs, ys)])
+
+
+def apply_J(problems, comm, xs, ys):
+    """ys = J xs of the split grid: each block's stencil SpMV, then its interface
+    couplings times the neighbours' x after a halo exchange of x."""
+    for q, x, y in zip(problems, xs, ys):
+        q.ctx.jacobian_apply(x, y)
+    comm.exchange(xs, [q.couple(0, y) for q, y in zip(problems, ys)])
+
+
+def fcg(problems, comm, b, eta, maxit):
+    """Flexible CG (Notay, truncation 1) for J x = b on the split grid, right-
+    preconditioned by each block's own V-cycle on its own hierarchy (decoupled
+    aggregation, Sec. 5.1-5.2).  Returns (x, iterations, converged, reason)."""
+    import math
+    import torch
+    new = lambda: [torch.empty_like(v) for v in b]
+    x = [torch.zeros_like(v) for v in b]
+    r, z, p, qv, qprev = new(), new(), new(), new(), new()
+    for q, rr, bb in zip(problems, r, b):
+        q.ctx.axpby(1.0, bb, 0.0, rr)
+    bn = math.sqrt(dot(problems, comm, b, b))
+    if not bn > 0:
+        return x, 0, True, None
+    target, best, pq_prev = eta * bn, bn, None
+    for it in range(1, maxit + 1):
+        for q, rr, zz in zip(problems, r, z):
+            q.ctx.vcycle(rr, zz)
+        if it == 1:
+            for q, zz, pp in zip(problems, z, p):
+                q.ctx.axpby(1.0, zz, 0.0, pp)
+        else:
+            beta = dot(problems, comm, z, qprev) / pq_prev
+            for q, zz, pp in zip(problems, z, p):
+                q.ctx.axpby(1.0, zz, -beta, pp)
+        apply_J(problems, comm, p, qv)
+        pq = dot(problems, comm, p, qv)
+        if not pq > 0:
+            return x, it, False, "curvature"
+        alpha = dot(problems, comm, p, r) / pq
+        for q, pp, qq, xx, rr in zip(problems, p, qv, x, r):
+            q.ctx.axpby(alpha, pp, 1.0, xx)
+            q.ctx.axpby(-alpha, qq, 1.0, rr)
+        rn = math.sqrt(dot(problems, comm, r, r))
+        if rn <= target:
+            return x, it, True, None
+        if rn > 10.0 * best:
+            return x, it, False, "growth"
+        best = min(best, rn)
+        qv, qprev, pq_prev = qprev, qv, pq
+    return x, maxit, False, "maxit"
+
+
+def newton_step(problems, comm, p, dt, opts):
+    """One backward-Euler step (Sec. 3) of the split grid: inexact Newton with the
+    Armijo line search, the halo of p exchanged before every residual and Jacobian,
+    the correction solved by `fcg` with each block's own hierarchy (set up at the
+    first iteration, refreshed at the next ones), norms and slopes summed over the
+    blocks.  p: the blocks' pressures (updated in place); opts: rich_newton_opts
+    (its rtol, atol, max_newton, armijo_c, lambda_min, krylov eta / maxit and amg
+    settings).  The convergence test is rtol ||Phi_0|| (or atol); the library's
+    round-off floor needs the residual's third norm, which rich_residual does not
+    return.  Returns (converged, newton iterations, linear iterations, reason)."""
+    import math
+    import torch
+    from paper_2112_05051_gb300 import richards as rb
+    new = lambda: [torch.empty_like(v) for v in p]
+    s_old, F, Ft, trial, rhs, Jd = new(), new(), new(), new(), new(), new()
+    for q, pp, so in zip(problems, p, s_old):
+        q.ctx.saturation(pp, so)
+
+    def phi(pp, out):
+        comm.exchange(pp)
+        parts = [q.residual(x, so, dt, f) for q, x, so, f in zip(problems, pp, s_old, out)]
+        return math.sqrt(comm.sum([a for a, _ in parts]))
+
+    fn = phi(p, F)
+    if not math.isfinite(fn):
+        return False, 0, 0, "nonfinite"
+    tol = max(opts.rtol * fn, opts.atol)
+    lin = 0
+    for it in range(opts.max_newton + 1):
+        if fn <= tol:
+            return True, it, lin, None
+        if it == opts.max_newton:
+            return False, it, lin, "newton"
+        for q, pp in zip(problems, p):  # the ghosts hold the halo of this p (its residual came last)
+            q.ctx.jacobian(pp, dt)
+            if it == 0:
+                q.ctx.amg_setup(opts.amg)
+            else:
+                q.ctx.amg_update(rb.AMG_REFRESH)
+        for q, f, r in zip(problems, F, rhs):
+            q.ctx.axpby(-1.0, f, 0.0, r)
+        d, its, ok, why = fcg(problems, comm, rhs, opts.krylov.eta, opts.krylov.maxit)
+        lin += its
+        if not ok:
+            return False, it, lin, "linear (%s)" % why
+        apply_J(problems, comm, d, Jd)
+        slope = dot(problems, comm, F, Jd)
+        if not slope < 0:
+            return False, it, lin, "line search (no descent)"
+        f0, lam = 0.5 * fn * fn, 1.0
+        while True:
+            for q, pp, dd, tt in zip(problems, p, d, trial):
+                q.ctx.axpby(1.0, pp, 0.0, tt)
+                q.ctx.axpby(lam, dd, 1.0, tt)
+            ft = phi(trial, Ft)
+            f_t = 0.5 * ft * ft
+            if not math.isfinite(f_t):
+                return False, it, lin, "nonfinite"
+            if f_t <= f0 + opts.armijo_c * lam * slope:
+                break
+            lq = -slope * lam * lam / (2.0 * (f_t - f0 - slope * lam))
+            lam = min(max(lq, 0.1 * lam), 0.5 * lam)
+            if lam < opts.lambda_min:
+                comm.exchange(p)  # the ghosts back to the accepted p
+                return False, it, lin, "line search"
+        for q, pp, tt in zip(problems, p, trial):
+            q.ctx.axpby(1.0, tt, 0.0, pp)
+        F, Ft = Ft, F
+        fn = ft

@@ -161,6 +161,8 @@ EXPORTS = {
     "rich_set_face_values": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "rich_pack_face": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "rich_face_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "rich_vec_dot": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rich_vec_axpby": (ctypes.c_int, [_P, ctypes.c_double, _P, ctypes.c_double, _P]),
     "rich_sell_layout": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "rich_profile_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "rich_profile_result": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -327,6 +329,16 @@ class Context:
     def pack_face(self, face, field, out):
         """out = the cells of `field` next to face `face`, in the face layout (device)."""
         check(load().rich_pack_face(self.h, face, _ptr(field), _ptr(out)), "rich_pack_face")
+
+    def dot(self, x, y):
+        """x . y over the context's cells (device vectors)."""
+        out = ctypes.c_double()
+        check(load().rich_vec_dot(self.h, _ptr(x), _ptr(y), ctypes.byref(out)), "rich_vec_dot")
+        return out.value
+
+    def axpby(self, a, x, b, y):
+        """y = a x + b y (y = a x when b == 0)."""
+        check(load().rich_vec_axpby(self.h, a, _ptr(x), b, _ptr(y)), "rich_vec_axpby")
 
     def face_apply(self, face, which, ghost, y):
         """y += (J if which == 0 else A_aux) coupling of interface face `face` times ghost."""

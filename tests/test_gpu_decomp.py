@@ -149,3 +149,61 @@ def test_interface_faces_need_their_ghost_pressures():
     with pytest.raises(rb.RichError):  # the face was created without per-cell values
         ctx.set_face_values(0, torch.zeros(grid.ny * grid.nz, dtype=torch.float64, device="cuda"))
     ctx.close()
+
+
+@pytest.mark.parametrize("px,py,kmean", [(2, 2, synth.KMEAN_UPSTREAM), (3, 1, synth.KMEAN_ARITH)])
+def test_split_grid_newton_step_matches_the_whole_grid(px, py, kmean):
+    """One backward-Euler step of the split grid (halo exchanges, FCG preconditioned
+    by each block's own hierarchy, sums over the blocks) converges to the whole
+    grid's step: the preconditioners differ (decoupled aggregation), so the Krylov
+    iterates do, and the pressures agree within the converged-step tolerance."""
+    rb = _rb()
+    grid = synth.Grid(24, 20, 12)
+    bc = synth.infiltration_bc()
+    ks = synth.ks_field(grid, 6, 0.5, (4.0, 4.0, 2.0))
+    p0 = np.full(grid.n, synth.P_INITIAL)
+    dt = 0.25
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, seed=3, coarse_max=100, smooth_levels=2)
+    whole = rb.Context(grid, SOIL, bc, kmean, ks)
+    pw = torch.tensor(p0, device="cuda")
+    st = whole.step(pw, dt, opts)
+    whole.close()
+    assert st.converged and st.fallbacks == 0
+    blocks = decomp.partition(grid, px, py)
+    probs = [decomp.BlockProblem(grid, SOIL, bc, kmean, ks, blocks, r) for r in range(len(blocks))]
+    pb = [torch.tensor(v, device="cuda") for v in _blocks_of(p0, grid, blocks)]
+    ok, its, lin, why = decomp.newton_step(probs, decomp.LocalComm(probs), pb, dt, opts)
+    assert ok, why
+    assert abs(its - st.newton_its) <= 1
+    ps = _whole([v.cpu().numpy() for v in pb], grid, blocks)
+    pwh = pw.cpu().numpy()
+    assert np.abs(ps - pwh).max() <= 1e-8 * np.abs(pwh).max()
+    for q in probs:
+        q.close()
+
+
+def test_split_grid_fcg_solves_the_whole_grids_system():
+    """FCG on the split grid solves the whole grid's J x = b to its tolerance."""
+    rb = _rb()
+    grid = synth.Grid(20, 18, 10)
+    bc = synth.infiltration_bc()
+    ks = synth.ks_field(grid, 2, 0.5, (4.0, 4.0, 2.0))
+    p = _state(grid, 3)
+    dt = 0.5
+    blocks = decomp.partition(grid, 2, 2)
+    probs = [decomp.BlockProblem(grid, SOIL, bc, synth.KMEAN_UPSTREAM, ks, blocks, r) for r in range(len(blocks))]
+    comm = decomp.LocalComm(probs)
+    pb = [torch.tensor(v, device="cuda") for v in _blocks_of(p, grid, blocks)]
+    comm.exchange(pb)
+    for q, x in zip(probs, pb):
+        q.ctx.jacobian(x, dt)
+        q.ctx.amg_setup(rb.default_amg_opts(seed=3, coarse_max=50))
+    b = np.random.default_rng(4).standard_normal(grid.n)
+    bb = [torch.tensor(v, device="cuda") for v in _blocks_of(b, grid, blocks)]
+    x, its, ok, why = decomp.fcg(probs, comm, bb, 1e-10, 400)
+    assert ok, why
+    J = disc.jacobian(grid, SOIL, bc, synth.KMEAN_UPSTREAM, p, dt, ks)
+    xs = _whole([v.cpu().numpy() for v in x], grid, blocks)
+    assert np.linalg.norm(J @ xs - b) <= 1e-10 * np.linalg.norm(b) * 1.0001
+    for q in probs:
+        q.close()
