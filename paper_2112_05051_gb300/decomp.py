@@ -291,7 +291,8 @@ class LocalComm:
 class DistComm:
     """One block per rank (torch.distributed, a device per rank): halo exchanges are
     point-to-point messages, sums gather every rank's value and add them in rank
-    order (the same result on every rank, whatever the backend's reduction order)."""
+    order with Python's compensated float sum (the same result on every rank,
+    whatever the backend's reduction order; LocalComm sums the same way)."""
 
     def __init__(self, dist, problem, device):
         self.dist, self.problems, self.device = dist, [problem], device

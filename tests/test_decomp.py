@@ -147,3 +147,27 @@ def test_halo_exchange_on_gloo_ranks(px, py, tmp_path):
     mp.spawn(_exchange_rank, args=(world, _free_port(), px, py, str(tmp_path)), nprocs=world, join=True)
     for r in range(world):
         assert (tmp_path / ("rank%d" % r)).read_text() == "ok"
+
+
+def _comm_rank(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        comm = decomp.DistComm(dist, None, "cpu")
+        vals = [1e16, 1.0, -1e16, 3.5][:world]  # a plain sum depends on the order of the terms
+        s = comm.sum([vals[rank]])
+        m = comm.max([vals[rank]])
+        ok = s == sum(vals) == 4.5 and m == max(vals)  # every rank's value, compensated, in rank order
+        open(os.path.join(out_dir, "rank%d" % rank), "w").write("%r %r %s" % (s, m, ok))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_dist_comm_sums_in_rank_order_on_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    world = 4
+    mp.spawn(_comm_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    outs = [(tmp_path / ("rank%d" % r)).read_text() for r in range(world)]
+    assert all(o.endswith("True") for o in outs) and len(set(outs)) == 1  # the same sum on every rank
