@@ -212,6 +212,12 @@ typedef struct {
                               its copy on first use.  RICH_LAYOUT_CSR: CSR only, no copy.
                               RICH_LAYOUT_SELL / _SELL8 / _SELL2 / _SELLP: the SELL copy for every such
                               matrix, with that SELL kernel (no timing) */
+  int graph;               /* 1 (default): with the l1-Jacobi AMG preconditioner, the V-cycle's second
+                              application is captured as one CUDA graph (on a stream of its own) and the
+                              later ones replay it: the same kernels on the same buffers, so the same
+                              results, with fewer launch gaps; a hierarchy whose capture fails, and any
+                              application while a kernel is being profiled, launches directly.  0: direct
+                              launches always */
 } rich_amg_opts;
 
 typedef struct {

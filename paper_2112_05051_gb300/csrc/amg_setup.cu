@@ -1559,6 +1559,12 @@ void amg_free(rich_ctx* c) {
   if (H.gj_exec) cudaGraphExecDestroy(H.gj_exec);
   H.gj_exec = nullptr;
   H.gj_nodes = 0;
+  if (H.vc_exec) cudaGraphExecDestroy(H.vc_exec);
+  H.vc_exec = nullptr;
+  H.vc_nodes = 0;
+  H.vc_out = nullptr;
+  H.vc_calls = 0;
+  H.vc_off = false;
   as_free(c);
   H.built = false;
 }
@@ -1847,6 +1853,7 @@ int amg_build(rich_ctx* c, const rich_amg_opts* o) {
     return RICH_EINVAL;
   if (H.opts.precond != RICH_PRECOND_AMG && H.opts.precond != RICH_PRECOND_AS) return RICH_EINVAL;
   if (H.opts.csr_layout < RICH_LAYOUT_AUTO || H.opts.csr_layout > RICH_LAYOUT_SELLP) return RICH_EINVAL;
+  if (H.opts.graph != 0 && H.opts.graph != 1) return RICH_EINVAL;
   if (H.opts.precond == RICH_PRECOND_AS) {  // one level: the subdomain factors of A_aux
     RICH_CHECK(fine_stencil(c));
     RICH_CHECK(as_setup(c));

@@ -215,6 +215,13 @@ struct Hierarchy {
   bool dense = true;              // coarsest level by dense inverse (else kCoarseSweeps l1-Jacobi sweeps)
   cudaGraphExec_t gj_exec = nullptr;  // the coarsest inverse (one launch per pivot) as one graph
   long long gj_nodes = 0;
+  // the V-cycle as one graph (opts.graph): captured at its second application,
+  // reading the level-0 right-hand side buffer and leaving its result at vc_out
+  cudaGraphExec_t vc_exec = nullptr;
+  long long vc_nodes = 0;
+  void* vc_out = nullptr;
+  int vc_calls = 0;
+  bool vc_off = false;            // capture failed: direct launches for this hierarchy
   // one-level additive Schwarz (precond = RICH_PRECOND_AS): ILU(0) diagonals and
   // subdomain solutions (hierarchy precision), FP32 staging of r and z in MIXED
   void* asD = nullptr;

@@ -424,6 +424,7 @@ void rich_default_amg_opts(rich_amg_opts* o) {
   o->autotune = 1;
   o->isolated_join = 1;
   o->csr_layout = RICH_LAYOUT_AUTO;
+  o->graph = 1;
 }
 
 void rich_default_newton_opts(rich_newton_opts* o) {

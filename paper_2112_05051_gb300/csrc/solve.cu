@@ -914,11 +914,89 @@ static int vcycle_level(rich_ctx* c, int l, const T* b, T** xres) {
   return RICH_OK;
 }
 
+// Captures the V-cycle from the level-0 right-hand side buffer L0.b as one graph
+// (H.vc_exec, its result at H.vc_out).  It runs after a direct application, so the
+// tuner's choices and the SELL copies exist and nothing in the cycle allocates or
+// synchronises.  The capture stream is a private non-blocking one (the context's
+// stream may be the legacy default stream, which cannot be captured).  A failed
+// capture leaves direct launches for the rest of this hierarchy.
+static int vcycle_capture(rich_ctx* c) {
+  Hierarchy& H = c->H;
+  Level& L0 = H.lv[0];
+  cudaStream_t cs;
+  RICH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = c->st;
+  RICH_CUDA(cudaStreamSynchronize(saved));
+  c->st = cs;
+  long long before = 0, after = 0;
+  rich_kernel_launches(&before);
+  cudaGraph_t graph = nullptr;
+  void* out = nullptr;
+  int rc = RICH_OK;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (c->prec == RICH_PREC_MIXED) {
+      float* x = nullptr;
+      rc = vcycle_level<float>(c, 0, (const float*)L0.b, &x);
+      out = x;
+    } else {
+      double* x = nullptr;
+      rc = vcycle_level<double>(c, 0, (const double*)L0.b, &x);
+      out = x;
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  c->st = saved;
+  rich_kernel_launches(&after);
+  count_launches(before - after);  // recorded, not launched
+  if (e == cudaSuccess && rc == RICH_OK) {
+    e = cudaGraphInstantiate(&H.vc_exec, graph, 0);
+    if (e == cudaSuccess) {
+      H.vc_nodes = after - before;
+      H.vc_out = out;
+    } else {
+      H.vc_exec = nullptr;
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || rc != RICH_OK || !H.vc_exec) {
+    cudaGetLastError();
+    if (H.vc_exec) cudaGraphExecDestroy(H.vc_exec);
+    H.vc_exec = nullptr;
+    H.vc_off = true;
+  }
+  return RICH_OK;
+}
+
 int vcycle_apply(rich_ctx* c, const double* r, double* z) {
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
   if (H.opts.precond == RICH_PRECOND_AS) return as_apply(c, r, z);
   long long n = c->g.n;
+  const bool graphable = H.opts.graph && H.opts.smoother == RICH_SMOOTH_L1JACOBI && !H.vc_off && !profiling_active();
+  if (graphable && H.vc_calls > 0) {  // the first application launched directly
+    if (!H.vc_exec) RICH_CHECK(vcycle_capture(c));
+    if (H.vc_exec) {
+      Level& L0 = H.lv[0];
+      if (c->prec == RICH_PREC_MIXED) {
+        k_d2f<<<grid_for(n), kBlock, 0, c->st>>>(n, r, (float*)L0.b);
+        RICH_LAUNCH_CHECK();
+      } else {
+        RICH_CUDA(cudaMemcpyAsync(L0.b, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+      }
+      RICH_CUDA(cudaGraphLaunch(H.vc_exec, c->st));
+      count_launches(H.vc_nodes);
+      if (c->prec == RICH_PREC_MIXED) {
+        k_f2d<<<grid_for(n), kBlock, 0, c->st>>>(n, (const float*)H.vc_out, z);
+        RICH_LAUNCH_CHECK();
+      } else {
+        RICH_CUDA(cudaMemcpyAsync(z, H.vc_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+      }
+      return RICH_OK;
+    }
+  }
+  ++H.vc_calls;
   if (c->prec == RICH_PREC_MIXED) {
     Level& L0 = H.lv[0];
     k_d2f<<<grid_for(n), kBlock, 0, c->st>>>(n, r, (float*)L0.b);

@@ -84,7 +84,7 @@ class AmgOpts(ctypes.Structure):
                 ("max_agg_size", ctypes.c_int), ("smoother", ctypes.c_int), ("hgs_seg", ctypes.c_int),
                 ("hgs_block", ctypes.c_int), ("precond", ctypes.c_int), ("as_block", ctypes.c_int),
                 ("as_overlap", ctypes.c_int), ("autotune", ctypes.c_int), ("isolated_join", ctypes.c_int),
-                ("csr_layout", ctypes.c_int)]
+                ("csr_layout", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -247,7 +247,7 @@ def default_newton_opts(**kw):
             setattr(o.krylov, k, v)
         elif k in ("theta", "seed", "coarse_max", "max_levels", "nu1", "nu2", "smooth_levels", "product_lists",
                    "aggregation", "max_agg_size", "isolated_join", "smoother", "hgs_seg", "hgs_block",
-                   "autotune", "precond", "as_block", "as_overlap", "csr_layout"):
+                   "autotune", "precond", "as_block", "as_overlap", "csr_layout", "graph"):
             setattr(o.amg, k, v)
         else:
             setattr(o, k, v)

@@ -194,6 +194,51 @@ def test_vcycle_parity_per_row_layout_after_refresh(layout):
         assert any(e[4] == 1 for e in rb.autotune_table())
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("layout", ["auto", "sell"])
+def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout):
+    """rich_amg_opts.graph: the first V-cycle launches directly, the second is
+    captured, the later ones replay the graph; every result equals the direct
+    launches' bit for bit, also after a Galerkin refresh (new values in the same
+    buffers), and the kernel count is the same."""
+    import ctypes
+    rb = _rb()
+    lay = {"auto": rb.LAYOUT_AUTO, "sell": rb.LAYOUT_SELL}[layout]
+    grid, p, ks, bc, dt, kmean = _problem((40, 36, 32), 9, 1)
+    p2 = p + np.random.default_rng(6).uniform(0, 10, grid.n)
+    rs = [torch.tensor(np.random.default_rng(20 + k).standard_normal(grid.n), device="cuda") for k in range(4)]
+    out, launches = {}, {}
+    for graph in (0, 1):
+        ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+        ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+        ctx.amg_setup(rb.default_amg_opts(seed=5, coarse_max=100, nu1=2, nu2=2, csr_layout=lay, graph=graph))
+        z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
+        zs = []
+        ctx.vcycle(rs[0], z)  # direct (tuning, copies) in both runs
+        torch.cuda.synchronize()
+        l0, l1 = ctx_launches(rb), None
+        for r in rs:
+            ctx.vcycle(r, z)
+            zs.append(z.cpu().numpy())
+        ctx.jacobian(torch.tensor(p2, device="cuda"), dt)
+        ctx.amg_update(rb.AMG_REFRESH)
+        ctx.vcycle(rs[1], z)
+        zs.append(z.cpu().numpy())
+        l1 = ctx_launches(rb)
+        out[graph], launches[graph] = zs, l1 - l0
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    assert launches[0] == launches[1] > 0
+
+
+def ctx_launches(rb):
+    import ctypes
+    v = ctypes.c_longlong()
+    rb.load().rich_kernel_launches(ctypes.byref(v))
+    return v.value
+
+
 @pytest.mark.parametrize("lists", [1, 0])
 @pytest.mark.parametrize("dims,coarse_max", [((18, 16, 14), 150), ((40, 36, 32), 2000)])
 def test_refresh_matches_oracle_galerkin_refresh(dims, coarse_max, lists):
