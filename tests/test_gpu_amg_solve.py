@@ -198,10 +198,13 @@ def test_vcycle_parity_per_row_layout_after_refresh(layout):
 @pytest.mark.parametrize("layout", ["auto", "sell"])
 def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout):
     """rich_amg_opts.graph: the first V-cycle launches directly, the second is
-    captured, the later ones replay the graph; every result equals the direct
-    launches' bit for bit, also after a Galerkin refresh (new values in the same
-    buffers), and the kernel count is the same."""
-    import ctypes
+    captured, the later ones replay the graph.  On one hierarchy the three give
+    the same result bit for bit.  Across two contexts, graph on and off, the
+    results are compared after a Galerkin refresh: the setup's first values of a
+    row with more than 1024 products are summed with shared-memory atomics (equal
+    to rounding level only), the refresh recomputes every value in a fixed order.
+    Both contexts then agree bit for bit, replays against direct launches, with
+    the same kernel count."""
     rb = _rb()
     lay = {"auto": rb.LAYOUT_AUTO, "sell": rb.LAYOUT_SELL}[layout]
     grid, p, ks, bc, dt, kmean = _problem((40, 36, 32), 9, 1)
@@ -213,19 +216,21 @@ def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout)
         ctx.jacobian(torch.tensor(p, device="cuda"), dt)
         ctx.amg_setup(rb.default_amg_opts(seed=5, coarse_max=100, nu1=2, nu2=2, csr_layout=lay, graph=graph))
         z = torch.empty(grid.n, dtype=torch.float64, device="cuda")
-        zs = []
-        ctx.vcycle(rs[0], z)  # direct (tuning, copies) in both runs
+        first = []
+        for _ in range(3):  # graph = 1: direct, captured and replayed, replayed
+            ctx.vcycle(rs[0], z)
+            first.append(z.cpu().numpy())
+        for a in first[1:]:
+            np.testing.assert_array_equal(a, first[0])
+        ctx.jacobian(torch.tensor(p2, device="cuda"), dt)
+        ctx.amg_update(rb.AMG_REFRESH)
         torch.cuda.synchronize()
-        l0, l1 = ctx_launches(rb), None
+        l0 = ctx_launches(rb)
+        zs = []
         for r in rs:
             ctx.vcycle(r, z)
             zs.append(z.cpu().numpy())
-        ctx.jacobian(torch.tensor(p2, device="cuda"), dt)
-        ctx.amg_update(rb.AMG_REFRESH)
-        ctx.vcycle(rs[1], z)
-        zs.append(z.cpu().numpy())
-        l1 = ctx_launches(rb)
-        out[graph], launches[graph] = zs, l1 - l0
+        out[graph], launches[graph] = zs, ctx_launches(rb) - l0
         ctx.close()
     for a, b in zip(out[0], out[1]):
         np.testing.assert_array_equal(a, b)
