@@ -1102,9 +1102,11 @@ static int spgemm_upper(rich_ctx* c, const Csr<double>& A, const Csr<double>& B,
 }
 
 // C = A B: structural pattern (sorted columns) and values.  *u_keep, if given,
-// receives the per-row product counts (kept for the numeric refresh).
+// receives the per-row product counts (kept for the numeric refresh); *hashed, if
+// given, whether rows with more than kEscCap products went through the hash kernel,
+// whose FP64 sums follow the order of shared-memory atomics.
 static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>& B, Csr<double>& C,
-                           int** u_keep = nullptr) {
+                           int** u_keep = nullptr, bool* hashed = nullptr) {
   int n = A.nrows;
   C.nrows = n;
   C.ncols = B.ncols;
@@ -1124,6 +1126,7 @@ static int spgemm_symbolic(rich_ctx* c, const Csr<double>& A, const Csr<double>&
   int nblk = (n + esc_warps - 1) / esc_warps;
   if (nblk > 65535 * 4) nblk = 65535 * 4;
   bool big = umax > kEscCap;
+  if (hashed) *hashed = big;
   size_t hsmem = (size_t)kHashSlots * (sizeof(int) + sizeof(double) + sizeof(uint64_t));
   if (big) RICH_CUDA(cudaFuncSetAttribute(k_spgemm_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
   int* ovf = c->iflag + 1;
@@ -1817,10 +1820,23 @@ static int coarsen(rich_ctx* c, int l, bool* stop) {
   dfree(Pt.rowptr);
   dfree(Pt.col);
   RICH_CHECK(transpose(c, L.P, L.R));
-  RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP, &L.u_ap));
+  bool hashed_ap = false, hashed_rap = false;
+  RICH_CHECK(spgemm_symbolic(c, L.A, L.P, L.AP, &L.u_ap, &hashed_ap));
   Level nxt;
   nxt.n = nc;
-  RICH_CHECK(spgemm_symbolic(c, L.R, L.AP, nxt.A, &L.u_rap));
+  RICH_CHECK(spgemm_symbolic(c, L.R, L.AP, nxt.A, &L.u_rap, &hashed_rap));
+  if ((hashed_ap || hashed_rap) && o.product_lists) {
+    // The next level's P is smoothed from these values and kept through every
+    // refresh: sum them in the product lists' fixed order now (the lists the first
+    // refresh would build), so that a setup does not depend on the order of atomics.
+    L.pl_tried = true;
+    RICH_CHECK(plist_build(c, L.A, L.P, L.AP, L.u_ap, L.pl_ap));
+    if (L.pl_ap.seg) RICH_CHECK(plist_build(c, L.R, L.AP, nxt.A, L.u_rap, L.pl_rap));
+    if (L.pl_ap.seg && L.pl_rap.seg) {
+      RICH_CHECK(spgemm_numeric(c, L.A, L.P, L.AP, L.u_ap, 0, l, &L.pl_ap));
+      RICH_CHECK(spgemm_numeric(c, L.R, L.AP, nxt.A, L.u_rap, 1, l, &L.pl_rap));
+    }
+  }
   if (c->prec == RICH_PREC_MIXED) {
     RICH_CHECK(dalloc(&L.P32, L.P.nnz));
     RICH_CHECK(dalloc(&L.R32, L.R.nnz));

@@ -199,12 +199,10 @@ def test_vcycle_parity_per_row_layout_after_refresh(layout):
 def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout):
     """rich_amg_opts.graph: the first V-cycle launches directly, the second is
     captured, the later ones replay the graph.  On one hierarchy the three give
-    the same result bit for bit.  Across two contexts, graph on and off, the
-    results are compared after a Galerkin refresh: the setup's first values of a
-    row with more than 1024 products are summed with shared-memory atomics (equal
-    to rounding level only), the refresh recomputes every value in a fixed order.
-    Both contexts then agree bit for bit, replays against direct launches, with
-    the same kernel count."""
+    the same result bit for bit; two contexts, graph on and off, agree bit for bit
+    (a setup is deterministic: rows of the symbolic Galerkin product that took
+    the hash kernel are re-summed in the product lists' order), before and after
+    a Galerkin refresh, with the same kernel count."""
     rb = _rb()
     lay = {"auto": rb.LAYOUT_AUTO, "sell": rb.LAYOUT_SELL}[layout]
     grid, p, ks, bc, dt, kmean = _problem((40, 36, 32), 9, 1)
@@ -222,6 +220,7 @@ def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout)
             first.append(z.cpu().numpy())
         for a in first[1:]:
             np.testing.assert_array_equal(a, first[0])
+        out[("setup", graph)] = first[0]
         ctx.jacobian(torch.tensor(p2, device="cuda"), dt)
         ctx.amg_update(rb.AMG_REFRESH)
         torch.cuda.synchronize()
@@ -232,6 +231,7 @@ def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout)
             zs.append(z.cpu().numpy())
         out[graph], launches[graph] = zs, ctx_launches(rb) - l0
         ctx.close()
+    np.testing.assert_array_equal(out[("setup", 0)], out[("setup", 1)])
     for a, b in zip(out[0], out[1]):
         np.testing.assert_array_equal(a, b)
     assert launches[0] == launches[1] > 0
