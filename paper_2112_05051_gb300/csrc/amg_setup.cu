@@ -1568,6 +1568,13 @@ void amg_free(rich_ctx* c) {
   H.vc_out = nullptr;
   H.vc_calls = 0;
   H.vc_off = false;
+  for (int q = 0; q < 2; ++q) {
+    if (H.fcg_exec[q]) cudaGraphExecDestroy(H.fcg_exec[q]);
+    H.fcg_exec[q] = nullptr;
+    H.fcg_nodes[q] = 0;
+  }
+  H.fcg_x = nullptr;
+  H.fcg_off = false;
   as_free(c);
   H.built = false;
 }

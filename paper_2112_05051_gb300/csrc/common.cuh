@@ -222,6 +222,12 @@ struct Hierarchy {
   void* vc_out = nullptr;
   int vc_calls = 0;
   bool vc_off = false;            // capture failed: direct launches for this hierarchy
+  // an FCG iteration (it >= 2, V-cycle to the read-back of its scalars) as one graph
+  // per parity of it (q and q_prev alternate), writing the correction fcg_x
+  cudaGraphExec_t fcg_exec[2] = {nullptr, nullptr};
+  long long fcg_nodes[2] = {0, 0};
+  const double* fcg_x = nullptr;
+  bool fcg_off = false;
   // one-level additive Schwarz (precond = RICH_PRECOND_AS): ILU(0) diagonals and
   // subdomain solutions (hierarchy precision), FP32 staging of r and z in MIXED
   void* asD = nullptr;

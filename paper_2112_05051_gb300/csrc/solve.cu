@@ -969,13 +969,39 @@ static int vcycle_capture(rich_ctx* c) {
   return RICH_OK;
 }
 
+// The V-cycle's kernels from r into z, launched (or captured) as they come.
+static int vcycle_direct(rich_ctx* c, const double* r, double* z) {
+  Hierarchy& H = c->H;
+  const long long n = c->g.n;
+  if (c->prec == RICH_PREC_MIXED) {
+    Level& L0 = H.lv[0];
+    k_d2f<<<grid_for(n), kBlock, 0, c->st>>>(n, r, (float*)L0.b);
+    RICH_LAUNCH_CHECK();
+    float* x = nullptr;
+    RICH_CHECK(vcycle_level<float>(c, 0, (const float*)L0.b, &x));
+    k_f2d<<<grid_for(n), kBlock, 0, c->st>>>(n, x, z);
+    RICH_LAUNCH_CHECK();
+  } else {
+    double* x = nullptr;
+    RICH_CHECK(vcycle_level<double>(c, 0, r, &x));
+    RICH_CUDA(cudaMemcpyAsync(z, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  }
+  return RICH_OK;
+}
+
+// Whether the V-cycle of this hierarchy may run from a captured graph now.
+static bool vcycle_graphable(rich_ctx* c) {
+  const Hierarchy& H = c->H;
+  return H.opts.graph && H.opts.precond == RICH_PRECOND_AMG && H.opts.smoother == RICH_SMOOTH_L1JACOBI && !H.vc_off &&
+         !profiling_active();
+}
+
 int vcycle_apply(rich_ctx* c, const double* r, double* z) {
   Hierarchy& H = c->H;
   if (!H.built) return RICH_ESTATE;
   if (H.opts.precond == RICH_PRECOND_AS) return as_apply(c, r, z);
   long long n = c->g.n;
-  const bool graphable = H.opts.graph && H.opts.smoother == RICH_SMOOTH_L1JACOBI && !H.vc_off && !profiling_active();
-  if (graphable && H.vc_calls > 0) {  // the first application launched directly
+  if (vcycle_graphable(c) && H.vc_calls > 0) {  // the first application launched directly
     if (!H.vc_exec) RICH_CHECK(vcycle_capture(c));
     if (H.vc_exec) {
       Level& L0 = H.lv[0];
@@ -997,20 +1023,7 @@ int vcycle_apply(rich_ctx* c, const double* r, double* z) {
     }
   }
   ++H.vc_calls;
-  if (c->prec == RICH_PREC_MIXED) {
-    Level& L0 = H.lv[0];
-    k_d2f<<<grid_for(n), kBlock, 0, c->st>>>(n, r, (float*)L0.b);
-    RICH_LAUNCH_CHECK();
-    float* x = nullptr;
-    RICH_CHECK(vcycle_level<float>(c, 0, (const float*)L0.b, &x));
-    k_f2d<<<grid_for(n), kBlock, 0, c->st>>>(n, x, z);
-    RICH_LAUNCH_CHECK();
-  } else {
-    double* x = nullptr;
-    RICH_CHECK(vcycle_level<double>(c, 0, r, &x));
-    RICH_CUDA(cudaMemcpyAsync(z, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
-  }
-  return RICH_OK;
+  return vcycle_direct(c, r, z);
 }
 
 // ---------------------------------------------------------------- Krylov kernels (FP64)
@@ -1177,14 +1190,85 @@ static int ensure_krylov(rich_ctx* c, int m) {
 
 // Flexible CG (Notay, truncation 1).  Returns RICH_ENOTCONV_LIN on maxit, on
 // (p, q) <= 0, or when ||r|| exceeds 10x the smallest seen.
+// One FCG iteration from the preconditioner application to the copy of its scalars
+// (rr, zq, pq) into the pinned host mirror; `first`: the first iteration (p = z).
+// Under capture the V-cycle's kernels are recorded directly.
+static int fcg_iteration(rich_ctx* c, double* x, double* q, const double* qprev, bool first, bool capturing) {
+  KrylovWork& k = c->kw;
+  const long long n = c->g.n;
+  const int g = grid_for(n), nb = red_grid(n);
+  double* s = c->dsc;  // 0 rr, 1 zq, 2 pq, 3 pr, 4 pq_prev
+  RICH_CHECK(capturing ? vcycle_direct(c, k.r, k.z) : vcycle_apply(c, k.r, k.z));
+  if (first) {
+    RICH_CUDA(cudaMemcpyAsync(k.p, k.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    RICH_CHECK(dot(c, k.z, qprev, n, s + 1));
+    k_fcg_dir<<<g, kBlock, 0, c->st>>>(n, k.z, k.p, s, 1, 4);
+    RICH_LAUNCH_CHECK();
+  }
+  RICH_CHECK(stencil_apply(c, c->J7, k.p, q));
+  k_dot2<<<nb, kBlock, 0, c->st>>>(n, k.p, q, k.p, k.r, c->partials);
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(finish_sums(c, c->partials, nb, 2, s + 2));
+  {
+    ProfScope ps("fcg_update", c->st, (double)n * 48.0);
+    k_fcg_update<<<nb, kBlock, 0, c->st>>>(n, x, k.r, k.p, q, s, 3, 2, c->partials);
+  }
+  RICH_LAUNCH_CHECK();
+  RICH_CHECK(finish_sums(c, c->partials, nb, 1, s + 0));
+  k_copy_scalar<<<1, 1, 0, c->st>>>(s, 2, 4);
+  RICH_LAUNCH_CHECK();
+  RICH_CUDA(cudaMemcpyAsync(c->hsc, s, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return RICH_OK;
+}
+
+// Captures fcg_iteration (not the first) with these q, q_prev and x as graph `par`,
+// as vcycle_capture does; a failed capture leaves direct launches.
+static void fcg_capture(rich_ctx* c, int par, double* x, double* q, const double* qprev) {
+  Hierarchy& H = c->H;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    H.fcg_off = true;
+    return;
+  }
+  cudaStream_t saved = c->st;
+  cudaError_t e = cudaStreamSynchronize(saved);
+  c->st = cs;
+  long long before = 0, after = 0;
+  rich_kernel_launches(&before);
+  cudaGraph_t graph = nullptr;
+  int rc = RICH_OK;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = fcg_iteration(c, x, q, qprev, false, true);
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  c->st = saved;
+  rich_kernel_launches(&after);
+  count_launches(before - after);  // recorded, not launched
+  if (e == cudaSuccess && rc == RICH_OK) {
+    e = cudaGraphInstantiate(&H.fcg_exec[par], graph, 0);
+    if (e == cudaSuccess) H.fcg_nodes[par] = after - before;
+    else H.fcg_exec[par] = nullptr;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || rc != RICH_OK || !H.fcg_exec[par]) {
+    cudaGetLastError();
+    H.fcg_off = true;
+  }
+}
+
 // Notay's flexible CG (truncation 1).  With o->stall > 0 it gives up when a window
 // of kStallWindow iterations reduced the residual by less than that fraction.
+// From the second iteration on, an iteration is a graph replay where the V-cycle
+// may be (rich_amg_opts.graph): the same kernels on the same buffers.
 static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* o, rich_krylov_stats* st) {
   KrylovWork& k = c->kw;
+  Hierarchy& H = c->H;
   long long n = c->g.n;
-  int g = grid_for(n);
-  int nb = red_grid(n);
-  double* s = c->dsc;  // 0 rr, 1 zq, 2 pq, 3 pr, 4 pq_prev
+  double* s = c->dsc;
   RICH_CHECK(nrm2sq(c, b, n, s + 0));
   double h[4];
   RICH_CHECK(fetch_scalars(c, s, 1, h));
@@ -1204,28 +1288,24 @@ static int fcg(rich_ctx* c, const double* b, double* x, const rich_krylov_opts* 
   double target = o->eta * bn, best = bn, window_start = bn;
   double* q = k.q;
   double* qprev = k.qprev;
+  const bool graphs = vcycle_graphable(c) && !H.fcg_off && (!H.fcg_x || H.fcg_x == x);
   for (int it = 1; it <= o->maxit; ++it) {
-    RICH_CHECK(vcycle_apply(c, k.r, k.z));
-    if (it == 1) {
-      RICH_CUDA(cudaMemcpyAsync(k.p, k.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
-    } else {
-      RICH_CHECK(dot(c, k.z, qprev, n, s + 1));
-      k_fcg_dir<<<g, kBlock, 0, c->st>>>(n, k.z, k.p, s, 1, 4);
-      RICH_LAUNCH_CHECK();
+    bool replayed = false;
+    if (graphs && it >= 2 && H.vc_calls > 0 && !H.fcg_off) {
+      const int par = it & 1;  // it even: q = k.qprev, q_prev = k.q; odd: the other way round
+      if (!H.fcg_exec[par]) {
+        H.fcg_x = x;
+        fcg_capture(c, par, x, q, qprev);
+      }
+      if (H.fcg_exec[par]) {
+        RICH_CUDA(cudaGraphLaunch(H.fcg_exec[par], c->st));
+        count_launches(H.fcg_nodes[par]);
+        replayed = true;
+      }
     }
-    RICH_CHECK(stencil_apply(c, c->J7, k.p, q));
-    k_dot2<<<nb, kBlock, 0, c->st>>>(n, k.p, q, k.p, k.r, c->partials);
-    RICH_LAUNCH_CHECK();
-    RICH_CHECK(finish_sums(c, c->partials, nb, 2, s + 2));
-    {
-      ProfScope ps("fcg_update", c->st, (double)n * 48.0);
-      k_fcg_update<<<nb, kBlock, 0, c->st>>>(n, x, k.r, k.p, q, s, 3, 2, c->partials);
-    }
-    RICH_LAUNCH_CHECK();
-    RICH_CHECK(finish_sums(c, c->partials, nb, 1, s + 0));
-    k_copy_scalar<<<1, 1, 0, c->st>>>(s, 2, 4);
-    RICH_LAUNCH_CHECK();
-    RICH_CHECK(fetch_scalars(c, s, 3, h));
+    if (!replayed) RICH_CHECK(fcg_iteration(c, x, q, qprev, it == 1, false));
+    RICH_CUDA(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < 3; ++i) h[i] = c->hsc[i];
     double rn = sqrt(h[0]);
     st->iterations = it;
     st->res = rn;

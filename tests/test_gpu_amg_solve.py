@@ -237,6 +237,39 @@ def test_vcycle_graph_replays_are_bit_identical_to_direct_launches(prec, layout)
     assert launches[0] == launches[1] > 0
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fcg_iteration_graphs_are_bit_identical_to_direct_launches(prec):
+    """FCG's iterations from the second on replay a graph per parity of the
+    iteration (rich_amg_opts.graph): a solve and a Newton step with graphs on and
+    off agree bit for bit, iterations and results."""
+    rb = _rb()
+    grid, p, ks, bc, dt, kmean = _problem((24, 22, 20), 4, 1)
+    b = torch.tensor(np.random.default_rng(8).standard_normal(grid.n), device="cuda")
+    res = {}
+    for graph in (0, 1):
+        ctx = rb.Context(grid, SOIL, bc, kmean, ks, precision=prec)
+        ctx.jacobian(torch.tensor(p, device="cuda"), dt)
+        ctx.amg_setup(rb.default_amg_opts(seed=3, coarse_max=100, graph=graph))
+        x = torch.empty_like(b)
+        xs, its = [], []
+        for _ in range(2):  # the second solve replays what the first captured
+            s, st = ctx.krylov_solve(b, x, kind=rb.KRYLOV_FCG, eta=1e-10, maxit=300)
+            xs.append(x.cpu().numpy())
+            its.append(st.iterations)
+        ctx.close()
+        ctx = rb.Context(grid, SOIL, synth.infiltration_bc(), synth.KMEAN_ARITH, synth.ks_field(grid, 2, 0.5),
+                         precision=prec)
+        pd = torch.tensor(np.full(grid.n, synth.P_INITIAL), device="cuda")
+        st = ctx.step(pd, 0.5, rb.default_newton_opts(kind=rb.KRYLOV_FCG, seed=3, coarse_max=100, graph=graph))
+        ctx.close()
+        res[graph] = (xs, its, pd.cpu().numpy(), st.newton_its, st.linear_its)
+    assert res[0][1] == res[1][1] and res[0][1][0] > 2
+    for a, c in zip(res[0][0], res[1][0]):
+        np.testing.assert_array_equal(a, c)
+    np.testing.assert_array_equal(res[0][2], res[1][2])
+    assert res[0][3:] == res[1][3:]
+
+
 def ctx_launches(rb):
     import ctypes
     v = ctypes.c_longlong()
