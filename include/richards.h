@@ -214,10 +214,11 @@ typedef struct {
                               matrix, with that SELL kernel (no timing) */
   int graph;               /* 1 (default): with the l1-Jacobi AMG preconditioner, the V-cycle's second
                               application is captured as one CUDA graph (on a stream of its own) and the
-                              later ones replay it: the same kernels on the same buffers, so the same
-                              results, with fewer launch gaps; a hierarchy whose capture fails, and any
-                              application while a kernel is being profiled, launches directly.  0: direct
-                              launches always */
+                              later ones replay it, and so are FCG's iterations from the second on (one
+                              graph per parity of the iteration, while the solve writes the same x): the
+                              same kernels on the same buffers, so the same results, with fewer launch
+                              gaps; a hierarchy whose capture fails, and any application while a kernel
+                              is being profiled, launches directly.  0: direct launches always */
 } rich_amg_opts;
 
 typedef struct {
