@@ -469,7 +469,8 @@ int rich_autotune_load(const char* text);
  * offsets of the slices (slice s spans 32 x its first row's length slots), and
  * *slots their total.  Host memory only; RICH_EINVAL on a bad argument or a
  * decreasing row pointer, RICH_ELIMIT when the slots exceed 32-bit offsets. */
-int rich_sell_layout(const int* rowptr_host, int n, int* perm_host, int* sptr_host, long long* slots);
+int rich_sell_layout(const int* rowptr_host, int n, int* perm_host, int* sptr_host,
+                     long long* slots);
 
 /* Number of kernels this library has launched since it was loaded. */
 int rich_kernel_launches(long long* out);
