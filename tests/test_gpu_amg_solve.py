@@ -446,6 +446,31 @@ def test_step_parity_richards16(policy):
         assert g.newton_its == o.newton_its
 
 
+@pytest.mark.parametrize("dims,kind", [((1, 1, 30), "fcg"), ((1, 1, 1), "fcg"), ((3, 1, 1), "fgmres"),
+                                       ((1, 2, 17), "fgmres")])
+def test_step_parity_on_degenerate_grids(dims, kind):
+    """One column, one cell, one row: a one-level hierarchy (its dense inverse is
+    the whole preconditioner, the V-cycle graph a single GEMV) and columns with
+    faces on both sides in x and y; three steps against the oracle."""
+    rb = _rb()
+    grid = synth.Grid(*dims, 30.0, 30.0, 30.0)
+    bc = synth.infiltration_bc()
+    ks = synth.ks_field(grid, 5, 0.5)
+    p0 = np.full(grid.n, synth.P_INITIAL)
+    k = rb.KRYLOV_FCG if kind == "fcg" else rb.KRYLOV_FGMRES
+    opts = rb.default_newton_opts(kind=k, seed=2, coarse_max=100)
+    ctx = rb.Context(grid, SOIL, bc, synth.KMEAN_UPSTREAM, ks)
+    pd = torch.tensor(p0, device="cuda")
+    prob = newton.Problem(grid, SOIL, bc, synth.KMEAN_UPSTREAM, ks)
+    po = p0.copy()
+    for dt in (0.5, 1.0, 2.0):
+        st = ctx.step(pd, dt, opts)
+        po, ost = newton.step(prob, po, dt, newton.NewtonOptions(krylov=kind, amg_seed=2, coarse_max=100))
+        assert st.converged and ost.converged and st.newton_its == ost.newton_its
+    assert _nrel(pd.cpu().numpy(), po) <= 1e-8
+    ctx.close()
+
+
 def test_step_parity_richards128_shape_at_32():
     # the 128^3 workload's settings (upstream mean, FGMRES(30), V(2,2), dt ramp) on a 32^3 grid
     pg, po, gs, os_ = _run_steps("richards128_fp64", 32, 4)
