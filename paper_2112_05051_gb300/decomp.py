@@ -373,9 +373,9 @@ def fcg(problems, comm, b, eta, maxit):
 def newton_step(problems, comm, p, dt, opts):
     """One backward-Euler step (Sec. 3) of the split grid: inexact Newton with the
     Armijo line search, the halo of p exchanged before every residual and Jacobian,
-    the correction solved by `fcg` with each block's own hierarchy (set up at the
-    first iteration, refreshed at the next ones), norms and slopes summed over the
-    blocks.  p: the blocks' pressures (updated in place); opts: rich_newton_opts
+    the correction solved by `fcg`, or `fgmres` when opts.krylov.kind asks for it,
+    with each block's own hierarchy (set up at the first iteration, refreshed at
+    the next ones), norms and slopes summed over the blocks.  p: the blocks' pressures (updated in place); opts: rich_newton_opts
     (its rtol, atol, max_newton, armijo_c, lambda_min, krylov eta / maxit and amg
     settings).  The convergence test is rtol ||Phi_0|| (or atol); the library's
     round-off floor needs the residual's third norm, which rich_residual does not
@@ -411,7 +411,10 @@ def newton_step(problems, comm, p, dt, opts):
                 q.ctx.amg_update(rb.AMG_REFRESH)
         for q, f, r in zip(problems, F, rhs):
             q.ctx.axpby(-1.0, f, 0.0, r)
-        d, its, ok, why = fcg(problems, comm, rhs, opts.krylov.eta, opts.krylov.maxit)
+        if opts.krylov.kind == rb.KRYLOV_FGMRES:
+            d, its, ok, why = fgmres(problems, comm, rhs, opts.krylov.eta, opts.krylov.maxit, opts.krylov.restart)
+        else:
+            d, its, ok, why = fcg(problems, comm, rhs, opts.krylov.eta, opts.krylov.maxit)
         lin += its
         if not ok:
             return False, it, lin, "linear (%s)" % why
@@ -439,3 +442,87 @@ def newton_step(problems, comm, p, dt, opts):
             q.ctx.axpby(1.0, tt, 0.0, pp)
         F, Ft = Ft, F
         fn = ft
+
+
+def fgmres(problems, comm, b, eta, maxit, m):
+    """Flexible GMRES(m) for J x = b on the split grid, right-preconditioned by each
+    block's own V-cycle: classical Gram-Schmidt with a second pass when
+    ||w'||^2 < ||w||^2 / 2 (DGKS), Givens rotations, restarts every m iterations
+    from the true residual.  Returns (x, iterations, converged, reason)."""
+    import math
+    import torch
+    nb = len(problems)
+    new = lambda: [torch.empty_like(v) for v in b]
+    x = [torch.zeros_like(v) for v in b]
+    r, w, jx = new(), new(), new()
+    for q, rr, bb in zip(problems, r, b):
+        q.ctx.axpby(1.0, bb, 0.0, rr)
+    beta = math.sqrt(dot(problems, comm, r, r))
+    if not beta > 0:
+        return x, 0, True, None
+    target, its = eta * beta, 0
+    while True:
+        V = [new() for _ in range(m + 1)]
+        Z = [new() for _ in range(m)]
+        H = [[0.0] * m for _ in range(m + 1)]
+        cs, sn, g = [0.0] * m, [0.0] * m, [0.0] * (m + 1)
+        g[0] = beta
+        for q, rr, v in zip(problems, r, V[0]):
+            q.ctx.axpby(1.0 / beta, rr, 0.0, v)
+        jdone, conv = 0, False
+        for j in range(m):
+            for q, v, z in zip(problems, V[j], Z[j]):
+                q.ctx.vcycle(v, z)
+            apply_J(problems, comm, Z[j], w)
+            wn2 = dot(problems, comm, w, w)
+            h1 = [dot(problems, comm, V[i], w) for i in range(j + 1)]
+            for i in range(j + 1):
+                for q, vi, ww in zip(problems, V[i], w):
+                    q.ctx.axpby(-h1[i], vi, 1.0, ww)
+            wp2 = dot(problems, comm, w, w)
+            if wp2 < 0.5 * wn2:  # DGKS: a second pass
+                h2 = [dot(problems, comm, V[i], w) for i in range(j + 1)]
+                for i in range(j + 1):
+                    for q, vi, ww in zip(problems, V[i], w):
+                        q.ctx.axpby(-h2[i], vi, 1.0, ww)
+                    h1[i] += h2[i]
+                wp2 = dot(problems, comm, w, w)
+            hn = math.sqrt(max(wp2, 0.0))
+            for i in range(j + 1):
+                H[i][j] = h1[i]
+            H[j + 1][j] = hn
+            if hn > 0:
+                for q, ww, v in zip(problems, w, V[j + 1]):
+                    q.ctx.axpby(1.0 / hn, ww, 0.0, v)
+            for i in range(j):
+                t = cs[i] * H[i][j] + sn[i] * H[i + 1][j]
+                H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j]
+                H[i][j] = t
+            den = math.hypot(H[j][j], H[j + 1][j])
+            cs[j], sn[j] = H[j][j] / den, H[j + 1][j] / den
+            H[j][j], H[j + 1][j] = den, 0.0
+            g[j + 1], g[j] = -sn[j] * g[j], cs[j] * g[j]
+            its += 1
+            jdone = j + 1
+            if abs(g[j + 1]) <= target or hn == 0.0:
+                conv = True
+                break
+            if its >= maxit:
+                break
+        y = [0.0] * jdone
+        for i in range(jdone - 1, -1, -1):
+            y[i] = (g[i] - sum(H[i][k] * y[k] for k in range(i + 1, jdone))) / H[i][i]
+        for i in range(jdone):
+            for q, zz, xx in zip(problems, Z[i], x):
+                q.ctx.axpby(y[i], zz, 1.0, xx)
+        if conv:
+            return x, its, True, None
+        if its >= maxit:
+            return x, its, False, "maxit"
+        apply_J(problems, comm, x, jx)  # restart from the true residual
+        for q, bb, jj, rr in zip(problems, b, jx, r):
+            q.ctx.axpby(1.0, bb, 0.0, rr)
+            q.ctx.axpby(-1.0, jj, 1.0, rr)
+        beta = math.sqrt(dot(problems, comm, r, r))
+        if beta <= target:
+            return x, its, True, None

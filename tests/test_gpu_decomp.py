@@ -151,8 +151,9 @@ def test_interface_faces_need_their_ghost_pressures():
     ctx.close()
 
 
-@pytest.mark.parametrize("px,py,kmean", [(2, 2, synth.KMEAN_UPSTREAM), (3, 1, synth.KMEAN_ARITH)])
-def test_split_grid_newton_step_matches_the_whole_grid(px, py, kmean):
+@pytest.mark.parametrize("px,py,kmean,kind", [(2, 2, synth.KMEAN_UPSTREAM, "fcg"), (3, 1, synth.KMEAN_ARITH, "fcg"),
+                                              (2, 2, synth.KMEAN_UPSTREAM, "fgmres")])
+def test_split_grid_newton_step_matches_the_whole_grid(px, py, kmean, kind):
     """One backward-Euler step of the split grid (halo exchanges, FCG preconditioned
     by each block's own hierarchy, sums over the blocks) converges to the whole
     grid's step: the preconditioners differ (decoupled aggregation), so the Krylov
@@ -163,7 +164,8 @@ def test_split_grid_newton_step_matches_the_whole_grid(px, py, kmean):
     ks = synth.ks_field(grid, 6, 0.5, (4.0, 4.0, 2.0))
     p0 = np.full(grid.n, synth.P_INITIAL)
     dt = 0.25
-    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, seed=3, coarse_max=100, smooth_levels=2)
+    k = rb.KRYLOV_FCG if kind == "fcg" else rb.KRYLOV_FGMRES
+    opts = rb.default_newton_opts(kind=k, restart=30, seed=3, coarse_max=100, smooth_levels=2)
     whole = rb.Context(grid, SOIL, bc, kmean, ks)
     pw = torch.tensor(p0, device="cuda")
     st = whole.step(pw, dt, opts)
@@ -182,8 +184,10 @@ def test_split_grid_newton_step_matches_the_whole_grid(px, py, kmean):
         q.close()
 
 
-def test_split_grid_fcg_solves_the_whole_grids_system():
-    """FCG on the split grid solves the whole grid's J x = b to its tolerance."""
+@pytest.mark.parametrize("kind", ["fcg", "fgmres"])
+def test_split_grid_krylov_solves_the_whole_grids_system(kind):
+    """FCG and FGMRES(10) on the split grid solve the whole grid's J x = b to their
+    tolerance."""
     rb = _rb()
     grid = synth.Grid(20, 18, 10)
     bc = synth.infiltration_bc()
@@ -200,7 +204,10 @@ def test_split_grid_fcg_solves_the_whole_grids_system():
         q.ctx.amg_setup(rb.default_amg_opts(seed=3, coarse_max=50))
     b = np.random.default_rng(4).standard_normal(grid.n)
     bb = [torch.tensor(v, device="cuda") for v in _blocks_of(b, grid, blocks)]
-    x, its, ok, why = decomp.fcg(probs, comm, bb, 1e-10, 400)
+    if kind == "fcg":
+        x, its, ok, why = decomp.fcg(probs, comm, bb, 1e-10, 400)
+    else:
+        x, its, ok, why = decomp.fgmres(probs, comm, bb, 1e-10, 400, 10)
     assert ok, why
     J = disc.jacobian(grid, SOIL, bc, synth.KMEAN_UPSTREAM, p, dt, ks)
     xs = _whole([v.cpu().numpy() for v in x], grid, blocks)
