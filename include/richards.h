@@ -339,6 +339,16 @@ int rich_saturation(rich_ctx* ctx, const double* p_dev, double* s_dev);
  * non-finite Phi returns RICH_ENONFINITE after writing F_dev. */
 int rich_residual(rich_ctx* ctx, const double* p_dev, const double* s_old_dev, double dt,
                   double* F_dev, double* norms_host);
+/* rich_residual with the scale of Phi's rounding error beside the norms:
+ * norms3_host (3 doubles, required) receives {||Phi||_2, ||Phi||_inf, ||m||_2},
+ * m_c the sum of the magnitudes of the products added into Phi_c before they
+ * cancel (storage terms |s|/dt, face terms K_av (|p_c| + |p_nb|)/h^2 and the
+ * gravity terms), so that eps ||m||_2 is the accuracy to which Phi can be
+ * evaluated: the round-off floor of the Newton convergence test (Sec. 3) that
+ * rich_step applies.  On the split grid the blocks' ||m||_2^2 add up to the
+ * whole grid's.  Synchronises; RICH_ENONFINITE as rich_residual. */
+int rich_residual3(rich_ctx* ctx, const double* p_dev, const double* s_old_dev, double dt,
+                   double* F_dev, double* norms3_host);
 
 /* The residual of rich_residual without a context and without any device
  * allocation.  The paper has no counterpart: this entry point exists for callers

@@ -639,6 +639,19 @@ int rich_residual(rich_ctx* c, const double* p, const double* s_old, double dt, 
   return RICH_OK;
 }
 
+int rich_residual3(rich_ctx* c, const double* p, const double* s_old, double dt, double* F, double* norms) {
+  if (!c || !p || !s_old || !F || !norms || !(dt > 0)) return RICH_EINVAL;
+  AllocStream guard(c->st);
+  RICH_CHECK(residual_eval(c, p, s_old, dt, F, true));
+  double h[3];
+  RICH_CHECK(fetch_scalars(c, c->dsc, 3, h));  // ||F||^2, ||F||_inf, ||m||^2
+  norms[0] = sqrt(h[0]);
+  norms[1] = h[1];
+  norms[2] = sqrt(h[2]);
+  if (!std::isfinite(norms[0]) || !std::isfinite(norms[1])) return RICH_ENONFINITE;
+  return RICH_OK;
+}
+
 int rich_jacobian(rich_ctx* c, const double* p, double dt, double* J7, double* A7) {
   if (!c || !p || !(dt > 0)) return RICH_EINVAL;
   AllocStream guard(c->st);

@@ -238,10 +238,11 @@ class BlockProblem:
         self.halo.exchange(dist, self.pack(x), self.couple(0, y), self.buffers)
 
     def residual(self, p, s_old, dt, F):
-        """Phi of the block (after an exchange); returns (sum of Phi^2, max |Phi|),
-        the pieces of the whole grid's norms."""
-        n2, ninf = self.ctx.residual(p, s_old, dt, F)
-        return n2 * n2, ninf
+        """Phi of the block (after an exchange); returns (sum of Phi^2, max |Phi|,
+        sum of m^2), the pieces of the whole grid's norms and of its round-off
+        scale ||m||_2 (m: the magnitudes of the terms summed into Phi per cell)."""
+        n2, ninf, nm = self.ctx.residual3(p, s_old, dt, F)
+        return n2 * n2, ninf, nm * nm
 
     def close(self):
         self.ctx.close()
@@ -377,9 +378,9 @@ def newton_step(problems, comm, p, dt, opts):
     with each block's own hierarchy (set up at the first iteration, refreshed at
     the next ones), norms and slopes summed over the blocks.  p: the blocks' pressures (updated in place); opts: rich_newton_opts
     (its rtol, atol, max_newton, armijo_c, lambda_min, krylov eta / maxit and amg
-    settings).  The convergence test is rtol ||Phi_0|| (or atol); the library's
-    round-off floor needs the residual's third norm, which rich_residual does not
-    return.  Returns (converged, newton iterations, linear iterations, reason)."""
+    settings).  Converged when ||Phi|| <= max(rtol ||Phi_0||, atol, eps ||m||_2), the
+    same test as the library's step, its round-off floor from the blocks' summed
+    m^2.  Returns (converged, newton iterations, linear iterations, reason)."""
     import math
     import torch
     from paper_2112_05051_gb300 import richards as rb
@@ -388,18 +389,20 @@ def newton_step(problems, comm, p, dt, opts):
     for q, pp, so in zip(problems, p, s_old):
         q.ctx.saturation(pp, so)
 
-    def phi(pp, out):
+    eps = 2.220446049250313e-16
+
+    def phi(pp, out):  # (||Phi||_2, its round-off floor)
         comm.exchange(pp)
         parts = [q.residual(x, so, dt, f) for q, x, so, f in zip(problems, pp, s_old, out)]
-        return math.sqrt(comm.sum([a for a, _ in parts]))
+        return math.sqrt(comm.sum([a for a, _, _ in parts])), eps * math.sqrt(comm.sum([c for _, _, c in parts]))
 
-    fn = phi(p, F)
+    fn, floor = phi(p, F)
     if not math.isfinite(fn):
         return False, 0, 0, "nonfinite"
     tol = max(opts.rtol * fn, opts.atol)
     lin = 0
     for it in range(opts.max_newton + 1):
-        if fn <= tol:
+        if fn <= max(tol, floor):
             return True, it, lin, None
         if it == opts.max_newton:
             return False, it, lin, "newton"
@@ -427,7 +430,7 @@ def newton_step(problems, comm, p, dt, opts):
             for q, pp, dd, tt in zip(problems, p, d, trial):
                 q.ctx.axpby(1.0, pp, 0.0, tt)
                 q.ctx.axpby(lam, dd, 1.0, tt)
-            ft = phi(trial, Ft)
+            ft, floor_t = phi(trial, Ft)
             f_t = 0.5 * ft * ft
             if not math.isfinite(f_t):
                 return False, it, lin, "nonfinite"
@@ -441,7 +444,7 @@ def newton_step(problems, comm, p, dt, opts):
         for q, pp, tt in zip(problems, p, trial):
             q.ctx.axpby(1.0, tt, 0.0, pp)
         F, Ft = Ft, F
-        fn = ft
+        fn, floor = ft, floor_t
 
 
 def fgmres(problems, comm, b, eta, maxit, m):

@@ -151,6 +151,7 @@ EXPORTS = {
     "rich_num_cells": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "rich_saturation": (ctypes.c_int, [_P, _P, _P]),
     "rich_residual": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rich_residual3": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double)]),
     "rich_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Soil), ctypes.c_int,
                                              ctypes.POINTER(BC), _P, _P, ctypes.c_double, _P,
                                              ctypes.POINTER(ctypes.c_double), _P]),
@@ -353,6 +354,13 @@ class Context:
         arr = (ctypes.c_double * 2)() if norms else None
         check(load().rich_residual(self.h, _ptr(p), _ptr(s_old), dt, _ptr(F), arr), "rich_residual")
         return (arr[0], arr[1]) if norms else None
+
+    def residual3(self, p, s_old, dt, F):
+        """Phi into F; returns (||Phi||_2, ||Phi||_inf, ||m||_2), eps ||m||_2 being the
+        accuracy of Phi (the Newton test's round-off floor)."""
+        arr = (ctypes.c_double * 3)()
+        check(load().rich_residual3(self.h, _ptr(p), _ptr(s_old), dt, _ptr(F), arr), "rich_residual3")
+        return arr[0], arr[1], arr[2]
 
     def jacobian(self, p, dt, J7=None, A7=None):
         check(load().rich_jacobian(self.h, _ptr(p), dt, _ptr(J7), _ptr(A7)), "rich_jacobian")

@@ -12,8 +12,12 @@ launches), reproduce the whole grid.
   couplings across an interface kept in the plane of that face;
 * J x of the split grid (each block's stencil SpMV plus its interface couplings
   times the neighbours' x after a halo exchange of x) is the whole grid's J x
-  within 1e-14 (the terms are summed in another order).
+  within 1e-14 (the terms are summed in another order);
+* the split grid's Newton step and Krylov solves reach the whole grid's, and
+  near a steady state stop at the same round-off floor.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -82,6 +86,10 @@ def test_blocks_reproduce_the_whole_grid(px, py, kmean, paper_bc):
     F = torch.empty_like(pd)
     n2, ninf = whole.residual(pd, torch.tensor(s_old, device="cuda"), dt, F)
     Fw = F.cpu().numpy()
+    F3 = torch.empty_like(pd)
+    n2_3, ninf_3, nm = whole.residual3(pd, torch.tensor(s_old, device="cuda"), dt, F3)
+    assert (n2_3, ninf_3) == (n2, ninf)
+    np.testing.assert_array_equal(F3.cpu().numpy(), Fw)
     J7 = torch.empty(7 * grid.n, dtype=torch.float64, device="cuda")
     A7 = torch.empty_like(J7)
     whole.jacobian(pd, dt, J7, A7)
@@ -91,7 +99,8 @@ def test_blocks_reproduce_the_whole_grid(px, py, kmean, paper_bc):
     whole.jacobian_apply(torch.tensor(x, device="cuda"), yw)
     yw = yw.cpu().numpy()
     whole.close()
-    ref = disc.residual(grid, SOIL, bc, kmean, p, s_old, dt, ks)
+    ref, ref_m = disc.residual(grid, SOIL, bc, kmean, p, s_old, dt, ks, with_scale=True)
+    assert abs(nm - ref_m) <= 1e-12 * ref_m  # the round-off scale ||m||_2 of the Newton test
     # the blocks, one context each, on this device
     blocks = decomp.partition(grid, px, py)
     probs = [decomp.BlockProblem(grid, SOIL, bc, kmean, ks, blocks, r) for r in range(len(blocks))]
@@ -135,6 +144,8 @@ def test_blocks_reproduce_the_whole_grid(px, py, kmean, paper_bc):
     assert np.abs(Fs - ref).max() <= 1e-12 * np.abs(ref).max()
     n2s, ninfs = decomp.combine_norms(parts)
     assert abs(n2s - n2) <= 1e-13 * n2 and ninfs == ninf
+    nms = math.sqrt(sum(pt[2] for pt in parts))  # the blocks' m^2 add up to the whole grid's
+    assert abs(nms - nm) <= 1e-13 * nm
     np.testing.assert_array_equal(_whole(Jb, grid, blocks, 7), J7w)
     np.testing.assert_array_equal(_whole(Ab, grid, blocks, 7), A7w)
 
@@ -180,6 +191,45 @@ def test_split_grid_newton_step_matches_the_whole_grid(px, py, kmean, kind):
     ps = _whole([v.cpu().numpy() for v in pb], grid, blocks)
     pwh = pw.cpu().numpy()
     assert np.abs(ps - pwh).max() <= 1e-8 * np.abs(pwh).max()
+    for q in probs:
+        q.close()
+
+
+@pytest.mark.parametrize("perturb", [0.0, 1e-9])
+def test_split_grid_step_stops_at_the_round_off_floor(perturb):
+    """Near a steady state the Newton test's round-off floor (eps ||m||_2, from the
+    blocks' summed m^2) decides, on the split grid as on the whole grid: the
+    hydrostatic column (arithmetic mean: Phi is rounding noise, ~0.02 of the floor)
+    needs no iteration, and perturbed by 1e-9 cm it needs one, after which
+    ||Phi|| is below the floor but far above rtol ||Phi_0||, which rounding alone
+    keeps out of reach."""
+    rb = _rb()
+    grid = synth.Grid(16, 16, 10)
+    hz = grid.h[2]
+    z = (np.arange(grid.nz) + 1) * hz
+    p0 = np.broadcast_to((-12.0 - z)[:, None, None], grid.shape).ravel().copy()
+    p0 = p0 + perturb * np.random.default_rng(4).standard_normal(grid.n)
+    bc = synth.BC(kind=(0, 0, 0, 0, 0, 1), value=(0, 0, 0, 0, 0, -12.0 - (grid.nz + 1) * hz))
+    ks = synth.ks_field(grid, 2, 0.5, (3.0, 3.0, 2.0))
+    kmean, dt = synth.KMEAN_ARITH, 0.25
+    opts = rb.default_newton_opts(kind=rb.KRYLOV_FCG, seed=3, coarse_max=100, smooth_levels=2)
+    whole = rb.Context(grid, SOIL, bc, kmean, ks)
+    pw = torch.tensor(p0, device="cuda")
+    st = whole.step(pw, dt, opts)
+    whole.close()
+    assert st.converged and st.newton_its == (0 if perturb == 0 else 1)
+    assert st.res > opts.rtol * st.res0  # the floor, not rtol, ended the step
+    blocks = decomp.partition(grid, 2, 2)
+    probs = [decomp.BlockProblem(grid, SOIL, bc, kmean, ks, blocks, r) for r in range(len(blocks))]
+    pb = [torch.tensor(v, device="cuda") for v in _blocks_of(p0, grid, blocks)]
+    ok, its, lin, why = decomp.newton_step(probs, decomp.LocalComm(probs), pb, dt, opts)
+    assert ok, why
+    assert its == st.newton_its
+    ps = _whole([v.cpu().numpy() for v in pb], grid, blocks)
+    pwh = pw.cpu().numpy()
+    if perturb == 0:
+        np.testing.assert_array_equal(ps, p0)
+    assert np.abs(ps - pwh).max() <= 1e-12 * np.abs(pwh).max()
     for q in probs:
         q.close()
 
