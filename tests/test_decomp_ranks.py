@@ -8,6 +8,12 @@ neighbour's cells, an exact block solve as its preconditioner).  Every rank's
 x and iteration count must equal, bit for bit, those of the same blocks driven
 in one process (`LocalComm`), and the assembled x must be the oracle's solution
 of the whole system with the same block-diagonal preconditioner.
+
+The split Newton step (`decomp.newton_step`: halo exchange of p before every
+residual and Jacobian, norms, round-off scales and slopes summed over the
+ranks) runs the same way on a monotone nonlinear stand-in of the backward-Euler
+residual: each rank's p and counts equal the one-process step's bit for bit,
+and the assembled p is the whole system's Newton solution.
 """
 import os
 import socket
@@ -163,3 +169,122 @@ def test_split_krylov_on_gloo_ranks_equals_one_process_and_the_oracle(px, py, tm
         assert ok_o and abs(its - its_o) <= 1
         assert np.linalg.norm(b - A @ x) <= ETA * np.linalg.norm(b) * (1 + 1e-6)
         assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+# ---------------------------------------------------------------- the split Newton step
+
+class _NonlinearCtx(_BlockCtx):
+    """A backward-Euler-like step of the block's rows: Phi(p) = (s(p) - s_old) / dt
+    + A p - rhs with s(p) = p + p^3 / 10 (monotone), the neighbours' p entering as
+    ghosts through the interface couplings; J = diag(s'(p)) / dt + A_bb; the
+    preconditioner is the exact solve with J (factored at setup and refresh)."""
+
+    def __init__(self, A, idx, b, rhs):
+        super().__init__(A, idx, b)
+        self.A_bb = self.Abb.tocsr()
+        self.absA = abs(self.A_bb)
+        self.rhs = rhs[self.g]
+        self.ghosts = {}
+
+    def saturation(self, p, s):
+        s.copy_(p + p ** 3 / 10)
+
+    def set_face_values(self, f, ghosts):
+        self.ghosts[f] = ghosts.numpy().copy()
+
+    def residual3(self, p, s_old, dt, F):
+        pn, so = p.numpy(), s_old.numpy()
+        ap, mag = self.A_bb @ pn, self.absA @ np.abs(pn)
+        for f, (lc, c) in self.face.items():
+            np.add.at(ap, lc.numpy(), c.numpy() * self.ghosts[f])
+            np.add.at(mag, lc.numpy(), np.abs(c.numpy() * self.ghosts[f]))
+        s = pn + pn ** 3 / 10
+        Fn = (s - so) / dt + ap - self.rhs
+        F.copy_(torch.from_numpy(Fn))
+        mag += (np.abs(s) + np.abs(so)) / dt + np.abs(self.rhs)
+        return float(np.linalg.norm(Fn)), float(np.abs(Fn).max()), float(np.linalg.norm(mag))
+
+    def jacobian(self, p, dt):
+        pn = p.numpy()
+        self.Abb = (sp.diags((1.0 + 0.3 * pn ** 2) / dt) + self.A_bb).tocsc()
+
+    def amg_setup(self, opts):
+        self.lu = spla.splu(self.Abb)
+
+    def amg_update(self, policy):
+        self.lu = spla.splu(self.Abb)
+
+
+def _nonlinear_problem(A, idx, blocks, r, rhs):
+    q = _problem(A, idx, blocks, r)
+    q.ctx = _NonlinearCtx(A, idx, q.block, rhs)
+    return q
+
+
+def _newton_opts(kind):
+    from types import SimpleNamespace
+    from paper_2112_05051_gb300 import richards as rb
+    k = rb.KRYLOV_FGMRES if kind == "fgmres" else rb.KRYLOV_FCG
+    return SimpleNamespace(rtol=1e-10, atol=1e-30, max_newton=30, armijo_c=1e-4, lambda_min=1e-8, amg=None,
+                           krylov=SimpleNamespace(kind=k, eta=1e-8, maxit=200, restart=RESTART))
+
+
+DT = 0.5
+
+
+def _step(probs, comm, kind):
+    p = [torch.zeros(q.ctx.g.size, dtype=torch.float64) for q in probs]
+    ok, its, lin, why = decomp.newton_step(probs, comm, p, DT, _newton_opts(kind))
+    return [v.numpy().copy() for v in p], its, lin, ok, why
+
+
+def _newton_rank(rank, world, port, px, py, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        grid, A, idx, b = _system()
+        blocks = decomp.partition(grid, px, py)
+        q = _nonlinear_problem(A, idx, blocks, rank, 8.0 * b)
+        out = {}
+        for kind in ("fcg", "fgmres"):
+            p, its, lin, ok, why = _step([q], decomp.DistComm(dist, q, "cpu"), kind)
+            out[kind + "_p"] = p[0]
+            out[kind + "_its"] = np.array([its, lin, int(ok)])
+        np.savez(os.path.join(out_dir, "newton%d.npz" % rank), **out)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("px,py", [(2, 1), (2, 2)])
+def test_split_newton_step_on_gloo_ranks_equals_one_process_and_solves_the_whole_system(px, py, tmp_path):
+    import torch.multiprocessing as mp
+    world = px * py
+    mp.spawn(_newton_rank, args=(world, _free_port(), px, py, str(tmp_path)), nprocs=world, join=True)
+    grid, A, idx, b = _system()
+    rhs = 8.0 * b
+    blocks = decomp.partition(grid, px, py)
+    parts = [np.load(tmp_path / ("newton%d.npz" % r)) for r in range(world)]
+    # the whole system's solution by Newton with direct solves
+    pw = np.zeros(grid.n)
+    phi = lambda p: (p + p ** 3 / 10) / DT + A @ p - rhs
+    for _ in range(50):
+        F = phi(pw)
+        if np.linalg.norm(F) <= 1e-14 * np.linalg.norm(rhs):
+            break
+        pw = pw - spla.spsolve((sp.diags((1.0 + 0.3 * pw ** 2) / DT) + A).tocsc(), F)
+    assert np.abs(pw).max() > 1.0  # the cubic term matters
+    for kind in ("fcg", "fgmres"):
+        probs = [_nonlinear_problem(A, idx, blocks, r, rhs) for r in range(world)]
+        p, its, lin, ok, why = _step(probs, decomp.LocalComm(probs), kind)
+        assert ok, why
+        assert its >= 3 and lin > its
+        for r, d in enumerate(parts):  # the ranks' step is the one-process step, bit for bit
+            assert list(d[kind + "_its"]) == [its, lin, 1]
+            np.testing.assert_array_equal(d[kind + "_p"], p[r])
+        x = np.empty(grid.n)
+        for q, pr in zip(probs, p):
+            x[q.ctx.g] = pr
+        assert np.linalg.norm(phi(x)) <= 1e-10 * np.linalg.norm(phi(np.zeros(grid.n))) * (1 + 1e-6)
+        assert np.abs(x - pw).max() <= 1e-9 * np.abs(pw).max()
