@@ -451,7 +451,9 @@ def fgmres(problems, comm, b, eta, maxit, m):
     """Flexible GMRES(m) for J x = b on the split grid, right-preconditioned by each
     block's own V-cycle: classical Gram-Schmidt with a second pass when
     ||w'||^2 < ||w||^2 / 2 (DGKS), Givens rotations, restarts every m iterations
-    from the true residual.  Returns (x, iterations, converged, reason)."""
+    from the true residual.  Returns (x, iterations, converged, reason); a column
+    whose rotation is undefined (J z = 0: both its entries vanish) ends the solve
+    with the columns before it and the reason "breakdown"."""
     import math
     import torch
     nb = len(problems)
@@ -464,15 +466,15 @@ def fgmres(problems, comm, b, eta, maxit, m):
     if not beta > 0:
         return x, 0, True, None
     target, its = eta * beta, 0
+    V = [new() for _ in range(m + 1)]  # the basis and the preconditioned directions, reused by every cycle
+    Z = [new() for _ in range(m)]
     while True:
-        V = [new() for _ in range(m + 1)]
-        Z = [new() for _ in range(m)]
         H = [[0.0] * m for _ in range(m + 1)]
         cs, sn, g = [0.0] * m, [0.0] * m, [0.0] * (m + 1)
         g[0] = beta
         for q, rr, v in zip(problems, r, V[0]):
             q.ctx.axpby(1.0 / beta, rr, 0.0, v)
-        jdone, conv = 0, False
+        jdone, conv, broke = 0, False, False
         for j in range(m):
             for q, v, z in zip(problems, V[j], Z[j]):
                 q.ctx.vcycle(v, z)
@@ -502,6 +504,9 @@ def fgmres(problems, comm, b, eta, maxit, m):
                 H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j]
                 H[i][j] = t
             den = math.hypot(H[j][j], H[j + 1][j])
+            if not den > 0:
+                broke = True
+                break
             cs[j], sn[j] = H[j][j] / den, H[j + 1][j] / den
             H[j][j], H[j + 1][j] = den, 0.0
             g[j + 1], g[j] = -sn[j] * g[j], cs[j] * g[j]
@@ -520,6 +525,8 @@ def fgmres(problems, comm, b, eta, maxit, m):
                 q.ctx.axpby(y[i], zz, 1.0, xx)
         if conv:
             return x, its, True, None
+        if broke:
+            return x, its, False, "breakdown"
         if its >= maxit:
             return x, its, False, "maxit"
         apply_J(problems, comm, x, jx)  # restart from the true residual

@@ -178,3 +178,29 @@ def test_split_krylov_zero_rhs_and_maxit():
     assert (its, ok, why) == (3, False, "maxit")
     xs, its, ok, why = decomp.fcg(probs, _Comm(probs), bs, 1e-14, 3)
     assert (its, ok, why) == (3, False, "maxit")
+
+
+def test_split_fgmres_breakdown_keeps_the_columns_before_it():
+    # a preconditioner that returns zero makes J z = 0: the column's rotation is
+    # undefined, and FGMRES stops with the columns it has instead of dividing by 0
+    A = _spd(80, 6)
+    b = np.random.default_rng(2).standard_normal(80)
+    bounds, probs, _ = _split(A, 2)
+    bs = [torch.from_numpy(b[bounds[r]:bounds[r + 1]].copy()) for r in range(2)]
+    for q in probs:
+        q.ctx.vcycle = lambda r, z: z.zero_()
+    xs, its, ok, why = decomp.fgmres(probs, _Comm(probs), bs, 1e-10, 50, 10)
+    assert (its, ok, why) == (0, False, "breakdown") and all(float(v.abs().max()) == 0.0 for v in xs)
+    calls = [0]
+    for q in probs:  # three good columns (identity), then zeros
+        def prec(r, z, calls=calls):
+            calls[0] += 1
+            return z.copy_(r) if calls[0] <= 2 * 3 else z.zero_()
+        q.ctx.vcycle = prec
+    xs, its, ok, why = decomp.fgmres(probs, _Comm(probs), bs, 1e-10, 50, 10)
+    assert (its, ok, why) == (3, False, "breakdown")
+    x = np.concatenate([v.numpy() for v in xs])
+    xo, its_o, _, hist = krylov.fgmres(lambda v: A @ v, lambda v: v.copy(), b, 1e-10, 3, 10)
+    assert its_o == 3
+    np.testing.assert_allclose(x, xo, rtol=0, atol=1e-12 * np.abs(xo).max())  # the 3-column minimiser
+    assert np.linalg.norm(b - A @ x) < np.linalg.norm(b)
