@@ -456,7 +456,6 @@ def fgmres(problems, comm, b, eta, maxit, m):
     with the columns before it and the reason "breakdown"."""
     import math
     import torch
-    nb = len(problems)
     new = lambda: [torch.empty_like(v) for v in b]
     x = [torch.zeros_like(v) for v in b]
     r, w, jx = new(), new(), new()
