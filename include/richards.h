@@ -304,6 +304,9 @@ const char* rich_strerror(int status);
 const char* rich_last_cuda_error(void);
 int rich_num_cells(const rich_ctx* ctx, long long* n_out);
 
+/* ---- Sec. 5.1: the split grid (x-y blocks with whole columns, a one-cell
+ * halo exchanged before each residual, Jacobian and SpMV, dot products summed
+ * over the blocks) ------------------------------------------------------- */
 /* Replaces the per-cell values of face f (Dirichlet pressures, or the ghost
  * pressures of a RICH_BC_INTERFACE face after a halo exchange) with values_dev
  * (device, the face's cell count, indexing of rich_bc.value_field_dev), copied on
@@ -471,7 +474,8 @@ int rich_autotune_table(char* buf, int cap);
  * Classes already tuned keep their choice.  RICH_EINVAL (nothing added) on a
  * malformed line or an unknown variant. */
 int rich_autotune_load(const char* text);
-/* The SELL-C-sigma layout (csr_layout) the library gives a CSR matrix of n rows,
+/* The SELL-C-sigma layout (csr_layout) the library gives a CSR matrix of n rows
+ * (the coarse operators, restrictions and prolongators of the Sec. 5.2 hierarchy),
  * computed on the host from its row pointer (rowptr_host, n + 1 entries,
  * non-decreasing): rows sorted by decreasing length (ties in row order) within
  * each window of 1024 rows, cut into slices of 32.  perm_host receives
