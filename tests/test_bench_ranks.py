@@ -1,5 +1,6 @@
-"""Host logic of the multi-replica bench path on two gloo ranks (CPU): the whole-job
-time is the slowest rank's and the work is summed over ranks."""
+"""Host logic of the bench on the CPU: the multi-replica path on two gloo ranks (the whole-job
+time is the slowest rank's, the work summed over ranks), the request-stream statistics,
+and the placement of each kernel on the roof its intensity selects."""
 import os
 import socket
 import sys
@@ -113,3 +114,29 @@ def test_serving_run_end_to_end_against_a_fake_server(monkeypatch):
     assert 0.0 < out["failure_rate"] < 1.0
     assert set(out["failed"]) <= {"RICH_ENOTCONV_LIN"}
     assert out["mix_vs_alone_max_rel_dev"] == 0.0
+
+
+def test_kernels_are_placed_on_the_roof_their_intensity_selects():
+    # the bound follows from algorithmic flops/byte against the FP64 balance point:
+    # FP64 kernels above it are FP64-FMA-bound, below it and every FP32 kernel HBM-bound
+    sys.path.insert(0, ROOT)
+    import bench
+    peak_gbs, fp64_tf = 6761.6, 1.0544
+    bal = bench.fp64_balance(peak_gbs, fp64_tf)
+    assert abs(bal - 0.15594) < 1e-4
+    n, nv, ms = 2097152, 20, 0.1
+    # CGS dots over nv basis vectors: 2 n nv flops on 8 n (nv + 1) bytes, intensity 0.238
+    r = bench.roofline_of("multidot", ms, 1, 8.0 * n * (nv + 1), 2.0 * n * nv, True, peak_gbs, fp64_tf, None)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == fp64_tf
+    assert abs(r["achieved"] - 2.0 * n * nv / 1e-4 / 1e12) < 1e-9 and abs(r["frac"] - r["achieved"] / fp64_tf) < 1e-12
+    # a prolongation: 2 flops per entry on 12 B per entry plus the vectors, intensity < 0.156
+    nnz = 3.4 * n
+    r = bench.roofline_of("prolong", ms, 1, 12.0 * nnz + 20.0 * n, 2.0 * nnz, True, peak_gbs, fp64_tf, None)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == peak_gbs
+    assert abs(r["frac"] - (12.0 * nnz + 20.0 * n) / 1e-4 / 1e9 / peak_gbs) < 1e-12
+    # the same CGS intensity in an FP32 kernel is HBM-bound (no FP64 pipe involved)
+    r = bench.roofline_of("l1jacobi", ms, 1, 8.0 * n * (nv + 1), 2.0 * n * nv, False, peak_gbs, fp64_tf, None)
+    assert r["bound"] == "hbm" and r["fp64_frac"] is None
+    # launch averages
+    r = bench.roofline_of("restrict", 2.0, 4, 4e8, 1e7, True, peak_gbs, fp64_tf, 1.1e8)
+    assert r["avg_launch_us"] == 500.0 and r["algorithmic_bytes_per_launch"] == 1e8 and r["traffic"] == 1.1e8
